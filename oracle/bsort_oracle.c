@@ -1,0 +1,363 @@
+/*
+ * bsort_oracle.c -- TEST INFRASTRUCTURE, not part of the library.
+ *
+ * A plain, slow, single-threaded CPU statement of GPU Bucket Sort
+ * (Dehne & Zaboli, "Deterministic Sample Sort for GPUs", Section 4,
+ * Algorithm 1, Steps 1-9), written from the paper's step definitions so that
+ * a reader can check every step against the text by eye.  Only the tests,
+ * the package's smoke check and the benchmark's CPU-baseline leg may load
+ * this file; the CUDA library never does, and the two share no code.
+ *
+ * Everything is integer work (comparisons, counts, copies); no floating
+ * point is involved except the order-preserving key transform for float32
+ * keys, which is a pure bit manipulation.
+ *
+ * Readings of points where the paper is silent (kept identical in the CUDA
+ * path, which is written separately):
+ *   - Elements are compared in "composite order": (key, position), so every
+ *     element is distinct.  Inside Steps 3-8 the position of an element of
+ *     sublist i at sorted rank r is p = i*t + r; because each sublist is
+ *     sorted stably and sublists are contiguous index ranges, this order is
+ *     the same as (key, original index).
+ *   - Step 3 takes, from each sorted sublist of t items, the samples at
+ *     ranks (k+1)*w - 1, k = 0..s-1, with w = t/s (the last item of each of
+ *     s equal chunks).
+ *   - Step 5 takes the global samples (splitters) g_j = S[(j+1)*m - 1],
+ *     j = 0..s-1, from the sorted sample list S; g_{s-1} is the global
+ *     maximum, so the s splitters define exactly s buckets.
+ *   - Bucket j of sublist i holds the items x with g_{j-1} < x <= g_j in
+ *     composite order (g_{-1} = minus infinity).
+ *   - n need not be a multiple of t: the input is padded virtually to
+ *     n' = ceil(n/t)*t with sentinels (key = the largest key of the type,
+ *     position >= n) that are larger than every real item in composite order;
+ *     they end in the tail of the output and are dropped.
+ *   - Parity is pinned by the tests (brute force on tiny inputs, an
+ *     independent textbook merge sort, closed-form bucket sizes and the
+ *     bucket-size bound), not by this file itself.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    uint64_t key;
+    uint64_t val;
+    uint64_t pos; /* original index (pads: >= n) */
+} oelem_t;
+
+/* Composite order used by Steps 2-9: (key, pos). */
+static int elem_less(const oelem_t *a, const oelem_t *b)
+{
+    if (a->key != b->key) return a->key < b->key;
+    return a->pos < b->pos;
+}
+
+/* Sample record of Step 3: (key, p) with p = i*t + r. */
+typedef struct {
+    uint64_t key;
+    uint64_t p;
+} orec_t;
+
+static int rec_less(const orec_t *a, const orec_t *b)
+{
+    if (a->key != b->key) return a->key < b->key;
+    return a->p < b->p;
+}
+
+/* ---- top-down merge sort (used for Steps 2, 4 and 9) ------------------- */
+
+static void msort_elems_rec(oelem_t *a, oelem_t *tmp, uint64_t lo, uint64_t hi)
+{
+    if (hi - lo < 2) return;
+    uint64_t mid = lo + (hi - lo) / 2;
+    msort_elems_rec(a, tmp, lo, mid);
+    msort_elems_rec(a, tmp, mid, hi);
+    uint64_t x = lo, y = mid, o = lo;
+    while (x < mid && y < hi) {
+        /* take from the left run unless the right item is strictly smaller */
+        if (elem_less(&a[y], &a[x])) tmp[o++] = a[y++];
+        else tmp[o++] = a[x++];
+    }
+    while (x < mid) tmp[o++] = a[x++];
+    while (y < hi) tmp[o++] = a[y++];
+    memcpy(a + lo, tmp + lo, (hi - lo) * sizeof(oelem_t));
+}
+
+static int msort_elems(oelem_t *a, uint64_t n)
+{
+    if (n < 2) return 0;
+    oelem_t *tmp = (oelem_t *)malloc(n * sizeof(oelem_t));
+    if (!tmp) return -1;
+    msort_elems_rec(a, tmp, 0, n);
+    free(tmp);
+    return 0;
+}
+
+static void msort_recs_rec(orec_t *a, orec_t *tmp, uint64_t lo, uint64_t hi)
+{
+    if (hi - lo < 2) return;
+    uint64_t mid = lo + (hi - lo) / 2;
+    msort_recs_rec(a, tmp, lo, mid);
+    msort_recs_rec(a, tmp, mid, hi);
+    uint64_t x = lo, y = mid, o = lo;
+    while (x < mid && y < hi) {
+        if (rec_less(&a[y], &a[x])) tmp[o++] = a[y++];
+        else tmp[o++] = a[x++];
+    }
+    while (x < mid) tmp[o++] = a[x++];
+    while (y < hi) tmp[o++] = a[y++];
+    memcpy(a + lo, tmp + lo, (hi - lo) * sizeof(orec_t));
+}
+
+static int msort_recs(orec_t *a, uint64_t n)
+{
+    if (n < 2) return 0;
+    orec_t *tmp = (orec_t *)malloc(n * sizeof(orec_t));
+    if (!tmp) return -1;
+    msort_recs_rec(a, tmp, 0, n);
+    free(tmp);
+    return 0;
+}
+
+/* ---- float32 key transform (reading of the paper's silence on key types) */
+
+/* Order-preserving map of IEEE-754 binary32 bits to uint32: negative values
+ * (sign set) are bit-inverted, non-negative values get the sign bit set.  The
+ * resulting unsigned order is -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN. */
+uint32_t oracle_f32_to_key(uint32_t bits)
+{
+    if (bits & 0x80000000u) return ~bits;
+    return bits | 0x80000000u;
+}
+
+uint32_t oracle_key_to_f32(uint32_t key)
+{
+    if (key & 0x80000000u) return key & 0x7FFFFFFFu;
+    return ~key;
+}
+
+void oracle_f32_to_key_array(const uint32_t *bits, uint32_t *keys, uint64_t n)
+{
+    for (uint64_t x = 0; x < n; ++x) keys[x] = oracle_f32_to_key(bits[x]);
+}
+
+void oracle_key_to_f32_array(const uint32_t *keys, uint32_t *bits, uint64_t n)
+{
+    for (uint64_t x = 0; x < n; ++x) bits[x] = oracle_key_to_f32(keys[x]);
+}
+
+/* ---- Algorithm 1 --------------------------------------------------------- */
+
+/* Plan quantities of Step 1. */
+uint64_t oracle_num_sublists(uint64_t n, uint64_t t)
+{
+    return t ? (n + t - 1) / t : 0;
+}
+
+/*
+ * GPU Bucket Sort, Algorithm 1 Steps 1-9, with every intermediate exposed.
+ *
+ *   keys, vals : n input items (vals may be NULL: keys only)
+ *   t          : sublist size n/m of Step 1 (a multiple of s)
+ *   s          : samples per sublist (Step 3) = global samples = buckets
+ *   key_max    : the largest key of the key type (pad sentinel key)
+ *   out_keys, out_vals : n sorted items (out_vals may be NULL)
+ *
+ * Optional intermediates (NULL to skip), with m = ceil(n/t), n' = m*t:
+ *   tile_keys, tile_pos   [n']   Step 2: sorted sublists, sublist-major
+ *   samp_keys, samp_p     [m*s]  Step 3: samples, sublist-major, p = i*t + r
+ *   spl_keys, spl_p       [s]    Step 5: global samples g_0..g_{s-1}
+ *   counts                [m*s]  Step 6: a_ij stored bucket-major a[j*m + i]
+ *   offsets               [m*s]  Step 7: l_ij stored bucket-major l[j*m + i]
+ *   reloc_keys, reloc_pos [n']   Step 8: relocated array B_1 ... B_s
+ *   bucket_start          [s+1]  start of B_j in the relocated array; [s] = n'
+ *
+ * Returns 0, or -1 on bad parameters / allocation failure.
+ */
+int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
+                      uint64_t t, uint64_t s, uint64_t key_max,
+                      uint64_t *out_keys, uint64_t *out_vals,
+                      uint64_t *tile_keys, uint64_t *tile_pos,
+                      uint64_t *samp_keys, uint64_t *samp_p,
+                      uint64_t *spl_keys, uint64_t *spl_p,
+                      uint64_t *counts, uint64_t *offsets,
+                      uint64_t *reloc_keys, uint64_t *reloc_pos,
+                      uint64_t *bucket_start)
+{
+    if (n == 0) return 0;
+    if (t == 0 || s == 0 || s > t || (t % s) != 0) return -1;
+
+    /* Step 1: split A into m sublists of t = n/m items (virtual padding). */
+    const uint64_t m = (n + t - 1) / t;
+    const uint64_t np = m * t;
+    const uint64_t w = t / s;
+
+    oelem_t *A = (oelem_t *)malloc(np * sizeof(oelem_t));
+    orec_t *S = (orec_t *)malloc(m * s * sizeof(orec_t));
+    orec_t *G = (orec_t *)malloc(s * sizeof(orec_t));
+    uint64_t *c = (uint64_t *)malloc(m * (s + 1) * sizeof(uint64_t));
+    uint64_t *a = (uint64_t *)malloc(m * s * sizeof(uint64_t));
+    uint64_t *l = (uint64_t *)malloc(m * s * sizeof(uint64_t));
+    oelem_t *B = (oelem_t *)malloc(np * sizeof(oelem_t));
+    if (!A || !S || !G || !c || !a || !l || !B) goto fail;
+
+    for (uint64_t x = 0; x < np; ++x) {
+        if (x < n) {
+            A[x].key = keys[x];
+            A[x].val = vals ? vals[x] : 0;
+        } else {
+            A[x].key = key_max;
+            A[x].val = 0;
+        }
+        A[x].pos = x;
+    }
+
+    /* Step 2: local sort of every sublist A_i (stable: composite order). */
+    for (uint64_t i = 0; i < m; ++i)
+        if (msort_elems(A + i * t, t)) goto fail;
+    if (tile_keys)
+        for (uint64_t x = 0; x < np; ++x) tile_keys[x] = A[x].key;
+    if (tile_pos)
+        for (uint64_t x = 0; x < np; ++x) tile_pos[x] = A[x].pos;
+
+    /* Step 3: s equidistant samples per sorted sublist, ranks (k+1)w - 1. */
+    for (uint64_t i = 0; i < m; ++i)
+        for (uint64_t k = 0; k < s; ++k) {
+            uint64_t r = (k + 1) * w - 1;
+            S[i * s + k].key = A[i * t + r].key;
+            S[i * s + k].p = i * t + r;
+        }
+    if (samp_keys)
+        for (uint64_t x = 0; x < m * s; ++x) samp_keys[x] = S[x].key;
+    if (samp_p)
+        for (uint64_t x = 0; x < m * s; ++x) samp_p[x] = S[x].p;
+
+    /* Step 4: sort all s*m samples. */
+    if (msort_recs(S, m * s)) goto fail;
+
+    /* Step 5: s equidistant global samples g_j = S[(j+1)m - 1]. */
+    for (uint64_t j = 0; j < s; ++j) G[j] = S[(j + 1) * m - 1];
+    if (spl_keys)
+        for (uint64_t j = 0; j < s; ++j) spl_keys[j] = G[j].key;
+    if (spl_p)
+        for (uint64_t j = 0; j < s; ++j) spl_p[j] = G[j].p;
+
+    /* Step 6: sample indexing.  c[i][j+1] = number of items of sorted
+     * sublist i that are <= g_j in composite order, where the item at rank r
+     * of sublist i is (key, i*t + r); found by binary search because the
+     * sublist is sorted in that order.  c[i][0] = 0.  Bucket A_ij is ranks
+     * [c[i][j], c[i][j+1]) and a_ij is its size. */
+    for (uint64_t i = 0; i < m; ++i) {
+        c[i * (s + 1) + 0] = 0;
+        for (uint64_t j = 0; j < s; ++j) {
+            uint64_t lo = 0, hi = t; /* first rank whose item is > g_j */
+            while (lo < hi) {
+                uint64_t mid = lo + (hi - lo) / 2;
+                orec_t item;
+                item.key = A[i * t + mid].key;
+                item.p = i * t + mid;
+                if (rec_less(&G[j], &item)) hi = mid;
+                else lo = mid + 1;
+            }
+            c[i * (s + 1) + j + 1] = lo;
+        }
+        for (uint64_t j = 0; j < s; ++j)
+            a[j * m + i] = c[i * (s + 1) + j + 1] - c[i * (s + 1) + j];
+    }
+    if (counts) memcpy(counts, a, m * s * sizeof(uint64_t));
+
+    /* Step 7: prefix sum over a_11..a_m1, a_12..a_m2, ..., a_1s..a_ms
+     * (bucket-major), exclusive: l_ij = start of A_ij in the final order. */
+    {
+        uint64_t run = 0;
+        for (uint64_t x = 0; x < m * s; ++x) {
+            l[x] = run;
+            run += a[x];
+        }
+    }
+    if (offsets) memcpy(offsets, l, m * s * sizeof(uint64_t));
+
+    /* Step 8: move every bucket A_ij to l_ij; B_j = A_1j u ... u A_mj. */
+    for (uint64_t i = 0; i < m; ++i)
+        for (uint64_t j = 0; j < s; ++j) {
+            uint64_t src = i * t + c[i * (s + 1) + j];
+            uint64_t len = a[j * m + i];
+            for (uint64_t q = 0; q < len; ++q) B[l[j * m + i] + q] = A[src + q];
+        }
+    if (reloc_keys)
+        for (uint64_t x = 0; x < np; ++x) reloc_keys[x] = B[x].key;
+    if (reloc_pos)
+        for (uint64_t x = 0; x < np; ++x) reloc_pos[x] = B[x].pos;
+    if (bucket_start) {
+        for (uint64_t j = 0; j < s; ++j) bucket_start[j] = l[j * m + 0];
+        bucket_start[s] = np;
+    }
+
+    /* Step 9: sort every sublist B_j. */
+    for (uint64_t j = 0; j < s; ++j) {
+        uint64_t lo = l[j * m + 0];
+        uint64_t hi = (j + 1 < s) ? l[(j + 1) * m + 0] : np;
+        if (msort_elems(B + lo, hi - lo)) goto fail;
+    }
+
+    /* Output: the first n items (pads are the largest items, so they are
+     * exactly the last n' - n). */
+    for (uint64_t x = 0; x < n; ++x) {
+        out_keys[x] = B[x].key;
+        if (out_vals) out_vals[x] = B[x].val;
+    }
+
+    free(A); free(S); free(G); free(c); free(a); free(l); free(B);
+    return 0;
+fail:
+    free(A); free(S); free(G); free(c); free(a); free(l); free(B);
+    return -1;
+}
+
+/* ---- O2: independent textbook bottom-up merge sort ----------------------- */
+
+/*
+ * Stable sort of (key, val) pairs by key: bottom-up merging of runs of width
+ * 1, 2, 4, ... between two buffers.  Written separately from the code above
+ * (no shared helpers) so that it can serve as an independent check of the
+ * final output of oracle_paper_sort.
+ */
+int oracle_textbook_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
+                         uint64_t *out_keys, uint64_t *out_vals)
+{
+    if (n == 0) return 0;
+    uint64_t *k0 = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint64_t *k1 = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint64_t *v0 = (uint64_t *)malloc(n * sizeof(uint64_t));
+    uint64_t *v1 = (uint64_t *)malloc(n * sizeof(uint64_t));
+    if (!k0 || !k1 || !v0 || !v1) {
+        free(k0); free(k1); free(v0); free(v1);
+        return -1;
+    }
+    for (uint64_t x = 0; x < n; ++x) {
+        k0[x] = keys[x];
+        v0[x] = vals ? vals[x] : 0;
+    }
+    for (uint64_t width = 1; width < n; width *= 2) {
+        for (uint64_t lo = 0; lo < n; lo += 2 * width) {
+            uint64_t mid = lo + width < n ? lo + width : n;
+            uint64_t hi = lo + 2 * width < n ? lo + 2 * width : n;
+            uint64_t x = lo, y = mid, o = lo;
+            while (o < hi) {
+                /* stable: the right run wins only on a strictly smaller key */
+                int take_right = (x >= mid) || (y < hi && k0[y] < k0[x]);
+                if (take_right) { k1[o] = k0[y]; v1[o] = v0[y]; ++y; }
+                else            { k1[o] = k0[x]; v1[o] = v0[x]; ++x; }
+                ++o;
+            }
+        }
+        uint64_t *tk = k0; k0 = k1; k1 = tk;
+        uint64_t *tv = v0; v0 = v1; v1 = tv;
+    }
+    for (uint64_t x = 0; x < n; ++x) {
+        out_keys[x] = k0[x];
+        if (out_vals) out_vals[x] = v0[x];
+    }
+    free(k0); free(k1); free(v0); free(v1);
+    return 0;
+}
