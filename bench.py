@@ -1,0 +1,422 @@
+"""Benchmark of GPU Bucket Sort (deterministic sample sort) on GB300.
+
+One step = one full sort (Algorithm 1, Steps 1-9) of a fixed synthetic array
+already resident in HBM.  Default workload: n = 2^28 uint32 keys drawn
+uniformly (SplitMix64), keys only.  Prints ONE JSON line on rank 0.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--n N] [--dist uniform] [--key-type u32|f32] [--dists]
+
+--impl reference times the CPU oracle (a plain C statement of Algorithm 1)
+on the host cores, on a bounded sample of the same workload per step.
+Multi-GPU: one process per GPU (torchrun); every rank sorts its own array
+(independent replicas, weak scaling); no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Gkeys/s (uint32, n=2^28) & HBM-roofline %"
+UNIT = "Gkeys/s"
+KERNEL_SOURCES = ["paper_1002_4464_gb300/csrc/bsort_kernels.cu",
+                  "paper_1002_4464_gb300/csrc/bsort_device.cuh"]
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=1 << 28)
+    p.add_argument("--dist", default="uniform")
+    p.add_argument("--key-type", default="u32", choices=["u32", "f32"])
+    p.add_argument("--dists", action="store_true",
+                   help="also time every distribution (spread across distributions)")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--cpu-sample", type=int, default=1 << 22,
+                   help="keys per CPU-oracle sample")
+    return p.parse_args()
+
+
+def _dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_hash():
+    h = hashlib.sha256()
+    for rel in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel, workload):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_sources_sha256_16") != _kernel_hash():
+        return None
+    e = d.get("kernels", {}).get(kernel)
+    if not e or e.get("workload") != workload:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_oracle_rate(keys_np, key_type, t, s):
+    """Time the CPU oracle (Algorithm 1 in plain C, single thread) on one
+    sample; returns (Gkeys/s, seconds)."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.paper_sort(keys_np, t, s, key_type, intermediates=False)
+    dt = time.perf_counter() - t0
+    return keys_np.size / dt / 1e9, dt
+
+
+def _oracle_plan(n):
+    """Sublist size and sample count for the CPU oracle sample: the paper's
+    own choice for its Tesla-era runs, n/m = 2K items and s = 64
+    (Section 4)."""
+    return 2048, 64
+
+
+def _sample_keys(args, rank, count):
+    import synth
+    if args.key_type == "f32":
+        return synth.keys_f32(args.dist, count, synth.seed_for(2, _dist_index(args.dist), rank))
+    return synth.keys_u32(args.dist, count, synth.seed_for(2, _dist_index(args.dist), rank))
+
+
+def _dist_index(name):
+    import synth
+    return synth.DISTRIBUTIONS.index(name)
+
+
+def run_reference(args):
+    rank, world, local = _dist_env()
+    if rank != 0:
+        return 0
+    sample_n = min(args.cpu_sample, args.n)
+    keys = _sample_keys(args, 0, sample_n)
+    t, s = _oracle_plan(sample_n)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(keys, args.key_type, t, s)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_rate(keys, args.key_type, t, s)
+        times.append(dt)
+    total = sum(times)
+    value = sample_n * len(times) / total / 1e9
+    sample_desc = ("first %d keys of the %s %s workload (n=%d), Algorithm 1 with t=%d, s=%d, "
+                   "single thread, per step" % (sample_n, args.dist, args.key_type, args.n, t, s))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total / len(times) * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": args.key_type,
+        "data": "synthetic", "config": _config(args, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def _config(args, world):
+    return {"workload": "%s %s keys-only sort, n=2^%d per GPU" % (
+                args.dist, args.key_type, max(args.n.bit_length() - 1, 0)) if args.n & (args.n - 1) == 0
+            else "%s %s keys-only sort, n=%d per GPU" % (args.dist, args.key_type, args.n),
+            "n": args.n, "key_type": args.key_type, "distribution": args.dist,
+            "global_keys": args.n * world, "parallelism": "replicas x%d" % world,
+            "l2_policy": "input (%d MB) larger than the 129 MB L2; no flush" % (args.n * 4 >> 20)
+            if args.n * 4 > 129 * 2 ** 20 else "input smaller than L2 (resident)"}
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1002_4464_gb300 as pkg
+    import synth
+
+    rank, world, local = _dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def make_keys(dname):
+        seed = synth.seed_for(2, _dist_index(dname), rank)
+        if args.key_type == "f32":
+            return synth.keys_f32_torch(dname, args.n, seed, device=dev)
+        return synth.keys_u32_torch(dname, args.n, seed, device=dev)
+
+    keys = make_keys(args.dist)
+    out = torch.empty_like(keys)
+    sorter = pkg.BucketSorter(device=local, timing=True)
+    plan = sorter.plan(args.n, args.key_type)
+    stream = torch.cuda.current_stream(dev)
+
+    def one_step(k_in):
+        sorter.sort_keys(k_in, out=out, key_type=args.key_type)
+
+    for _ in range(max(args.warmup, 3)):
+        one_step(keys)
+    sorter.sync()
+    # correctness gate (outside the timed region): nondecreasing and same multiset
+    o = out.view(torch.int32).to(torch.int64) & 0xFFFFFFFF if args.key_type == "u32" else None
+    if o is not None:
+        assert bool((o[1:] >= o[:-1]).all()), "output not sorted"
+        kin = keys.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        assert int(kin.sum()) == int(o.sum()), "multiset changed"
+        del kin
+    del o
+    sorter.kernel_times()  # reset the timing ring
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        one_step(keys)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_total = ev0.elapsed_time(ev1)
+    sorter.sync()
+    ktimes, kcalls = sorter.kernel_times()
+    if world > 1:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    value = args.n * world * args.steps / (ms_total / 1e3) / 1e9
+
+    # per-kernel breakdown and the dominant kernel's roofline
+    per_kernel = {}
+    for name, ms in ktimes:
+        per_kernel[name] = per_kernel.get(name, 0.0) + ms / max(kcalls, 1)
+    launches_per_kernel = {}
+    for name, _ in ktimes:
+        launches_per_kernel[name] = launches_per_kernel.get(name, 0) + 1
+    dom = max(per_kernel, key=per_kernel.get) if per_kernel else None
+    peak, peak_kind = _peaks()
+    roofline = None
+    if dom is not None:
+        # algorithmic bytes of one pass over the data (read + write, keys only)
+        np_pad = plan.n_padded if not plan.single_tile else plan.n
+        alg_bytes = 2 * np_pad * 4
+        dom_ms = per_kernel[dom] / launches_per_kernel[dom]
+        achieved = alg_bytes / (dom_ms / 1e3) / 1e9
+        workload = _config(args, 1)["workload"]
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
+                    "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
+                    if peak_kind == "measured" else "fallback 6.8 TB/s",
+                    "unit": "GB/s", "frac": achieved / peak,
+                    "traffic": _traffic_for(dom, workload),
+                    "alg_bytes_per_launch": alg_bytes, "ms_per_launch": dom_ms}
+        # whole-step roofline: three read+write passes (Steps 2, 8, 9)
+        whole = 6 * args.n * 4 / (ms_step / 1e3) / 1e9
+        roofline["step_achieved_gbs"] = whole
+        roofline["step_frac"] = whole / peak
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if args.e2e_steps > 0:
+        h_in = keys.cpu().pin_memory()
+        h_out = torch.empty_like(h_in).pin_memory()
+        sorter.sort_keys_host(h_in, h_out, key_type=args.key_type)  # warm-up (workspace)
+        sorter.sync()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            sorter.sort_keys_host(h_in, h_out, key_type=args.key_type)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sorter.sync()
+        ems = e0.elapsed_time(e1) / args.e2e_steps
+        e2e = {"value": args.n / (ems / 1e3) / 1e9 * world, "unit": UNIT,
+               "h2d_bytes_per_step": args.n * 4, "d2h_bytes_per_step": args.n * 4,
+               "ms_per_step": ems}
+        del h_in, h_out
+
+    dists = None
+    if args.dists:
+        dists = {}
+        for dname in synth.DISTRIBUTIONS:
+            kd = make_keys(dname)
+            for _ in range(3):
+                one_step(kd)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            reps = max(3, args.steps // 2)
+            a.record(stream)
+            for _ in range(reps):
+                one_step(kd)
+            b.record(stream)
+            torch.cuda.synchronize()
+            dms = a.elapsed_time(b) / reps
+            dists[dname] = {"ms_per_step": dms, "gkeys_s": args.n / (dms / 1e3) / 1e9}
+            del kd
+        sorter.kernel_times()
+        rates = [v["ms_per_step"] for v in dists.values()]
+        dists["spread"] = (max(rates) - min(rates)) / (sum(rates) / len(rates))
+
+    cpu = None
+    if rank == 0:
+        sample_n = min(args.cpu_sample, args.n)
+        t_o, s_o = _oracle_plan(sample_n)
+        keys_np = keys[:sample_n].cpu().numpy()
+        if args.key_type == "u32":
+            keys_np = keys_np.view(np.uint32)
+        rates = []
+        t_spent = 0.0
+        while t_spent < 10.0 and len(rates) < 8:
+            r, dt = cpu_oracle_rate(keys_np, args.key_type, t_o, s_o)
+            rates.append(r)
+            t_spent += dt
+        cpu = {"value": statistics.median(rates), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "first %d keys of this workload, %d repetitions, Algorithm 1 with "
+                         "t=%d, s=%d, single-threaded C (host has %d cores)"
+                         % (sample_n, len(rates), t_o, s_o, _cpu_cores())}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.key_type, "data": "synthetic (SplitMix64 %s keys)" % args.dist,
+            "config": _config(args, world), "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": plan.num_kernels * args.steps,
+            "clocks": clk, "per_kernel_ms": per_kernel,
+            "plan": {k: v for k, v in plan.as_dict().items()
+                     if k in ("t", "s", "m", "w", "bucket_bound", "unit_capacity",
+                              "tile_ctas", "unit_ctas", "num_kernels")},
+        }
+        if dists is not None:
+            line["distributions"] = dists
+        print(json.dumps(line), flush=True)
+    sorter.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

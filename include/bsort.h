@@ -1,0 +1,176 @@
+/*
+ * bsort.h -- C ABI of a GB300 (sm_103a) implementation of GPU Bucket Sort,
+ * the deterministic sample sort of Dehne & Zaboli ("Deterministic Sample Sort
+ * for GPUs", Section 4, Algorithm 1).
+ *
+ * The problem (Algorithm 1, "Input"/"Output"): an array A of n items in
+ * global memory is to be sorted.  Every call below computes exactly the
+ * sorted permutation: keys in nondecreasing order, and for key/value pairs
+ * the stable order (equal keys keep their input order).  Steps 1-9 of
+ * Algorithm 1 each run as hand-written CUDA kernels on one GPU; nothing here
+ * falls back to the CPU.
+ *
+ * Conventions common to all entry points
+ *   - Pointers named d_* are device pointers on the handle's device; h_* are
+ *     host pointers.  The caller owns every key/value buffer and the stream.
+ *   - cuda_stream is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Sort calls are asynchronous on that stream: they return
+ *     after enqueueing work.  bsort_sync() waits and reports device-side
+ *     errors.
+ *   - Input and output may be the same buffer (in-place sort, as in the
+ *     paper); otherwise they must not overlap.  The input is never modified
+ *     when it differs from the output.
+ *   - n = 0 and n = 1 are valid.  n must satisfy n < 2^32 - 2^16 (positions
+ *     are 32-bit on the device); larger n returns BSORT_EUNSUPPORTED.
+ *   - A handle is not thread-safe; use one handle per host thread.  Calls on
+ *     one handle must be ordered on one stream (they share its workspace).
+ *   - Errors: argument and launch errors are returned directly.  A device
+ *     consistency check or a bounded device wait that ran out sets a device
+ *     error word; bsort_sync() returns it (BSORT_EINTERNAL / BSORT_ETIMEOUT)
+ *     and clears it.  No kernel aborts, traps or spins without a limit.
+ */
+#ifndef BSORT_H
+#define BSORT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bsort_ctx *bsort_t;
+
+typedef enum {
+    BSORT_OK = 0,
+    BSORT_EINVAL = 1,        /* bad argument (null pointer, bad size, bad flag) */
+    BSORT_ENOMEM = 2,        /* workspace too small / device allocation failed */
+    BSORT_ECUDA = 3,         /* a CUDA runtime call failed; see bsort_last_error */
+    BSORT_ETIMEOUT = 4,      /* a bounded device-side wait ran out */
+    BSORT_EBUSY = 5,         /* reserved */
+    BSORT_ENOTREADY = 6,     /* no completed call to report on */
+    BSORT_EUNSUPPORTED = 7,  /* valid request that this build does not serve */
+    BSORT_EINTERNAL = 8      /* a device-side consistency check failed */
+} bsort_status;
+
+typedef enum {
+    BSORT_U32 = 0,  /* unsigned 32-bit keys */
+    BSORT_F32 = 1,  /* IEEE binary32 keys, total order
+                       -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN;
+                       bit patterns are preserved */
+    BSORT_U64 = 2   /* unsigned 64-bit keys (not served by this build) */
+} bsort_key_type;
+
+/* Flags for bsort_config.flags. */
+#define BSORT_FLAG_TIMING 0x1u  /* record CUDA events between the kernels of
+                                   every call; see bsort_kernel_times() */
+
+typedef struct {
+    int device;                /* CUDA device ordinal the handle works on */
+    uint64_t mem_budget_bytes; /* library-owned workspace: if > 0 and
+                                  workspace == NULL, allocated once at create;
+                                  a job that needs more returns BSORT_ENOMEM.
+                                  0 with workspace == NULL: the library grows
+                                  its workspace on demand (cudaMalloc). */
+    void *workspace;           /* caller-owned device workspace (may be NULL);
+                                  when set, the library never allocates device
+                                  memory and must not outlive it */
+    uint64_t workspace_bytes;  /* size of workspace */
+    uint32_t tile;             /* t = n/m of Step 1 (0 = planner's choice) */
+    uint32_t samples;          /* s of Step 3 (0 = planner's choice) */
+    uint32_t flags;            /* BSORT_FLAG_* */
+} bsort_config;
+
+/* The plan of one job (Step 1 parameters and the Step-9 unit). */
+typedef struct {
+    uint64_t n;              /* items */
+    uint64_t n_padded;       /* n' = m * t (the last sublist padded) */
+    uint32_t t;              /* sublist size n/m (Step 1) */
+    uint32_t s;              /* samples per sublist = buckets (Steps 3, 5) */
+    uint32_t m;              /* number of sublists */
+    uint32_t w;              /* t / s, distance between samples (Step 3) */
+    uint64_t bucket_bound;   /* max |B_j| = n'/s + (m-1)(w-1) <= 2n'/s */
+    uint32_t tile_ctas;      /* CTAs that sort one sublist (Step 2) */
+    uint32_t unit_ctas;      /* CTAs that sort one bucket (Step 9) */
+    uint64_t unit_capacity;  /* items one Step-9 unit holds (>= bucket_bound) */
+    uint32_t single_tile;    /* 1: n fits one unit, sorted directly */
+    uint32_t num_kernels;    /* kernel launches per call */
+    uint64_t workspace_bytes;/* device workspace this job needs */
+} bsort_plan_info;
+
+/* Intermediates of the last call (for parity checks), see bsort_get_intermediate. */
+typedef enum {
+    BSORT_IM_TILES = 0,      /* Step 2: sorted sublists, n' keys (transformed
+                                key domain for F32), sublist-major */
+    BSORT_IM_SAMPLES = 1,    /* Step 3: m*s records (key << 32 | p), p = i*t + r,
+                                sublist-major */
+    BSORT_IM_SPLITTERS = 2,  /* Step 5: s records g_0..g_{s-1} */
+    BSORT_IM_COUNTS = 3,     /* Step 6: a_ij, uint32, bucket-major a[j*m + i] */
+    BSORT_IM_OFFSETS = 4,    /* Step 7: l_ij, uint32, bucket-major */
+    BSORT_IM_RELOCATED = 5   /* Step 8: n' keys B_1 ... B_s */
+} bsort_intermediate;
+
+/* Create a handle on cfg->device.  cfg may be NULL (device 0, on-demand
+ * workspace, planner's t and s).  Returns BSORT_ENOMEM if mem_budget_bytes
+ * cannot be allocated. */
+bsort_status bsort_create(const bsort_config *cfg, bsort_t *out);
+
+/* Release the handle and any workspace the library allocated.  Waits for
+ * no stream; the caller must make sure no call is in flight. */
+bsort_status bsort_destroy(bsort_t h);
+
+/* Compute the plan for sorting n items of key type kt (val_bytes = 0 for
+ * keys only, 4 or 8 for pairs).  Host-only; touches no device memory. */
+bsort_status bsort_plan(bsort_t h, bsort_key_type kt, uint32_t val_bytes,
+                        uint64_t n, bsort_plan_info *out);
+
+/* Algorithm 1 on n keys: d_keys_out receives the keys in nondecreasing
+ * order.  Returns BSORT_ENOMEM if the workspace cannot hold the job. */
+bsort_status bsort_sort_keys(bsort_t h, bsort_key_type kt, const void *d_keys_in,
+                             void *d_keys_out, uint64_t n, void *cuda_stream);
+
+/* Algorithm 1 on n (key, value) pairs, stable: equal keys keep their input
+ * order.  val_bytes is 4 or 8; values are moved, never interpreted. */
+bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_in,
+                              const void *d_vals_in, void *d_keys_out,
+                              void *d_vals_out, uint32_t val_bytes, uint64_t n,
+                              void *cuda_stream);
+
+/* bsort_sort_keys on HOST buffers: copies h_keys_in to the device, sorts,
+ * and copies the result back into h_keys_out, all on cuda_stream (the
+ * copies are part of the call).  Pinned host memory gives asynchronous
+ * copies.  Uses extra workspace for the device copy of the keys. */
+bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_keys_in,
+                                  void *h_keys_out, uint64_t n, void *cuda_stream);
+
+/* Wait for cuda_stream, then return and clear the device error word:
+ * BSORT_OK, BSORT_ETIMEOUT or BSORT_EINTERNAL. */
+bsort_status bsort_sync(bsort_t h, void *cuda_stream);
+
+/* Copy one intermediate of the last sort call into host memory (waits for
+ * the device).  bytes must equal the intermediate's size for that call's
+ * plan; intermediates that the plan skipped (single_tile) give
+ * BSORT_ENOTREADY. */
+bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which,
+                                    void *h_dst, uint64_t bytes);
+
+/* With BSORT_FLAG_TIMING: milliseconds spent in each kernel launch, in
+ * launch order, summed over the calls made since the previous
+ * bsort_kernel_times (at most the last 64 calls, and only those with the same
+ * launch sequence as the last call; *calls receives how many were summed).
+ * Waits for the last call.  *written receives the number of entries
+ * (<= count).  bsort_kernel_name(h, i) names entry i of the last call. */
+bsort_status bsort_kernel_times(bsort_t h, float *ms, uint32_t count,
+                                uint32_t *written, uint32_t *calls);
+const char *bsort_kernel_name(bsort_t h, uint32_t index);
+
+/* Last error message on this handle (never NULL). */
+const char *bsort_last_error(bsort_t h);
+
+/* Name of a status code (never NULL). */
+const char *bsort_status_string(bsort_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSORT_H */

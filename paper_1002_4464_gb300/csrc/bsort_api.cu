@@ -1,0 +1,633 @@
+// bsort_api.cu -- host runtime behind include/bsort.h: the planner (Step 1
+// parameters and the Step-9 unit), the workspace layout, the launch sequence
+// of Algorithm 1 (Dehne & Zaboli, Section 4) and the error word.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/bsort.h"
+#include "bsort_internal.h"
+
+namespace {
+
+using namespace bsort;
+
+constexpr uint64_t kAlign = 256;
+constexpr uint64_t kMaxN = (1ull << 32) - (1ull << 16);
+constexpr int kMaxTimed = 40;   // launches recorded per call
+constexpr int kRing = 64;       // calls kept for bsort_kernel_times
+
+uint64_t align_up(uint64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Full plan of one job, including the workspace layout.
+struct Plan {
+    bsort_plan_info info;
+    bool pairs;
+    int vb;          // value bytes (0 keys only)
+    int tile_cap;    // CTA shape of Step 2 (== t)
+    int unit_cap;    // CTA shape of Step 9
+    uint32_t n_rec;      // m*s sample records
+    uint32_t n_rec_pad;  // rounded up to kRecordChunk
+    uint32_t scan_chunks;
+    // workspace offsets (bytes)
+    uint64_t off_hdr, off_tiles_k, off_tiles_v, off_reloc_k, off_reloc_v, off_samples,
+        off_rec_a, off_rec_b, off_spl, off_counts, off_cum, off_offsets, off_status,
+        off_stage_in, off_stage_out, total;
+};
+
+}  // namespace
+
+struct bsort_ctx {
+    int device = 0;
+    uint32_t flags = 0;
+    uint32_t force_t = 0, force_s = 0;
+    void *ws = nullptr;
+    uint64_t ws_bytes = 0;
+    bool ws_owned = false;
+    bool ws_fixed = false;  // caller workspace or fixed budget: never grow
+    bool kernels_ready = false;
+    Plan last{};
+    bool have_last = false;
+    char err[512] = {0};
+    // timing ring: call c uses ev[c % kRing][0 .. n_ev[c % kRing]]
+    cudaEvent_t ev[kRing][kMaxTimed + 1] = {};
+    const char *ev_name[kMaxTimed] = {};
+    int n_ev[kRing] = {};
+    uint64_t calls_recorded = 0;  // calls since the last bsort_kernel_times
+    uint64_t call_seq = 0;
+    bool events_made = false;
+};
+
+namespace {
+
+bsort_status fail(bsort_t h, bsort_status st, const char *fmt, ...)
+{
+    if (h) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(h->err, sizeof(h->err), fmt, ap);
+        va_end(ap);
+    }
+    return st;
+}
+
+bsort_status cuda_fail(bsort_t h, cudaError_t e, const char *what)
+{
+    return fail(h, BSORT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+uint64_t bound_for(uint64_t n_pad, uint64_t m, uint64_t s)
+{
+    const uint64_t t = n_pad / m;
+    const uint64_t w = t / s;
+    return n_pad / s + (m - 1) * (w - 1);
+}
+
+int smallest_cap(uint64_t items, bool pairs)
+{
+    const int caps_k[] = {2048, 4096, 8192, 16384, 32768};
+    const int caps_p[] = {2048, 4096, 8192, 16384};
+    if (pairs) {
+        for (int c : caps_p)
+            if ((uint64_t)c >= items) return c;
+    } else {
+        for (int c : caps_k)
+            if ((uint64_t)c >= items) return c;
+    }
+    return 0;
+}
+
+bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P)
+{
+    memset(P, 0, sizeof(*P));
+    if (kt == BSORT_U64) return fail(h, BSORT_EUNSUPPORTED, "64-bit keys are not served by this build");
+    if (kt != BSORT_U32 && kt != BSORT_F32) return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
+    if (vb != 0 && vb != 4 && vb != 8) return fail(h, BSORT_EINVAL, "val_bytes must be 0, 4 or 8");
+    if (n >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "n = %llu exceeds 2^32 - 2^16", (unsigned long long)n);
+    const bool pairs = vb != 0;
+    const int capmax = pairs ? kMaxCapPairs : kMaxCapKeys;
+    P->pairs = pairs;
+    P->vb = (int)vb;
+    bsort_plan_info &I = P->info;
+    I.n = n;
+    const uint64_t forced_t = h ? h->force_t : 0;
+    const uint64_t forced_s = h ? h->force_s : 0;
+
+    if (n <= (uint64_t)capmax && (forced_t == 0 || n <= forced_t)) {
+        // c7: n fits one Step-9 unit; the sort needs no sampling.
+        I.single_tile = 1;
+        I.n_padded = n;
+        I.t = (uint32_t)n;
+        I.s = 1;
+        I.m = n ? 1 : 0;
+        I.w = (uint32_t)n;
+        I.bucket_bound = n;
+        I.tile_ctas = 0;
+        I.unit_ctas = n ? 1 : 0;
+        P->unit_cap = smallest_cap(n, pairs);
+        I.unit_capacity = (uint64_t)P->unit_cap;
+        I.num_kernels = n > 1 ? 1 : 0;
+    } else {
+        const uint64_t t = forced_t ? forced_t : (uint64_t)capmax;
+        if (!cap_supported((int)t, pairs))
+            return fail(h, BSORT_EUNSUPPORTED, "sublist size t = %llu not supported (%s)",
+                        (unsigned long long)t, pairs ? "2048 .. 16384" : "2048 .. 32768");
+        const uint64_t m = (n + t - 1) / t;
+        const uint64_t np = m * t;
+        uint64_t s = forced_s;
+        if (s) {
+            if (s > t || t % s != 0)
+                return fail(h, BSORT_EINVAL, "s = %llu must divide t = %llu", (unsigned long long)s,
+                            (unsigned long long)t);
+            if (bound_for(np, m, s) > (uint64_t)capmax)
+                return fail(h, BSORT_EUNSUPPORTED,
+                            "bucket bound %llu exceeds the Step-9 unit capacity %d",
+                            (unsigned long long)bound_for(np, m, s), capmax);
+        } else {
+            for (uint64_t c = 1; c <= t / 16; c <<= 1) {
+                if (bound_for(np, m, c) <= (uint64_t)capmax) {
+                    s = c;
+                    break;
+                }
+            }
+            if (!s)
+                return fail(h, BSORT_EUNSUPPORTED,
+                            "no sample count gives buckets within one Step-9 unit for n = %llu",
+                            (unsigned long long)n);
+        }
+        if (s > 4096) return fail(h, BSORT_EUNSUPPORTED, "s = %llu > 4096", (unsigned long long)s);
+        I.single_tile = 0;
+        I.n_padded = np;
+        I.t = (uint32_t)t;
+        I.s = (uint32_t)s;
+        I.m = (uint32_t)m;
+        I.w = (uint32_t)(t / s);
+        I.bucket_bound = bound_for(np, m, s);
+        I.tile_ctas = 1;
+        I.unit_ctas = 1;
+        P->tile_cap = (int)t;
+        P->unit_cap = smallest_cap(I.bucket_bound, pairs);
+        I.unit_capacity = (uint64_t)P->unit_cap;
+        P->n_rec = (uint32_t)(m * s);
+        P->n_rec_pad = (uint32_t)((P->n_rec + kRecordChunk - 1) / kRecordChunk * kRecordChunk);
+        P->scan_chunks = (P->n_rec + kScanChunk - 1) / kScanChunk;
+        uint32_t merges = 0;
+        for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
+        I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
+                        1 /*S6*/ + 1 /*S7*/ + 1 /*S8*/ + 1 /*S9*/;
+    }
+
+    // workspace layout
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) {
+        uint64_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    P->off_hdr = take(kAlign);  // error word (int) + scan ticket (uint32)
+    if (!I.single_tile) {
+        const uint64_t np = I.n_padded;
+        P->off_tiles_k = take(np * 4);
+        P->off_tiles_v = take(np * (uint64_t)vb);
+        P->off_reloc_k = take(np * 4);
+        P->off_reloc_v = take(np * (uint64_t)vb);
+        P->off_samples = take((uint64_t)P->n_rec * 8);
+        P->off_rec_a = take((uint64_t)P->n_rec_pad * 8);
+        P->off_rec_b = take(P->n_rec_pad > (uint32_t)kRecordChunk ? (uint64_t)P->n_rec_pad * 8 : 0);
+        P->off_spl = take((uint64_t)I.s * 8);
+        P->off_counts = take((uint64_t)P->n_rec * 4);
+        P->off_cum = take((uint64_t)P->n_rec * 4);
+        P->off_offsets = take((uint64_t)P->n_rec * 4);
+        P->off_status = take((uint64_t)P->scan_chunks * 8);
+    }
+    P->total = o;
+    I.workspace_bytes = o;
+    return BSORT_OK;
+}
+
+bsort_status ensure_workspace(bsort_t h, uint64_t bytes)
+{
+    if (bytes <= h->ws_bytes) return BSORT_OK;
+    if (h->ws_fixed)
+        return fail(h, BSORT_ENOMEM, "job needs %llu workspace bytes, handle has %llu",
+                    (unsigned long long)bytes, (unsigned long long)h->ws_bytes);
+    if (h->ws_owned && h->ws) {
+        cudaError_t e = cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaFree(workspace)");
+    }
+    void *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, BSORT_ENOMEM, "cudaMalloc(%llu) failed: %s", (unsigned long long)bytes,
+                    cudaGetErrorString(e));
+    }
+    h->ws = p;
+    h->ws_bytes = bytes;
+    h->ws_owned = true;
+    // the error word starts cleared
+    e = cudaMemset(p, 0, kAlign);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaMemset(header)");
+    return BSORT_OK;
+}
+
+bsort_status prepare(bsort_t h)
+{
+    if (!h) return BSORT_EINVAL;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaSetDevice");
+    if (!h->kernels_ready) {
+        e = init_kernels();
+        if (e != cudaSuccess) return cuda_fail(h, e, "kernel attributes");
+        h->kernels_ready = true;
+    }
+    if ((h->flags & BSORT_FLAG_TIMING) && !h->events_made) {
+        for (int r = 0; r < kRing; ++r)
+            for (int i = 0; i <= kMaxTimed; ++i) {
+                e = cudaEventCreate(&h->ev[r][i]);
+                if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+            }
+        h->events_made = true;
+    }
+    return BSORT_OK;
+}
+
+// Launch-sequence helper: with BSORT_FLAG_TIMING, records an event before
+// the first launch and after each launch of the call, in the next slot of
+// the handle's ring.
+struct Seq {
+    bsort_t h;
+    cudaStream_t st;
+    bool timing;
+    int slot = 0;
+    int n = 0;
+    Seq(bsort_t h_, cudaStream_t st_) : h(h_), st(st_), timing((h_->flags & BSORT_FLAG_TIMING) != 0)
+    {
+        if (!timing) return;
+        slot = (int)(h->call_seq % kRing);
+        ++h->call_seq;
+        if (h->calls_recorded < (uint64_t)kRing) ++h->calls_recorded;
+        h->n_ev[slot] = 0;
+        cudaEventRecord(h->ev[slot][0], st);
+    }
+    bsort_status after(cudaError_t e, const char *name)
+    {
+        if (e != cudaSuccess) return cuda_fail(h, e, name);
+        if (timing && n < kMaxTimed) {
+            h->ev_name[n] = name;
+            cudaEventRecord(h->ev[slot][n + 1], st);
+            ++n;
+            h->n_ev[slot] = n;
+        }
+        return BSORT_OK;
+    }
+};
+
+#define SEQ(call, name)                                  \
+    do {                                                 \
+        bsort_status s_ = seq.after((call), (name));     \
+        if (s_ != BSORT_OK) return s_;                   \
+    } while (0)
+
+bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void *vin, void *kout,
+                      void *vout, uint32_t vb, uint64_t n, cudaStream_t st)
+{
+    bsort_status rs = prepare(h);
+    if (rs != BSORT_OK) return rs;
+    Plan P;
+    rs = make_plan(h, kt, vb, n, &P);
+    if (rs != BSORT_OK) return rs;
+    rs = ensure_workspace(h, P.total);
+    if (rs != BSORT_OK) return rs;
+    h->last = P;
+    h->have_last = true;
+    unsigned char *ws = static_cast<unsigned char *>(h->ws);
+    int *err = reinterpret_cast<int *>(ws + P.off_hdr);
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(ws + P.off_hdr + 64);
+    const int is_f32 = kt == BSORT_F32;
+    const bsort_plan_info &I = P.info;
+    Seq seq(h, st);
+    if (n == 0) return BSORT_OK;
+    if (I.single_tile) {
+        if (n == 1) {
+            if (kout != kin) {
+                cudaError_t e = cudaMemcpyAsync(kout, kin, 4, cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "copy n=1");
+                if (vb) {
+                    e = cudaMemcpyAsync(vout, vin, vb, cudaMemcpyDeviceToDevice, st);
+                    if (e != cudaSuccess) return cuda_fail(h, e, "copy n=1");
+                }
+            }
+            return BSORT_OK;
+        }
+        SEQ(launch_bucket_sort(P.unit_cap, P.pairs, kin, vin, nullptr, 1, 1, n, n, is_f32, (int)vb,
+                               kout, vout, err, st),
+            "step9_single_unit");
+        return BSORT_OK;
+    }
+    uint32_t *tiles_k = reinterpret_cast<uint32_t *>(ws + P.off_tiles_k);
+    void *tiles_v = ws + P.off_tiles_v;
+    uint32_t *reloc_k = reinterpret_cast<uint32_t *>(ws + P.off_reloc_k);
+    void *reloc_v = ws + P.off_reloc_v;
+    uint64_t *samples = reinterpret_cast<uint64_t *>(ws + P.off_samples);
+    uint64_t *rec_a = reinterpret_cast<uint64_t *>(ws + P.off_rec_a);
+    uint64_t *rec_b = reinterpret_cast<uint64_t *>(ws + P.off_rec_b);
+    uint64_t *spl = reinterpret_cast<uint64_t *>(ws + P.off_spl);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(ws + P.off_counts);
+    uint32_t *cum = reinterpret_cast<uint32_t *>(ws + P.off_cum);
+    uint32_t *offsets = reinterpret_cast<uint32_t *>(ws + P.off_offsets);
+    unsigned long long *status = reinterpret_cast<unsigned long long *>(ws + P.off_status);
+
+    // look-back state must start at zero
+    cudaError_t e = cudaMemsetAsync(status, 0, (size_t)P.scan_chunks * 8, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan status)");
+    e = cudaMemsetAsync(ticket, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan ticket)");
+
+    // Steps 1-3
+    SEQ(launch_sublist_sort(P.tile_cap, P.pairs, kin, vin, n, I.m, is_f32, (int)vb, I.s, tiles_k,
+                            tiles_v, samples, st),
+        "step1_3_sublist_sort");
+    // Steps 4-5
+    const bool one_chunk = P.n_rec_pad == (uint32_t)kRecordChunk;
+    SEQ(launch_records_chunk_sort(samples, rec_a, P.n_rec, P.n_rec_pad, one_chunk ? spl : nullptr,
+                                  I.m, I.s, st),
+        "step4_sample_chunks");
+    if (!one_chunk) {
+        uint64_t *src = rec_a, *dst = rec_b;
+        for (uint32_t L = kRecordChunk; L < P.n_rec_pad; L <<= 1) {
+            SEQ(launch_merge_pass(src, dst, P.n_rec_pad, L, st), "step4_sample_merge");
+            uint64_t *tmp = src;
+            src = dst;
+            dst = tmp;
+        }
+        SEQ(launch_select_splitters(src, I.m, I.s, spl, st), "step5_splitters");
+    }
+    // Step 6
+    SEQ(launch_sample_index(tiles_k, samples, spl, I.t, I.s, I.m, counts, cum, st),
+        "step6_sample_index");
+    // Step 7
+    SEQ(launch_scan(counts, offsets, P.n_rec, status, ticket, err, st), "step7_prefix_sum");
+    // Step 8
+    SEQ(launch_relocate(tiles_k, tiles_v, cum, offsets, I.t, I.s, I.m, (int)vb, reloc_k, reloc_v,
+                        err, st),
+        "step8_relocate");
+    // Step 9
+    SEQ(launch_bucket_sort(P.unit_cap, P.pairs, reloc_k, reloc_v, offsets, I.m, I.s, n,
+                           I.n_padded, is_f32, (int)vb, kout, vout, err, st),
+        "step9_bucket_sort");
+    return BSORT_OK;
+}
+
+bool overlaps(const void *a, uint64_t abytes, const void *b, uint64_t bbytes)
+{
+    const char *pa = static_cast<const char *>(a);
+    const char *pb = static_cast<const char *>(b);
+    return pa < pb + bbytes && pb < pa + abytes;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bsort_status_string(bsort_status st)
+{
+    switch (st) {
+    case BSORT_OK: return "BSORT_OK";
+    case BSORT_EINVAL: return "BSORT_EINVAL";
+    case BSORT_ENOMEM: return "BSORT_ENOMEM";
+    case BSORT_ECUDA: return "BSORT_ECUDA";
+    case BSORT_ETIMEOUT: return "BSORT_ETIMEOUT";
+    case BSORT_EBUSY: return "BSORT_EBUSY";
+    case BSORT_ENOTREADY: return "BSORT_ENOTREADY";
+    case BSORT_EUNSUPPORTED: return "BSORT_EUNSUPPORTED";
+    case BSORT_EINTERNAL: return "BSORT_EINTERNAL";
+    }
+    return "BSORT_UNKNOWN";
+}
+
+bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
+{
+    if (!out) return BSORT_EINVAL;
+    *out = nullptr;
+    bsort_t h = new (std::nothrow) bsort_ctx();
+    if (!h) return BSORT_ENOMEM;
+    if (cfg) {
+        h->device = cfg->device;
+        h->flags = cfg->flags;
+        h->force_t = cfg->tile;
+        h->force_s = cfg->samples;
+        if (cfg->flags & ~(uint32_t)BSORT_FLAG_TIMING) {
+            delete h;
+            return BSORT_EINVAL;
+        }
+        if (cfg->workspace) {
+            if (cfg->workspace_bytes < kAlign || (reinterpret_cast<uintptr_t>(cfg->workspace) % kAlign)) {
+                delete h;
+                return BSORT_EINVAL;
+            }
+            h->ws = cfg->workspace;
+            h->ws_bytes = cfg->workspace_bytes;
+            h->ws_fixed = true;
+            cudaError_t e = cudaSetDevice(h->device);
+            if (e == cudaSuccess) e = cudaMemset(h->ws, 0, kAlign);
+            if (e != cudaSuccess) {
+                delete h;
+                return BSORT_ECUDA;
+            }
+        } else if (cfg->mem_budget_bytes) {
+            cudaError_t e = cudaSetDevice(h->device);
+            if (e != cudaSuccess) {
+                delete h;
+                return BSORT_ECUDA;
+            }
+            h->ws_fixed = false;
+            bsort_status st = ensure_workspace(h, align_up(cfg->mem_budget_bytes));
+            if (st != BSORT_OK) {
+                delete h;
+                return st;
+            }
+            h->ws_fixed = true;
+        }
+    }
+    *out = h;
+    return BSORT_OK;
+}
+
+bsort_status bsort_destroy(bsort_t h)
+{
+    if (!h) return BSORT_EINVAL;
+    if (h->ws_owned && h->ws) {
+        cudaSetDevice(h->device);
+        cudaFree(h->ws);
+    }
+    if (h->events_made)
+        for (int r = 0; r < kRing; ++r)
+            for (int i = 0; i <= kMaxTimed; ++i) cudaEventDestroy(h->ev[r][i]);
+    delete h;
+    return BSORT_OK;
+}
+
+bsort_status bsort_plan(bsort_t h, bsort_key_type kt, uint32_t val_bytes, uint64_t n,
+                        bsort_plan_info *out)
+{
+    if (!out) return fail(h, BSORT_EINVAL, "null plan pointer");
+    Plan P;
+    bsort_status st = make_plan(h, kt, val_bytes, n, &P);
+    if (st != BSORT_OK) return st;
+    *out = P.info;
+    return BSORT_OK;
+}
+
+bsort_status bsort_sort_keys(bsort_t h, bsort_key_type kt, const void *d_keys_in, void *d_keys_out,
+                             uint64_t n, void *cuda_stream)
+{
+    if (!h) return BSORT_EINVAL;
+    if (n && (!d_keys_in || !d_keys_out)) return fail(h, BSORT_EINVAL, "null key pointer");
+    if (n && d_keys_in != d_keys_out && overlaps(d_keys_in, n * 4, d_keys_out, n * 4))
+        return fail(h, BSORT_EINVAL, "input and output overlap partially");
+    return run_sort(h, kt, d_keys_in, nullptr, d_keys_out, nullptr, 0, n,
+                    static_cast<cudaStream_t>(cuda_stream));
+}
+
+bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_in,
+                              const void *d_vals_in, void *d_keys_out, void *d_vals_out,
+                              uint32_t val_bytes, uint64_t n, void *cuda_stream)
+{
+    if (!h) return BSORT_EINVAL;
+    if (val_bytes != 4 && val_bytes != 8) return fail(h, BSORT_EINVAL, "val_bytes must be 4 or 8");
+    if (n && (!d_keys_in || !d_keys_out || !d_vals_in || !d_vals_out))
+        return fail(h, BSORT_EINVAL, "null key/value pointer");
+    if (n && d_keys_in != d_keys_out && overlaps(d_keys_in, n * 4, d_keys_out, n * 4))
+        return fail(h, BSORT_EINVAL, "key input and output overlap partially");
+    if (n && d_vals_in != d_vals_out &&
+        overlaps(d_vals_in, n * val_bytes, d_vals_out, n * val_bytes))
+        return fail(h, BSORT_EINVAL, "value input and output overlap partially");
+    return run_sort(h, kt, d_keys_in, d_vals_in, d_keys_out, d_vals_out, val_bytes, n,
+                    static_cast<cudaStream_t>(cuda_stream));
+}
+
+bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_keys_in,
+                                  void *h_keys_out, uint64_t n, void *cuda_stream)
+{
+    if (!h) return BSORT_EINVAL;
+    if (n && (!h_keys_in || !h_keys_out)) return fail(h, BSORT_EINVAL, "null key pointer");
+    if (n == 0) return BSORT_OK;
+    bsort_status rs = prepare(h);
+    if (rs != BSORT_OK) return rs;
+    Plan P;
+    rs = make_plan(h, kt, 0, n, &P);
+    if (rs != BSORT_OK) return rs;
+    // staging: one device copy of the keys placed after the job's workspace
+    const uint64_t stage = P.total;
+    rs = ensure_workspace(h, stage + align_up(n * 4));
+    if (rs != BSORT_OK) return rs;
+    cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+    void *d_buf = static_cast<unsigned char *>(h->ws) + stage;
+    cudaError_t e = cudaMemcpyAsync(d_buf, h_keys_in, n * 4, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
+    rs = run_sort(h, kt, d_buf, nullptr, d_buf, nullptr, 0, n, st);
+    if (rs != BSORT_OK) return rs;
+    e = cudaMemcpyAsync(h_keys_out, d_buf, n * 4, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+    return BSORT_OK;
+}
+
+bsort_status bsort_sync(bsort_t h, void *cuda_stream)
+{
+    if (!h) return BSORT_EINVAL;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(static_cast<cudaStream_t>(cuda_stream));
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+    if (!h->ws) return BSORT_OK;
+    int word = 0;
+    e = cudaMemcpy(&word, h->ws, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "read error word");
+    if (word == 0) return BSORT_OK;
+    int zero = 0;
+    e = cudaMemcpy(h->ws, &zero, sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(h, e, "clear error word");
+    if (word == BSORT_ETIMEOUT)
+        return fail(h, BSORT_ETIMEOUT, "a bounded device wait ran out (scan look-back)");
+    return fail(h, BSORT_EINTERNAL, "device consistency check failed (code %d)", word);
+}
+
+bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which, void *h_dst,
+                                    uint64_t bytes)
+{
+    if (!h || !h_dst) return BSORT_EINVAL;
+    if (!h->have_last || h->last.info.single_tile || h->last.info.n == 0)
+        return fail(h, BSORT_ENOTREADY, "no intermediates: no multi-sublist call yet");
+    const Plan &P = h->last;
+    uint64_t off = 0, size = 0;
+    switch (which) {
+    case BSORT_IM_TILES: off = P.off_tiles_k; size = P.info.n_padded * 4; break;
+    case BSORT_IM_SAMPLES: off = P.off_samples; size = (uint64_t)P.n_rec * 8; break;
+    case BSORT_IM_SPLITTERS: off = P.off_spl; size = (uint64_t)P.info.s * 8; break;
+    case BSORT_IM_COUNTS: off = P.off_counts; size = (uint64_t)P.n_rec * 4; break;
+    case BSORT_IM_OFFSETS: off = P.off_offsets; size = (uint64_t)P.n_rec * 4; break;
+    case BSORT_IM_RELOCATED: off = P.off_reloc_k; size = P.info.n_padded * 4; break;
+    default: return fail(h, BSORT_EINVAL, "unknown intermediate %d", (int)which);
+    }
+    if (bytes != size)
+        return fail(h, BSORT_EINVAL, "intermediate %d has %llu bytes, %llu requested", (int)which,
+                    (unsigned long long)size, (unsigned long long)bytes);
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy(h_dst, static_cast<unsigned char *>(h->ws) + off, size,
+                       cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy intermediate");
+    return BSORT_OK;
+}
+
+bsort_status bsort_kernel_times(bsort_t h, float *ms, uint32_t count, uint32_t *written,
+                                uint32_t *calls)
+{
+    if (!h || !written) return BSORT_EINVAL;
+    *written = 0;
+    if (calls) *calls = 0;
+    if (!(h->flags & BSORT_FLAG_TIMING)) return fail(h, BSORT_EINVAL, "handle has no TIMING flag");
+    if (h->calls_recorded == 0) return fail(h, BSORT_ENOTREADY, "no timed call yet");
+    const int last = (int)((h->call_seq - 1) % kRing);
+    const int nk = h->n_ev[last];
+    cudaError_t e = cudaEventSynchronize(h->ev[last][nk]);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventSynchronize");
+    uint32_t k = 0;
+    for (; k < (uint32_t)nk && k < count; ++k)
+        if (ms) ms[k] = 0.f;
+    uint32_t used = 0;
+    for (uint64_t c = 0; c < h->calls_recorded; ++c) {
+        const int slot = (int)((h->call_seq - 1 - c) % kRing);
+        if (h->n_ev[slot] != nk) continue;  // a call with another launch sequence
+        for (uint32_t q = 0; q < k; ++q) {
+            float t = 0.f;
+            e = cudaEventElapsedTime(&t, h->ev[slot][q], h->ev[slot][q + 1]);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventElapsedTime");
+            if (ms) ms[q] += t;
+        }
+        ++used;
+    }
+    h->calls_recorded = 0;
+    *written = k;
+    if (calls) *calls = used;
+    return BSORT_OK;
+}
+
+const char *bsort_kernel_name(bsort_t h, uint32_t index)
+{
+    if (!h || index >= (uint32_t)kMaxTimed || !h->ev_name[index]) return "";
+    return h->ev_name[index];
+}
+
+const char *bsort_last_error(bsort_t h)
+{
+    if (!h) return "null handle";
+    return h->err;
+}
+
+}  // extern "C"

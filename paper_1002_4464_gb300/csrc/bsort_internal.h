@@ -1,0 +1,78 @@
+// bsort_internal.h -- launch interface between the host runtime (bsort_api.cu)
+// and the kernels (bsort_kernels.cu).  Not part of the public C ABI.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bsort {
+
+// Sort-unit shapes: one CTA sorts `cap` items, T threads x E items each.
+// Keys-only units sort uint32 keys; pair units sort uint64 composite keys
+// (key << 32 | local index) and gather the values afterwards.
+constexpr int kMaxCapKeys = 32768;   // 1024 threads x 32 keys, 132 KB SMEM
+constexpr int kMaxCapPairs = 16384;  // 1024 threads x 16 records, 136 KB SMEM
+constexpr int kRecordChunk = 16384;  // Step-4 chunk sorted by one CTA
+constexpr int kMergeTile = 4096;     // outputs per CTA in a Step-4 merge pass
+constexpr int kScanChunk = 4096;     // items per CTA of the Step-7 scan
+
+bool cap_supported(int cap, bool pairs);
+int smem_bytes_for_cap(int cap, bool pairs);
+
+// Configure kernel attributes (max dynamic SMEM) once per device.
+cudaError_t init_kernels();
+
+// Steps 1-3: sort every sublist of t = cap items; write sorted keys (and
+// values), and s sample records per sublist.
+cudaError_t launch_sublist_sort(int cap, bool pairs, const void *keys_in,
+                                const void *vals_in, uint64_t n, uint32_t m,
+                                int is_f32, int val_bytes, uint32_t s,
+                                uint32_t *tiles_k, void *tiles_v,
+                                uint64_t *samples, cudaStream_t st);
+
+// Step 4 (chunks): sort the n_rec records of src in chunks of kRecordChunk
+// into dst (which holds n_pad = chunks * kRecordChunk records, the tail
+// filled with all-ones); if the whole array is one chunk and spl != nullptr,
+// also writes the splitters (Step 5).
+cudaError_t launch_records_chunk_sort(const uint64_t *src, uint64_t *dst, uint32_t n_rec,
+                                      uint32_t n_pad, uint64_t *spl, uint32_t m,
+                                      uint32_t s, cudaStream_t st);
+// Step 4 (merges): merge sorted runs of length L of src into dst.
+cudaError_t launch_merge_pass(const uint64_t *src, uint64_t *dst, uint32_t n_pad,
+                              uint32_t L, cudaStream_t st);
+// Step 5: splitters g_j = sorted[(j+1)m - 1].
+cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t m, uint32_t s,
+                                    uint64_t *spl, cudaStream_t st);
+
+// Step 6: counts a_ij (bucket-major) and cumulative counts c_ij
+// (sublist-major, c[i*s + j] = items of sublist i <= g_j).
+cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
+                                const uint64_t *spl, uint32_t t, uint32_t s,
+                                uint32_t m, uint32_t *counts, uint32_t *cum,
+                                cudaStream_t st);
+
+// Step 7: exclusive scan of n_items uint32 counts (decoupled look-back);
+// status must hold ceil(n_items / kScanChunk) words and ticket one word,
+// both zero on entry.
+cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
+                        unsigned long long *status, uint32_t *ticket, int *err,
+                        cudaStream_t st);
+
+// Step 8: move every run A_ij to l_ij.
+cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v,
+                            const uint32_t *cum, const uint32_t *offsets,
+                            uint32_t t, uint32_t s, uint32_t m, int val_bytes,
+                            uint32_t *reloc_k, void *reloc_v, int *err, cudaStream_t st);
+
+// Step 9: sort every bucket B_j (one unit of `cap` items per bucket) and
+// write the first n positions of the result.  With offsets == nullptr the
+// whole input [0, n) is one bucket read from src (raw keys, transformed on
+// load): the single-unit path for n <= cap.
+cudaError_t launch_bucket_sort(int cap, bool pairs, const void *src_k,
+                               const void *src_v, const uint32_t *offsets,
+                               uint32_t m, uint32_t s, uint64_t n,
+                               uint64_t n_pad, int is_f32, int val_bytes,
+                               void *out_k, void *out_v, int *err,
+                               cudaStream_t st);
+
+}  // namespace bsort

@@ -1,0 +1,203 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
+element by element and bit-exactly (sorting is integer work: the bar is
+bit-exact for keys, values, intermediates and indices)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # collected on CPU machines, run on the GPU machine
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1002_4464_gb300 as pkg  # noqa: E402
+
+
+def _rec(k, p):
+    return (np.asarray(k).astype(np.uint64) << np.uint64(32)) | np.asarray(p).astype(np.uint64)
+
+
+def _to_dev_u32(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+
+
+def _gpu_sort_keys(sorter, keys, key_type="u32"):
+    d_in = _to_dev_u32(keys)
+    d_out = sorter.sort_keys(d_in, key_type=key_type)
+    sorter.sync()
+    return d_out.cpu().numpy().view(np.uint32)
+
+
+def _check_intermediates(sorter, want, n_pad, m, s):
+    im = pkg
+    got_t = sorter.intermediate(im.BSORT_IM_TILES, n_pad * 4, np.uint32)
+    assert np.array_equal(got_t, want["tile_keys"].astype(np.uint32)), "Step 2 sublists"
+    got_s = sorter.intermediate(im.BSORT_IM_SAMPLES, m * s * 8, np.uint64)
+    assert np.array_equal(got_s, _rec(want["samp_keys"], want["samp_p"])), "Step 3 samples"
+    got_g = sorter.intermediate(im.BSORT_IM_SPLITTERS, s * 8, np.uint64)
+    assert np.array_equal(got_g, _rec(want["spl_keys"], want["spl_p"])), "Step 5 splitters"
+    got_a = sorter.intermediate(im.BSORT_IM_COUNTS, m * s * 4, np.uint32)
+    assert np.array_equal(got_a, want["counts"].astype(np.uint32)), "Step 6 counts"
+    got_l = sorter.intermediate(im.BSORT_IM_OFFSETS, m * s * 4, np.uint32)
+    assert np.array_equal(got_l, want["offsets"].astype(np.uint32)), "Step 7 offsets"
+    got_r = sorter.intermediate(im.BSORT_IM_RELOCATED, n_pad * 4, np.uint32)
+    assert np.array_equal(got_r, want["reloc_keys"].astype(np.uint32)), "Step 8 relocation"
+
+
+@pytest.mark.parametrize("dist", synth.DISTRIBUTIONS)
+def test_config1_all_intermediates(dist):
+    """n = 2^20 uint32 keys, m = 256 sublists, s = 64 samples each."""
+    n, t, s = 1 << 20, 4096, 64
+    keys = synth.keys_u32(dist, n, synth.seed_for(1, synth.DISTRIBUTIONS.index(dist)))
+    want = oracle.paper_sort(keys, t, s, "u32")
+    sorter = pkg.BucketSorter(tile=t, samples=s)
+    got = _gpu_sort_keys(sorter, keys)
+    assert np.array_equal(got, want["keys"])
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], s)
+    sorter.close()
+
+
+@pytest.mark.parametrize("n,t,s", [
+    (4097, 4096, 64),             # two sublists, the second almost all padding
+    (3 * 4096 + 1000, 4096, 16),  # ragged tail
+    (123457, 8192, 128),
+    (200003, 16384, 256),
+    (70001, 2048, 32),
+])
+def test_ragged_intermediates(n, t, s):
+    keys = synth.keys_u32("uniform", n, synth.seed_for(2, 7, n % 97))
+    keys[::3] = keys[::3] & np.uint32(0xFF)  # duplicates across sublists
+    keys[-5:] = np.uint32(0xFFFFFFFF)        # real maximal keys next to the pads
+    want = oracle.paper_sort(keys, t, s, "u32")
+    sorter = pkg.BucketSorter(tile=t, samples=s)
+    got = _gpu_sort_keys(sorter, keys)
+    assert np.array_equal(got, want["keys"])
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], s)
+    sorter.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 3, 31, 2047, 2048, 4095, 4096, 4097, 32767, 32768,
+                               32769, 65536 + 5, 1 << 20, (1 << 20) + 12345, 1 << 22])
+def test_auto_plan_sizes(n):
+    keys = synth.keys_u32("gaussian", n, synth.seed_for(2, 1, n % 1000)) if n else \
+        np.zeros(0, np.uint32)
+    sorter = pkg.BucketSorter()
+    got = _gpu_sort_keys(sorter, keys) if n else np.zeros(0, np.uint32)
+    assert np.array_equal(got, oracle.textbook_sort(keys, "u32"))
+    sorter.close()
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zero", "sorted", "reverse", "staggered"])
+def test_f32_keys(dist):
+    n = 300001
+    f = synth.keys_f32(dist, n, synth.seed_for(2, 3))
+    f[:16] = np.array([np.inf, -np.inf, np.nan, -0.0, 0.0, 1e-45, -1e-45, 3.4e38, -3.4e38,
+                       np.float32(-np.nan), 1.0, -1.0, 0.5, -0.5, 2.0, -2.0], np.float32)
+    sorter = pkg.BucketSorter()
+    d_in = torch.from_numpy(f.copy()).cuda()
+    d_out = sorter.sort_keys(d_in, key_type="f32")
+    sorter.sync()
+    got = d_out.cpu().numpy().view(np.uint32)
+    want = oracle.textbook_sort(f, "f32").view(np.uint32)
+    assert np.array_equal(got, want)
+    sorter.close()
+
+
+@pytest.mark.parametrize("kind", ["zipf", "distinct16", "uniform"])
+@pytest.mark.parametrize("vdtype", [np.uint32, np.uint64])
+def test_pairs_stable(kind, vdtype):
+    n = 400009
+    seed = synth.seed_for(3, 1)
+    if kind == "zipf":
+        keys = synth.keys_zipf(n, seed)
+    elif kind == "distinct16":
+        keys = synth.keys_16distinct(n, seed)
+    else:
+        keys = synth.keys_u32("uniform", n, seed)
+    vals = np.arange(n, dtype=vdtype)
+    if vdtype == np.uint64:
+        vals = vals | (np.uint64(0xABCD) << np.uint64(40))
+    sorter = pkg.BucketSorter()
+    tdt = torch.int32 if vdtype == np.uint32 else torch.int64
+    d_k = _to_dev_u32(keys)
+    d_v = torch.from_numpy(vals.view(np.int32 if vdtype == np.uint32 else np.int64)).cuda()
+    ok, ov = sorter.sort_pairs(d_k, d_v)
+    sorter.sync()
+    wk, wv = oracle.textbook_sort(keys, "u32", vals=vals)
+    assert np.array_equal(ok.cpu().numpy().view(np.uint32), wk)
+    assert np.array_equal(ov.cpu().numpy().view(vdtype), wv)
+    assert tdt is not None
+    sorter.close()
+
+
+def test_pairs_intermediates_forced_plan():
+    n, t, s = 100000, 4096, 64
+    keys = synth.keys_zipf(n, synth.seed_for(3, 2))
+    vals = np.arange(n, dtype=np.uint32)
+    want = oracle.paper_sort(keys, t, s, "u32", vals=vals)
+    sorter = pkg.BucketSorter(tile=t, samples=s)
+    ok, ov = sorter.sort_pairs(_to_dev_u32(keys), _to_dev_u32(vals))
+    sorter.sync()
+    assert np.array_equal(ok.cpu().numpy().view(np.uint32), want["keys"])
+    assert np.array_equal(ov.cpu().numpy().view(np.uint32), want["vals"])
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], s)
+    sorter.close()
+
+
+def test_in_place_and_repeat_determinism():
+    n = (1 << 21) + 3
+    keys = synth.keys_u32("bucket", n, synth.seed_for(2, 5))
+    sorter = pkg.BucketSorter()
+    d = _to_dev_u32(keys)
+    sorter.sort_keys(d, out=d)
+    sorter.sync()
+    first = d.cpu().numpy().view(np.uint32).copy()
+    assert np.array_equal(first, np.sort(keys))
+    d2 = _to_dev_u32(keys)
+    out = sorter.sort_keys(d2)
+    sorter.sync()
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), first)
+    assert np.array_equal(d2.cpu().numpy().view(np.uint32), keys)  # input untouched
+    sorter.close()
+
+
+def test_host_entry_point():
+    n = 1 << 20
+    keys = synth.keys_u32("uniform", n, synth.seed_for(2, 6))
+    sorter = pkg.BucketSorter()
+    h_in = torch.from_numpy(keys.view(np.int32)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    sorter.sort_keys_host(h_in, h_out)
+    sorter.sync()
+    assert np.array_equal(h_out.numpy().view(np.uint32), np.sort(keys))
+    sorter.close()
+
+
+def test_workspace_too_small_is_enomem():
+    cfg = pkg.bsort_config(device=0)
+    ws = torch.empty(4096, dtype=torch.uint8, device="cuda")
+    cfg.workspace = ws.data_ptr()
+    cfg.workspace_bytes = 4096
+    h = pkg.bsort_create(cfg)
+    d = torch.zeros(1 << 20, dtype=torch.int32, device="cuda")
+    with pytest.raises(pkg.BsortError) as e:
+        pkg.bsort_sort_keys(h, pkg.BSORT_U32, d.data_ptr(), d.data_ptr(), 1 << 20, None)
+    assert e.value.status == pkg.BSORT_ENOMEM
+    pkg.bsort_destroy(h)
+
+
+def test_bucket_bound_holds_on_device():
+    """Every bucket B_j built on the GPU obeys |B_j| <= n'/s + (m-1)(w-1)."""
+    for dist in synth.DISTRIBUTIONS:
+        n = 1 << 20
+        keys = synth.keys_u32(dist, n, synth.seed_for(2, 9))
+        sorter = pkg.BucketSorter(tile=4096, samples=64)
+        _gpu_sort_keys(sorter, keys)
+        p = sorter.plan(n)
+        l = sorter.intermediate(pkg.BSORT_IM_OFFSETS, p.m * p.s * 4, np.uint32).astype(np.int64)
+        starts = np.append(l.reshape(p.s, p.m)[:, 0], p.n_padded)
+        assert np.diff(starts).max() <= p.bucket_bound <= 2 * p.n_padded // p.s
+        sorter.close()
