@@ -34,7 +34,7 @@ struct Plan {
     // workspace offsets (bytes)
     uint64_t off_hdr, off_tiles_k, off_tiles_v, off_reloc_k, off_reloc_v, off_samples,
         off_rec_a, off_rec_b, off_spl, off_counts, off_cum, off_offsets, off_status,
-        off_stage_in, off_stage_out, total;
+        off_units, total;
 };
 
 }  // namespace
@@ -176,7 +176,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         uint32_t merges = 0;
         for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
         I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
-                        1 /*S6*/ + 1 /*S7*/ + 1 /*S8*/ + 1 /*S9*/;
+                        1 /*S6*/ + 1 /*S7*/ + 1 /*S8*/ + 1 /*units*/ + 1 /*S9*/;
     }
 
     // workspace layout
@@ -201,6 +201,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->off_cum = take((uint64_t)P->n_rec * 4);
         P->off_offsets = take((uint64_t)P->n_rec * 4);
         P->off_status = take((uint64_t)P->scan_chunks * 8);
+        P->off_units = take((1 + 2 * (uint64_t)I.s) * 4);
     }
     P->total = o;
     I.workspace_bytes = o;
@@ -324,7 +325,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
             }
             return BSORT_OK;
         }
-        SEQ(launch_bucket_sort(P.unit_cap, P.pairs, kin, vin, nullptr, 1, 1, n, n, is_f32, (int)vb,
+        SEQ(launch_bucket_sort(P.unit_cap, P.pairs, kin, vin, nullptr, 1, n, n, is_f32, (int)vb,
                                kout, vout, err, st),
             "step9_single_unit");
         return BSORT_OK;
@@ -376,9 +377,13 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     SEQ(launch_relocate(tiles_k, tiles_v, cum, offsets, I.t, I.s, I.m, (int)vb, reloc_k, reloc_v,
                         err, st),
         "step8_relocate");
-    // Step 9
-    SEQ(launch_bucket_sort(P.unit_cap, P.pairs, reloc_k, reloc_v, offsets, I.m, I.s, n,
-                           I.n_padded, is_f32, (int)vb, kout, vout, err, st),
+    // Step 9: buckets packed into units of at most unit_capacity items
+    uint32_t *units = reinterpret_cast<uint32_t *>(ws + P.off_units);
+    SEQ(launch_pack_units(offsets, I.m, I.s, (uint32_t)I.n_padded, (uint32_t)I.unit_capacity,
+                          units, err, st),
+        "step9_pack_units");
+    SEQ(launch_bucket_sort(P.unit_cap, P.pairs, reloc_k, reloc_v, units, I.s, n, I.n_padded,
+                           is_f32, (int)vb, kout, vout, err, st),
         "step9_bucket_sort");
     return BSORT_OK;
 }

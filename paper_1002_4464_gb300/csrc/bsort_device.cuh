@@ -14,6 +14,9 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
+#include <utility>
+
 #include <cuda_runtime.h>
 
 namespace bsort {
@@ -81,24 +84,49 @@ __device__ __forceinline__ void cmp_swap<uint32_t>(uint32_t &a, uint32_t &b)
     b = hi;
 }
 
-// Batcher's odd-even merge sort network on E (power of two) registers.
+// Batcher's odd-even merge sort network on E (power of two) registers,
+// expanded at compile time (p: merged run size, k: comparator distance,
+// j: block start, i: offset in block) so that every register index is a
+// constant.
+template <int E, int P, int K, int J, int I, typename KT>
+__device__ __forceinline__ void oem_ce(KT (&v)[E])
+{
+    if constexpr (I + J + K < E && (I + J) / (2 * P) == (I + J + K) / (2 * P))
+        cmp_swap(v[I + J], v[I + J + K]);
+}
+template <int E, int P, int K, int J, typename KT, int... I>
+__device__ __forceinline__ void oem_i(KT (&v)[E], std::integer_sequence<int, I...>)
+{
+    (oem_ce<E, P, K, J, I>(v), ...);
+}
+template <int E, int P, int K, int J, typename KT>
+__device__ __forceinline__ void oem_j(KT (&v)[E])
+{
+    if constexpr (J + K < E) {
+        oem_i<E, P, K, J>(v, std::make_integer_sequence<int, K>{});
+        oem_j<E, P, K, J + 2 * K>(v);
+    }
+}
+template <int E, int P, int K, typename KT>
+__device__ __forceinline__ void oem_k(KT (&v)[E])
+{
+    if constexpr (K >= 1) {
+        oem_j<E, P, K, K % P>(v);
+        oem_k<E, P, K / 2>(v);
+    }
+}
+template <int E, int P, typename KT>
+__device__ __forceinline__ void oem_p(KT (&v)[E])
+{
+    if constexpr (P < E) {
+        oem_k<E, P, P>(v);
+        oem_p<E, 2 * P>(v);
+    }
+}
 template <int E, typename K>
 __device__ __forceinline__ void sort_network(K (&v)[E])
 {
-#pragma unroll
-    for (int p = 1; p < E; p <<= 1) {
-#pragma unroll
-        for (int k = p; k >= 1; k >>= 1) {
-#pragma unroll
-            for (int j = k % p; j + k < E; j += 2 * k) {
-#pragma unroll
-                for (int i = 0; i < k; ++i) {
-                    if (i + j + k < E && (i + j) / (2 * p) == (i + j + k) / (2 * p))
-                        cmp_swap(v[i + j], v[i + j + k]);
-                }
-            }
-        }
-    }
+    oem_p<E, 1>(v);
 }
 
 // ---------------------------------------------------------------- merge path
@@ -150,28 +178,182 @@ __device__ __forceinline__ void merge_serial_smem(const K *sm, int a0, int la, i
     }
 }
 
-// Sort T*E keys held E per thread (any assignment of keys to threads) into
-// shared memory sm (padded layout).  On return sm[pidx(x)] is the x-th
-// smallest key and v holds positions [tid*E, tid*E + E) of the sorted tile.
-template <typename K, int T, int E>
-__device__ __forceinline__ void cta_sort(K (&v)[E], K *sm)
+// ---------------------------------------------------------------- warp merges
+template <typename K>
+__device__ __forceinline__ K kmin(K a, K b) { return a < b ? a : b; }
+template <typename K>
+__device__ __forceinline__ K kmax(K a, K b) { return a < b ? b : a; }
+template <>
+__device__ __forceinline__ uint32_t kmin<uint32_t>(uint32_t a, uint32_t b) { return min(a, b); }
+template <>
+__device__ __forceinline__ uint32_t kmax<uint32_t>(uint32_t a, uint32_t b) { return max(a, b); }
+
+// Bitonic merge network across the lanes of a warp.  On entry every lane
+// holds E keys sorted ascending; on exit the warp holds 32*E keys sorted
+// ascending in blocked order (lane l holds ranks [l*E, l*E + E)).  Level l
+// merges runs of 2^(l-1) lanes: one "flip" stage (element x against
+// element 2M-1-x), half-cleaners at lane distances 2^(l-2)..1 (shuffles),
+// then half-cleaners at register distances E/2..1.
+template <typename K, int E>
+__device__ __forceinline__ void warp_merge_levels(K (&v)[E], int lane)
 {
-    const int tid = threadIdx.x;
-    sort_network<E>(v);
 #pragma unroll
-    for (int k = 0; k < E; ++k) sm[pidx<K>(tid * E + k)] = v[k];
+    for (int l = 1; l <= 5; ++l) {
+        const int fm = (1 << l) - 1;
+        const bool lo_f = (lane & (1 << (l - 1))) == 0;
+#pragma unroll
+        for (int k = 0; k < E / 2; ++k) {
+            K x1 = __shfl_xor_sync(0xFFFFFFFFu, v[E - 1 - k], fm);
+            K x2 = __shfl_xor_sync(0xFFFFFFFFu, v[k], fm);
+            v[k] = lo_f ? kmin(v[k], x1) : kmax(v[k], x1);
+            v[E - 1 - k] = lo_f ? kmin(v[E - 1 - k], x2) : kmax(v[E - 1 - k], x2);
+        }
+#pragma unroll
+        for (int d = (1 << l) >> 2; d >= 1; d >>= 1) {
+            const bool lo = (lane & d) == 0;
+#pragma unroll
+            for (int k = 0; k < E; ++k) {
+                K x = __shfl_xor_sync(0xFFFFFFFFu, v[k], d);
+                v[k] = lo ? kmin(v[k], x) : kmax(v[k], x);
+            }
+        }
+#pragma unroll
+        for (int h = E / 2; h >= 1; h >>= 1) {
+#pragma unroll
+            for (int k = 0; k < E; ++k)
+                if ((k & h) == 0) cmp_swap(v[k], v[k + h]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------- block merges
+// Runs of one block level alternate direction: run q is stored ascending if
+// q is even and descending if q is odd, so every pair (A ascending, B
+// descending) is a bitonic sequence.  A thread producing outputs [d, d+E) of
+// the merge walks A upwards and B "downwards in storage" from its co-rank:
+// the two pointers converge and never cross, so no bounds checks are needed
+// (an exhausted run's pointer reads the other run's extreme element, which
+// never wins a comparison it should lose).
+template <typename K>
+__device__ __forceinline__ int corank_bitonic(const K *sm, int a0, int bend, int L, int d)
+{
+    // number of A items among the first d outputs; A = sm[a0 .. a0+L)
+    // ascending, B = sm[bend-L .. bend) descending (B[j] at bend-1-j)
+    int lo = d > L ? d - L : 0;
+    int hi = d < L ? d : L;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const K am = sm[pidx<K>(a0 + mid)];
+        const K bm = sm[pidx<K>(bend - d + mid)];  // B[d-1-mid]
+        if (am <= bm) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <typename K, int E>
+__device__ __forceinline__ void merge_bitonic_pair(const K *sm, int ia, int ib, K (&v)[E])
+{
+    // ia: storage index of the next A item (moving up);
+    // ib: storage index of the next B item (moving down)
+    K a = sm[pidx<K>(ia)];
+    K b = sm[pidx<K>(ib)];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const bool p = a <= b;
+        v[k] = p ? a : b;
+        if (k + 1 < E) {
+            ia += p ? 1 : 0;
+            ib -= p ? 0 : 1;
+            const K nxt = sm[pidx<K>(p ? ia : ib)];
+            a = p ? nxt : a;
+            b = p ? b : nxt;
+        }
+    }
+}
+
+// Store E keys (ranks [r, r+E) of a run of length RL stored at base) in
+// the run's direction.
+template <typename K, int E>
+__device__ __forceinline__ void store_run(K *sm, int base, int RL, int r, bool desc,
+                                          const K (&v)[E])
+{
+    if (!desc) {
+#pragma unroll
+        for (int k = 0; k < E; ++k) sm[pidx<K>(base + r + k)] = v[k];
+    } else {
+#pragma unroll
+        for (int k = 0; k < E; ++k) sm[pidx<K>(base + RL - 1 - r - k)] = v[k];
+    }
+}
+
+// Position of register k of thread (warp, lane) in the CTA's tile under the
+// "warp-blocked" layout: warp w owns the contiguous chunk [w*32E, (w+1)*32E)
+// and lane l its items l, l+32, l+64, ... of that chunk, so that global
+// loads are coalesced and padding (items >= len) fills whole trailing warps.
+template <int E>
+__device__ __forceinline__ int wb_pos(int warp, int lane, int k)
+{
+    return warp * (32 * E) + k * 32 + lane;
+}
+
+// Sort T*E keys held E per thread into shared memory sm (padded layout),
+// ascending.  Items at tile positions >= len are padding holding the
+// maximal key (the caller loads them that way, in the warp-blocked layout);
+// warps and merge pairs made only of padding skip their work.  On return
+// sm[pidx(x)] is the x-th smallest key.
+template <typename K, int T, int E>
+__device__ __forceinline__ void cta_sort(K (&v)[E], K *sm, int len = T * E)
+{
+    static_assert(T % 32 == 0 && T >= 32, "whole warps");
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    constexpr int W = 32 * E;  // warp run
+    if (warp * W < len) {
+        sort_network<E>(v);
+        warp_merge_levels<K, E>(v, lane);
+    }
+    store_run<K, E>(sm, warp * W, W, lane * E, (warp & 1) != 0, v);
     __syncthreads();
 #pragma unroll 1
-    for (int L = E; L < T * E; L <<= 1) {
+    for (int L = W; L < T * E; L <<= 1) {
+        const int dg = tid * E;
+        const int a0 = dg & ~(2 * L - 1);  // start of the pair
+        const bool work = a0 < len;
+        if (work) {
+            const int d = dg - a0;
+            const int bend = a0 + 2 * L;
+            const int i = corank_bitonic<K>(sm, a0, bend, L, d);
+            merge_bitonic_pair<K, E>(sm, a0 + i, bend - 1 - (d - i), v);
+        }
+        __syncthreads();
+        if (work) {
+            const bool desc = ((a0 / (2 * L)) & 1) != 0;
+            store_run<K, E>(sm, a0, 2 * L, dg - a0, desc, v);
+        }
+        __syncthreads();
+    }
+}
+
+// The same sort when the tile already consists of sorted runs of length R
+// (R a power of two, 32*E <= R < T*E) stored in sm with run q ascending if q
+// is even and descending if q is odd: only the block levels from R run.
+template <typename K, int T, int E>
+__device__ __forceinline__ void cta_merge_runs(K *sm, int R)
+{
+    const int tid = threadIdx.x;
+    K v[E];
+#pragma unroll 1
+    for (int L = R; L < T * E; L <<= 1) {
         const int dg = tid * E;
         const int a0 = dg & ~(2 * L - 1);
         const int d = dg - a0;
-        const int b0 = a0 + L;
-        int i = merge_path_smem<K>(sm, a0, L, b0, L, d);
-        merge_serial_smem<K, E>(sm, a0, L, b0, L, i, d - i, v);
+        const int bend = a0 + 2 * L;
+        const int i = corank_bitonic<K>(sm, a0, bend, L, d);
+        merge_bitonic_pair<K, E>(sm, a0 + i, bend - 1 - (d - i), v);
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < E; ++k) sm[pidx<K>(tid * E + k)] = v[k];
+        const bool desc = ((a0 / (2 * L)) & 1) != 0;
+        store_run<K, E>(sm, a0, 2 * L, d, desc, v);
         __syncthreads();
     }
 }

@@ -58,21 +58,28 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
                         unsigned long long *status, uint32_t *ticket, int *err,
                         cudaStream_t st);
 
+constexpr int kRelocateSmemMax = 220 * 1024;
+
 // Step 8: move every run A_ij to l_ij.
 cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v,
                             const uint32_t *cum, const uint32_t *offsets,
                             uint32_t t, uint32_t s, uint32_t m, int val_bytes,
                             uint32_t *reloc_k, void *reloc_v, int *err, cudaStream_t st);
 
-// Step 9: sort every bucket B_j (one unit of `cap` items per bucket) and
-// write the first n positions of the result.  With offsets == nullptr the
-// whole input [0, n) is one bucket read from src (raw keys, transformed on
-// load): the single-unit path for n <= cap.
+// Step 9 units: pack consecutive buckets into units of at most Q items;
+// units holds 1 + 2*s words (count, then begin/end pairs).
+cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t s,
+                              uint32_t n_pad, uint32_t Q, uint32_t *units, int *err,
+                              cudaStream_t st);
+
+// Step 9: sort every unit (one CTA of `cap` items each; grid = max_units,
+// surplus CTAs exit) and write the first n positions of the result.  With
+// units == nullptr the whole input [0, n) is one unit read from src (raw
+// keys, transformed on load): the single-unit path for n <= cap.
 cudaError_t launch_bucket_sort(int cap, bool pairs, const void *src_k,
-                               const void *src_v, const uint32_t *offsets,
-                               uint32_t m, uint32_t s, uint64_t n,
-                               uint64_t n_pad, int is_f32, int val_bytes,
-                               void *out_k, void *out_v, int *err,
-                               cudaStream_t st);
+                               const void *src_v, const uint32_t *units,
+                               uint32_t max_units, uint64_t n, uint64_t n_pad,
+                               int is_f32, int val_bytes, void *out_k, void *out_v,
+                               int *err, cudaStream_t st);
 
 }  // namespace bsort

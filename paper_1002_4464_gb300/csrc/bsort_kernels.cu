@@ -38,10 +38,11 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
     const uint64_t base = (uint64_t)blockIdx.x * CAP;
     const uint64_t avail = n > base ? n - base : 0;
 
+    const int lane = tid & 31, warp = tid >> 5;
     K v[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) {
-        const int x = k * T + tid;
+        const int x = wb_pos<E>(warp, lane, k);
         uint32_t key = 0xFFFFFFFFu;  // pad sentinel (position >= n)
         if ((uint64_t)x < avail) {
             key = keys_in[base + x];
@@ -50,7 +51,7 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
         if constexpr (PAIRS) v[k] = ((uint64_t)key << 32) | (uint32_t)x;
         else v[k] = (K)key;
     }
-    cta_sort<K, T, E>(v, sm);
+    cta_sort<K, T, E>(v, sm, avail < (uint64_t)CAP ? (int)avail : CAP);
 
 #pragma unroll 4
     for (int k = 0; k < E; ++k) {
@@ -83,6 +84,9 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
 }
 
 // ============================================================ Step 4 (chunks)
+// The records of one sublist (s consecutive records) are already sorted, so
+// when s >= 32*E the chunk is loaded as sorted runs (odd runs reversed) and
+// only the remaining merge levels run; otherwise the chunk is sorted whole.
 template <int T, int E>
 __global__ void __launch_bounds__(T, 1)
 k_records_sort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uint32_t n_rec,
@@ -92,14 +96,27 @@ k_records_sort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uin
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *sm = reinterpret_cast<uint64_t *>(smem_raw);
     const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
     const uint64_t base = (uint64_t)blockIdx.x * CAP;
-    uint64_t v[E];
+    if (s >= 32u * E && s < (uint32_t)CAP) {
+        for (int x = tid; x < CAP; x += T) {
+            const uint64_t g = base + x;
+            const uint64_t r = g < n_rec ? src[g] : 0xFFFFFFFFFFFFFFFFull;
+            const int q = x / (int)s, o = x % (int)s;
+            const int pos = (q & 1) ? q * (int)s + (int)s - 1 - o : x;
+            sm[pidx<uint64_t>(pos)] = r;
+        }
+        __syncthreads();
+        cta_merge_runs<uint64_t, T, E>(sm, (int)s);
+    } else {
+        uint64_t v[E];
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-        const uint64_t x = base + k * T + tid;
-        v[k] = x < n_rec ? src[x] : 0xFFFFFFFFFFFFFFFFull;
+        for (int k = 0; k < E; ++k) {
+            const uint64_t x = base + wb_pos<E>(warp, lane, k);
+            v[k] = x < n_rec ? src[x] : 0xFFFFFFFFFFFFFFFFull;
+        }
+        cta_sort<uint64_t, T, E>(v, sm);
     }
-    cta_sort<uint64_t, T, E>(v, sm);
 #pragma unroll 4
     for (int k = 0; k < E; ++k) {
         const int x = k * T + tid;
@@ -321,59 +338,195 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 }
 
 // ============================================================ Step 8
-// One CTA per sublist; each warp copies whole runs A_ij (lanes in parallel).
+// One CTA per sublist: the sorted sublist (keys, and values when they fit),
+// its cumulative counts c_i. and its offsets l_.i are staged in shared memory
+// with coalesced loads; then each warp copies whole runs A_ij to l_ij
+// (lanes in parallel, coalesced stores).
 template <int T>
-__global__ void __launch_bounds__(T)
+__global__ void __launch_bounds__(T, 1)
 k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_v,
            const uint32_t *__restrict__ cum, const uint32_t *__restrict__ offsets,
-           uint32_t t, uint32_t s, uint32_t m, uint64_t n_pad, int val_bytes,
+           uint32_t t, uint32_t s, uint32_t m, uint64_t n_pad, int val_bytes, int stage_vals,
            uint32_t *__restrict__ reloc_k, void *__restrict__ reloc_v, int *err)
 {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *s_k = reinterpret_cast<uint32_t *>(smem_raw);
+    uint32_t *s_cum = s_k + t;
+    uint32_t *s_off = s_cum + s;
+    unsigned char *s_v = reinterpret_cast<unsigned char *>(s_off + s);
     const uint32_t i = blockIdx.x;
     const uint64_t base = (uint64_t)i * t;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    {
+        const uint4 *src4 = reinterpret_cast<const uint4 *>(tiles_k + base);
+        uint4 *dst4 = reinterpret_cast<uint4 *>(s_k);
+        for (uint32_t x = tid; x < t / 4; x += T) dst4[x] = src4[x];
+        if (stage_vals) {
+            const uint4 *v4 = reinterpret_cast<const uint4 *>(
+                static_cast<const unsigned char *>(tiles_v) + base * val_bytes);
+            uint4 *d4 = reinterpret_cast<uint4 *>(s_v);
+            for (uint32_t x = tid; x < t * val_bytes / 16; x += T) d4[x] = v4[x];
+        }
+        for (uint32_t j = tid; j < s; j += T) {
+            s_cum[j] = cum[(uint64_t)i * s + j];
+            s_off[j] = offsets[(uint64_t)j * m + i];
+        }
+    }
+    __syncthreads();
     for (uint32_t j = warp; j < s; j += T / 32) {
-        const uint32_t start = j ? cum[(uint64_t)i * s + j - 1] : 0u;
-        const uint32_t end = cum[(uint64_t)i * s + j];
-        const uint64_t dst = offsets[(uint64_t)j * m + i];
+        const uint32_t start = j ? s_cum[j - 1] : 0u;
+        const uint32_t end = s_cum[j];
+        const uint64_t dst = s_off[j];
         if (end < start || end > t || dst + (end - start) > n_pad) {  // never for a valid plan
             if (lane == 0) set_error(err, DEV_INTERNAL);
             continue;
         }
         for (uint32_t x = start + lane; x < end; x += 32) {
-            reloc_k[dst + (x - start)] = tiles_k[base + x];
-            if (val_bytes == 4)
-                static_cast<uint32_t *>(reloc_v)[dst + (x - start)] =
-                    static_cast<const uint32_t *>(tiles_v)[base + x];
-            else if (val_bytes == 8)
-                static_cast<uint64_t *>(reloc_v)[dst + (x - start)] =
-                    static_cast<const uint64_t *>(tiles_v)[base + x];
+            reloc_k[dst + (x - start)] = s_k[x];
+            if (val_bytes == 4) {
+                const uint32_t val = stage_vals ? reinterpret_cast<const uint32_t *>(s_v)[x]
+                                                : static_cast<const uint32_t *>(tiles_v)[base + x];
+                static_cast<uint32_t *>(reloc_v)[dst + (x - start)] = val;
+            } else if (val_bytes == 8) {
+                const uint64_t val = stage_vals ? reinterpret_cast<const uint64_t *>(s_v)[x]
+                                                : static_cast<const uint64_t *>(tiles_v)[base + x];
+                static_cast<uint64_t *>(reloc_v)[dst + (x - start)] = val;
+            }
         }
     }
+}
+
+// Step 9 units: consecutive buckets packed greedily into units of at most Q
+// items (every bucket fits one unit, since |B_j| <= bound <= Q).  One CTA:
+// nxt[j] = the bucket after the longest run of buckets from j that fits, the
+// chain 0, nxt[0], nxt[nxt[0]], ... marks the unit starts (found by pointer
+// doubling), and a scan numbers them.  units[0] = U, then (begin, end) pairs.
+template <int T>
+__global__ void __launch_bounds__(T, 1)
+k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t s, uint32_t n_pad,
+             uint32_t Q, uint32_t *__restrict__ units, int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem_raw);  // s + 1
+    uint32_t *nxt = Lb + (s + 1);                             // s + 1
+    uint32_t *jmp = nxt + (s + 1);                            // s + 1
+    uint32_t *on = jmp + (s + 1);                             // s + 1
+    __shared__ uint32_t s_warp[T / 32];
+    __shared__ uint32_t s_total;
+    const int tid = threadIdx.x;
+    for (uint32_t j = tid; j <= s; j += T) {
+        Lb[j] = j < s ? offsets[(uint64_t)j * m] : n_pad;
+        on[j] = j == 0 ? 1u : 0u;
+    }
+    __syncthreads();
+    for (uint32_t j = tid; j <= s; j += T) {
+        uint32_t e = j;
+        if (j < s) {
+            uint32_t lo = j + 1, hi = s;  // largest e in [j+1, s] with Lb[e] - Lb[j] <= Q
+            const uint32_t lim = Lb[j] + Q;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) >> 1;
+                if (Lb[mid] <= lim) lo = mid;
+                else hi = mid - 1;
+            }
+            e = lo;
+            if (Lb[e] - Lb[j] > Q) set_error(err, DEV_INTERNAL);  // a bucket exceeds Q
+        }
+        nxt[j] = e;
+        jmp[j] = e;
+    }
+    __syncthreads();
+    for (uint32_t span = 1; span <= s; span <<= 1) {
+        for (uint32_t j = tid; j <= s; j += T)
+            if (on[j]) on[jmp[j]] = 1u;
+        __syncthreads();
+        for (uint32_t j = tid; j <= s; j += T) {
+            const uint32_t a = jmp[j];
+            nxt[j] = jmp[a];  // use nxt as scratch for the doubled jump
+        }
+        __syncthreads();
+        for (uint32_t j = tid; j <= s; j += T) jmp[j] = nxt[j];
+        __syncthreads();
+    }
+    // recompute the single-step successor (nxt was used as scratch)
+    for (uint32_t j = tid; j <= s; j += T) {
+        uint32_t e = j;
+        if (j < s) {
+            uint32_t lo = j + 1, hi = s;
+            const uint32_t lim = Lb[j] + Q;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) >> 1;
+                if (Lb[mid] <= lim) lo = mid;
+                else hi = mid - 1;
+            }
+            e = lo;
+        }
+        nxt[j] = e;
+    }
+    __syncthreads();
+    // number the unit starts (chain members j < s) in order: block scan
+    const uint32_t per = (s + T - 1) / T;
+    const uint32_t j0 = tid * per;
+    uint32_t cnt = 0;
+    for (uint32_t q = 0; q < per; ++q)
+        if (j0 + q < s && on[j0 + q]) ++cnt;
+    const int lane = tid & 31, warp = tid >> 5;
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t wv = lane < T / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < T / 32) s_warp[lane] = wi - wv;
+        if (lane == T / 32 - 1) s_total = wi;
+    }
+    __syncthreads();
+    uint32_t u = s_warp[warp] + incl - cnt;
+    for (uint32_t q = 0; q < per; ++q) {
+        const uint32_t j = j0 + q;
+        if (j < s && on[j]) {
+            units[1 + 2 * u] = Lb[j];
+            units[2 + 2 * u] = Lb[nxt[j]];
+            ++u;
+        }
+    }
+    if (tid == 0) units[0] = s_total;
 }
 
 // ============================================================ Step 9
 template <int T, int E, bool PAIRS>
 __global__ void __launch_bounds__(T, 1)
 k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
-              const uint32_t *__restrict__ offsets, uint32_t m, uint32_t s, uint64_t n,
-              uint64_t n_pad, int is_f32, int val_bytes, uint32_t *__restrict__ out_k,
-              void *__restrict__ out_v, int *err)
+              const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
+              int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v, int *err)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
     constexpr int CAP = T * E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     K *sm = reinterpret_cast<K *>(smem_raw);
     const int tid = threadIdx.x;
-    const uint32_t j = blockIdx.x;
-    const bool direct = offsets == nullptr;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t u = blockIdx.x;
+    const bool direct = units == nullptr;
     uint64_t L = 0, R = n;
     if (!direct) {
-        L = offsets[(uint64_t)j * m];
-        R = (j + 1 < s) ? offsets[(uint64_t)(j + 1) * m] : n_pad;
+        if (u >= units[0]) return;  // fewer units than the grid
+        L = units[1 + 2 * u];
+        R = units[2 + 2 * u];
     }
     const uint64_t len = R - L;
-    if (R < L || R > n_pad || len > (uint64_t)CAP) {  // the plan guarantees |B_j| <= CAP
+    if (R < L || R > n_pad || len > (uint64_t)CAP) {  // the plan guarantees a unit fits
         if (tid == 0) set_error(err, DEV_INTERNAL);
         return;
     }
@@ -381,7 +534,7 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
     K v[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) {
-        const int x = k * T + tid;
+        const int x = wb_pos<E>(warp, lane, k);
         uint32_t key = 0xFFFFFFFFu;
         if ((uint64_t)x < len) {
             key = src_k[L + x];
@@ -390,7 +543,7 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
         if constexpr (PAIRS) v[k] = ((uint64_t)key << 32) | (uint32_t)x;
         else v[k] = (K)key;
     }
-    cta_sort<K, T, E>(v, sm);
+    cta_sort<K, T, E>(v, sm, (int)len);
     const uint64_t lim = min((unsigned long long)len, (unsigned long long)(n > L ? n - L : 0));
 #pragma unroll 4
     for (int k = 0; k < E; ++k) {
@@ -400,7 +553,7 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
             uint32_t key = PAIRS ? (uint32_t)((uint64_t)e >> 32) : (uint32_t)e;
             if (is_f32) key = f32_decode(key);
             out_k[L + x] = key;
-            if (PAIRS) {
+            if constexpr (PAIRS) {
                 const uint32_t idx = (uint32_t)((uint64_t)e & 0xFFFFFFFFull);
                 if (val_bytes == 4)
                     static_cast<uint32_t *>(out_v)[L + x] =
@@ -459,6 +612,8 @@ cudaError_t init_kernels()
     BSORT_TRY(set_smem(k_bucket_sort<1024, 16, true>, smem_bytes_for_cap(16384, true)));
     BSORT_TRY(set_smem(k_records_sort<1024, 16>, smem_bytes_for_cap(kRecordChunk, true)));
     BSORT_TRY(set_smem(k_sample_index<256>, 64 * 1024));
+    BSORT_TRY(set_smem(k_relocate<1024>, kRelocateSmemMax));
+    BSORT_TRY(set_smem(k_pack_units<1024>, 16 * 4097));
     return cudaSuccess;
 }
 
@@ -536,28 +691,49 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
     return cudaGetLastError();
 }
 
+int relocate_smem_bytes(uint32_t t, uint32_t s, int val_bytes, int *stage_vals)
+{
+    int bytes = (int)(t * 4 + 2 * s * 4);
+    bytes = (bytes + 15) / 16 * 16;
+    const int with_vals = bytes + (int)(t * val_bytes);
+    *stage_vals = (val_bytes > 0 && with_vals <= kRelocateSmemMax) ? 1 : 0;
+    return *stage_vals ? with_vals : bytes;
+}
+
 cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const uint32_t *cum,
                             const uint32_t *offsets, uint32_t t, uint32_t s, uint32_t m,
                             int val_bytes, uint32_t *reloc_k, void *reloc_v, int *err,
                             cudaStream_t st)
 {
-    k_relocate<256><<<m, 256, 0, st>>>(tiles_k, tiles_v, cum, offsets, t, s, m,
-                                       (uint64_t)m * t, val_bytes, reloc_k, reloc_v, err);
+    int stage_vals = 0;
+    const int sm = relocate_smem_bytes(t, s, val_bytes, &stage_vals);
+    if (sm > kRelocateSmemMax) return cudaErrorInvalidValue;
+    k_relocate<1024><<<m, 1024, sm, st>>>(tiles_k, tiles_v, cum, offsets, t, s, m,
+                                          (uint64_t)m * t, val_bytes, stage_vals, reloc_k,
+                                          reloc_v, err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t s, uint32_t n_pad,
+                              uint32_t Q, uint32_t *units, int *err, cudaStream_t st)
+{
+    const int sm = (int)(4 * (s + 1) * 4);
+    k_pack_units<1024><<<1, 1024, sm, st>>>(offsets, m, s, n_pad, Q, units, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bucket_sort(int cap, bool pairs, const void *src_k, const void *src_v,
-                               const uint32_t *offsets, uint32_t m, uint32_t s, uint64_t n,
+                               const uint32_t *units, uint32_t max_units, uint64_t n,
                                uint64_t n_pad, int is_f32, int val_bytes, void *out_k,
                                void *out_v, int *err, cudaStream_t st)
 {
     const int sm = smem_bytes_for_cap(cap, pairs);
-    const uint32_t grid = offsets ? s : 1u;
+    const uint32_t grid = units ? max_units : 1u;
     const uint32_t *sk = static_cast<const uint32_t *>(src_k);
     uint32_t *ok = static_cast<uint32_t *>(out_k);
 #define BSORT_L9(T_, E_, P_)                                                                 \
-    k_bucket_sort<T_, E_, P_><<<grid, T_, sm, st>>>(sk, src_v, offsets, m, s, n, n_pad,      \
-                                                    is_f32, val_bytes, ok, out_v, err)
+    k_bucket_sort<T_, E_, P_><<<grid, T_, sm, st>>>(sk, src_v, units, n, n_pad, is_f32,      \
+                                                    val_bytes, ok, out_v, err)
     if (!pairs) {
         switch (cap) {
         case 2048: BSORT_L9(128, 16, false); break;
