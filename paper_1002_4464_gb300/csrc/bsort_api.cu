@@ -16,6 +16,7 @@ using namespace bsort;
 
 constexpr uint64_t kAlign = 256;
 constexpr uint64_t kMaxN = (1ull << 32) - (1ull << 16);
+constexpr uint64_t kMaxSamples = 8192;  // s per sublist (Step 6 keeps 12*s bytes in SMEM)
 constexpr int kMaxTimed = 40;   // launches recorded per call
 constexpr int kRing = 64;       // calls kept for bsort_kernel_times
 
@@ -26,8 +27,8 @@ struct Plan {
     bsort_plan_info info;
     bool pairs;
     int vb;          // value bytes (0 keys only)
-    int tile_cap;    // CTA shape of Step 2 (== t)
-    int unit_cap;    // CTA shape of Step 9
+    int tile_chunk;  // items per CTA in Step 2 (t = tile_ctas * tile_chunk)
+    int unit_chunk;  // items per CTA in Step 9 (capacity = unit_ctas * unit_chunk)
     uint32_t n_rec;      // m*s sample records
     uint32_t n_rec_pad;  // rounded up to kRecordChunk
     uint32_t scan_chunks;
@@ -85,18 +86,72 @@ uint64_t bound_for(uint64_t n_pad, uint64_t m, uint64_t s)
     return n_pad / s + (m - 1) * (w - 1);
 }
 
-int smallest_cap(uint64_t items, bool pairs)
+// Sort-unit shapes (items per CTA) and cluster sizes the kernels provide.
+const int kChunks[] = {2048, 4096, 8192, 16384, 32768};
+const int kClusters[] = {1, 2, 4, 8};
+
+int max_chunk(bool pairs) { return pairs ? kMaxCapPairs : kMaxCapKeys; }
+
+// Smallest unit (chunk, ctas) holding `items`: one CTA with the smallest
+// chunk that fits, else a cluster of the largest chunk.  Returns false if
+// even the largest cluster is too small.
+bool unit_for(uint64_t items, bool pairs, int *chunk, int *ctas)
 {
-    const int caps_k[] = {2048, 4096, 8192, 16384, 32768};
-    const int caps_p[] = {2048, 4096, 8192, 16384};
-    if (pairs) {
-        for (int c : caps_p)
-            if ((uint64_t)c >= items) return c;
-    } else {
-        for (int c : caps_k)
-            if ((uint64_t)c >= items) return c;
+    const int cm = max_chunk(pairs);
+    for (int c : kChunks) {
+        if (c > cm) break;
+        if ((uint64_t)c >= items) {
+            *chunk = c;
+            *ctas = 1;
+            return true;
+        }
     }
-    return 0;
+    for (int k : kClusters) {
+        if ((uint64_t)k * cm >= items) {
+            *chunk = cm;
+            *ctas = k;
+            return true;
+        }
+    }
+    return false;
+}
+
+// Sublist size t -> (chunk, ctas): t <= max chunk is one CTA, larger t a
+// cluster of max-chunk CTAs.
+bool tile_shape(uint64_t t, bool pairs, int *chunk, int *ctas)
+{
+    const int cm = max_chunk(pairs);
+    for (int c : kChunks)
+        if (c <= cm && (uint64_t)c == t) {
+            *chunk = c;
+            *ctas = 1;
+            return true;
+        }
+    for (int k : kClusters)
+        if (k > 1 && (uint64_t)k * cm == t) {
+            *chunk = cm;
+            *ctas = k;
+            return true;
+        }
+    return false;
+}
+
+double log2d(double x) { return x > 1 ? __builtin_log2(x) : 0.0; }
+
+// Modelled cost (in item-merge-levels) of a plan: Steps 2 and 9 cost about
+// log2(chunk) levels per item plus ~2 levels per cluster merge round (Step 9
+// over the expected unit fill); the samples cost about 50 levels per record
+// (64-bit records sorted through L2 in several passes, then searched).
+double plan_cost(uint64_t np, uint64_t s, int tchunk, int tctas, int uchunk, int uctas)
+{
+    const double n = (double)np;
+    const double avg = n / (double)s;  // average bucket
+    const double q = (double)uchunk * uctas;
+    const double fill = q >= 2 * avg ? 0.8 : avg / q;
+    const double k1 = n * (log2d(tchunk) + 2.0 * log2d(tctas));
+    const double k9 = n / fill * (log2d(uchunk) + 2.0 * log2d(uctas));
+    const double smp = n / ((double)tchunk * tctas) * (double)s * 100.0;
+    return k1 + k9 + smp;
 }
 
 bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P)
@@ -107,15 +162,17 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
     if (vb != 0 && vb != 4 && vb != 8) return fail(h, BSORT_EINVAL, "val_bytes must be 0, 4 or 8");
     if (n >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "n = %llu exceeds 2^32 - 2^16", (unsigned long long)n);
     const bool pairs = vb != 0;
-    const int capmax = pairs ? kMaxCapPairs : kMaxCapKeys;
+    const int cm = max_chunk(pairs);
     P->pairs = pairs;
     P->vb = (int)vb;
     bsort_plan_info &I = P->info;
     I.n = n;
     const uint64_t forced_t = h ? h->force_t : 0;
     const uint64_t forced_s = h ? h->force_s : 0;
+    int uchunk = 0, uctas = 0;
 
-    if (n <= (uint64_t)capmax && (forced_t == 0 || n <= forced_t)) {
+    if (forced_t == 0 && forced_s == 0 && unit_for(n, pairs, &uchunk, &uctas) ||
+        (forced_t && n <= forced_t && unit_for(n, pairs, &uchunk, &uctas))) {
         // c7: n fits one Step-9 unit; the sort needs no sampling.
         I.single_tile = 1;
         I.n_padded = n;
@@ -125,52 +182,71 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         I.w = (uint32_t)n;
         I.bucket_bound = n;
         I.tile_ctas = 0;
-        I.unit_ctas = n ? 1 : 0;
-        P->unit_cap = smallest_cap(n, pairs);
-        I.unit_capacity = (uint64_t)P->unit_cap;
+        I.unit_ctas = n ? (uint32_t)uctas : 0;
+        P->unit_chunk = uchunk;
+        I.unit_capacity = (uint64_t)uchunk * uctas;
         I.num_kernels = n > 1 ? 1 : 0;
     } else {
-        const uint64_t t = forced_t ? forced_t : (uint64_t)capmax;
-        if (!cap_supported((int)t, pairs))
-            return fail(h, BSORT_EUNSUPPORTED, "sublist size t = %llu not supported (%s)",
-                        (unsigned long long)t, pairs ? "2048 .. 16384" : "2048 .. 32768");
-        const uint64_t m = (n + t - 1) / t;
-        const uint64_t np = m * t;
-        uint64_t s = forced_s;
-        if (s) {
-            if (s > t || t % s != 0)
-                return fail(h, BSORT_EINVAL, "s = %llu must divide t = %llu", (unsigned long long)s,
-                            (unsigned long long)t);
-            if (bound_for(np, m, s) > (uint64_t)capmax)
-                return fail(h, BSORT_EUNSUPPORTED,
-                            "bucket bound %llu exceeds the Step-9 unit capacity %d",
-                            (unsigned long long)bound_for(np, m, s), capmax);
-        } else {
-            for (uint64_t c = 1; c <= t / 16; c <<= 1) {
-                if (bound_for(np, m, c) <= (uint64_t)capmax) {
-                    s = c;
-                    break;
+        // candidates: forced t or every sublist shape; forced s or every
+        // power of two with w = t/s >= 16 and s <= 4096
+        double best = -1.0;
+        uint64_t bt = 0, bs = 0;
+        int btc = 0, btk = 0, buc = 0, buk = 0;
+        const uint64_t tlist[] = {2048, 4096, 8192, 16384, 32768, 65536, 131072, 262144};
+        for (uint64_t t : tlist) {
+            if (forced_t && t != forced_t) continue;
+            int tc, tk;
+            if (!tile_shape(t, pairs, &tc, &tk)) continue;
+            if (!forced_t && t < (uint64_t)cm) continue;  // smaller sublists only on request
+            const uint64_t m = (n + t - 1) / t;
+            const uint64_t np = m * t;
+            if (np >= kMaxN) continue;
+            for (uint64_t sv = 1; sv <= t; sv <<= 1) {
+                if (forced_s ? sv != forced_s : (sv > kMaxSamples || t / sv < 16)) continue;
+                const uint64_t bound = bound_for(np, m, sv);
+                int uc, uk;
+                if (!unit_for(bound, pairs, &uc, &uk)) continue;
+                const double c = plan_cost(np, sv, tc, tk, uc, uk);
+                if (best < 0 || c < best) {
+                    best = c;
+                    bt = t; bs = sv; btc = tc; btk = tk; buc = uc; buk = uk;
                 }
             }
-            if (!s)
-                return fail(h, BSORT_EUNSUPPORTED,
-                            "no sample count gives buckets within one Step-9 unit for n = %llu",
-                            (unsigned long long)n);
+            if (forced_s && !bs) {
+                if (forced_s > t || t % forced_s != 0)
+                    return fail(h, BSORT_EINVAL, "s = %llu must divide t = %llu",
+                                (unsigned long long)forced_s, (unsigned long long)t);
+            }
         }
-        if (s > 4096) return fail(h, BSORT_EUNSUPPORTED, "s = %llu > 4096", (unsigned long long)s);
+        if (forced_t && !bt && !forced_s) {
+            int tc, tk;
+            if (!tile_shape(forced_t, pairs, &tc, &tk))
+                return fail(h, BSORT_EUNSUPPORTED, "sublist size t = %llu not supported",
+                            (unsigned long long)forced_t);
+        }
+        if (!bt) {
+            if (forced_t && forced_s) {
+                const uint64_t m = (n + forced_t - 1) / forced_t;
+                return fail(h, BSORT_EUNSUPPORTED,
+                            "bucket bound %llu exceeds the largest Step-9 unit (%d items)",
+                            (unsigned long long)bound_for(m * forced_t, m, forced_s), 8 * cm);
+            }
+            return fail(h, BSORT_EUNSUPPORTED, "no plan keeps every bucket within a Step-9 unit");
+        }
+        const uint64_t m = (n + bt - 1) / bt;
         I.single_tile = 0;
-        I.n_padded = np;
-        I.t = (uint32_t)t;
-        I.s = (uint32_t)s;
+        I.n_padded = m * bt;
+        I.t = (uint32_t)bt;
+        I.s = (uint32_t)bs;
         I.m = (uint32_t)m;
-        I.w = (uint32_t)(t / s);
-        I.bucket_bound = bound_for(np, m, s);
-        I.tile_ctas = 1;
-        I.unit_ctas = 1;
-        P->tile_cap = (int)t;
-        P->unit_cap = smallest_cap(I.bucket_bound, pairs);
-        I.unit_capacity = (uint64_t)P->unit_cap;
-        P->n_rec = (uint32_t)(m * s);
+        I.w = (uint32_t)(bt / bs);
+        I.bucket_bound = bound_for(I.n_padded, m, bs);
+        I.tile_ctas = (uint32_t)btk;
+        I.unit_ctas = (uint32_t)buk;
+        P->tile_chunk = btc;
+        P->unit_chunk = buc;
+        I.unit_capacity = (uint64_t)buc * buk;
+        P->n_rec = (uint32_t)(m * bs);
         P->n_rec_pad = (uint32_t)((P->n_rec + kRecordChunk - 1) / kRecordChunk * kRecordChunk);
         P->scan_chunks = (P->n_rec + kScanChunk - 1) / kScanChunk;
         uint32_t merges = 0;
@@ -325,8 +401,10 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
             }
             return BSORT_OK;
         }
-        SEQ(launch_bucket_sort(P.unit_cap, P.pairs, kin, vin, nullptr, 1, n, n, is_f32, (int)vb,
-                               kout, vout, err, st),
+        SEQ(P.pairs ? launch_bucket_sort_pairs(P.unit_chunk, (int)I.unit_ctas, kin, vin, nullptr,
+                                               1, n, n, is_f32, (int)vb, kout, vout, err, st)
+                    : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, kin, nullptr, 1, n,
+                                              n, is_f32, kout, err, st),
             "step9_single_unit");
         return BSORT_OK;
     }
@@ -350,8 +428,10 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan ticket)");
 
     // Steps 1-3
-    SEQ(launch_sublist_sort(P.tile_cap, P.pairs, kin, vin, n, I.m, is_f32, (int)vb, I.s, tiles_k,
-                            tiles_v, samples, st),
+    SEQ(P.pairs ? launch_sublist_sort_pairs(P.tile_chunk, (int)I.tile_ctas, kin, vin, n, I.m,
+                                            is_f32, (int)vb, I.s, tiles_k, tiles_v, samples, st)
+                : launch_sublist_sort_keys(P.tile_chunk, (int)I.tile_ctas, kin, n, I.m, is_f32,
+                                           I.s, tiles_k, samples, st),
         "step1_3_sublist_sort");
     // Steps 4-5
     const bool one_chunk = P.n_rec_pad == (uint32_t)kRecordChunk;
@@ -382,8 +462,11 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     SEQ(launch_pack_units(offsets, I.m, I.s, (uint32_t)I.n_padded, (uint32_t)I.unit_capacity,
                           units, err, st),
         "step9_pack_units");
-    SEQ(launch_bucket_sort(P.unit_cap, P.pairs, reloc_k, reloc_v, units, I.s, n, I.n_padded,
-                           is_f32, (int)vb, kout, vout, err, st),
+    SEQ(P.pairs ? launch_bucket_sort_pairs(P.unit_chunk, (int)I.unit_ctas, reloc_k, reloc_v,
+                                           units, I.s, n, I.n_padded, is_f32, (int)vb, kout,
+                                           vout, err, st)
+                : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, reloc_k, units, I.s, n,
+                                          I.n_padded, is_f32, kout, err, st),
         "step9_bucket_sort");
     return BSORT_OK;
 }

@@ -17,6 +17,7 @@
 #include <type_traits>
 #include <utility>
 
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 namespace bsort {
@@ -287,6 +288,25 @@ __device__ __forceinline__ void store_run(K *sm, int base, int RL, int r, bool d
     }
 }
 
+// Number of A items among the first d outputs of the merge of A = sm[0..la)
+// ascending with B stored descending at sm[la .. la+lb) (B[j] at
+// la + lb - 1 - j): the unequal-length form of corank_bitonic.
+template <typename K>
+__device__ __forceinline__ int corank_bitonic_gen(const K *sm, int la, int lb, int d)
+{
+    const int end = la + lb;
+    int lo = d > lb ? d - lb : 0;
+    int hi = d < la ? d : la;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const K am = sm[pidx<K>(mid)];
+        const K bm = sm[pidx<K>(end - d + mid)];  // B[d-1-mid]
+        if (am <= bm) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
 // Position of register k of thread (warp, lane) in the CTA's tile under the
 // "warp-blocked" layout: warp w owns the contiguous chunk [w*32E, (w+1)*32E)
 // and lane l its items l, l+32, l+64, ... of that chunk, so that global
@@ -355,6 +375,117 @@ __device__ __forceinline__ void cta_merge_runs(K *sm, int R)
         const bool desc = ((a0 / (2 * L)) & 1) != 0;
         store_run<K, E>(sm, a0, 2 * L, d, desc, v);
         __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- cluster merges
+// C CTAs of a thread-block cluster each hold a sorted chunk of `chunk` items
+// (ascending, padded layout).  log2(C) rounds of pairwise merges through
+// distributed shared memory leave CTA r holding ranks [r*chunk, (r+1)*chunk)
+// of the cluster's items.  In the round with groups of G CTAs, the first G/2
+// CTAs of a group hold run A and the rest run B; CTA r finds the co-ranks of
+// its output range by a 32-ary search over the remote chunks, gathers the
+// A and B pieces into registers, waits for the whole cluster, stores them as
+// a bitonic sequence in its own SMEM, and merges locally.
+template <typename K>
+__device__ __forceinline__ K cl_load(cooperative_groups::cluster_group &cl, K *sm, int first_cta,
+                                     int chunk_shift, int x)
+{
+    const int cta = first_cta + (x >> chunk_shift);
+    const int off = x & ((1 << chunk_shift) - 1);
+    const K *p = cl.map_shared_rank(sm, cta);
+    return p[pidx<K>(off)];
+}
+
+template <typename K>
+__device__ __forceinline__ int corank_cluster(cooperative_groups::cluster_group &cl, K *sm,
+                                              int a_cta, int b_cta, int chunk_shift, int la,
+                                              int lb, int d, int lane)
+{
+    int lo = d > lb ? d - lb : 0;
+    int hi = d < la ? d : la;
+    while (hi - lo > 32) {
+        const int span = hi - lo;
+        const int c = lo + (int)(((long long)span * (lane + 1)) / 33);
+        const bool pred = cl_load<K>(cl, sm, a_cta, chunk_shift, c) >
+                          cl_load<K>(cl, sm, b_cta, chunk_shift, d - 1 - c);
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
+        if (ball == 0) {
+            lo = lo + (int)(((long long)span * 32) / 33) + 1;
+        } else {
+            const int f = __ffs(ball) - 1;
+            const int cf = lo + (int)(((long long)span * (f + 1)) / 33);
+            const int cp = f ? lo + (int)(((long long)span * f) / 33) + 1 : lo;
+            lo = cp;
+            hi = cf;
+        }
+    }
+    const int c = lo + lane;
+    bool pred = true;
+    if (c < hi)
+        pred = cl_load<K>(cl, sm, a_cta, chunk_shift, c) >
+               cl_load<K>(cl, sm, b_cta, chunk_shift, d - 1 - c);
+    const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
+    return ball ? lo + __ffs(ball) - 1 : hi;
+}
+
+// len: number of real items of the whole cluster (positions >= len hold the
+// maximal key); groups made only of padding skip their work.
+template <typename K, int T, int E, int C>
+__device__ __forceinline__ void cluster_merge(K *sm, int len)
+{
+    if constexpr (C > 1) {
+        constexpr int CH = T * E;
+        constexpr int SH = __builtin_ctz(CH);
+        cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+        const int r = (int)cl.block_rank();
+        const int tid = threadIdx.x;
+        const int lane = tid & 31, warp = tid >> 5;
+        __shared__ int s_split[2];
+#pragma unroll 1
+        for (int G = 2; G <= C; G <<= 1) {
+            cl.sync();  // every chunk of the previous round is final
+            const int g0 = r & ~(G - 1);
+            const int h = G / 2;
+            const bool work = g0 * CH < len;
+            K v[E];
+            int na = 0;
+            if (work) {
+                const int d0 = (r - g0) * CH;
+                if (warp < 2) {
+                    const int i = corank_cluster<K>(cl, sm, g0, g0 + h, SH, h * CH, h * CH,
+                                                    d0 + warp * CH, lane);
+                    if (lane == 0) s_split[warp] = i;
+                }
+                __syncthreads();
+                const int i0 = s_split[0], i1 = s_split[1];
+                const int j0 = d0 - i0;
+                na = i1 - i0;
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const int z = k * T + tid;
+                    v[k] = z < na ? cl_load<K>(cl, sm, g0, SH, i0 + z)
+                                  : cl_load<K>(cl, sm, g0 + h, SH, j0 + (z - na));
+                }
+            }
+            cl.sync();  // all remote reads of this round are done
+            if (work) {
+#pragma unroll
+                for (int k = 0; k < E; ++k) {
+                    const int z = k * T + tid;
+                    const int pos = z < na ? z : CH - 1 - (z - na);
+                    sm[pidx<K>(pos)] = v[k];
+                }
+                __syncthreads();
+                const int d = tid * E;
+                const int i = corank_bitonic_gen<K>(sm, na, CH - na, d);
+                merge_bitonic_pair<K, E>(sm, i, CH - 1 - (d - i), v);
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < E; ++k) sm[pidx<K>(d + k)] = v[k];
+                __syncthreads();
+            }
+        }
     }
 }
 

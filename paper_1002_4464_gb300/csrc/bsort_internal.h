@@ -16,19 +16,37 @@ constexpr int kRecordChunk = 16384;  // Step-4 chunk sorted by one CTA
 constexpr int kMergeTile = 4096;     // outputs per CTA in a Step-4 merge pass
 constexpr int kScanChunk = 4096;     // items per CTA of the Step-7 scan
 
-bool cap_supported(int cap, bool pairs);
 int smem_bytes_for_cap(int cap, bool pairs);
 
-// Configure kernel attributes (max dynamic SMEM) once per device.
+// Configure kernel attributes (max dynamic SMEM, cluster sizes) once per
+// device.
 cudaError_t init_kernels();
+cudaError_t init_misc_kernels();
+cudaError_t init_sort_keys_kernels();
+cudaError_t init_sort_pairs_kernels();
 
-// Steps 1-3: sort every sublist of t = cap items; write sorted keys (and
-// values), and s sample records per sublist.
-cudaError_t launch_sublist_sort(int cap, bool pairs, const void *keys_in,
-                                const void *vals_in, uint64_t n, uint32_t m,
-                                int is_f32, int val_bytes, uint32_t s,
-                                uint32_t *tiles_k, void *tiles_v,
-                                uint64_t *samples, cudaStream_t st);
+// Steps 1-3: sort every sublist of t = ctas * chunk items with a cluster of
+// `ctas` CTAs of `chunk` items each; write the sorted sublists (keys, and
+// values for pairs) and s sample records per sublist.
+cudaError_t launch_sublist_sort_keys(int chunk, int ctas, const void *keys_in, uint64_t n,
+                                     uint32_t m, int is_f32, uint32_t s, uint32_t *tiles_k,
+                                     uint64_t *samples, cudaStream_t st);
+cudaError_t launch_sublist_sort_pairs(int chunk, int ctas, const void *keys_in,
+                                      const void *vals_in, uint64_t n, uint32_t m, int is_f32,
+                                      int val_bytes, uint32_t s, uint32_t *tiles_k,
+                                      void *tiles_v, uint64_t *samples, cudaStream_t st);
+
+// Step 9: sort every unit with a cluster of `ctas` CTAs of `chunk` items
+// (grid = max_units clusters, surplus clusters exit) and write the first n
+// positions of the result.  With units == nullptr the whole input [0, n)
+// is one unit read from src (raw keys, transformed on load).
+cudaError_t launch_bucket_sort_keys(int chunk, int ctas, const void *src_k, const uint32_t *units,
+                                    uint32_t max_units, uint64_t n, uint64_t n_pad, int is_f32,
+                                    void *out_k, int *err, cudaStream_t st);
+cudaError_t launch_bucket_sort_pairs(int chunk, int ctas, const void *src_k, const void *src_v,
+                                     const uint32_t *units, uint32_t max_units, uint64_t n,
+                                     uint64_t n_pad, int is_f32, int val_bytes, void *out_k,
+                                     void *out_v, int *err, cudaStream_t st);
 
 // Step 4 (chunks): sort the n_rec records of src in chunks of kRecordChunk
 // into dst (which holds n_pad = chunks * kRecordChunk records, the tail
@@ -59,6 +77,7 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
                         cudaStream_t st);
 
 constexpr int kRelocateSmemMax = 220 * 1024;
+constexpr int kRelocPart = 8192;  // sublist items per Step-8 CTA
 
 // Step 8: move every run A_ij to l_ij.
 cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v,
@@ -71,15 +90,5 @@ cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v,
 cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t s,
                               uint32_t n_pad, uint32_t Q, uint32_t *units, int *err,
                               cudaStream_t st);
-
-// Step 9: sort every unit (one CTA of `cap` items each; grid = max_units,
-// surplus CTAs exit) and write the first n positions of the result.  With
-// units == nullptr the whole input [0, n) is one unit read from src (raw
-// keys, transformed on load): the single-unit path for n <= cap.
-cudaError_t launch_bucket_sort(int cap, bool pairs, const void *src_k,
-                               const void *src_v, const uint32_t *units,
-                               uint32_t max_units, uint64_t n, uint64_t n_pad,
-                               int is_f32, int val_bytes, void *out_k, void *out_v,
-                               int *err, cudaStream_t st);
 
 }  // namespace bsort

@@ -1,14 +1,15 @@
 // bsort_kernels.cu -- the kernels of GPU Bucket Sort (Dehne & Zaboli,
 // Section 4, Algorithm 1) for sm_103a, and their launch wrappers.
 //
-//   Steps 1-3  k_sublist_sort      sort each sublist in SMEM, emit samples
+//   Steps 1-3  k_sublist_sort      (bsort_sort.cuh) sort each sublist, emit samples
 //   Step 4     k_records_sort      sort the s*m samples (chunks of 16K) ...
 //              k_merge_pass        ... then merge-path passes through L2
 //   Step 5     k_select_splitters  every m-th sorted sample
 //   Step 6     k_sample_index      locate the s splitters in every sublist
 //   Step 7     k_scan              bucket-major exclusive scan (look-back)
 //   Step 8     k_relocate          move each run A_ij to l_ij
-//   Step 9     k_bucket_sort       sort each bucket B_j in SMEM
+//   Step 9     k_pack_units        pack consecutive buckets into Step-9 units
+//              k_bucket_sort       (bsort_sort.cuh) sort each unit
 //
 // Items are compared in composite order (key, position): keys-only sorts
 // compare keys (equal keys are indistinguishable), pair sorts compare the
@@ -18,70 +19,6 @@
 #include "bsort_internal.h"
 
 namespace bsort {
-
-// ============================================================ Steps 1-3
-// One CTA per sublist i of t = T*E items.  Loads are striped (coalesced);
-// a keys-only sort needs no particular assignment of keys to threads, and a
-// pair sort carries the local index inside the composite key.
-template <int T, int E, bool PAIRS>
-__global__ void __launch_bounds__(T, 1)
-k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ vals_in,
-               uint64_t n, int is_f32, int val_bytes, uint32_t s,
-               uint32_t *__restrict__ tiles_k, void *__restrict__ tiles_v,
-               uint64_t *__restrict__ samples)
-{
-    using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
-    constexpr int CAP = T * E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    K *sm = reinterpret_cast<K *>(smem_raw);
-    const int tid = threadIdx.x;
-    const uint64_t base = (uint64_t)blockIdx.x * CAP;
-    const uint64_t avail = n > base ? n - base : 0;
-
-    const int lane = tid & 31, warp = tid >> 5;
-    K v[E];
-#pragma unroll
-    for (int k = 0; k < E; ++k) {
-        const int x = wb_pos<E>(warp, lane, k);
-        uint32_t key = 0xFFFFFFFFu;  // pad sentinel (position >= n)
-        if ((uint64_t)x < avail) {
-            key = keys_in[base + x];
-            if (is_f32) key = f32_encode(key);
-        }
-        if constexpr (PAIRS) v[k] = ((uint64_t)key << 32) | (uint32_t)x;
-        else v[k] = (K)key;
-    }
-    cta_sort<K, T, E>(v, sm, avail < (uint64_t)CAP ? (int)avail : CAP);
-
-#pragma unroll 4
-    for (int k = 0; k < E; ++k) {
-        const int x = k * T + tid;
-        const K e = sm[pidx<K>(x)];
-        if constexpr (PAIRS) {
-            const uint32_t idx = (uint32_t)(e & 0xFFFFFFFFull);
-            tiles_k[base + x] = (uint32_t)((uint64_t)e >> 32);
-            if (val_bytes == 4) {
-                uint32_t val = (uint64_t)idx < avail
-                                   ? static_cast<const uint32_t *>(vals_in)[base + idx] : 0u;
-                static_cast<uint32_t *>(tiles_v)[base + x] = val;
-            } else {
-                uint64_t val = (uint64_t)idx < avail
-                                   ? static_cast<const uint64_t *>(vals_in)[base + idx] : 0ull;
-                static_cast<uint64_t *>(tiles_v)[base + x] = val;
-            }
-        } else {
-            tiles_k[base + x] = (uint32_t)e;
-        }
-    }
-    // Step 3: samples at ranks (k+1)w - 1 as (key, p = i*t + r).
-    const uint32_t w = CAP / s;
-    for (uint32_t k = tid; k < s; k += T) {
-        const uint32_t r = (k + 1) * w - 1;
-        const K e = sm[pidx<K>(r)];
-        const uint32_t key = PAIRS ? (uint32_t)((uint64_t)e >> 32) : (uint32_t)e;
-        samples[(uint64_t)blockIdx.x * s + k] = ((uint64_t)key << 32) | (uint32_t)(base + r);
-    }
-}
 
 // ============================================================ Step 4 (chunks)
 // The records of one sublist (s consecutive records) are already sorted, so
@@ -142,6 +79,38 @@ __device__ __forceinline__ uint32_t merge_path_global(const uint64_t *A, uint32_
     return lo;
 }
 
+// The same co-rank found by one warp: each round the 32 lanes test 32
+// evenly spaced candidates and the range shrinks to one gap (about 32x).
+__device__ __forceinline__ uint32_t merge_path_warp(const uint64_t *A, uint32_t la,
+                                                    const uint64_t *B, uint32_t lb, uint32_t d,
+                                                    int lane)
+{
+    uint32_t lo = d > lb ? d - lb : 0;
+    uint32_t hi = d < la ? d : la;
+    // invariant: the answer i is in [lo, hi]; pred(i) = A[i] > B[d-1-i] is
+    // monotone (false ... true) on [lo, hi), and the answer is the first true
+    while (hi - lo > 32) {
+        const uint32_t span = hi - lo;
+        const uint32_t c = lo + (uint32_t)(((uint64_t)span * (lane + 1)) / 33);  // in [lo, hi)
+        const bool pred = A[c] > B[d - 1 - c];
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
+        if (ball == 0) {
+            lo = lo + (uint32_t)(((uint64_t)span * 32) / 33) + 1;
+        } else {
+            const int f = __ffs(ball) - 1;  // first candidate where pred holds
+            const uint32_t cf = lo + (uint32_t)(((uint64_t)span * (f + 1)) / 33);
+            const uint32_t cp = f ? lo + (uint32_t)(((uint64_t)span * f) / 33) + 1 : lo;
+            lo = cp;
+            hi = cf;
+        }
+    }
+    // final: at most 32 candidates lo .. hi-1, one per lane
+    const uint32_t c = lo + lane;
+    const bool pred = c < hi ? (A[c] > B[d - 1 - c]) : true;
+    const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
+    return ball ? lo + (uint32_t)(__ffs(ball) - 1) : hi;
+}
+
 // One CTA produces kMergeTile outputs of the merge of two runs: it finds
 // the input ranges of its outputs by merge path in global memory, stages
 // them in SMEM, merges per thread, and writes back through SMEM.
@@ -161,8 +130,11 @@ k_merge_pass(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uint3
     const uint32_t lb = b0 < n_pad ? min(L, n_pad - b0) : 0;
     const uint32_t d0 = o0 - a0;
     const uint32_t d1 = min(d0 + TILE, la + lb);
-    if (tid == 0) s_split[0] = merge_path_global(src + a0, la, src + b0, lb, d0);
-    if (tid == 32) s_split[1] = merge_path_global(src + a0, la, src + b0, lb, d1);
+    if (tid < 64) {
+        const uint32_t dd = tid < 32 ? d0 : d1;
+        const uint32_t r = merge_path_warp(src + a0, la, src + b0, lb, dd, tid & 31);
+        if ((tid & 31) == 0) s_split[tid >> 5] = r;
+    }
     __syncthreads();
     const uint32_t i0 = s_split[0], i1 = s_split[1];
     const uint32_t j0 = d0 - i0, j1 = d1 - i1;
@@ -266,6 +238,7 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
     __shared__ uint32_t s_chunk;
     __shared__ uint32_t s_warp[T / 32];
     __shared__ uint32_t s_prefix;
+    __shared__ uint32_t s_last;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_chunk = atomicAdd(ticket, 1u);
@@ -297,36 +270,50 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
             if (lane >= o) wi += y;
         }
         if (lane < T / 32) s_warp[lane] = wi - wv;  // exclusive warp offsets
-        if (lane == T / 32 - 1) {
-            const uint32_t agg = wi;
-            // decoupled look-back (bounded waits)
-            uint32_t prefix = 0;
-            if (chunk == 0) {
-                atomicExch(&status[0], kFlagInc | agg);
-            } else {
-                atomicExch(&status[chunk], kFlagAgg | agg);
-                int p = (int)chunk - 1;
-                while (p >= 0) {
-                    unsigned long long st = ld_volatile(&status[p]);
-                    int spins = 0;
-                    while ((st >> 62) == 0) {
-                        if (++spins > kSpinLimit) break;
-                        __nanosleep(128);
-                        st = ld_volatile(&status[p]);
-                    }
-                    if ((st >> 62) == 0) {
-                        set_error(err, DEV_TIMEOUT);
+        if (lane == T / 32 - 1) s_last = wv;
+    }
+    __syncthreads();
+    if (warp == 0) {
+        // decoupled look-back by the whole first warp (bounded waits): lane l
+        // inspects chunk p - l; the nearest inclusive prefix ends the walk
+        const uint32_t agg = s_warp[T / 32 - 1] + s_last;
+        uint32_t prefix = 0;
+        if (chunk == 0) {
+            if (lane == 0) atomicExch(&status[0], kFlagInc | agg);
+        } else {
+            if (lane == 0) atomicExch(&status[chunk], kFlagAgg | agg);
+            int p = (int)chunk - 1;
+            int spins = 0;
+            bool timed_out = false;
+            while (p >= 0) {
+                const int q = p - lane;
+                unsigned long long st = q >= 0 ? ld_volatile(&status[q]) : (kFlagInc | 0ull);
+                // wait until every inspected chunk has published something
+                while (__any_sync(0xFFFFFFFFu, (st >> 62) == 0)) {
+                    if (++spins > kSpinLimit) {
+                        timed_out = true;
                         break;
                     }
-                    prefix += (uint32_t)(st & kValMask);
-                    if ((st & kFlagInc) == kFlagInc && (st >> 62) == 2) break;
-                    --p;
+                    __nanosleep(64);
+                    if ((st >> 62) == 0) st = ld_volatile(&status[q]);
                 }
+                if (timed_out) break;
+                const unsigned inc = __ballot_sync(0xFFFFFFFFu, (st >> 62) == 2);
+                const int stop = inc ? __ffs(inc) - 1 : 31;  // nearest inclusive lane
+                uint32_t val = (lane <= stop) ? (uint32_t)(st & kValMask) : 0u;
+#pragma unroll
+                for (int o = 16; o >= 1; o >>= 1) val += __shfl_xor_sync(0xFFFFFFFFu, val, o);
+                prefix += val;
+                if (inc) break;
+                p -= 32;
+            }
+            if (timed_out && lane == 0) set_error(err, DEV_TIMEOUT);
+            if (lane == 0) {
                 __threadfence();
                 atomicExch(&status[chunk], kFlagInc | (unsigned long long)(prefix + agg));
             }
-            s_prefix = prefix;
         }
+        if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
     uint32_t run = s_prefix + s_warp[warp] + (incl - sum);
@@ -338,43 +325,60 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 }
 
 // ============================================================ Step 8
-// One CTA per sublist: the sorted sublist (keys, and values when they fit),
-// its cumulative counts c_i. and its offsets l_.i are staged in shared memory
-// with coalesced loads; then each warp copies whole runs A_ij to l_ij
-// (lanes in parallel, coalesced stores).
+// One CTA per part of kRelocPart items of a sublist: the part's sorted keys
+// (and values), the sublist's cumulative counts c_i. and the offsets l_ij of
+// the runs that overlap the part are staged in shared memory with coalesced
+// loads; then each warp copies the overlapping pieces of runs A_ij to
+// l_ij + (position in the run), lanes in parallel (coalesced stores).
 template <int T>
-__global__ void __launch_bounds__(T, 1)
+__global__ void __launch_bounds__(T)
 k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_v,
            const uint32_t *__restrict__ cum, const uint32_t *__restrict__ offsets,
-           uint32_t t, uint32_t s, uint32_t m, uint64_t n_pad, int val_bytes, int stage_vals,
+           uint32_t t, uint32_t s, uint32_t m, uint32_t part, uint64_t n_pad, int val_bytes,
            uint32_t *__restrict__ reloc_k, void *__restrict__ reloc_v, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t *s_k = reinterpret_cast<uint32_t *>(smem_raw);
-    uint32_t *s_cum = s_k + t;
-    uint32_t *s_off = s_cum + s;
-    unsigned char *s_v = reinterpret_cast<unsigned char *>(s_off + s);
-    const uint32_t i = blockIdx.x;
+    uint32_t *s_k = reinterpret_cast<uint32_t *>(smem_raw);           // part
+    unsigned char *s_v = reinterpret_cast<unsigned char *>(s_k + part);  // part * val_bytes
+    uint32_t *s_cum = reinterpret_cast<uint32_t *>(s_v + (size_t)part * val_bytes);  // s
+    uint32_t *s_off = s_cum + s;                                      // s
+    __shared__ uint32_t s_j[2];
+    const uint32_t parts = t / part;
+    const uint32_t i = blockIdx.x / parts;
+    const uint32_t h0 = (blockIdx.x % parts) * part, h1 = h0 + part;
     const uint64_t base = (uint64_t)i * t;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     {
-        const uint4 *src4 = reinterpret_cast<const uint4 *>(tiles_k + base);
+        const uint4 *src4 = reinterpret_cast<const uint4 *>(tiles_k + base + h0);
         uint4 *dst4 = reinterpret_cast<uint4 *>(s_k);
-        for (uint32_t x = tid; x < t / 4; x += T) dst4[x] = src4[x];
-        if (stage_vals) {
+        for (uint32_t x = tid; x < part / 4; x += T) dst4[x] = src4[x];
+        if (val_bytes) {
             const uint4 *v4 = reinterpret_cast<const uint4 *>(
-                static_cast<const unsigned char *>(tiles_v) + base * val_bytes);
+                static_cast<const unsigned char *>(tiles_v) + (base + h0) * val_bytes);
             uint4 *d4 = reinterpret_cast<uint4 *>(s_v);
-            for (uint32_t x = tid; x < t * val_bytes / 16; x += T) d4[x] = v4[x];
+            for (uint32_t x = tid; x < part * val_bytes / 16; x += T) d4[x] = v4[x];
         }
-        for (uint32_t j = tid; j < s; j += T) {
-            s_cum[j] = cum[(uint64_t)i * s + j];
-            s_off[j] = offsets[(uint64_t)j * m + i];
-        }
+        for (uint32_t j = tid; j < s; j += T) s_cum[j] = cum[(uint64_t)i * s + j];
     }
     __syncthreads();
-    for (uint32_t j = warp; j < s; j += T / 32) {
+    // runs overlapping [h0, h1): j from the first with c_ij > h0 to the first
+    // with c_ij >= h1
+    if (tid < 2) {
+        const uint32_t key = tid == 0 ? h0 : h1 - 1;
+        uint32_t lo = 0, hi = s;  // first j with s_cum[j] > key
+        while (lo < hi) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (s_cum[mid] > key) hi = mid;
+            else lo = mid + 1;
+        }
+        s_j[tid] = lo;
+    }
+    __syncthreads();
+    const uint32_t j_lo = s_j[0], j_hi = min(s_j[1], s - 1);
+    for (uint32_t j = j_lo + tid; j <= j_hi; j += T) s_off[j] = offsets[(uint64_t)j * m + i];
+    __syncthreads();
+    for (uint32_t j = j_lo + warp; j <= j_hi; j += T / 32) {
         const uint32_t start = j ? s_cum[j - 1] : 0u;
         const uint32_t end = s_cum[j];
         const uint64_t dst = s_off[j];
@@ -382,17 +386,14 @@ k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_
             if (lane == 0) set_error(err, DEV_INTERNAL);
             continue;
         }
-        for (uint32_t x = start + lane; x < end; x += 32) {
-            reloc_k[dst + (x - start)] = s_k[x];
-            if (val_bytes == 4) {
-                const uint32_t val = stage_vals ? reinterpret_cast<const uint32_t *>(s_v)[x]
-                                                : static_cast<const uint32_t *>(tiles_v)[base + x];
-                static_cast<uint32_t *>(reloc_v)[dst + (x - start)] = val;
-            } else if (val_bytes == 8) {
-                const uint64_t val = stage_vals ? reinterpret_cast<const uint64_t *>(s_v)[x]
-                                                : static_cast<const uint64_t *>(tiles_v)[base + x];
-                static_cast<uint64_t *>(reloc_v)[dst + (x - start)] = val;
-            }
+        const uint32_t x0 = max(start, h0), x1 = min(end, h1);
+        for (uint32_t x = x0 + lane; x < x1; x += 32) {
+            const uint64_t o = dst + (x - start);
+            reloc_k[o] = s_k[x - h0];
+            if (val_bytes == 4)
+                static_cast<uint32_t *>(reloc_v)[o] = reinterpret_cast<const uint32_t *>(s_v)[x - h0];
+            else if (val_bytes == 8)
+                static_cast<uint64_t *>(reloc_v)[o] = reinterpret_cast<const uint64_t *>(s_v)[x - h0];
         }
     }
 }
@@ -504,75 +505,7 @@ k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t s, uint3
     if (tid == 0) units[0] = s_total;
 }
 
-// ============================================================ Step 9
-template <int T, int E, bool PAIRS>
-__global__ void __launch_bounds__(T, 1)
-k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
-              const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
-              int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v, int *err)
-{
-    using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
-    constexpr int CAP = T * E;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    K *sm = reinterpret_cast<K *>(smem_raw);
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const uint32_t u = blockIdx.x;
-    const bool direct = units == nullptr;
-    uint64_t L = 0, R = n;
-    if (!direct) {
-        if (u >= units[0]) return;  // fewer units than the grid
-        L = units[1 + 2 * u];
-        R = units[2 + 2 * u];
-    }
-    const uint64_t len = R - L;
-    if (R < L || R > n_pad || len > (uint64_t)CAP) {  // the plan guarantees a unit fits
-        if (tid == 0) set_error(err, DEV_INTERNAL);
-        return;
-    }
-    if (len == 0) return;
-    K v[E];
-#pragma unroll
-    for (int k = 0; k < E; ++k) {
-        const int x = wb_pos<E>(warp, lane, k);
-        uint32_t key = 0xFFFFFFFFu;
-        if ((uint64_t)x < len) {
-            key = src_k[L + x];
-            if (direct && is_f32) key = f32_encode(key);
-        }
-        if constexpr (PAIRS) v[k] = ((uint64_t)key << 32) | (uint32_t)x;
-        else v[k] = (K)key;
-    }
-    cta_sort<K, T, E>(v, sm, (int)len);
-    const uint64_t lim = min((unsigned long long)len, (unsigned long long)(n > L ? n - L : 0));
-#pragma unroll 4
-    for (int k = 0; k < E; ++k) {
-        const int x = k * T + tid;
-        if ((uint64_t)x < lim) {
-            const K e = sm[pidx<K>(x)];
-            uint32_t key = PAIRS ? (uint32_t)((uint64_t)e >> 32) : (uint32_t)e;
-            if (is_f32) key = f32_decode(key);
-            out_k[L + x] = key;
-            if constexpr (PAIRS) {
-                const uint32_t idx = (uint32_t)((uint64_t)e & 0xFFFFFFFFull);
-                if (val_bytes == 4)
-                    static_cast<uint32_t *>(out_v)[L + x] =
-                        static_cast<const uint32_t *>(src_v)[L + idx];
-                else
-                    static_cast<uint64_t *>(out_v)[L + x] =
-                        static_cast<const uint64_t *>(src_v)[L + idx];
-            }
-        }
-    }
-}
-
 // ============================================================ launch wrappers
-bool cap_supported(int cap, bool pairs)
-{
-    if (pairs) return cap == 2048 || cap == 4096 || cap == 8192 || cap == 16384;
-    return cap == 2048 || cap == 4096 || cap == 8192 || cap == 16384 || cap == 32768;
-}
-
 int smem_bytes_for_cap(int cap, bool pairs)
 {
     return pairs ? padded_elems<uint64_t>(cap) * 8 : padded_elems<uint32_t>(cap) * 4;
@@ -590,63 +523,13 @@ static cudaError_t set_smem(KernelT kern, int bytes)
         if (e_ != cudaSuccess) return e_; \
     } while (0)
 
-cudaError_t init_kernels()
+cudaError_t init_misc_kernels()
 {
-    BSORT_TRY(set_smem(k_sublist_sort<128, 16, false>, smem_bytes_for_cap(2048, false)));
-    BSORT_TRY(set_smem(k_sublist_sort<128, 16, true>, smem_bytes_for_cap(2048, true)));
-    BSORT_TRY(set_smem(k_bucket_sort<128, 16, false>, smem_bytes_for_cap(2048, false)));
-    BSORT_TRY(set_smem(k_bucket_sort<128, 16, true>, smem_bytes_for_cap(2048, true)));
-    BSORT_TRY(set_smem(k_sublist_sort<256, 16, false>, smem_bytes_for_cap(4096, false)));
-    BSORT_TRY(set_smem(k_sublist_sort<512, 16, false>, smem_bytes_for_cap(8192, false)));
-    BSORT_TRY(set_smem(k_sublist_sort<1024, 16, false>, smem_bytes_for_cap(16384, false)));
-    BSORT_TRY(set_smem(k_sublist_sort<1024, 32, false>, smem_bytes_for_cap(32768, false)));
-    BSORT_TRY(set_smem(k_sublist_sort<256, 16, true>, smem_bytes_for_cap(4096, true)));
-    BSORT_TRY(set_smem(k_sublist_sort<512, 16, true>, smem_bytes_for_cap(8192, true)));
-    BSORT_TRY(set_smem(k_sublist_sort<1024, 16, true>, smem_bytes_for_cap(16384, true)));
-    BSORT_TRY(set_smem(k_bucket_sort<256, 16, false>, smem_bytes_for_cap(4096, false)));
-    BSORT_TRY(set_smem(k_bucket_sort<512, 16, false>, smem_bytes_for_cap(8192, false)));
-    BSORT_TRY(set_smem(k_bucket_sort<1024, 16, false>, smem_bytes_for_cap(16384, false)));
-    BSORT_TRY(set_smem(k_bucket_sort<1024, 32, false>, smem_bytes_for_cap(32768, false)));
-    BSORT_TRY(set_smem(k_bucket_sort<256, 16, true>, smem_bytes_for_cap(4096, true)));
-    BSORT_TRY(set_smem(k_bucket_sort<512, 16, true>, smem_bytes_for_cap(8192, true)));
-    BSORT_TRY(set_smem(k_bucket_sort<1024, 16, true>, smem_bytes_for_cap(16384, true)));
     BSORT_TRY(set_smem(k_records_sort<1024, 16>, smem_bytes_for_cap(kRecordChunk, true)));
-    BSORT_TRY(set_smem(k_sample_index<256>, 64 * 1024));
-    BSORT_TRY(set_smem(k_relocate<1024>, kRelocateSmemMax));
-    BSORT_TRY(set_smem(k_pack_units<1024>, 16 * 4097));
+    BSORT_TRY(set_smem(k_sample_index<256>, 96 * 1024));
+    BSORT_TRY(set_smem(k_relocate<256>, kRelocateSmemMax));
+    BSORT_TRY(set_smem(k_pack_units<1024>, 16 * 8193));
     return cudaSuccess;
-}
-
-cudaError_t launch_sublist_sort(int cap, bool pairs, const void *keys_in, const void *vals_in,
-                                uint64_t n, uint32_t m, int is_f32, int val_bytes, uint32_t s,
-                                uint32_t *tiles_k, void *tiles_v, uint64_t *samples,
-                                cudaStream_t st)
-{
-    const int sm = smem_bytes_for_cap(cap, pairs);
-    const uint32_t *kin = static_cast<const uint32_t *>(keys_in);
-#define BSORT_L1(T_, E_, P_)                                                                \
-    k_sublist_sort<T_, E_, P_><<<m, T_, sm, st>>>(kin, vals_in, n, is_f32, val_bytes, s,   \
-                                                   tiles_k, tiles_v, samples)
-    if (!pairs) {
-        switch (cap) {
-        case 2048: BSORT_L1(128, 16, false); break;
-        case 4096: BSORT_L1(256, 16, false); break;
-        case 8192: BSORT_L1(512, 16, false); break;
-        case 16384: BSORT_L1(1024, 16, false); break;
-        case 32768: BSORT_L1(1024, 32, false); break;
-        default: return cudaErrorInvalidValue;
-        }
-    } else {
-        switch (cap) {
-        case 2048: BSORT_L1(128, 16, true); break;
-        case 4096: BSORT_L1(256, 16, true); break;
-        case 8192: BSORT_L1(512, 16, true); break;
-        case 16384: BSORT_L1(1024, 16, true); break;
-        default: return cudaErrorInvalidValue;
-        }
-    }
-#undef BSORT_L1
-    return cudaGetLastError();
 }
 
 cudaError_t launch_records_chunk_sort(const uint64_t *src, uint64_t *dst, uint32_t n_rec,
@@ -678,7 +561,7 @@ cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples
                                 uint32_t *counts, uint32_t *cum, cudaStream_t st)
 {
     const int sm = (int)(s * 12);
-    if (sm > 64 * 1024) return cudaErrorInvalidValue;
+    if (sm > 96 * 1024) return cudaErrorInvalidValue;
     k_sample_index<256><<<m, 256, sm, st>>>(tiles_k, samples, spl, t, s, m, counts, cum);
     return cudaGetLastError();
 }
@@ -691,26 +574,17 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
     return cudaGetLastError();
 }
 
-int relocate_smem_bytes(uint32_t t, uint32_t s, int val_bytes, int *stage_vals)
-{
-    int bytes = (int)(t * 4 + 2 * s * 4);
-    bytes = (bytes + 15) / 16 * 16;
-    const int with_vals = bytes + (int)(t * val_bytes);
-    *stage_vals = (val_bytes > 0 && with_vals <= kRelocateSmemMax) ? 1 : 0;
-    return *stage_vals ? with_vals : bytes;
-}
-
 cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const uint32_t *cum,
                             const uint32_t *offsets, uint32_t t, uint32_t s, uint32_t m,
                             int val_bytes, uint32_t *reloc_k, void *reloc_v, int *err,
                             cudaStream_t st)
 {
-    int stage_vals = 0;
-    const int sm = relocate_smem_bytes(t, s, val_bytes, &stage_vals);
+    const uint32_t part = t < (uint32_t)kRelocPart ? t : (uint32_t)kRelocPart;
+    const int sm = (int)(part * (4 + val_bytes) + 2 * s * 4);
     if (sm > kRelocateSmemMax) return cudaErrorInvalidValue;
-    k_relocate<1024><<<m, 1024, sm, st>>>(tiles_k, tiles_v, cum, offsets, t, s, m,
-                                          (uint64_t)m * t, val_bytes, stage_vals, reloc_k,
-                                          reloc_v, err);
+    k_relocate<256><<<m * (t / part), 256, sm, st>>>(tiles_k, tiles_v, cum, offsets, t, s, m,
+                                                      part, (uint64_t)m * t, val_bytes, reloc_k,
+                                                      reloc_v, err);
     return cudaGetLastError();
 }
 
@@ -722,38 +596,12 @@ cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t s, u
     return cudaGetLastError();
 }
 
-cudaError_t launch_bucket_sort(int cap, bool pairs, const void *src_k, const void *src_v,
-                               const uint32_t *units, uint32_t max_units, uint64_t n,
-                               uint64_t n_pad, int is_f32, int val_bytes, void *out_k,
-                               void *out_v, int *err, cudaStream_t st)
+cudaError_t init_kernels()
 {
-    const int sm = smem_bytes_for_cap(cap, pairs);
-    const uint32_t grid = units ? max_units : 1u;
-    const uint32_t *sk = static_cast<const uint32_t *>(src_k);
-    uint32_t *ok = static_cast<uint32_t *>(out_k);
-#define BSORT_L9(T_, E_, P_)                                                                 \
-    k_bucket_sort<T_, E_, P_><<<grid, T_, sm, st>>>(sk, src_v, units, n, n_pad, is_f32,      \
-                                                    val_bytes, ok, out_v, err)
-    if (!pairs) {
-        switch (cap) {
-        case 2048: BSORT_L9(128, 16, false); break;
-        case 4096: BSORT_L9(256, 16, false); break;
-        case 8192: BSORT_L9(512, 16, false); break;
-        case 16384: BSORT_L9(1024, 16, false); break;
-        case 32768: BSORT_L9(1024, 32, false); break;
-        default: return cudaErrorInvalidValue;
-        }
-    } else {
-        switch (cap) {
-        case 2048: BSORT_L9(128, 16, true); break;
-        case 4096: BSORT_L9(256, 16, true); break;
-        case 8192: BSORT_L9(512, 16, true); break;
-        case 16384: BSORT_L9(1024, 16, true); break;
-        default: return cudaErrorInvalidValue;
-        }
-    }
-#undef BSORT_L9
-    return cudaGetLastError();
+    cudaError_t e = init_misc_kernels();
+    if (e == cudaSuccess) e = init_sort_keys_kernels();
+    if (e == cudaSuccess) e = init_sort_pairs_kernels();
+    return e;
 }
 
 }  // namespace bsort

@@ -1,0 +1,233 @@
+// bsort_sort.cuh -- the two sorting kernels of GPU Bucket Sort (Dehne &
+// Zaboli, Section 4, Algorithm 1): Steps 1-3 (sort every sublist, take its
+// samples) and Step 9 (sort every bucket).  Both sort one unit of C*T*E
+// items with a thread-block cluster of C CTAs: every CTA sorts a chunk of
+// T*E items in shared memory (cta_sort), then the cluster merges the chunks
+// through distributed shared memory (cluster_merge).  C = 1 is a plain CTA.
+//
+// Keys-only units sort uint32 keys; pair units sort the 64-bit words
+// key << 32 | position-in-unit, which makes the order stable, and gather
+// each value from its position afterwards.
+#pragma once
+
+#include "bsort_device.cuh"
+
+namespace bsort {
+
+// ============================================================ Steps 1-3
+// Cluster i sorts sublist i (t = C*T*E items); CTA r loads positions
+// [r*T*E, (r+1)*T*E) of the sublist and, after the merge, holds its ranks
+// [r*T*E, (r+1)*T*E): it writes them to the sorted-sublist array and emits
+// the samples (ranks (k+1)w - 1) that fall in that range as key << 32 | p,
+// p = i*t + r.
+template <int T, int E, bool PAIRS, int C>
+__global__ void __launch_bounds__(T, 1)
+k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ vals_in,
+               uint64_t n, int is_f32, int val_bytes, uint32_t s,
+               uint32_t *__restrict__ tiles_k, void *__restrict__ tiles_v,
+               uint64_t *__restrict__ samples)
+{
+    using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+    constexpr int CH = T * E;
+    constexpr uint32_t TT = (uint32_t)C * CH;  // sublist size t
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    K *sm = reinterpret_cast<K *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t tile = blockIdx.x / C;
+    const int r = (int)(blockIdx.x % C);
+    const uint64_t base = (uint64_t)tile * TT;
+    const uint64_t avail = n > base ? n - base : 0;  // real items of the sublist
+    const int len = avail < (uint64_t)TT ? (int)avail : (int)TT;
+    const int off = r * CH;  // this CTA's chunk in the sublist
+
+    K v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int x = off + wb_pos<E>(warp, lane, k);
+        uint32_t key = 0xFFFFFFFFu;  // pad sentinel (position >= n)
+        if (x < len) {
+            key = keys_in[base + x];
+            if (is_f32) key = f32_encode(key);
+        }
+        if constexpr (PAIRS) v[k] = ((uint64_t)key << 32) | (uint32_t)x;
+        else v[k] = (K)key;
+    }
+    const int clen = len - off;
+    cta_sort<K, T, E>(v, sm, clen < 0 ? 0 : (clen > CH ? CH : clen));
+    cluster_merge<K, T, E, C>(sm, len);
+
+#pragma unroll 4
+    for (int k = 0; k < E; ++k) {
+        const int x = k * T + tid;
+        const K e = sm[pidx<K>(x)];
+        if constexpr (PAIRS) {
+            const uint32_t idx = (uint32_t)(e & 0xFFFFFFFFull);
+            tiles_k[base + off + x] = (uint32_t)((uint64_t)e >> 32);
+            if (val_bytes == 4) {
+                uint32_t val = (uint64_t)idx < avail
+                                   ? static_cast<const uint32_t *>(vals_in)[base + idx] : 0u;
+                static_cast<uint32_t *>(tiles_v)[base + off + x] = val;
+            } else {
+                uint64_t val = (uint64_t)idx < avail
+                                   ? static_cast<const uint64_t *>(vals_in)[base + idx] : 0ull;
+                static_cast<uint64_t *>(tiles_v)[base + off + x] = val;
+            }
+        } else {
+            tiles_k[base + off + x] = (uint32_t)e;
+        }
+    }
+    // Step 3: samples at ranks (k+1)w - 1 in [off, off + CH) as (key, p = i*t + r).
+    const uint32_t w = TT / s;
+    const uint32_t k0 = (uint32_t)off / w;                // first sample in range
+    const uint32_t k1 = (uint32_t)(off + CH) / w;         // one past the last
+    for (uint32_t k = k0 + tid; k < k1 && k < s; k += T) {
+        const uint32_t rank = (k + 1) * w - 1;
+        const K e = sm[pidx<K>((int)(rank - off))];
+        const uint32_t key = PAIRS ? (uint32_t)((uint64_t)e >> 32) : (uint32_t)e;
+        samples[(uint64_t)tile * s + k] = ((uint64_t)key << 32) | (uint32_t)(base + rank);
+    }
+}
+
+// ============================================================ Step 9
+// Cluster u sorts unit u = [units[1+2u], units[2+2u]) of the relocated array
+// (consecutive whole buckets, at most C*T*E items) and writes the positions
+// below n of the result.  With units == nullptr there is one unit, [0, n),
+// read from the caller's input (raw keys, transformed on load).
+template <int T, int E, bool PAIRS, int C>
+__global__ void __launch_bounds__(T, 1)
+k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
+              const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
+              int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v, int *err)
+{
+    using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+    constexpr int CH = T * E;
+    constexpr uint64_t CAP = (uint64_t)C * CH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    K *sm = reinterpret_cast<K *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t u = blockIdx.x / C;
+    const int r = (int)(blockIdx.x % C);
+    const bool direct = units == nullptr;
+    uint64_t L = 0, R = n;
+    if (!direct) {
+        if (u >= units[0]) return;  // fewer units than clusters (uniform per cluster)
+        L = units[1 + 2 * u];
+        R = units[2 + 2 * u];
+    }
+    const uint64_t len64 = R - L;
+    if (R < L || R > n_pad || len64 > CAP) {  // the plan guarantees a unit fits
+        if (tid == 0) set_error(err, DEV_INTERNAL);
+        return;  // uniform per cluster: no CTA of it reaches a cluster barrier
+    }
+    if (len64 == 0) return;
+    const int len = (int)len64;
+    const int off = r * CH;
+    K v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int x = off + wb_pos<E>(warp, lane, k);
+        uint32_t key = 0xFFFFFFFFu;
+        if (x < len) {
+            key = src_k[L + x];
+            if (direct && is_f32) key = f32_encode(key);
+        }
+        if constexpr (PAIRS) v[k] = ((uint64_t)key << 32) | (uint32_t)x;
+        else v[k] = (K)key;
+    }
+    const int clen = len - off;
+    cta_sort<K, T, E>(v, sm, clen < 0 ? 0 : (clen > CH ? CH : clen));
+    cluster_merge<K, T, E, C>(sm, len);
+    const uint64_t lim64 = min((unsigned long long)len, (unsigned long long)(n > L ? n - L : 0));
+    const int lim = (int)lim64;
+#pragma unroll 4
+    for (int k = 0; k < E; ++k) {
+        const int x = k * T + tid;
+        if (off + x < lim) {
+            const K e = sm[pidx<K>(x)];
+            uint32_t key = PAIRS ? (uint32_t)((uint64_t)e >> 32) : (uint32_t)e;
+            if (is_f32) key = f32_decode(key);
+            out_k[L + off + x] = key;
+            if constexpr (PAIRS) {
+                const uint32_t idx = (uint32_t)((uint64_t)e & 0xFFFFFFFFull);
+                if (val_bytes == 4)
+                    static_cast<uint32_t *>(out_v)[L + off + x] =
+                        static_cast<const uint32_t *>(src_v)[L + idx];
+                else
+                    static_cast<uint64_t *>(out_v)[L + off + x] =
+                        static_cast<const uint64_t *>(src_v)[L + idx];
+            }
+        }
+    }
+}
+
+// ============================================================ launching
+template <typename KernelT, typename... Args>
+inline cudaError_t launch_maybe_cluster(KernelT kern, unsigned grid, int block, int smem,
+                                        int csize, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid, 1, 1);
+    cfg.blockDim = dim3(block, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)csize;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = csize > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
+template <int T, int E, bool PAIRS, int C>
+inline cudaError_t init_sort_pair_of_kernels()
+{
+    using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+    const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
+    cudaError_t e = cudaFuncSetAttribute(k_sublist_sort<T, E, PAIRS, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_bucket_sort<T, E, PAIRS, C>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
+    if (C > 8) {
+        e = cudaFuncSetAttribute(k_sublist_sort<T, E, PAIRS, C>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_bucket_sort<T, E, PAIRS, C>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
+    return e;
+}
+
+template <int T, int E, bool PAIRS, int C>
+inline cudaError_t launch_sublist_sort_t(const void *keys_in, const void *vals_in, uint64_t n,
+                                         uint32_t m, int is_f32, int val_bytes, uint32_t s,
+                                         uint32_t *tiles_k, void *tiles_v, uint64_t *samples,
+                                         cudaStream_t st)
+{
+    using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+    const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
+    return launch_maybe_cluster(k_sublist_sort<T, E, PAIRS, C>, m * C, T, sm, C, st,
+                                static_cast<const uint32_t *>(keys_in), vals_in, n, is_f32,
+                                val_bytes, s, tiles_k, tiles_v, samples);
+}
+
+template <int T, int E, bool PAIRS, int C>
+inline cudaError_t launch_bucket_sort_t(const void *src_k, const void *src_v,
+                                        const uint32_t *units, uint32_t max_units, uint64_t n,
+                                        uint64_t n_pad, int is_f32, int val_bytes, void *out_k,
+                                        void *out_v, int *err, cudaStream_t st)
+{
+    using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+    const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
+    const unsigned grid = (units ? max_units : 1u) * C;
+    return launch_maybe_cluster(k_bucket_sort<T, E, PAIRS, C>, grid, T, sm, C, st,
+                                static_cast<const uint32_t *>(src_k), src_v, units, n, n_pad,
+                                is_f32, val_bytes, static_cast<uint32_t *>(out_k), out_v, err);
+}
+
+}  // namespace bsort

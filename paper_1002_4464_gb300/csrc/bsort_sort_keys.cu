@@ -1,0 +1,74 @@
+// bsort_sort_keys.cu -- instantiations of the Step 1-3 and Step 9 sorting
+// kernels for keys-only sorts (uint32 / transformed float32 keys).
+#include "bsort_internal.h"
+#include "bsort_sort.cuh"
+
+namespace bsort {
+
+// chunk shapes: 2048 = 128x16, 4096 = 256x16, 8192 = 512x16, 16384 = 1024x16,
+// 32768 = 1024x32; clusters of 2, 4, 8 CTAs on the 32768-item chunk.
+cudaError_t init_sort_keys_kernels()
+{
+    cudaError_t e;
+#define I(T_, E_, C_)                                            \
+    e = init_sort_pair_of_kernels<T_, E_, false, C_>();          \
+    if (e != cudaSuccess) return e
+    I(128, 16, 1); I(256, 16, 1); I(512, 16, 1); I(1024, 16, 1); I(1024, 32, 1);
+    I(1024, 32, 2); I(1024, 32, 4); I(1024, 32, 8);
+#undef I
+    return cudaSuccess;
+}
+
+cudaError_t launch_sublist_sort_keys(int chunk, int ctas, const void *keys_in, uint64_t n,
+                                     uint32_t m, int is_f32, uint32_t s, uint32_t *tiles_k,
+                                     uint64_t *samples, cudaStream_t st)
+{
+#define L(T_, E_, C_)                                                                       \
+    return launch_sublist_sort_t<T_, E_, false, C_>(keys_in, nullptr, n, m, is_f32, 0, s,   \
+                                                    tiles_k, nullptr, samples, st)
+    if (ctas == 1) {
+        switch (chunk) {
+        case 2048: L(128, 16, 1);
+        case 4096: L(256, 16, 1);
+        case 8192: L(512, 16, 1);
+        case 16384: L(1024, 16, 1);
+        case 32768: L(1024, 32, 1);
+        }
+    } else if (chunk == 32768) {
+        switch (ctas) {
+        case 2: L(1024, 32, 2);
+        case 4: L(1024, 32, 4);
+        case 8: L(1024, 32, 8);
+        }
+    }
+#undef L
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bucket_sort_keys(int chunk, int ctas, const void *src_k, const uint32_t *units,
+                                    uint32_t max_units, uint64_t n, uint64_t n_pad, int is_f32,
+                                    void *out_k, int *err, cudaStream_t st)
+{
+#define L(T_, E_, C_)                                                                        \
+    return launch_bucket_sort_t<T_, E_, false, C_>(src_k, nullptr, units, max_units, n,      \
+                                                   n_pad, is_f32, 0, out_k, nullptr, err, st)
+    if (ctas == 1) {
+        switch (chunk) {
+        case 2048: L(128, 16, 1);
+        case 4096: L(256, 16, 1);
+        case 8192: L(512, 16, 1);
+        case 16384: L(1024, 16, 1);
+        case 32768: L(1024, 32, 1);
+        }
+    } else if (chunk == 32768) {
+        switch (ctas) {
+        case 2: L(1024, 32, 2);
+        case 4: L(1024, 32, 4);
+        case 8: L(1024, 32, 8);
+        }
+    }
+#undef L
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace bsort

@@ -62,7 +62,7 @@ def test_plan_auto_bound_fits_unit(n):
     h = _handle()
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, n)
     if p.single_tile:
-        assert n <= 32768 and p.unit_capacity >= n
+        assert n <= 8 * 32768 and p.unit_capacity >= n
     else:
         assert p.t % p.s == 0 and p.m * p.t == p.n_padded >= n > p.n_padded - p.t
         w = p.t // p.s

@@ -201,3 +201,71 @@ def test_bucket_bound_holds_on_device():
         starts = np.append(l.reshape(p.s, p.m)[:, 0], p.n_padded)
         assert np.diff(starts).max() <= p.bucket_bound <= 2 * p.n_padded // p.s
         sorter.close()
+
+
+@pytest.mark.parametrize("n,t,s", [
+    (1 << 22, 65536, 2048),         # sublists sorted by 2-CTA clusters
+    ((1 << 22) + 999, 131072, 1024),  # 4-CTA clusters, ragged tail, 2-CTA units
+    (1 << 23, 262144, 1024),        # 8-CTA clusters, 4-CTA units
+    (3 << 20, 32768, 256),          # single-CTA sublists, 8-CTA units
+])
+def test_cluster_plans_intermediates(n, t, s):
+    keys = synth.keys_u32("staggered", n, synth.seed_for(2, 6, t))
+    keys[::7] = keys[::7] & np.uint32(0xFFF)
+    want = oracle.paper_sort(keys, t, s, "u32")
+    sorter = pkg.BucketSorter(tile=t, samples=s)
+    p = sorter.plan(n)
+    assert p.tile_ctas * (32768 if p.tile_ctas > 1 else p.t) == p.t
+    got = _gpu_sort_keys(sorter, keys)
+    assert np.array_equal(got, want["keys"])
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], s)
+    sorter.close()
+
+
+@pytest.mark.parametrize("n,t,s", [(1 << 21, 65536, 1024), ((1 << 21) + 77, 131072, 2048)])
+def test_cluster_plans_pairs(n, t, s):
+    keys = synth.keys_zipf(n, synth.seed_for(3, 4))
+    vals = np.arange(n, dtype=np.uint32)
+    want = oracle.paper_sort(keys, t, s, "u32", vals=vals)
+    sorter = pkg.BucketSorter(tile=t, samples=s)
+    ok, ov = sorter.sort_pairs(_to_dev_u32(keys), _to_dev_u32(vals))
+    sorter.sync()
+    assert np.array_equal(ok.cpu().numpy().view(np.uint32), want["keys"])
+    assert np.array_equal(ov.cpu().numpy().view(np.uint32), want["vals"])
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], s)
+    sorter.close()
+
+
+@pytest.mark.parametrize("n", [40000, 100000, 262144])
+def test_single_cluster_unit(n):
+    """n above one CTA's chunk but within one cluster: one unit, no sampling."""
+    keys = synth.keys_u32("reverse", n, synth.seed_for(2, 8))
+    sorter = pkg.BucketSorter()
+    assert sorter.plan(n).single_tile == 1
+    got = _gpu_sort_keys(sorter, keys)
+    assert np.array_equal(got, np.sort(keys))
+    vals = np.arange(n, dtype=np.uint64)
+    ok, ov = sorter.sort_pairs(_to_dev_u32(keys & np.uint32(0xFF)),
+                               torch.from_numpy(vals.view(np.int64)).cuda())
+    sorter.sync()
+    wk, wv = oracle.textbook_sort(keys & np.uint32(0xFF), "u32", vals=vals)
+    assert np.array_equal(ok.cpu().numpy().view(np.uint32), wk)
+    assert np.array_equal(ov.cpu().numpy().view(np.uint64), wv)
+    sorter.close()
+
+
+@pytest.mark.parametrize("n,kt", [(1 << 26, "u32"), ((1 << 25) + 3, "f32")])
+def test_large_auto_plans(n, kt):
+    """Large planner-chosen plans (clusters in Steps 2 and 9); the result is
+    compared with an independent library sort (numpy) of the same keys."""
+    if kt == "u32":
+        keys = synth.keys_u32("uniform", n, synth.seed_for(2, 0, 1))
+        got = _gpu_sort_keys(pkg.BucketSorter(), keys)
+        assert np.array_equal(got, np.sort(keys))
+    else:
+        f = synth.keys_f32("gaussian", n, synth.seed_for(2, 1, 1))
+        sorter = pkg.BucketSorter()
+        d = torch.from_numpy(f).cuda()
+        out = sorter.sort_keys(d, key_type="f32")
+        sorter.sync()
+        assert np.array_equal(out.cpu().numpy().view(np.uint32), np.sort(f).view(np.uint32))
