@@ -163,6 +163,36 @@ bsort_status bsort_kernel_times(bsort_t h, float *ms, uint32_t count,
                                 uint32_t *written, uint32_t *calls);
 const char *bsort_kernel_name(bsort_t h, uint32_t index);
 
+/* Largest n that bsort_sort_keys_noalloc accepts. */
+#define BSORT_NOALLOC_MAX_KEYS (1ull << 20)
+
+/* Keys-only sort that allocates nothing, for callers that cannot allocate
+ * device memory: code running where cudaMalloc is not allowed or not wanted
+ * (inside a memory pool that must not grow, under a strict memory budget, in
+ * a plugin whose host owns every allocation).  It needs no handle.  The paper
+ * has no counterpart: this is a packaging of the same sort.
+ *
+ * It sorts n <= BSORT_NOALLOC_MAX_KEYS (2^20) uint32 or float32 keys on the
+ * current CUDA device (kt = BSORT_U32 or BSORT_F32), from d_keys_in into
+ * d_keys_out (the same buffer or disjoint), with the same result as
+ * bsort_sort_keys.  Its scratch memory is one fixed array of 12 MiB inside
+ * the library, which every GPU that loads the library keeps until the
+ * process exits.  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  The call makes no cudaMalloc, cudaFree or other allocating call.
+ * Every call uses the same array, so calls whose work overlaps on the GPU
+ * (on different streams, or from different threads) race and corrupt each
+ * other; order them on one stream.
+ *
+ * Returns BSORT_EINVAL for n > BSORT_NOALLOC_MAX_KEYS, a null or partially
+ * overlapping pointer, or a key type other than U32/F32 (BSORT_EUNSUPPORTED
+ * for U64).  The call is asynchronous on cuda_stream; with wait != 0 it
+ * waits for the stream and also returns the device error status
+ * (BSORT_ETIMEOUT / BSORT_EINTERNAL) of this call. */
+bsort_status bsort_sort_keys_noalloc(bsort_key_type kt, const void *d_keys_in,
+                                     void *d_keys_out, uint64_t n, void *cuda_stream,
+                                     int wait);
+
 /* Last error message on this handle (never NULL). */
 const char *bsort_last_error(bsort_t h);
 

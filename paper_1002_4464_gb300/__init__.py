@@ -20,7 +20,7 @@ __all__ = [
     "bsort_create", "bsort_destroy", "bsort_plan", "bsort_sort_keys",
     "bsort_sort_pairs", "bsort_sort_keys_host", "bsort_sync",
     "bsort_get_intermediate", "bsort_kernel_times", "bsort_kernel_name",
-    "bsort_last_error", "bsort_status_string", "BucketSorter",
+    "bsort_last_error", "bsort_status_string", "bsort_sort_keys_noalloc", "BucketSorter",
     "EXPORTED_SYMBOLS",
 ]
 
@@ -36,7 +36,7 @@ EXPORTED_SYMBOLS = (
     "bsort_create", "bsort_destroy", "bsort_plan", "bsort_sort_keys",
     "bsort_sort_pairs", "bsort_sort_keys_host", "bsort_sync",
     "bsort_get_intermediate", "bsort_kernel_times", "bsort_kernel_name",
-    "bsort_last_error", "bsort_status_string",
+    "bsort_last_error", "bsort_status_string", "bsort_sort_keys_noalloc",
 )
 
 
@@ -92,6 +92,7 @@ def load_library(rebuild: bool = False):
         "bsort_kernel_name": (ctypes.c_char_p, [H, u32]),
         "bsort_last_error": (ctypes.c_char_p, [H]),
         "bsort_status_string": (ctypes.c_char_p, [i32]),
+        "bsort_sort_keys_noalloc": (i32, [i32, vp, vp, u64, vp, i32]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -169,6 +170,13 @@ def bsort_kernel_times(h, count=64):
     _check(h, load_library().bsort_kernel_times(h, arr, count, ctypes.byref(written),
                                                 ctypes.byref(calls)))
     return [(bsort_kernel_name(h, i), arr[i]) for i in range(written.value)], calls.value
+
+
+def bsort_sort_keys_noalloc(key_type, d_keys_in, d_keys_out, n, stream, wait=0):
+    """Keys-only sort of n <= 2^20 keys that allocates nothing (fixed scratch
+    inside the library; see include/bsort.h)."""
+    return _check(None, load_library().bsort_sort_keys_noalloc(key_type, d_keys_in, d_keys_out,
+                                                               n, stream, wait))
 
 
 def bsort_kernel_name(h, index):

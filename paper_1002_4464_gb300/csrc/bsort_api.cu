@@ -4,6 +4,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -719,3 +720,63 @@ const char *bsort_last_error(bsort_t h)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- no-alloc entry
+// Scratch for bsort_sort_keys_noalloc: a fixed device array in this file,
+// sized for the largest plan of at most BSORT_NOALLOC_MAX_KEYS keys (about
+// 8.5 MiB).  Host code may not use the symbol as a device address; the
+// device address is looked up once per device with cudaGetSymbolAddress.
+namespace {
+constexpr size_t kNoallocScratchBytes = (size_t)12 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kNoallocMaxDevices] = {};
+}  // namespace
+
+extern "C" bsort_status bsort_sort_keys_noalloc(bsort_key_type kt, const void *d_keys_in,
+                                                void *d_keys_out, uint64_t n,
+                                                void *cuda_stream, int wait)
+{
+    if (n > BSORT_NOALLOC_MAX_KEYS) return BSORT_EINVAL;
+    if (n && (!d_keys_in || !d_keys_out)) return BSORT_EINVAL;
+    if (n && d_keys_in != d_keys_out && overlaps(d_keys_in, n * 4, d_keys_out, n * 4))
+        return BSORT_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoallocMaxDevices)
+        return BSORT_ECUDA;
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+                return BSORT_ECUDA;
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    // a handle on the stack whose fixed workspace is the scratch array
+    bsort_ctx ctx;
+    ctx.device = dev;
+    ctx.ws = scratch;
+    ctx.ws_bytes = kNoallocScratchBytes;
+    ctx.ws_fixed = true;
+    ctx.ws_owned = false;
+    Plan P;
+    bsort_status st = make_plan(&ctx, kt, 0, n, &P);
+    if (st != BSORT_OK) return st;
+    if (P.total > kNoallocScratchBytes) return BSORT_ENOMEM;
+    cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
+    // the array keeps the previous call's contents: the error word must start
+    // at zero (the scan's state is cleared by the sort itself)
+    if (cudaMemsetAsync(scratch, 0, kAlign, stream) != cudaSuccess) return BSORT_ECUDA;
+    st = run_sort(&ctx, kt, d_keys_in, nullptr, d_keys_out, nullptr, 0, n, stream);
+    if (st != BSORT_OK || !wait) return st;
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return BSORT_ECUDA;
+    int word = 0;
+    if (cudaMemcpy(&word, scratch, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return BSORT_ECUDA;
+    if (word == 0) return BSORT_OK;
+    return word == BSORT_ETIMEOUT ? BSORT_ETIMEOUT : BSORT_EINTERNAL;
+}
