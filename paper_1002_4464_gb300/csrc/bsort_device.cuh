@@ -385,30 +385,60 @@ __device__ __forceinline__ void cta_merge_runs(K *sm, int R)
 // of the cluster's items.  In the round with groups of G CTAs, the first G/2
 // CTAs of a group hold run A and the rest run B; CTA r finds the co-ranks of
 // its output range by a 32-ary search over the remote chunks, gathers the
-// A and B pieces into registers, waits for the whole cluster, stores them as
-// a bitonic sequence in its own SMEM, and merges locally.
-template <typename K>
-__device__ __forceinline__ K cl_load(cooperative_groups::cluster_group &cl, K *sm, int first_cta,
-                                     int chunk_shift, int x)
+// A and B pieces into registers (pieces held by CTA r itself are read from
+// its own shared memory; each piece spans at most two chunks), waits for the
+// whole cluster, stores them as a bitonic sequence in its own SMEM, and
+// merges locally.
+__device__ __forceinline__ uint32_t smem_u32addr(const void *p)
 {
-    const int cta = first_cta + (x >> chunk_shift);
-    const int off = x & ((1 << chunk_shift) - 1);
-    const K *p = cl.map_shared_rank(sm, cta);
-    return p[pidx<K>(off)];
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ uint32_t cl_mapa(uint32_t saddr, uint32_t rank)
+{
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
 }
 
 template <typename K>
-__device__ __forceinline__ int corank_cluster(cooperative_groups::cluster_group &cl, K *sm,
-                                              int a_cta, int b_cta, int chunk_shift, int la,
-                                              int lb, int d, int lane)
+__device__ __forceinline__ K cl_ld(uint32_t addr);
+template <>
+__device__ __forceinline__ uint32_t cl_ld<uint32_t>(uint32_t addr)
+{
+    uint32_t v;
+    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+template <>
+__device__ __forceinline__ uint64_t cl_ld<uint64_t>(uint32_t addr)
+{
+    uint64_t v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// Item x of the run held by CTAs first_cta, first_cta+1, ... (chunks of
+// 2^chunk_shift items), read through distributed shared memory.
+template <typename K>
+__device__ __forceinline__ K cl_load(uint32_t sm_base, int first_cta, int chunk_shift, int x)
+{
+    const int cta = first_cta + (x >> chunk_shift);
+    const int off = x & ((1 << chunk_shift) - 1);
+    return cl_ld<K>(cl_mapa(sm_base, (uint32_t)cta) + (uint32_t)(pidx<K>(off) * (int)sizeof(K)));
+}
+
+template <typename K>
+__device__ __forceinline__ int corank_cluster(uint32_t sm_base, int a_cta, int b_cta,
+                                              int chunk_shift, int la, int lb, int d, int lane)
 {
     int lo = d > lb ? d - lb : 0;
     int hi = d < la ? d : la;
     while (hi - lo > 32) {
         const int span = hi - lo;
         const int c = lo + (int)(((long long)span * (lane + 1)) / 33);
-        const bool pred = cl_load<K>(cl, sm, a_cta, chunk_shift, c) >
-                          cl_load<K>(cl, sm, b_cta, chunk_shift, d - 1 - c);
+        const bool pred = cl_load<K>(sm_base, a_cta, chunk_shift, c) >
+                          cl_load<K>(sm_base, b_cta, chunk_shift, d - 1 - c);
         const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
         if (ball == 0) {
             lo = lo + (int)(((long long)span * 32) / 33) + 1;
@@ -423,10 +453,36 @@ __device__ __forceinline__ int corank_cluster(cooperative_groups::cluster_group 
     const int c = lo + lane;
     bool pred = true;
     if (c < hi)
-        pred = cl_load<K>(cl, sm, a_cta, chunk_shift, c) >
-               cl_load<K>(cl, sm, b_cta, chunk_shift, d - 1 - c);
+        pred = cl_load<K>(sm_base, a_cta, chunk_shift, c) >
+               cl_load<K>(sm_base, b_cta, chunk_shift, d - 1 - c);
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
     return ball ? lo + __ffs(ball) - 1 : hi;
+}
+
+// One contiguous piece [x0, x0 + len) of a run held by CTAs first_cta, ...:
+// at most two chunks.  Describes where item z of the piece lives.
+struct Piece {
+    int cta0, off0, split;  // items [0, split) in cta0 from off0; the rest in cta0 + 1 from 0
+};
+
+__device__ __forceinline__ Piece make_piece(int first_cta, int chunk_shift, int x0)
+{
+    Piece p;
+    p.cta0 = first_cta + (x0 >> chunk_shift);
+    p.off0 = x0 & ((1 << chunk_shift) - 1);
+    p.split = (1 << chunk_shift) - p.off0;
+    return p;
+}
+
+template <typename K>
+__device__ __forceinline__ K piece_load(const K *sm, uint32_t sm_base, int my_rank,
+                                        const Piece &pc, int z)
+{
+    const bool first = z < pc.split;
+    const int cta = first ? pc.cta0 : pc.cta0 + 1;
+    const int off = first ? pc.off0 + z : z - pc.split;
+    if (cta == my_rank) return sm[pidx<K>(off)];
+    return cl_ld<K>(cl_mapa(sm_base, (uint32_t)cta) + (uint32_t)(pidx<K>(off) * (int)sizeof(K)));
 }
 
 // len: number of real items of the whole cluster (positions >= len hold the
@@ -441,6 +497,7 @@ __device__ __forceinline__ void cluster_merge(K *sm, int len)
         const int r = (int)cl.block_rank();
         const int tid = threadIdx.x;
         const int lane = tid & 31, warp = tid >> 5;
+        const uint32_t sm_base = smem_u32addr(sm);
         __shared__ int s_split[2];
 #pragma unroll 1
         for (int G = 2; G <= C; G <<= 1) {
@@ -453,7 +510,7 @@ __device__ __forceinline__ void cluster_merge(K *sm, int len)
             if (work) {
                 const int d0 = (r - g0) * CH;
                 if (warp < 2) {
-                    const int i = corank_cluster<K>(cl, sm, g0, g0 + h, SH, h * CH, h * CH,
+                    const int i = corank_cluster<K>(sm_base, g0, g0 + h, SH, h * CH, h * CH,
                                                     d0 + warp * CH, lane);
                     if (lane == 0) s_split[warp] = i;
                 }
@@ -461,14 +518,16 @@ __device__ __forceinline__ void cluster_merge(K *sm, int len)
                 const int i0 = s_split[0], i1 = s_split[1];
                 const int j0 = d0 - i0;
                 na = i1 - i0;
+                const Piece pa = make_piece(g0, SH, i0);
+                const Piece pb = make_piece(g0 + h, SH, j0);
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     const int z = k * T + tid;
-                    v[k] = z < na ? cl_load<K>(cl, sm, g0, SH, i0 + z)
-                                  : cl_load<K>(cl, sm, g0 + h, SH, j0 + (z - na));
+                    v[k] = z < na ? piece_load<K>(sm, sm_base, r, pa, z)
+                                  : piece_load<K>(sm, sm_base, r, pb, z - na);
                 }
             }
-            cl.sync();  // all remote reads of this round are done
+            cl.sync();  // all reads of this round are done
             if (work) {
 #pragma unroll
                 for (int k = 0; k < E; ++k) {

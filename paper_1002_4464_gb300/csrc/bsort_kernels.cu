@@ -325,11 +325,13 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 }
 
 // ============================================================ Step 8
-// One CTA per part of kRelocPart items of a sublist: the part's sorted keys
-// (and values), the sublist's cumulative counts c_i. and the offsets l_ij of
-// the runs that overlap the part are staged in shared memory with coalesced
-// loads; then each warp copies the overlapping pieces of runs A_ij to
-// l_ij + (position in the run), lanes in parallel (coalesced stores).
+// One CTA per part of kRelocPart items of a sublist.  The part's sorted keys
+// (and values) are staged in shared memory with coalesced vector loads,
+// together with, for the runs A_ij overlapping the part, their end c_ij and
+// delta_j = l_ij - c_i(j-1) (destination of item x of run j is x + delta_j).
+// Each warp then walks a contiguous piece of the part with its lanes on
+// consecutive items: every lane advances its own run index as x grows, so
+// the stores of a warp are consecutive addresses within a run.
 template <int T>
 __global__ void __launch_bounds__(T)
 k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_v,
@@ -338,10 +340,10 @@ k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_
            uint32_t *__restrict__ reloc_k, void *__restrict__ reloc_v, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t *s_k = reinterpret_cast<uint32_t *>(smem_raw);           // part
-    unsigned char *s_v = reinterpret_cast<unsigned char *>(s_k + part);  // part * val_bytes
-    uint32_t *s_cum = reinterpret_cast<uint32_t *>(s_v + (size_t)part * val_bytes);  // s
-    uint32_t *s_off = s_cum + s;                                      // s
+    uint32_t *s_k = reinterpret_cast<uint32_t *>(smem_raw);               // part
+    unsigned char *s_v = reinterpret_cast<unsigned char *>(s_k + part);    // part * val_bytes
+    uint32_t *s_end = reinterpret_cast<uint32_t *>(s_v + (size_t)part * val_bytes);  // s + 1
+    uint32_t *s_delta = s_end + (s + 1);                                   // s
     __shared__ uint32_t s_j[2];
     const uint32_t parts = t / part;
     const uint32_t i = blockIdx.x / parts;
@@ -359,42 +361,58 @@ k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_
             uint4 *d4 = reinterpret_cast<uint4 *>(s_v);
             for (uint32_t x = tid; x < part * val_bytes / 16; x += T) d4[x] = v4[x];
         }
-        for (uint32_t j = tid; j < s; j += T) s_cum[j] = cum[(uint64_t)i * s + j];
+        for (uint32_t j = tid; j < s; j += T) s_end[j] = cum[(uint64_t)i * s + j];
+        if (tid == 0) s_end[s] = 0xFFFFFFFFu;  // sentinel past the last run
     }
     __syncthreads();
-    // runs overlapping [h0, h1): j from the first with c_ij > h0 to the first
+    // runs overlapping [h0, h1): from the first with c_ij > h0 to the first
     // with c_ij >= h1
     if (tid < 2) {
         const uint32_t key = tid == 0 ? h0 : h1 - 1;
-        uint32_t lo = 0, hi = s;  // first j with s_cum[j] > key
+        uint32_t lo = 0, hi = s;  // first j with s_end[j] > key
         while (lo < hi) {
             uint32_t mid = (lo + hi) >> 1;
-            if (s_cum[mid] > key) hi = mid;
+            if (s_end[mid] > key) hi = mid;
             else lo = mid + 1;
         }
         s_j[tid] = lo;
     }
     __syncthreads();
     const uint32_t j_lo = s_j[0], j_hi = min(s_j[1], s - 1);
-    for (uint32_t j = j_lo + tid; j <= j_hi; j += T) s_off[j] = offsets[(uint64_t)j * m + i];
-    __syncthreads();
-    for (uint32_t j = j_lo + warp; j <= j_hi; j += T / 32) {
-        const uint32_t start = j ? s_cum[j - 1] : 0u;
-        const uint32_t end = s_cum[j];
-        const uint64_t dst = s_off[j];
+    for (uint32_t j = j_lo + tid; j <= j_hi; j += T) {
+        const uint32_t start = j ? s_end[j - 1] : 0u;
+        const uint32_t end = s_end[j];
+        const uint64_t dst = offsets[(uint64_t)j * m + i];
         if (end < start || end > t || dst + (end - start) > n_pad) {  // never for a valid plan
-            if (lane == 0) set_error(err, DEV_INTERNAL);
+            set_error(err, DEV_INTERNAL);
+            s_delta[j] = 0;
             continue;
         }
-        const uint32_t x0 = max(start, h0), x1 = min(end, h1);
-        for (uint32_t x = x0 + lane; x < x1; x += 32) {
-            const uint64_t o = dst + (x - start);
-            reloc_k[o] = s_k[x - h0];
-            if (val_bytes == 4)
-                static_cast<uint32_t *>(reloc_v)[o] = reinterpret_cast<const uint32_t *>(s_v)[x - h0];
-            else if (val_bytes == 8)
-                static_cast<uint64_t *>(reloc_v)[o] = reinterpret_cast<const uint64_t *>(s_v)[x - h0];
+        s_delta[j] = (uint32_t)(dst - start);  // wraps; dst = x + delta (mod 2^32)
+    }
+    __syncthreads();
+    // warp w walks [p0, p1) of the part
+    const uint32_t per = part / (T / 32);
+    const uint32_t p0 = h0 + warp * per, p1 = p0 + per;
+    uint32_t x = p0 + lane;
+    uint32_t j = j_lo;
+    {   // first run of this lane: first j with s_end[j] > x
+        uint32_t lo = j_lo, hi = j_hi;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi) >> 1;
+            if (s_end[mid] > x) hi = mid;
+            else lo = mid + 1;
         }
+        j = lo;
+    }
+    for (; x < p1; x += 32) {
+        while (s_end[j] <= x) ++j;
+        const uint32_t o = x + s_delta[j];
+        reloc_k[o] = s_k[x - h0];
+        if (val_bytes == 4)
+            static_cast<uint32_t *>(reloc_v)[o] = reinterpret_cast<const uint32_t *>(s_v)[x - h0];
+        else if (val_bytes == 8)
+            static_cast<uint64_t *>(reloc_v)[o] = reinterpret_cast<const uint64_t *>(s_v)[x - h0];
     }
 }
 
@@ -580,7 +598,7 @@ cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const 
                             cudaStream_t st)
 {
     const uint32_t part = t < (uint32_t)kRelocPart ? t : (uint32_t)kRelocPart;
-    const int sm = (int)(part * (4 + val_bytes) + 2 * s * 4);
+    const int sm = (int)(part * (4 + val_bytes) + (2 * s + 1) * 4);
     if (sm > kRelocateSmemMax) return cudaErrorInvalidValue;
     k_relocate<256><<<m * (t / part), 256, sm, st>>>(tiles_k, tiles_v, cum, offsets, t, s, m,
                                                       part, (uint64_t)m * t, val_bytes, reloc_k,
