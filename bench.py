@@ -29,8 +29,20 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "Gkeys/s (uint32, n=2^28) & HBM-roofline %"
+# kernels of the launch sequence (library names -> CUDA kernel names)
+KERNEL_FN = {
+    "step1_3_sublist_sort": "k_sublist_sort", "step4_sample_chunks": "k_records_sort",
+    "step4_sample_merge": "k_merge_pass", "step5_splitters": "k_select_splitters",
+    "step6_sample_index": "k_sample_index", "step7_prefix_sum": "k_scan",
+    "step8_relocate": "k_relocate", "step9_pack_units": "k_pack_units",
+    "step9_bucket_sort": "k_bucket_sort", "step9_single_unit": "k_bucket_sort",
+}
+ALU_KERNELS = ("step1_3_sublist_sort", "step9_bucket_sort", "step9_single_unit")
+# integer ALU pipe: 16 lanes per SM sub-partition x 4 x 152 SMs x 2.07 GHz
+ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12
 UNIT = "Gkeys/s"
 KERNEL_SOURCES = ["paper_1002_4464_gb300/csrc/bsort_kernels.cu",
+                  "paper_1002_4464_gb300/csrc/bsort_sort.cuh",
                   "paper_1002_4464_gb300/csrc/bsort_device.cuh"]
 
 
@@ -48,6 +60,8 @@ def _args():
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--cpu-sample", type=int, default=1 << 22,
                    help="keys per CPU-oracle sample")
+    p.add_argument("--tile", type=int, default=0, help="force the sublist size t (0: planner)")
+    p.add_argument("--samples", type=int, default=0, help="force s (0: planner)")
     return p.parse_args()
 
 
@@ -252,7 +266,7 @@ def run_ours(args):
 
     keys = make_keys(args.dist)
     out = torch.empty_like(keys)
-    sorter = pkg.BucketSorter(device=local, timing=True)
+    sorter = pkg.BucketSorter(device=local, timing=True, tile=args.tile, samples=args.samples)
     plan = sorter.plan(args.n, args.key_type)
     stream = torch.cuda.current_stream(dev)
 
@@ -300,31 +314,42 @@ def run_ours(args):
 
     # per-kernel breakdown and the dominant kernel's roofline
     per_kernel = {}
+    launches_per_kernel = {}
     for name, ms in ktimes:
         per_kernel[name] = per_kernel.get(name, 0.0) + ms / max(kcalls, 1)
-    launches_per_kernel = {}
-    for name, _ in ktimes:
         launches_per_kernel[name] = launches_per_kernel.get(name, 0) + 1
     dom = max(per_kernel, key=per_kernel.get) if per_kernel else None
-    peak, peak_kind = _peaks()
+    hbm_peak, peak_kind = _peaks()
     roofline = None
     if dom is not None:
-        # algorithmic bytes of one pass over the data (read + write, keys only)
-        np_pad = plan.n_padded if not plan.single_tile else plan.n
-        alg_bytes = 2 * np_pad * 4
         dom_ms = per_kernel[dom] / launches_per_kernel[dom]
-        achieved = alg_bytes / (dom_ms / 1e3) / 1e9
-        workload = _config(args, 1)["workload"]
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak,
-                    "peak_kind": "%s (MEASURED_PEAKS.json hbm_gbs)" % peak_kind
-                    if peak_kind == "measured" else "fallback 6.8 TB/s",
-                    "unit": "GB/s", "frac": achieved / peak,
-                    "traffic": _traffic_for(dom, workload),
-                    "alg_bytes_per_launch": alg_bytes, "ms_per_launch": dom_ms}
-        # whole-step roofline: three read+write passes (Steps 2, 8, 9)
+        if dom in ALU_KERNELS:
+            # comparison sort: ALU-bound.  Algorithmic work of one launch =
+            # 2 integer ops (compare + select) per item per merge level,
+            # levels = log2(items per sort unit).
+            unit = plan.unit_capacity if dom != "step1_3_sublist_sort" else plan.t
+            levels = max(1, (int(unit) - 1).bit_length())
+            alg = 2.0 * args.n * levels
+            achieved = alg / (dom_ms / 1e3) / 1e12
+            roofline = {"bound": "alu", "kernel": KERNEL_FN.get(dom, dom),
+                        "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
+                        "frac": achieved / ALU_PEAK_TOPS,
+                        "peak_kind": "derived: 152 SMs x 64 int ops/clk (ALU pipe) x 2.07 GHz",
+                        "alg_ops_per_launch": alg, "merge_levels": levels,
+                        "ms_per_launch": dom_ms}
+        else:
+            alg = 2 * plan.n_padded * 4
+            achieved = alg / (dom_ms / 1e3) / 1e9
+            roofline = {"bound": "hbm", "kernel": KERNEL_FN.get(dom, dom), "achieved": achieved,
+                        "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                        "peak_kind": peak_kind, "alg_bytes_per_launch": alg,
+                        "ms_per_launch": dom_ms}
+        roofline["traffic"] = _traffic_for(KERNEL_FN.get(dom, dom), _config(args, 1)["workload"])
+        # whole-step HBM roofline: three read+write passes (Steps 2, 8, 9)
         whole = 6 * args.n * 4 / (ms_step / 1e3) / 1e9
-        roofline["step_achieved_gbs"] = whole
-        roofline["step_frac"] = whole / peak
+        roofline["step_hbm_achieved_gbs"] = whole
+        roofline["step_hbm_peak_gbs"] = hbm_peak
+        roofline["step_hbm_frac"] = whole / hbm_peak
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     e2e = None

@@ -139,20 +139,26 @@ bool tile_shape(uint64_t t, bool pairs, int *chunk, int *ctas)
 
 double log2d(double x) { return x > 1 ? __builtin_log2(x) : 0.0; }
 
-// Modelled cost (in item-merge-levels) of a plan: Steps 2 and 9 cost about
-// log2(chunk) levels per item plus ~2 levels per cluster merge round (Step 9
-// over the expected unit fill); the samples cost about 50 levels per record
-// (64-bit records sorted through L2 in several passes, then searched).
+// Modelled cost of a plan, in units of one single-CTA sort pass over the
+// items.  The factors are measured on GB300 at n = 2^28 uint32 keys: a
+// Step-2 sublist sorted by a cluster of 2 / 4 / 8 CTAs costs 1.24 / 1.68 /
+// 2.5 passes (distributed-shared-memory merge rounds; 8-CTA clusters also
+// leave SMs idle), a Step-9 unit of 2 / 4 / 8 CTAs costs 1.65 / 2.1 / 3.1
+// passes (rounds plus unit fill); the samples cost about 1.6e-2 passes per
+// sample per key-equivalent (sorting, searching and scanning m*s records),
+// and Step 8 about 0.35 passes (0.3 with runs of w >= 32 items).
 double plan_cost(uint64_t np, uint64_t s, int tchunk, int tctas, int uchunk, int uctas)
 {
     const double n = (double)np;
-    const double avg = n / (double)s;  // average bucket
-    const double q = (double)uchunk * uctas;
-    const double fill = q >= 2 * avg ? 0.8 : avg / q;
-    const double k1 = n * (log2d(tchunk) + 2.0 * log2d(tctas));
-    const double k9 = n / fill * (log2d(uchunk) + 2.0 * log2d(uctas));
-    const double smp = n / ((double)tchunk * tctas) * (double)s * 100.0;
-    return k1 + k9 + smp;
+    auto f1 = [](int c) { return c == 1 ? 1.0 : c == 2 ? 1.24 : c == 4 ? 1.68 : 2.5; };
+    auto f9 = [](int c) { return c == 1 ? 1.3 : c == 2 ? 1.65 : c == 4 ? 2.1 : 3.1; };
+    const double chunk_levels = log2d(tchunk) / 15.0;  // smaller chunks sort faster
+    const double unit_levels = log2d(uchunk) / 15.0;
+    const double t = (double)tchunk * tctas;
+    const double w = t / (double)s;
+    const double samples = n / w;
+    return n * (f1(tctas) * chunk_levels + f9(uctas) * unit_levels +
+                (w >= 32 ? 0.3 : 0.35)) + samples * 0.45;
 }
 
 bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P)

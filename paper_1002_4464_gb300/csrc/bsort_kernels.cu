@@ -325,94 +325,89 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 }
 
 // ============================================================ Step 8
-// One CTA per part of kRelocPart items of a sublist.  The part's sorted keys
-// (and values) are staged in shared memory with coalesced vector loads,
-// together with, for the runs A_ij overlapping the part, their end c_ij and
-// delta_j = l_ij - c_i(j-1) (destination of item x of run j is x + delta_j).
-// Each warp then walks a contiguous piece of the part with its lanes on
-// consecutive items: every lane advances its own run index as x grows, so
-// the stores of a warp are consecutive addresses within a run.
-template <int T>
+// Relocation organised by destination.  CTA (g, b) moves the runs A_ij of
+// the TG sublists i in [g*TG, (g+1)*TG) and the BB buckets j in
+// [b*BB, (b+1)*BB).  Because offsets are bucket-major, the runs of bucket j
+// from these TG consecutive sublists are adjacent in the relocated array:
+// one contiguous destination range per bucket.  A warp walks that range with
+// its lanes on consecutive destinations (long coalesced stores) and reads
+// each item from its sorted sublist; a lane advances its sublist index as
+// its destination passes each run.
+template <int T, int TG, int BB>
 __global__ void __launch_bounds__(T)
 k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_v,
            const uint32_t *__restrict__ cum, const uint32_t *__restrict__ offsets,
-           uint32_t t, uint32_t s, uint32_t m, uint32_t part, uint64_t n_pad, int val_bytes,
+           uint32_t t, uint32_t s, uint32_t m, uint64_t n_pad, int val_bytes,
            uint32_t *__restrict__ reloc_k, void *__restrict__ reloc_v, int *err)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t *s_k = reinterpret_cast<uint32_t *>(smem_raw);               // part
-    unsigned char *s_v = reinterpret_cast<unsigned char *>(s_k + part);    // part * val_bytes
-    uint32_t *s_end = reinterpret_cast<uint32_t *>(s_v + (size_t)part * val_bytes);  // s + 1
-    uint32_t *s_delta = s_end + (s + 1);                                   // s
-    __shared__ uint32_t s_j[2];
-    const uint32_t parts = t / part;
-    const uint32_t i = blockIdx.x / parts;
-    const uint32_t h0 = (blockIdx.x % parts) * part, h1 = h0 + part;
-    const uint64_t base = (uint64_t)i * t;
+    __shared__ uint32_t s_c[TG][BB + 1];   // c_i(j-1) for j = j0 .. j0+BB (column 0: j0-1)
+    __shared__ uint32_t s_l[BB][TG];       // l_ij
+    __shared__ uint32_t s_rs[BB][TG + 1];  // run start within the bucket's range; [TG] = total
+    __shared__ uint32_t s_src[BB][TG];     // run start within its sublist, c_i(j-1)
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    {
-        const uint4 *src4 = reinterpret_cast<const uint4 *>(tiles_k + base + h0);
-        uint4 *dst4 = reinterpret_cast<uint4 *>(s_k);
-        for (uint32_t x = tid; x < part / 4; x += T) dst4[x] = src4[x];
-        if (val_bytes) {
-            const uint4 *v4 = reinterpret_cast<const uint4 *>(
-                static_cast<const unsigned char *>(tiles_v) + (base + h0) * val_bytes);
-            uint4 *d4 = reinterpret_cast<uint4 *>(s_v);
-            for (uint32_t x = tid; x < part * val_bytes / 16; x += T) d4[x] = v4[x];
+    const uint32_t i0 = blockIdx.x * TG;
+    const uint32_t j0 = blockIdx.y * BB;
+    const uint32_t ni = min((uint32_t)TG, m - i0);
+    const uint32_t nj = min((uint32_t)BB, s - j0);
+    for (uint32_t idx = tid; idx < TG * (BB + 1); idx += T) {
+        const uint32_t i = idx / (BB + 1), jj = idx % (BB + 1);
+        uint32_t v = 0;
+        if (i < ni) {
+            const uint32_t j = j0 + jj;  // holds c_i(j-1), i.e. cum column j-1
+            if (j > 0 && j - 1 < s) v = cum[(uint64_t)(i0 + i) * s + j - 1];
+            else if (j > 0) v = t;
         }
-        for (uint32_t j = tid; j < s; j += T) s_end[j] = cum[(uint64_t)i * s + j];
-        if (tid == 0) s_end[s] = 0xFFFFFFFFu;  // sentinel past the last run
+        s_c[i][jj] = v;
+    }
+    for (uint32_t idx = tid; idx < BB * TG; idx += T) {
+        const uint32_t jj = idx / TG, i = idx % TG;
+        s_l[jj][i] = (i < ni && jj < nj) ? offsets[(uint64_t)(j0 + jj) * m + i0 + i] : 0u;
     }
     __syncthreads();
-    // runs overlapping [h0, h1): from the first with c_ij > h0 to the first
-    // with c_ij >= h1
-    if (tid < 2) {
-        const uint32_t key = tid == 0 ? h0 : h1 - 1;
-        uint32_t lo = 0, hi = s;  // first j with s_end[j] > key
-        while (lo < hi) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (s_end[mid] > key) hi = mid;
-            else lo = mid + 1;
+    for (uint32_t jj = tid; jj < BB; jj += T) {
+        uint32_t acc = 0;
+        for (uint32_t i = 0; i < TG; ++i) {
+            uint32_t len = 0, src = 0;
+            if (i < ni && jj < nj) {
+                src = s_c[i][jj];
+                const uint32_t end = s_c[i][jj + 1];
+                len = end - src;
+                const uint64_t want = (uint64_t)s_l[jj][0] + acc;  // runs of a bucket are adjacent
+                if (end < src || end > t || s_l[jj][i] != want || want + len > n_pad) {
+                    set_error(err, DEV_INTERNAL);  // never for a valid plan
+                    len = 0;
+                }
+            }
+            s_rs[jj][i] = acc;
+            s_src[jj][i] = src;
+            acc += len;
         }
-        s_j[tid] = lo;
+        s_rs[jj][TG] = acc;
     }
     __syncthreads();
-    const uint32_t j_lo = s_j[0], j_hi = min(s_j[1], s - 1);
-    for (uint32_t j = j_lo + tid; j <= j_hi; j += T) {
-        const uint32_t start = j ? s_end[j - 1] : 0u;
-        const uint32_t end = s_end[j];
-        const uint64_t dst = offsets[(uint64_t)j * m + i];
-        if (end < start || end > t || dst + (end - start) > n_pad) {  // never for a valid plan
-            set_error(err, DEV_INTERNAL);
-            s_delta[j] = 0;
-            continue;
+    for (uint32_t jj = warp; jj < nj; jj += T / 32) {
+        const uint32_t total = s_rs[jj][TG];
+        const uint64_t D = s_l[jj][0];
+        uint32_t i = 0;
+        {   // last i with s_rs[jj][i] <= lane (runs may be empty)
+            uint32_t lo = 0, hi = TG - 1;
+            while (lo < hi) {
+                uint32_t mid = (lo + hi + 1) >> 1;
+                if (s_rs[jj][mid] <= (uint32_t)lane) lo = mid;
+                else hi = mid - 1;
+            }
+            i = lo;
         }
-        s_delta[j] = (uint32_t)(dst - start);  // wraps; dst = x + delta (mod 2^32)
-    }
-    __syncthreads();
-    // warp w walks [p0, p1) of the part
-    const uint32_t per = part / (T / 32);
-    const uint32_t p0 = h0 + warp * per, p1 = p0 + per;
-    uint32_t x = p0 + lane;
-    uint32_t j = j_lo;
-    {   // first run of this lane: first j with s_end[j] > x
-        uint32_t lo = j_lo, hi = j_hi;
-        while (lo < hi) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (s_end[mid] > x) hi = mid;
-            else lo = mid + 1;
+        for (uint32_t q = lane; q < total; q += 32) {
+            while (s_rs[jj][i + 1] <= q) ++i;
+            const uint64_t src = (uint64_t)(i0 + i) * t + s_src[jj][i] + (q - s_rs[jj][i]);
+            reloc_k[D + q] = tiles_k[src];
+            if (val_bytes == 4)
+                static_cast<uint32_t *>(reloc_v)[D + q] = static_cast<const uint32_t *>(tiles_v)[src];
+            else if (val_bytes == 8)
+                static_cast<uint64_t *>(reloc_v)[D + q] = static_cast<const uint64_t *>(tiles_v)[src];
         }
-        j = lo;
-    }
-    for (; x < p1; x += 32) {
-        while (s_end[j] <= x) ++j;
-        const uint32_t o = x + s_delta[j];
-        reloc_k[o] = s_k[x - h0];
-        if (val_bytes == 4)
-            static_cast<uint32_t *>(reloc_v)[o] = reinterpret_cast<const uint32_t *>(s_v)[x - h0];
-        else if (val_bytes == 8)
-            static_cast<uint64_t *>(reloc_v)[o] = reinterpret_cast<const uint64_t *>(s_v)[x - h0];
     }
 }
 
@@ -545,7 +540,6 @@ cudaError_t init_misc_kernels()
 {
     BSORT_TRY(set_smem(k_records_sort<1024, 16>, smem_bytes_for_cap(kRecordChunk, true)));
     BSORT_TRY(set_smem(k_sample_index<256>, 96 * 1024));
-    BSORT_TRY(set_smem(k_relocate<256>, kRelocateSmemMax));
     BSORT_TRY(set_smem(k_pack_units<1024>, 16 * 8193));
     return cudaSuccess;
 }
@@ -597,12 +591,11 @@ cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const 
                             int val_bytes, uint32_t *reloc_k, void *reloc_v, int *err,
                             cudaStream_t st)
 {
-    const uint32_t part = t < (uint32_t)kRelocPart ? t : (uint32_t)kRelocPart;
-    const int sm = (int)(part * (4 + val_bytes) + (2 * s + 1) * 4);
-    if (sm > kRelocateSmemMax) return cudaErrorInvalidValue;
-    k_relocate<256><<<m * (t / part), 256, sm, st>>>(tiles_k, tiles_v, cum, offsets, t, s, m,
-                                                      part, (uint64_t)m * t, val_bytes, reloc_k,
-                                                      reloc_v, err);
+    constexpr int TG = 32, BB = 32;
+    const dim3 grid((m + TG - 1) / TG, (s + BB - 1) / BB);
+    k_relocate<256, TG, BB><<<grid, 256, 0, st>>>(tiles_k, tiles_v, cum, offsets, t, s, m,
+                                                   (uint64_t)m * t, val_bytes, reloc_k, reloc_v,
+                                                   err);
     return cudaGetLastError();
 }
 
