@@ -202,6 +202,23 @@ def _dist_index(name):
     return synth.DISTRIBUTIONS.index(name)
 
 
+def job_time_ms(local_ms, world, device):
+    """Time of the whole job: the slowest rank's timed region (max over ranks)."""
+    if world <= 1:
+        return float(local_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(n_per_rank, world, steps, ms_total):
+    """Whole-job keys per second in G: every rank sorts its own n keys per
+    step (independent replicas), over the slowest rank's time."""
+    return n_per_rank * world * steps / (ms_total / 1e3) / 1e9
+
+
 def run_reference(args):
     rank, world, local = _dist_env()
     if rank != 0:
@@ -305,12 +322,9 @@ def run_ours(args):
     ms_total = ev0.elapsed_time(ev1)
     sorter.sync()
     ktimes, kcalls = sorter.kernel_times()
-    if world > 1:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
+    ms_total = job_time_ms(ms_total, world, dev)
     ms_step = ms_total / args.steps
-    value = args.n * world * args.steps / (ms_total / 1e3) / 1e9
+    value = job_throughput(args.n, world, args.steps, ms_total)
 
     # per-kernel breakdown and the dominant kernel's roofline
     per_kernel = {}

@@ -61,8 +61,15 @@ typedef enum {
 } bsort_key_type;
 
 /* Flags for bsort_config.flags. */
-#define BSORT_FLAG_TIMING 0x1u  /* record CUDA events between the kernels of
-                                   every call; see bsort_kernel_times() */
+#define BSORT_FLAG_TIMING 0x1u   /* record CUDA events between the kernels of
+                                    every call; see bsort_kernel_times() */
+#define BSORT_FLAG_LOW_MEMORY 0x2u /* do not materialise the relocated array
+                                      of Step 8: Step 9 gathers its items from
+                                      the runs A_ij of the sorted sublists
+                                      directly.  Same result; the workspace
+                                      shrinks by n'*(key+value) bytes, at some
+                                      cost in speed; BSORT_IM_RELOCATED is then
+                                      not available */
 
 typedef struct {
     int device;                /* CUDA device ordinal the handle works on */
@@ -106,7 +113,8 @@ typedef enum {
     BSORT_IM_SPLITTERS = 2,  /* Step 5: s records g_0..g_{s-1} */
     BSORT_IM_COUNTS = 3,     /* Step 6: a_ij, uint32, bucket-major a[j*m + i] */
     BSORT_IM_OFFSETS = 4,    /* Step 7: l_ij, uint32, bucket-major */
-    BSORT_IM_RELOCATED = 5   /* Step 8: n' keys B_1 ... B_s */
+    BSORT_IM_RELOCATED = 5   /* Step 8: n' keys B_1 ... B_s (not with
+                                BSORT_FLAG_LOW_MEMORY) */
 } bsort_intermediate;
 
 /* Create a handle on cfg->device.  cfg may be NULL (device 0, on-demand

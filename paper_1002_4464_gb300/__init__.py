@@ -15,7 +15,7 @@ from . import build as _build
 __all__ = [
     "BSORT_OK", "BSORT_EINVAL", "BSORT_ENOMEM", "BSORT_ECUDA", "BSORT_ETIMEOUT",
     "BSORT_EBUSY", "BSORT_ENOTREADY", "BSORT_EUNSUPPORTED", "BSORT_EINTERNAL",
-    "BSORT_U32", "BSORT_F32", "BSORT_U64", "BSORT_FLAG_TIMING",
+    "BSORT_U32", "BSORT_F32", "BSORT_U64", "BSORT_FLAG_TIMING", "BSORT_FLAG_LOW_MEMORY",
     "bsort_config", "bsort_plan_info", "BsortError", "load_library",
     "bsort_create", "bsort_destroy", "bsort_plan", "bsort_sort_keys",
     "bsort_sort_pairs", "bsort_sort_keys_host", "bsort_sync",
@@ -28,6 +28,7 @@ BSORT_OK, BSORT_EINVAL, BSORT_ENOMEM, BSORT_ECUDA, BSORT_ETIMEOUT = 0, 1, 2, 3, 
 BSORT_EBUSY, BSORT_ENOTREADY, BSORT_EUNSUPPORTED, BSORT_EINTERNAL = 5, 6, 7, 8
 BSORT_U32, BSORT_F32, BSORT_U64 = 0, 1, 2
 BSORT_FLAG_TIMING = 0x1
+BSORT_FLAG_LOW_MEMORY = 0x2
 (BSORT_IM_TILES, BSORT_IM_SAMPLES, BSORT_IM_SPLITTERS, BSORT_IM_COUNTS,
  BSORT_IM_OFFSETS, BSORT_IM_RELOCATED) = range(6)
 
@@ -194,11 +195,11 @@ class BucketSorter:
     given as torch.int32 bit patterns) and run on the current torch stream."""
 
     def __init__(self, device: int = 0, tile: int = 0, samples: int = 0,
-                 timing: bool = False, workspace_bytes: int = 0):
+                 timing: bool = False, workspace_bytes: int = 0, low_memory: bool = False):
         import torch
         self.torch = torch
         self.device = device
-        self.flags = BSORT_FLAG_TIMING if timing else 0
+        self.flags = (BSORT_FLAG_TIMING if timing else 0) | (BSORT_FLAG_LOW_MEMORY if low_memory else 0)
         self.tile, self.samples = tile, samples
         self.ws = None
         self.h = None

@@ -36,7 +36,8 @@ struct Plan {
     // workspace offsets (bytes)
     uint64_t off_hdr, off_tiles_k, off_tiles_v, off_reloc_k, off_reloc_v, off_samples,
         off_rec_a, off_rec_b, off_spl, off_counts, off_cum, off_offsets, off_status,
-        off_units, total;
+        off_units, off_srcb, off_blk, total;
+    bool relocate;  // materialise Step 8 (else fused into Step 9's load)
 };
 
 }  // namespace
@@ -258,8 +259,10 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->scan_chunks = (P->n_rec + kScanChunk - 1) / kScanChunk;
         uint32_t merges = 0;
         for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
+        const bool reloc = !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
         I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
-                        1 /*S6*/ + 1 /*S7*/ + 1 /*S8*/ + 1 /*units*/ + 1 /*S9*/;
+                        1 /*S6*/ + 1 /*S7*/ + (reloc ? 1 : 0) /*S8*/ + 1 /*units*/ +
+                        (reloc ? 0 : 1) /*run index*/ + 1 /*S9*/;
     }
 
     // workspace layout
@@ -269,22 +272,25 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         o = align_up(o + bytes);
         return at;
     };
+    P->relocate = !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
     P->off_hdr = take(kAlign);  // error word (int) + scan ticket (uint32)
     if (!I.single_tile) {
         const uint64_t np = I.n_padded;
         P->off_tiles_k = take(np * 4);
         P->off_tiles_v = take(np * (uint64_t)vb);
-        P->off_reloc_k = take(np * 4);
-        P->off_reloc_v = take(np * (uint64_t)vb);
+        P->off_reloc_k = take(P->relocate ? np * 4 : 0);
+        P->off_reloc_v = take(P->relocate ? np * (uint64_t)vb : 0);
         P->off_samples = take((uint64_t)P->n_rec * 8);
         P->off_rec_a = take((uint64_t)P->n_rec_pad * 8);
         P->off_rec_b = take(P->n_rec_pad > (uint32_t)kRecordChunk ? (uint64_t)P->n_rec_pad * 8 : 0);
         P->off_spl = take((uint64_t)I.s * 8);
         P->off_counts = take((uint64_t)P->n_rec * 4);
         P->off_cum = take((uint64_t)P->n_rec * 4);
-        P->off_offsets = take((uint64_t)P->n_rec * 4);
+        P->off_offsets = take(((uint64_t)P->n_rec + 1) * 4);
         P->off_status = take((uint64_t)P->scan_chunks * 8);
         P->off_units = take((1 + 2 * (uint64_t)I.s) * 4);
+        P->off_srcb = take((uint64_t)P->n_rec * 4);
+        P->off_blk = take((np + kBlockItems - 1) / kBlockItems * 4);
     }
     P->total = o;
     I.workspace_bytes = o;
@@ -408,10 +414,12 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
             }
             return BSORT_OK;
         }
+        const GatherSrc none;
         SEQ(P.pairs ? launch_bucket_sort_pairs(P.unit_chunk, (int)I.unit_ctas, kin, vin, nullptr,
-                                               1, n, n, is_f32, (int)vb, kout, vout, err, st)
+                                               1, n, n, is_f32, (int)vb, kout, vout, err, none,
+                                               st)
                     : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, kin, nullptr, 1, n,
-                                              n, is_f32, kout, err, st),
+                                              n, is_f32, kout, err, none, st),
             "step9_single_unit");
         return BSORT_OK;
     }
@@ -455,25 +463,43 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
         }
         SEQ(launch_select_splitters(src, I.m, I.s, spl, st), "step5_splitters");
     }
+    uint32_t *srcb = reinterpret_cast<uint32_t *>(ws + P.off_srcb);
+    uint32_t *blk = reinterpret_cast<uint32_t *>(ws + P.off_blk);
     // Step 6
-    SEQ(launch_sample_index(tiles_k, samples, spl, I.t, I.s, I.m, counts, cum, st),
+    SEQ(launch_sample_index(tiles_k, samples, spl, I.t, I.s, I.m, counts, cum, srcb, st),
         "step6_sample_index");
     // Step 7
     SEQ(launch_scan(counts, offsets, P.n_rec, status, ticket, err, st), "step7_prefix_sum");
-    // Step 8
-    SEQ(launch_relocate(tiles_k, tiles_v, cum, offsets, I.t, I.s, I.m, (int)vb, reloc_k, reloc_v,
-                        err, st),
-        "step8_relocate");
+    // Step 8: materialised, unless BSORT_FLAG_LOW_MEMORY fuses it into the
+    // load of Step 9, which then gathers every unit from the runs A_ij
+    GatherSrc g;
+    if (P.relocate) {
+        SEQ(launch_relocate(tiles_k, tiles_v, cum, offsets, I.t, I.s, I.m, (int)vb, reloc_k,
+                            reloc_v, err, st),
+            "step8_relocate");
+    }
     // Step 9: buckets packed into units of at most unit_capacity items
     uint32_t *units = reinterpret_cast<uint32_t *>(ws + P.off_units);
     SEQ(launch_pack_units(offsets, I.m, I.s, (uint32_t)I.n_padded, (uint32_t)I.unit_capacity,
                           units, err, st),
         "step9_pack_units");
-    SEQ(P.pairs ? launch_bucket_sort_pairs(P.unit_chunk, (int)I.unit_ctas, reloc_k, reloc_v,
-                                           units, I.s, n, I.n_padded, is_f32, (int)vb, kout,
-                                           vout, err, st)
-                : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, reloc_k, units, I.s, n,
-                                          I.n_padded, is_f32, kout, err, st),
+    if (!P.relocate) {
+        SEQ(launch_block_index(offsets, P.n_rec, (uint32_t)I.n_padded, blk, st),
+            "step9_run_index");
+        g.offsets = offsets;
+        g.srcb = srcb;
+        g.blk = blk;
+        g.m = I.m;
+        g.t = I.t;
+        g.runs = P.n_rec;
+    }
+    const void *s9k = P.relocate ? (const void *)reloc_k : (const void *)tiles_k;
+    const void *s9v = P.relocate ? (const void *)reloc_v : (const void *)tiles_v;
+    SEQ(P.pairs ? launch_bucket_sort_pairs(P.unit_chunk, (int)I.unit_ctas, s9k, s9v, units, I.s,
+                                           n, I.n_padded, is_f32, (int)vb, kout, vout, err, g,
+                                           st)
+                : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, s9k, units, I.s, n,
+                                          I.n_padded, is_f32, kout, err, g, st),
         "step9_bucket_sort");
     return BSORT_OK;
 }
@@ -516,7 +542,7 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
         h->flags = cfg->flags;
         h->force_t = cfg->tile;
         h->force_s = cfg->samples;
-        if (cfg->flags & ~(uint32_t)BSORT_FLAG_TIMING) {
+        if (cfg->flags & ~(uint32_t)(BSORT_FLAG_TIMING | BSORT_FLAG_LOW_MEMORY)) {
             delete h;
             return BSORT_EINVAL;
         }
@@ -665,7 +691,13 @@ bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which, void *h
     case BSORT_IM_SPLITTERS: off = P.off_spl; size = (uint64_t)P.info.s * 8; break;
     case BSORT_IM_COUNTS: off = P.off_counts; size = (uint64_t)P.n_rec * 4; break;
     case BSORT_IM_OFFSETS: off = P.off_offsets; size = (uint64_t)P.n_rec * 4; break;
-    case BSORT_IM_RELOCATED: off = P.off_reloc_k; size = P.info.n_padded * 4; break;
+    case BSORT_IM_RELOCATED:
+        if (!P.relocate)
+            return fail(h, BSORT_ENOTREADY,
+                        "the relocated array is not materialised under BSORT_FLAG_LOW_MEMORY");
+        off = P.off_reloc_k;
+        size = P.info.n_padded * 4;
+        break;
     default: return fail(h, BSORT_EINVAL, "unknown intermediate %d", (int)which);
     }
     if (bytes != size)

@@ -485,10 +485,12 @@ __device__ __forceinline__ K piece_load(const K *sm, uint32_t sm_base, int my_ra
     return cl_ld<K>(cl_mapa(sm_base, (uint32_t)cta) + (uint32_t)(pidx<K>(off) * (int)sizeof(K)));
 }
 
-// len: number of real items of the whole cluster (positions >= len hold the
-// maximal key); groups made only of padding skip their work.
+// len: number of real items of the whole cluster; before the first round
+// CTA r holds the real items [r*per, min((r+1)*per, len)) followed by
+// padding (the maximal key), so a group of CTAs starting at g0 holds real
+// items iff g0*per < len, and groups made only of padding skip their work.
 template <typename K, int T, int E, int C>
-__device__ __forceinline__ void cluster_merge(K *sm, int len)
+__device__ __forceinline__ void cluster_merge(K *sm, int len, int per = T * E)
 {
     if constexpr (C > 1) {
         constexpr int CH = T * E;
@@ -504,7 +506,7 @@ __device__ __forceinline__ void cluster_merge(K *sm, int len)
             cl.sync();  // every chunk of the previous round is final
             const int g0 = r & ~(G - 1);
             const int h = G / 2;
-            const bool work = g0 * CH < len;
+            const bool work = g0 * per < len;
             K v[E];
             int na = 0;
             if (work) {

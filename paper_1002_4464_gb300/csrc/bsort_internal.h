@@ -40,13 +40,25 @@ cudaError_t launch_sublist_sort_pairs(int chunk, int ctas, const void *keys_in,
 // (grid = max_units clusters, surplus clusters exit) and write the first n
 // positions of the result.  With units == nullptr the whole input [0, n)
 // is one unit read from src (raw keys, transformed on load).
+// Where Step 9 reads its items: either a materialised relocated array
+// (src_k/src_v, Step 8 run before), or, with runs != nullptr, straight from
+// the sorted sublists: position y of the relocated order lies in the
+// bucket-major run q (offsets[q] <= y < offsets[q+1]) of sublist i = q mod m,
+// at rank srcb[q] + (y - offsets[q]).
+struct GatherSrc {
+    const uint32_t *offsets = nullptr;  // l_q, runs + 1 words
+    const uint32_t *srcb = nullptr;     // c_i(j-1) per run q = j*m + i
+    const uint32_t *blk = nullptr;      // run index per kBlockItems positions
+    uint32_t m = 0, t = 0, runs = 0;
+};
+
 cudaError_t launch_bucket_sort_keys(int chunk, int ctas, const void *src_k, const uint32_t *units,
                                     uint32_t max_units, uint64_t n, uint64_t n_pad, int is_f32,
-                                    void *out_k, int *err, cudaStream_t st);
+                                    void *out_k, int *err, const GatherSrc &g, cudaStream_t st);
 cudaError_t launch_bucket_sort_pairs(int chunk, int ctas, const void *src_k, const void *src_v,
                                      const uint32_t *units, uint32_t max_units, uint64_t n,
                                      uint64_t n_pad, int is_f32, int val_bytes, void *out_k,
-                                     void *out_v, int *err, cudaStream_t st);
+                                     void *out_v, int *err, const GatherSrc &g, cudaStream_t st);
 
 // Step 4 (chunks): sort the n_rec records of src in chunks of kRecordChunk
 // into dst (which holds n_pad = chunks * kRecordChunk records, the tail
@@ -67,7 +79,7 @@ cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t m, uint32_t
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
                                 const uint64_t *spl, uint32_t t, uint32_t s,
                                 uint32_t m, uint32_t *counts, uint32_t *cum,
-                                cudaStream_t st);
+                                uint32_t *srcb, cudaStream_t st);
 
 // Step 7: exclusive scan of n_items uint32 counts (decoupled look-back);
 // status must hold ceil(n_items / kScanChunk) words and ticket one word,
@@ -84,6 +96,15 @@ cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v,
                             const uint32_t *cum, const uint32_t *offsets,
                             uint32_t t, uint32_t s, uint32_t m, int val_bytes,
                             uint32_t *reloc_k, void *reloc_v, int *err, cudaStream_t st);
+
+// Positions per entry of the run index used by Step 9's gathering load.
+constexpr int kBlockItems = 1024;
+
+// Run index for the gathering load of Step 9: blk[b] = bucket-major run
+// containing position b*kBlockItems of the relocated order; also writes
+// offsets[runs] = n_pad (offsets must hold runs + 1 words).
+cudaError_t launch_block_index(uint32_t *offsets, uint32_t runs, uint32_t n_pad, uint32_t *blk,
+                               cudaStream_t st);
 
 // Step 9 units: pack consecutive buckets into units of at most Q items;
 // units holds 1 + 2*s words (count, then begin/end pairs).

@@ -176,7 +176,8 @@ template <int T>
 __global__ void __launch_bounds__(T)
 k_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ samples,
                const uint64_t *__restrict__ spl, uint32_t t, uint32_t s, uint32_t m,
-               uint32_t *__restrict__ counts, uint32_t *__restrict__ cum)
+               uint32_t *__restrict__ counts, uint32_t *__restrict__ cum,
+               uint32_t *__restrict__ srcb)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t *s_samp = reinterpret_cast<uint64_t *>(smem_raw);
@@ -216,6 +217,7 @@ k_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict_
         const uint32_t prev = j ? s_c[j - 1] : 0u;
         counts[(uint64_t)j * m + i] = c - prev;
         cum[(uint64_t)i * s + j] = c;
+        srcb[(uint64_t)j * m + i] = prev;  // run A_ij starts at rank c_i(j-1)
     }
 }
 
@@ -518,6 +520,27 @@ k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t s, uint3
     if (tid == 0) units[0] = s_total;
 }
 
+// Run index of every block of kBlockItems positions of the (virtual)
+// relocated array: blk[b] = the bucket-major run q = j*m + i containing
+// position b*kBlockItems (last q with l_q <= position; runs are in position
+// order, empty runs share their start with the next one).  Also writes the
+// sentinel l_{m*s} = n'.
+__global__ void k_block_index(uint32_t *__restrict__ offsets, uint32_t runs, uint32_t n_pad,
+                              uint32_t *__restrict__ blk, uint32_t nblk)
+{
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b == 0) offsets[runs] = n_pad;
+    if (b >= nblk) return;
+    const uint32_t y = b * (uint32_t)kBlockItems;
+    uint32_t lo = 0, hi = runs - 1;  // last q in [0, runs) with offsets[q] <= y
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= y) lo = mid;
+        else hi = mid - 1;
+    }
+    blk[b] = lo;
+}
+
 // ============================================================ launch wrappers
 int smem_bytes_for_cap(int cap, bool pairs)
 {
@@ -570,11 +593,12 @@ cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t m, uint32_t
 
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
                                 const uint64_t *spl, uint32_t t, uint32_t s, uint32_t m,
-                                uint32_t *counts, uint32_t *cum, cudaStream_t st)
+                                uint32_t *counts, uint32_t *cum, uint32_t *srcb,
+                                cudaStream_t st)
 {
     const int sm = (int)(s * 12);
     if (sm > 96 * 1024) return cudaErrorInvalidValue;
-    k_sample_index<256><<<m, 256, sm, st>>>(tiles_k, samples, spl, t, s, m, counts, cum);
+    k_sample_index<256><<<m, 256, sm, st>>>(tiles_k, samples, spl, t, s, m, counts, cum, srcb);
     return cudaGetLastError();
 }
 
@@ -596,6 +620,14 @@ cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const 
     k_relocate<256, TG, BB><<<grid, 256, 0, st>>>(tiles_k, tiles_v, cum, offsets, t, s, m,
                                                    (uint64_t)m * t, val_bytes, reloc_k, reloc_v,
                                                    err);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_block_index(uint32_t *offsets, uint32_t runs, uint32_t n_pad, uint32_t *blk,
+                               cudaStream_t st)
+{
+    const uint32_t nblk = (n_pad + kBlockItems - 1) / kBlockItems;
+    k_block_index<<<(nblk + 255) / 256, 256, 0, st>>>(offsets, runs, n_pad, blk, nblk);
     return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 #pragma once
 
 #include "bsort_device.cuh"
+#include "bsort_internal.h"
 
 namespace bsort {
 
@@ -90,15 +91,24 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
 }
 
 // ============================================================ Step 9
-// Cluster u sorts unit u = [units[1+2u], units[2+2u]) of the relocated array
+// Cluster u sorts unit u = [units[1+2u], units[2+2u]) of the relocated order
 // (consecutive whole buckets, at most C*T*E items) and writes the positions
 // below n of the result.  With units == nullptr there is one unit, [0, n),
 // read from the caller's input (raw keys, transformed on load).
+//
+// The unit's items are read either from a materialised relocated array
+// (src_k / src_v) or, when g.offsets != nullptr, gathered straight from the
+// sorted sublists (Step 8 fused into this load): every lane walks the
+// bucket-major runs as its position grows.  Pair units then sort
+// key << 32 | (position in the sorted-sublist array), which orders equal
+// keys by original index exactly as the relocated order does, and fetch
+// each value from that position.
 template <int T, int E, bool PAIRS, int C>
 __global__ void __launch_bounds__(T, 1)
 k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
               const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
-              int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v, int *err)
+              int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v, int *err,
+              GatherSrc g)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
     constexpr int CH = T * E;
@@ -110,6 +120,7 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
     const uint32_t u = blockIdx.x / C;
     const int r = (int)(blockIdx.x % C);
     const bool direct = units == nullptr;
+    const bool gather = g.offsets != nullptr;
     uint64_t L = 0, R = n;
     if (!direct) {
         if (u >= units[0]) return;  // fewer units than clusters (uniform per cluster)
@@ -123,22 +134,73 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
     }
     if (len64 == 0) return;
     const int len = (int)len64;
-    const int off = r * CH;
+    const int off = r * CH;  // ranks of the sorted unit this CTA writes
+    // the unit's real items are spread evenly over the cluster's CTAs, so
+    // that padding (skipped by whole warps) is shared by all of them
+    const int per = C == 1 ? CH : (len + C - 1) / C;
+    const int ustart = r * per;
+    const int uend = min(ustart + per, len);
     K v[E];
+    if (!gather) {
 #pragma unroll
-    for (int k = 0; k < E; ++k) {
-        const int x = off + wb_pos<E>(warp, lane, k);
-        uint32_t key = 0xFFFFFFFFu;
-        if (x < len) {
-            key = src_k[L + x];
-            if (direct && is_f32) key = f32_encode(key);
+        for (int k = 0; k < E; ++k) {
+            const int x = ustart + wb_pos<E>(warp, lane, k);
+            uint32_t key = 0xFFFFFFFFu;
+            uint32_t idx = 0xFFFFFFFFu;  // pads sort after every real item
+            if (x < uend) {
+                key = src_k[L + x];
+                if (direct && is_f32) key = f32_encode(key);
+                idx = (uint32_t)x;
+            }
+            if constexpr (PAIRS) v[k] = ((uint64_t)key << 32) | idx;
+            else v[k] = (K)key;
         }
-        if constexpr (PAIRS) v[k] = ((uint64_t)key << 32) | (uint32_t)x;
-        else v[k] = (K)key;
+    } else {
+        // lane's first position, and the run containing it: search the runs
+        // of its block and the next (positions of a warp span < 2 blocks)
+        const uint32_t y0 = (uint32_t)(L + ustart + wb_pos<E>(warp, lane, 0));
+        uint32_t q = 0;
+        if (ustart + wb_pos<E>(warp, 0, 0) < uend) {  // the warp holds real items
+            const uint32_t wy = (uint32_t)(L + ustart + wb_pos<E>(warp, 0, 0));
+            const uint32_t nblk = (uint32_t)((n_pad + kBlockItems - 1) / kBlockItems);
+            const uint32_t b = wy / (uint32_t)kBlockItems;  // < nblk since wy < R <= n_pad
+            uint32_t lo = g.blk[b];
+            uint32_t hi = b + 2 < nblk ? g.blk[b + 2] : g.runs - 1;
+            while (lo < hi) {  // last q with offsets[q] <= y0
+                const uint32_t mid = (lo + hi + 1) >> 1;
+                if (g.offsets[mid] <= y0) lo = mid;
+                else hi = mid - 1;
+            }
+            q = lo;
+        }
+        uint32_t ti = q % g.m;  // sublist of run q
+        uint32_t rs = g.offsets[q], re = g.offsets[q + 1];
+        uint32_t base = ti * g.t + g.srcb[q];  // position of run q's first item
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int x = ustart + wb_pos<E>(warp, lane, k);
+            const uint32_t y = y0 + 32u * (uint32_t)k;
+            uint32_t key = 0xFFFFFFFFu;
+            uint32_t pos = 0xFFFFFFFFu;  // pads sort after every real item
+            if (x < uend) {
+                if (y >= re) {
+                    do {
+                        ++q;
+                        if (++ti == g.m) ti = 0;
+                        rs = re;
+                        re = g.offsets[q + 1];
+                    } while (y >= re);
+                    base = ti * g.t + g.srcb[q];
+                }
+                pos = base + (y - rs);
+                key = src_k[pos];
+            }
+            if constexpr (PAIRS) v[k] = ((uint64_t)key << 32) | pos;
+            else v[k] = (K)key;
+        }
     }
-    const int clen = len - off;
-    cta_sort<K, T, E>(v, sm, clen < 0 ? 0 : (clen > CH ? CH : clen));
-    cluster_merge<K, T, E, C>(sm, len);
+    cta_sort<K, T, E>(v, sm, uend > ustart ? uend - ustart : 0);
+    cluster_merge<K, T, E, C>(sm, len, per);
     const uint64_t lim64 = min((unsigned long long)len, (unsigned long long)(n > L ? n - L : 0));
     const int lim = (int)lim64;
 #pragma unroll 4
@@ -151,12 +213,13 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
             out_k[L + off + x] = key;
             if constexpr (PAIRS) {
                 const uint32_t idx = (uint32_t)((uint64_t)e & 0xFFFFFFFFull);
+                const uint64_t from = gather ? (uint64_t)idx : L + idx;
                 if (val_bytes == 4)
                     static_cast<uint32_t *>(out_v)[L + off + x] =
-                        static_cast<const uint32_t *>(src_v)[L + idx];
+                        static_cast<const uint32_t *>(src_v)[from];
                 else
                     static_cast<uint64_t *>(out_v)[L + off + x] =
-                        static_cast<const uint64_t *>(src_v)[L + idx];
+                        static_cast<const uint64_t *>(src_v)[from];
             }
         }
     }
@@ -220,14 +283,15 @@ template <int T, int E, bool PAIRS, int C>
 inline cudaError_t launch_bucket_sort_t(const void *src_k, const void *src_v,
                                         const uint32_t *units, uint32_t max_units, uint64_t n,
                                         uint64_t n_pad, int is_f32, int val_bytes, void *out_k,
-                                        void *out_v, int *err, cudaStream_t st)
+                                        void *out_v, int *err, const GatherSrc &g,
+                                        cudaStream_t st)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
     const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
     const unsigned grid = (units ? max_units : 1u) * C;
     return launch_maybe_cluster(k_bucket_sort<T, E, PAIRS, C>, grid, T, sm, C, st,
                                 static_cast<const uint32_t *>(src_k), src_v, units, n, n_pad,
-                                is_f32, val_bytes, static_cast<uint32_t *>(out_k), out_v, err);
+                                is_f32, val_bytes, static_cast<uint32_t *>(out_k), out_v, err, g);
 }
 
 }  // namespace bsort

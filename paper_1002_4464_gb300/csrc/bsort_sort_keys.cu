@@ -47,11 +47,11 @@ cudaError_t launch_sublist_sort_keys(int chunk, int ctas, const void *keys_in, u
 
 cudaError_t launch_bucket_sort_keys(int chunk, int ctas, const void *src_k, const uint32_t *units,
                                     uint32_t max_units, uint64_t n, uint64_t n_pad, int is_f32,
-                                    void *out_k, int *err, cudaStream_t st)
+                                    void *out_k, int *err, const GatherSrc &g, cudaStream_t st)
 {
 #define L(T_, E_, C_)                                                                        \
     return launch_bucket_sort_t<T_, E_, false, C_>(src_k, nullptr, units, max_units, n,      \
-                                                   n_pad, is_f32, 0, out_k, nullptr, err, st)
+                                                   n_pad, is_f32, 0, out_k, nullptr, err, g, st)
     if (ctas == 1) {
         switch (chunk) {
         case 2048: L(128, 16, 1);

@@ -49,11 +49,11 @@ cudaError_t launch_sublist_sort_pairs(int chunk, int ctas, const void *keys_in,
 cudaError_t launch_bucket_sort_pairs(int chunk, int ctas, const void *src_k, const void *src_v,
                                      const uint32_t *units, uint32_t max_units, uint64_t n,
                                      uint64_t n_pad, int is_f32, int val_bytes, void *out_k,
-                                     void *out_v, int *err, cudaStream_t st)
+                                     void *out_v, int *err, const GatherSrc &g, cudaStream_t st)
 {
 #define L(T_, E_, C_)                                                                          \
     return launch_bucket_sort_t<T_, E_, true, C_>(src_k, src_v, units, max_units, n, n_pad,    \
-                                                  is_f32, val_bytes, out_k, out_v, err, st)
+                                                  is_f32, val_bytes, out_k, out_v, err, g, st)
     if (ctas == 1) {
         switch (chunk) {
         case 2048: L(128, 16, 1);

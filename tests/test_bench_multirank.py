@@ -1,0 +1,50 @@
+"""The N > 1 path of bench.py: independent replicas, one per rank, whose
+job time is the slowest rank's (max over ranks) and whose throughput counts
+every rank's keys.  Run as two gloo ranks on the CPU."""
+import os
+import socket
+
+import pytest
+
+torch = pytest.importorskip("torch")
+import torch.distributed as dist  # noqa: E402
+import torch.multiprocessing as mp  # noqa: E402
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, out):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    local_ms = [12.5, 20.0][rank]
+    t = bench.job_time_ms(local_ms, world, torch.device("cpu"))
+    v = bench.job_throughput(1 << 28, world, 10, t)
+    out[rank] = (t, v)
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_max_time_and_whole_job_rate():
+    world = 2
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    mgr = ctx.Manager()
+    out = mgr.dict()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, out)) for r in range(world)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    for r in range(world):
+        t, v = out[r]
+        assert t == 20.0  # the slower rank's time
+        assert abs(v - (1 << 28) * 2 * 10 / 0.020 / 1e9) < 1e-6

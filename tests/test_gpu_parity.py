@@ -269,3 +269,76 @@ def test_large_auto_plans(n, kt):
         out = sorter.sort_keys(d, key_type="f32")
         sorter.sync()
         assert np.array_equal(out.cpu().numpy().view(np.uint32), np.sort(f).view(np.uint32))
+
+
+def _u32_as_i64(t):
+    return t.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+
+
+@pytest.mark.parametrize("dist", ["uniform", "staggered"])
+def test_full_size_2e28_u32(dist):
+    """The benchmark workload itself (2^28 uint32 keys, planner's plan): the
+    output equals an independent library sort (torch.sort) of the same keys,
+    element by element."""
+    n = 1 << 28
+    keys = synth.keys_u32_torch(dist, n, synth.seed_for(2, synth.DISTRIBUTIONS.index(dist)),
+                                device="cuda")
+    sorter = pkg.BucketSorter()
+    out = sorter.sort_keys(keys)
+    sorter.sync()
+    want = torch.sort(_u32_as_i64(keys)).values
+    assert torch.equal(_u32_as_i64(out), want)
+    sorter.close()
+
+
+@pytest.mark.parametrize("kind", ["zipf", "distinct16"])
+def test_full_size_2e27_pairs(kind):
+    """Key-value pairs at 2^27 (value = original index): keys equal an
+    independent sort, values are a permutation, and equal keys keep their
+    input order (stability), checked on every element."""
+    n = 1 << 27
+    seed = synth.seed_for(3, 0 if kind == "zipf" else 1)
+    k_np = synth.keys_zipf(n, seed) if kind == "zipf" else synth.keys_16distinct(n, seed)
+    keys = torch.from_numpy(k_np.view(np.int32)).cuda()
+    vals = torch.arange(n, dtype=torch.int32, device="cuda")
+    sorter = pkg.BucketSorter()
+    ok, ov = sorter.sort_pairs(keys, vals)
+    sorter.sync()
+    ok64, ov64 = _u32_as_i64(ok), ov.to(torch.int64)
+    assert torch.equal(ok64, torch.sort(_u32_as_i64(keys)).values)
+    # stable: (key, value) strictly increasing lexicographically
+    same = ok64[1:] == ok64[:-1]
+    assert bool((ov64[1:][same] > ov64[:-1][same]).all())
+    assert torch.equal(torch.sort(ov64).values, torch.arange(n, device="cuda"))
+    # every value points at an input item with the sorted key
+    assert torch.equal(_u32_as_i64(keys)[ov64], ok64)
+    sorter.close()
+
+
+@pytest.mark.parametrize("n,t,s,kind", [
+    ((1 << 22) + 5, 65536, 2048, "keys"),
+    (1 << 21, 131072, 1024, "pairs"),
+    ((1 << 20) + 333, 4096, 64, "pairs"),
+])
+def test_low_memory_equals_materialised(n, t, s, kind):
+    """Step 9 gathering its units straight from the runs A_ij (low-memory
+    mode) gives the same result as reading the materialised relocated array."""
+    keys = synth.keys_zipf(n, synth.seed_for(3, 7, t))
+    outs = []
+    for low in (True, False):
+        sorter = pkg.BucketSorter(tile=t, samples=s, low_memory=low)
+        if kind == "keys":
+            outs.append(_gpu_sort_keys(sorter, keys))
+        else:
+            vals = np.arange(n, dtype=np.uint32)
+            ok, ov = sorter.sort_pairs(_to_dev_u32(keys), _to_dev_u32(vals))
+            sorter.sync()
+            outs.append((ok.cpu().numpy().view(np.uint32), ov.cpu().numpy().view(np.uint32)))
+        sorter.close()
+    if kind == "keys":
+        assert np.array_equal(outs[0], outs[1])
+        assert np.array_equal(outs[0], np.sort(keys))
+    else:
+        wk, wv = oracle.textbook_sort(keys, "u32", vals=np.arange(n, dtype=np.uint32))
+        for ok, ov in outs:
+            assert np.array_equal(ok, wk) and np.array_equal(ov, wv)
