@@ -395,6 +395,8 @@ def run_ours(args):
             for _ in range(3):
                 one_step(kd)
             torch.cuda.synchronize()
+            sorter.sync()
+            sorter.kernel_times()  # drop the warm-up calls from the timing ring
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             reps = max(3, args.steps // 2)
@@ -404,9 +406,14 @@ def run_ours(args):
             b.record(stream)
             torch.cuda.synchronize()
             dms = a.elapsed_time(b) / reps
-            dists[dname] = {"ms_per_step": dms, "gkeys_s": args.n / (dms / 1e3) / 1e9}
+            sorter.sync()
+            kt, kc = sorter.kernel_times()
+            dk = {}
+            for name, ms in kt:
+                dk[name] = round(dk.get(name, 0.0) + ms / max(kc, 1), 4)
+            dists[dname] = {"ms_per_step": dms, "gkeys_s": args.n / (dms / 1e3) / 1e9,
+                            "per_kernel_ms": dk}
             del kd
-        sorter.kernel_times()
         rates = [v["ms_per_step"] for v in dists.values()]
         dists["spread"] = (max(rates) - min(rates)) / (sum(rates) / len(rates))
 

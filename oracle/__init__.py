@@ -48,7 +48,7 @@ def _load():
         lib.oracle_paper_sort.restype = ctypes.c_int
         lib.oracle_paper_sort.argtypes = [u64p, u64p, ctypes.c_uint64,
                                           ctypes.c_uint64, ctypes.c_uint64,
-                                          ctypes.c_uint64] + [u64p] * 13
+                                          ctypes.c_uint64, ctypes.c_uint64] + [u64p] * 13
         lib.oracle_textbook_sort.restype = ctypes.c_int
         lib.oracle_textbook_sort.argtypes = [u64p, u64p, ctypes.c_uint64,
                                              u64p, u64p]
@@ -117,23 +117,25 @@ def _from_u64_keys(k: np.ndarray, key_type: str) -> np.ndarray:
 
 def paper_sort(keys: np.ndarray, t: int, s: int, key_type: str = "u32",
                vals: Optional[np.ndarray] = None,
-               intermediates: bool = True) -> Dict[str, np.ndarray]:
+               intermediates: bool = True, b: int = 0) -> Dict[str, np.ndarray]:
     """Run Algorithm 1 on the CPU.  Returns the sorted keys (and values) and,
     if ``intermediates``, every intermediate of Steps 2-8 (in the transformed
-    key domain for float32)."""
+    key domain for float32).  ``b`` is the number of buckets (0: b = s, the
+    paper's choice)."""
     lib = _load()
     n = int(np.asarray(keys).size)
     k64 = _to_u64_keys(np.asarray(keys).ravel(), key_type)
     v64 = None if vals is None else np.ascontiguousarray(vals).astype(np.uint64)
     m = int(lib.oracle_num_sublists(n, t)) if n else 0
     npad = m * t
+    nb = b if b else s
     out_k = np.zeros(n, np.uint64)
     out_v = np.zeros(n, np.uint64) if vals is not None else None
     res: Dict[str, np.ndarray] = {}
     names = [("tile_keys", npad), ("tile_pos", npad), ("samp_keys", m * s),
-             ("samp_p", m * s), ("spl_keys", s), ("spl_p", s),
-             ("counts", m * s), ("offsets", m * s), ("reloc_keys", npad),
-             ("reloc_pos", npad), ("bucket_start", s + 1)]
+             ("samp_p", m * s), ("spl_keys", nb), ("spl_p", nb),
+             ("counts", m * nb), ("offsets", m * nb), ("reloc_keys", npad),
+             ("reloc_pos", npad), ("bucket_start", nb + 1)]
     bufs = []
     for name, size in names:
         if intermediates and n:
@@ -142,11 +144,11 @@ def paper_sort(keys: np.ndarray, t: int, s: int, key_type: str = "u32",
             bufs.append(arr)
         else:
             bufs.append(None)
-    rc = lib.oracle_paper_sort(_ptr(k64), _ptr(v64), n, t, s,
+    rc = lib.oracle_paper_sort(_ptr(k64), _ptr(v64), n, t, s, b,
                                KEY_MAX[key_type], _ptr(out_k), _ptr(out_v),
                                *[_ptr(b) for b in bufs])
     if rc != 0:
-        raise ValueError("oracle_paper_sort failed (n=%d t=%d s=%d)" % (n, t, s))
+        raise ValueError("oracle_paper_sort failed (n=%d t=%d s=%d b=%d)" % (n, t, s, b))
     res["keys"] = _from_u64_keys(out_k, key_type)
     if out_v is not None:
         res["vals"] = out_v.astype(np.asarray(vals).dtype)
@@ -173,10 +175,12 @@ def textbook_sort(keys: np.ndarray, key_type: str = "u32",
     return keys_out, out_v.astype(np.asarray(vals).dtype)
 
 
-def bucket_bound(n_padded: int, m: int, s: int) -> int:
-    """Upper bound on |B_j| for the sampling rule above: n'/s + (m-1)(w-1),
-    derived from the positions of the regular samples (tighter than the
-    paper's 2n/s, Section 4, Step 8 discussion)."""
+def bucket_bound(n_padded: int, m: int, s: int, b: int = 0) -> int:
+    """Upper bound on |B_j| for the sampling rule above: n'/s + (m-1)(w-1)
+    for b = s, derived from the positions of the regular samples (tighter
+    than the paper's 2n/s, Section 4, Step 8 discussion); with b buckets,
+    ceil(m*s/b)*w + (m-1)(w-1)."""
     t = n_padded // m
     w = t // s
-    return n_padded // s + (m - 1) * (w - 1)
+    b = b or s
+    return -(-(m * s) // b) * w + (m - 1) * (w - 1)

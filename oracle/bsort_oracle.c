@@ -24,7 +24,10 @@
  *     s equal chunks).
  *   - Step 5 takes the global samples (splitters) g_j = S[(j+1)*m - 1],
  *     j = 0..s-1, from the sorted sample list S; g_{s-1} is the global
- *     maximum, so the s splitters define exactly s buckets.
+ *     maximum, so the s splitters define exactly s buckets.  As an extension
+ *     the number of buckets b may differ from s: then g_j = S[r_j] with
+ *     r_j = floor((j+1)*m*s/b) - 1, j = 0..b-1 (equidistant in the sample
+ *     list; b = s gives the paper's choice).
  *   - Bucket j of sublist i holds the items x with g_{j-1} < x <= g_j in
  *     composite order (g_{-1} = minus infinity).
  *   - n need not be a multiple of t: the input is padded virtually to
@@ -159,23 +162,24 @@ uint64_t oracle_num_sublists(uint64_t n, uint64_t t)
  *
  *   keys, vals : n input items (vals may be NULL: keys only)
  *   t          : sublist size n/m of Step 1 (a multiple of s)
- *   s          : samples per sublist (Step 3) = global samples = buckets
+ *   s          : samples per sublist (Step 3)
+ *   b          : global samples = buckets (Step 5); 0 means b = s (paper)
  *   key_max    : the largest key of the key type (pad sentinel key)
  *   out_keys, out_vals : n sorted items (out_vals may be NULL)
  *
  * Optional intermediates (NULL to skip), with m = ceil(n/t), n' = m*t:
  *   tile_keys, tile_pos   [n']   Step 2: sorted sublists, sublist-major
  *   samp_keys, samp_p     [m*s]  Step 3: samples, sublist-major, p = i*t + r
- *   spl_keys, spl_p       [s]    Step 5: global samples g_0..g_{s-1}
- *   counts                [m*s]  Step 6: a_ij stored bucket-major a[j*m + i]
- *   offsets               [m*s]  Step 7: l_ij stored bucket-major l[j*m + i]
- *   reloc_keys, reloc_pos [n']   Step 8: relocated array B_1 ... B_s
- *   bucket_start          [s+1]  start of B_j in the relocated array; [s] = n'
+ *   spl_keys, spl_p       [b]    Step 5: global samples g_0..g_{b-1}
+ *   counts                [m*b]  Step 6: a_ij stored bucket-major a[j*m + i]
+ *   offsets               [m*b]  Step 7: l_ij stored bucket-major l[j*m + i]
+ *   reloc_keys, reloc_pos [n']   Step 8: relocated array B_1 ... B_b
+ *   bucket_start          [b+1]  start of B_j in the relocated array; [b] = n'
  *
  * Returns 0, or -1 on bad parameters / allocation failure.
  */
 int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
-                      uint64_t t, uint64_t s, uint64_t key_max,
+                      uint64_t t, uint64_t s, uint64_t b, uint64_t key_max,
                       uint64_t *out_keys, uint64_t *out_vals,
                       uint64_t *tile_keys, uint64_t *tile_pos,
                       uint64_t *samp_keys, uint64_t *samp_p,
@@ -191,13 +195,15 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
     const uint64_t m = (n + t - 1) / t;
     const uint64_t np = m * t;
     const uint64_t w = t / s;
+    if (b == 0) b = s;
+    if (b > m * s) return -1;
 
     oelem_t *A = (oelem_t *)malloc(np * sizeof(oelem_t));
     orec_t *S = (orec_t *)malloc(m * s * sizeof(orec_t));
-    orec_t *G = (orec_t *)malloc(s * sizeof(orec_t));
-    uint64_t *c = (uint64_t *)malloc(m * (s + 1) * sizeof(uint64_t));
-    uint64_t *a = (uint64_t *)malloc(m * s * sizeof(uint64_t));
-    uint64_t *l = (uint64_t *)malloc(m * s * sizeof(uint64_t));
+    orec_t *G = (orec_t *)malloc(b * sizeof(orec_t));
+    uint64_t *c = (uint64_t *)malloc(m * (b + 1) * sizeof(uint64_t));
+    uint64_t *a = (uint64_t *)malloc(m * b * sizeof(uint64_t));
+    uint64_t *l = (uint64_t *)malloc(m * b * sizeof(uint64_t));
     oelem_t *B = (oelem_t *)malloc(np * sizeof(oelem_t));
     if (!A || !S || !G || !c || !a || !l || !B) goto fail;
 
@@ -235,12 +241,13 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
     /* Step 4: sort all s*m samples. */
     if (msort_recs(S, m * s)) goto fail;
 
-    /* Step 5: s equidistant global samples g_j = S[(j+1)m - 1]. */
-    for (uint64_t j = 0; j < s; ++j) G[j] = S[(j + 1) * m - 1];
+    /* Step 5: b equidistant global samples g_j = S[r_j],
+     * r_j = floor((j+1)*m*s/b) - 1 (= (j+1)m - 1 when b = s). */
+    for (uint64_t j = 0; j < b; ++j) G[j] = S[(j + 1) * m * s / b - 1];
     if (spl_keys)
-        for (uint64_t j = 0; j < s; ++j) spl_keys[j] = G[j].key;
+        for (uint64_t j = 0; j < b; ++j) spl_keys[j] = G[j].key;
     if (spl_p)
-        for (uint64_t j = 0; j < s; ++j) spl_p[j] = G[j].p;
+        for (uint64_t j = 0; j < b; ++j) spl_p[j] = G[j].p;
 
     /* Step 6: sample indexing.  c[i][j+1] = number of items of sorted
      * sublist i that are <= g_j in composite order, where the item at rank r
@@ -248,8 +255,8 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
      * sublist is sorted in that order.  c[i][0] = 0.  Bucket A_ij is ranks
      * [c[i][j], c[i][j+1]) and a_ij is its size. */
     for (uint64_t i = 0; i < m; ++i) {
-        c[i * (s + 1) + 0] = 0;
-        for (uint64_t j = 0; j < s; ++j) {
+        c[i * (b + 1) + 0] = 0;
+        for (uint64_t j = 0; j < b; ++j) {
             uint64_t lo = 0, hi = t; /* first rank whose item is > g_j */
             while (lo < hi) {
                 uint64_t mid = lo + (hi - lo) / 2;
@@ -259,28 +266,28 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
                 if (rec_less(&G[j], &item)) hi = mid;
                 else lo = mid + 1;
             }
-            c[i * (s + 1) + j + 1] = lo;
+            c[i * (b + 1) + j + 1] = lo;
         }
-        for (uint64_t j = 0; j < s; ++j)
-            a[j * m + i] = c[i * (s + 1) + j + 1] - c[i * (s + 1) + j];
+        for (uint64_t j = 0; j < b; ++j)
+            a[j * m + i] = c[i * (b + 1) + j + 1] - c[i * (b + 1) + j];
     }
-    if (counts) memcpy(counts, a, m * s * sizeof(uint64_t));
+    if (counts) memcpy(counts, a, m * b * sizeof(uint64_t));
 
     /* Step 7: prefix sum over a_11..a_m1, a_12..a_m2, ..., a_1s..a_ms
      * (bucket-major), exclusive: l_ij = start of A_ij in the final order. */
     {
         uint64_t run = 0;
-        for (uint64_t x = 0; x < m * s; ++x) {
+        for (uint64_t x = 0; x < m * b; ++x) {
             l[x] = run;
             run += a[x];
         }
     }
-    if (offsets) memcpy(offsets, l, m * s * sizeof(uint64_t));
+    if (offsets) memcpy(offsets, l, m * b * sizeof(uint64_t));
 
     /* Step 8: move every bucket A_ij to l_ij; B_j = A_1j u ... u A_mj. */
     for (uint64_t i = 0; i < m; ++i)
-        for (uint64_t j = 0; j < s; ++j) {
-            uint64_t src = i * t + c[i * (s + 1) + j];
+        for (uint64_t j = 0; j < b; ++j) {
+            uint64_t src = i * t + c[i * (b + 1) + j];
             uint64_t len = a[j * m + i];
             for (uint64_t q = 0; q < len; ++q) B[l[j * m + i] + q] = A[src + q];
         }
@@ -289,14 +296,14 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
     if (reloc_pos)
         for (uint64_t x = 0; x < np; ++x) reloc_pos[x] = B[x].pos;
     if (bucket_start) {
-        for (uint64_t j = 0; j < s; ++j) bucket_start[j] = l[j * m + 0];
-        bucket_start[s] = np;
+        for (uint64_t j = 0; j < b; ++j) bucket_start[j] = l[j * m + 0];
+        bucket_start[b] = np;
     }
 
     /* Step 9: sort every sublist B_j. */
-    for (uint64_t j = 0; j < s; ++j) {
+    for (uint64_t j = 0; j < b; ++j) {
         uint64_t lo = l[j * m + 0];
-        uint64_t hi = (j + 1 < s) ? l[(j + 1) * m + 0] : np;
+        uint64_t hi = (j + 1 < b) ? l[(j + 1) * m + 0] : np;
         if (msort_elems(B + lo, hi - lo)) goto fail;
     }
 

@@ -261,8 +261,8 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
         const bool reloc = !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
         I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
-                        1 /*S6*/ + 1 /*S7*/ + (reloc ? 1 : 0) /*S8*/ + 1 /*units*/ +
-                        (reloc ? 0 : 1) /*run index*/ + 1 /*S9*/;
+                        1 /*S6*/ + 1 /*S7*/ + 1 /*run index*/ + (reloc ? 1 : 0) /*S8*/ +
+                        1 /*units*/ + 1 /*S9*/;
     }
 
     // workspace layout
@@ -473,9 +473,10 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     // Step 8: materialised, unless BSORT_FLAG_LOW_MEMORY fuses it into the
     // load of Step 9, which then gathers every unit from the runs A_ij
     GatherSrc g;
+    SEQ(launch_block_index(offsets, P.n_rec, (uint32_t)I.n_padded, blk, st), "step8_run_index");
     if (P.relocate) {
-        SEQ(launch_relocate(tiles_k, tiles_v, cum, offsets, I.t, I.s, I.m, (int)vb, reloc_k,
-                            reloc_v, err, st),
+        SEQ(launch_relocate(tiles_k, tiles_v, offsets, srcb, blk, I.t, I.m, P.n_rec,
+                            (uint32_t)I.n_padded, (int)vb, reloc_k, reloc_v, st),
             "step8_relocate");
     }
     // Step 9: buckets packed into units of at most unit_capacity items
@@ -484,8 +485,6 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
                           units, err, st),
         "step9_pack_units");
     if (!P.relocate) {
-        SEQ(launch_block_index(offsets, P.n_rec, (uint32_t)I.n_padded, blk, st),
-            "step9_run_index");
         g.offsets = offsets;
         g.srcb = srcb;
         g.blk = blk;

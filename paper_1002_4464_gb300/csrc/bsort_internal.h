@@ -91,11 +91,13 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
 constexpr int kRelocateSmemMax = 220 * 1024;
 constexpr int kRelocPart = 8192;  // sublist items per Step-8 CTA
 
-// Step 8: move every run A_ij to l_ij.
-cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v,
-                            const uint32_t *cum, const uint32_t *offsets,
-                            uint32_t t, uint32_t s, uint32_t m, int val_bytes,
-                            uint32_t *reloc_k, void *reloc_v, int *err, cudaStream_t st);
+// Step 8: fill the relocated array B_1 ... B_s position by position from
+// the runs A_ij (offsets: l in bucket-major order with the sentinel
+// offsets[runs] = n_pad; srcb: run starts c_i(j-1); blk: run index).
+cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const uint32_t *offsets,
+                            const uint32_t *srcb, const uint32_t *blk, uint32_t t, uint32_t m,
+                            uint32_t runs, uint32_t n_pad, int val_bytes, uint32_t *reloc_k,
+                            void *reloc_v, cudaStream_t st);
 
 // Positions per entry of the run index used by Step 9's gathering load.
 constexpr int kBlockItems = 1024;

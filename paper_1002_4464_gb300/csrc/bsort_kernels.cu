@@ -168,56 +168,94 @@ __global__ void k_select_splitters(const uint64_t *__restrict__ sorted, uint32_t
 }
 
 // ============================================================ Step 6
-// One CTA per sublist i.  The sublist's own s samples (sorted, every w-th
-// item) index the sorted sublist: for splitter g, q = #samples <= g gives
-// c in [q*w, q*w + w - 1], and a binary search over the w - 1 items of that
-// window gives c exactly.  Items compare as key << 32 | (i*t + r).
+// CTA x handles sublist i = x / gpt for a block of splitters; thread k of it
+// a contiguous run of JB splitters j0 .. j0+JB-1 (and j0-1 for the count of
+// the first).  The sublist's own s samples (every w-th item, sorted) index
+// the sorted sublist: q = #samples <= g_j (found by a binary search for j0,
+// then a forward walk, since q grows with j) gives c_ij in
+// [q*w, q*w + w - 1]; for w <= 64 the w items of that window (16-byte
+// aligned when w is a multiple of 4) are read with independent 16-byte
+// loads and the ones <= g_j counted, otherwise a binary search over the
+// window finds the count.  Items compare as key << 32 | (i*t + r).
+__device__ __forceinline__ uint32_t window_count(const uint32_t *__restrict__ tiles_k,
+                                                 uint64_t base, uint32_t q, uint32_t w,
+                                                 uint32_t t, uint32_t s, uint64_t g)
+{
+    if (q >= s) return t;
+    const uint32_t r0 = q * w;
+    const uint32_t gk = (uint32_t)(g >> 32);
+    const uint32_t gp = (uint32_t)g;
+    uint32_t cnt = 0;
+    if (w <= 64 && (w & 3) == 0) {  // 16-byte aligned: base and q*w are multiples of 4
+        const uint4 *p = reinterpret_cast<const uint4 *>(tiles_k + base + r0);
+        for (uint32_t v = 0; v < w / 4; ++v) {
+            const uint4 x = p[v];
+            const uint32_t pos = (uint32_t)(base + r0 + 4 * v);
+            cnt += (x.x < gk || (x.x == gk && pos + 0 <= gp)) ? 1u : 0u;
+            cnt += (x.y < gk || (x.y == gk && pos + 1 <= gp)) ? 1u : 0u;
+            cnt += (x.z < gk || (x.z == gk && pos + 2 <= gp)) ? 1u : 0u;
+            cnt += (x.w < gk || (x.w == gk && pos + 3 <= gp)) ? 1u : 0u;
+        }
+        return r0 + cnt;
+    }
+    uint32_t a = r0, b = r0 + w - 1;  // the item at rank b is > g
+    while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        const uint64_t item = ((uint64_t)tiles_k[base + mid] << 32) | (uint32_t)(base + mid);
+        if (item <= g) a = mid + 1;
+        else b = mid;
+    }
+    return a;
+}
+
 template <int T>
 __global__ void __launch_bounds__(T)
 k_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ samples,
                const uint64_t *__restrict__ spl, uint32_t t, uint32_t s, uint32_t m,
                uint32_t *__restrict__ counts, uint32_t *__restrict__ cum,
-               uint32_t *__restrict__ srcb)
+               uint32_t *__restrict__ srcb, uint32_t jb)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t *s_samp = reinterpret_cast<uint64_t *>(smem_raw);
-    uint32_t *s_c = reinterpret_cast<uint32_t *>(s_samp + s);
-    const uint32_t i = blockIdx.x;
+    const uint32_t gpt = (s + T * jb - 1) / (T * jb);  // CTAs per sublist
+    const uint32_t i = blockIdx.x / gpt;
+    const uint32_t j0 = ((blockIdx.x % gpt) * T + threadIdx.x) * jb;
+    if (j0 >= s) return;
+    const uint32_t j1 = min(j0 + jb, s);
     const uint64_t base = (uint64_t)i * t;
     const uint32_t w = t / s;
-    for (uint32_t k = threadIdx.x; k < s; k += T) s_samp[k] = samples[(uint64_t)i * s + k];
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < s; j += T) {
-        const uint64_t g = spl[j];
-        uint32_t lo = 0, hi = s;
-        while (lo < hi) {
-            uint32_t mid = (lo + hi) >> 1;
-            if (s_samp[mid] <= g) lo = mid + 1;
-            else hi = mid;
-        }
-        const uint32_t q = lo;
-        uint32_t c;
-        if (q == s) {
-            c = t;
-        } else {
-            uint32_t a = q * w, b = q * w + w - 1;  // item at rank b is > g
-            while (a < b) {
-                uint32_t mid = (a + b) >> 1;
-                uint64_t item = ((uint64_t)tiles_k[base + mid] << 32) | (uint32_t)(base + mid);
-                if (item <= g) a = mid + 1;
-                else b = mid;
-            }
-            c = a;
-        }
-        s_c[j] = c;
+    const uint64_t *smp = samples + (uint64_t)i * s;
+    // q for the first splitter considered (j0 - 1, or j0 when j0 = 0)
+    const uint32_t jf = j0 ? j0 - 1 : 0;
+    uint64_t g = spl[jf];
+    uint32_t lo = 0, hi = s;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (smp[mid] <= g) lo = mid + 1;
+        else hi = mid;
     }
-    __syncthreads();
-    for (uint32_t j = threadIdx.x; j < s; j += T) {
-        const uint32_t c = s_c[j];
-        const uint32_t prev = j ? s_c[j - 1] : 0u;
+    uint32_t q = lo;
+    uint32_t prev = j0 ? window_count(tiles_k, base, q, w, t, s, g) : 0u;
+    for (uint32_t j = j0; j < j1; ++j) {
+        g = spl[j];
+        if (q < s && smp[q] <= g) {  // q grows: gallop, then binary search
+            uint32_t step = 1, lo2 = q + 1, hi2 = q + 1;
+            while (hi2 < s && smp[hi2] <= g) {
+                lo2 = hi2 + 1;
+                step <<= 1;
+                hi2 = min(s, q + step);
+            }
+            hi2 = min(hi2, s);
+            while (lo2 < hi2) {  // first index in [lo2, hi2) with smp > g
+                const uint32_t mid = (lo2 + hi2) >> 1;
+                if (smp[mid] <= g) lo2 = mid + 1;
+                else hi2 = mid;
+            }
+            q = lo2;
+        }
+        const uint32_t c = window_count(tiles_k, base, q, w, t, s, g);
         counts[(uint64_t)j * m + i] = c - prev;
         cum[(uint64_t)i * s + j] = c;
         srcb[(uint64_t)j * m + i] = prev;  // run A_ij starts at rank c_i(j-1)
+        prev = c;
     }
 }
 
@@ -327,89 +365,56 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 }
 
 // ============================================================ Step 8
-// Relocation organised by destination.  CTA (g, b) moves the runs A_ij of
-// the TG sublists i in [g*TG, (g+1)*TG) and the BB buckets j in
-// [b*BB, (b+1)*BB).  Because offsets are bucket-major, the runs of bucket j
-// from these TG consecutive sublists are adjacent in the relocated array:
-// one contiguous destination range per bucket.  A warp walks that range with
-// its lanes on consecutive destinations (long coalesced stores) and reads
-// each item from its sorted sublist; a lane advances its sublist index as
-// its destination passes each run.
-template <int T, int TG, int BB>
-__global__ void __launch_bounds__(T)
+// Relocation by destination: CTA c fills positions [c*kRelocPart,
+// (c+1)*kRelocPart) of the relocated array, so every CTA moves the same
+// number of items whatever the key distribution.  Position y lies in the
+// bucket-major run q = j*m + i (offsets[q] <= y < offsets[q+1]) of sublist
+// i, at rank srcb[q] + (y - offsets[q]).  Each warp covers kBlockItems
+// consecutive positions with its lanes on consecutive positions (coalesced
+// stores); a lane finds its first run from the run index of its block and
+// then advances its run as its position grows.
+template <int T>
+__global__ void __launch_bounds__(T, 4)
 k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_v,
-           const uint32_t *__restrict__ cum, const uint32_t *__restrict__ offsets,
-           uint32_t t, uint32_t s, uint32_t m, uint64_t n_pad, int val_bytes,
-           uint32_t *__restrict__ reloc_k, void *__restrict__ reloc_v, int *err)
+           const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ srcb,
+           const uint32_t *__restrict__ blk, uint32_t t, uint32_t m, uint32_t runs,
+           uint32_t n_pad, int val_bytes, uint32_t *__restrict__ reloc_k,
+           void *__restrict__ reloc_v)
 {
-    __shared__ uint32_t s_c[TG][BB + 1];   // c_i(j-1) for j = j0 .. j0+BB (column 0: j0-1)
-    __shared__ uint32_t s_l[BB][TG];       // l_ij
-    __shared__ uint32_t s_rs[BB][TG + 1];  // run start within the bucket's range; [TG] = total
-    __shared__ uint32_t s_src[BB][TG];     // run start within its sublist, c_i(j-1)
-    const int tid = threadIdx.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    const uint32_t i0 = blockIdx.x * TG;
-    const uint32_t j0 = blockIdx.y * BB;
-    const uint32_t ni = min((uint32_t)TG, m - i0);
-    const uint32_t nj = min((uint32_t)BB, s - j0);
-    for (uint32_t idx = tid; idx < TG * (BB + 1); idx += T) {
-        const uint32_t i = idx / (BB + 1), jj = idx % (BB + 1);
-        uint32_t v = 0;
-        if (i < ni) {
-            const uint32_t j = j0 + jj;  // holds c_i(j-1), i.e. cum column j-1
-            if (j > 0 && j - 1 < s) v = cum[(uint64_t)(i0 + i) * s + j - 1];
-            else if (j > 0) v = t;
-        }
-        s_c[i][jj] = v;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t wy = blockIdx.x * (uint32_t)kRelocPart + (uint32_t)warp * kBlockItems;
+    if (wy >= n_pad) return;
+    const uint32_t b = wy / kBlockItems;
+    const uint32_t nblk = (n_pad + kBlockItems - 1) / kBlockItems;
+    uint32_t y = wy + lane;
+    uint32_t lo = blk[b];
+    uint32_t hi = b + 1 < nblk ? blk[b + 1] : runs - 1;
+    while (lo < hi) {  // last run q with offsets[q] <= y
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= y) lo = mid;
+        else hi = mid - 1;
     }
-    for (uint32_t idx = tid; idx < BB * TG; idx += T) {
-        const uint32_t jj = idx / TG, i = idx % TG;
-        s_l[jj][i] = (i < ni && jj < nj) ? offsets[(uint64_t)(j0 + jj) * m + i0 + i] : 0u;
-    }
-    __syncthreads();
-    for (uint32_t jj = tid; jj < BB; jj += T) {
-        uint32_t acc = 0;
-        for (uint32_t i = 0; i < TG; ++i) {
-            uint32_t len = 0, src = 0;
-            if (i < ni && jj < nj) {
-                src = s_c[i][jj];
-                const uint32_t end = s_c[i][jj + 1];
-                len = end - src;
-                const uint64_t want = (uint64_t)s_l[jj][0] + acc;  // runs of a bucket are adjacent
-                if (end < src || end > t || s_l[jj][i] != want || want + len > n_pad) {
-                    set_error(err, DEV_INTERNAL);  // never for a valid plan
-                    len = 0;
-                }
-            }
-            s_rs[jj][i] = acc;
-            s_src[jj][i] = src;
-            acc += len;
+    uint32_t q = lo;
+    uint32_t ti = q % m;
+    uint32_t rs = offsets[q], re = offsets[q + 1];
+    uint32_t base = ti * t + srcb[q];
+    const uint32_t yend = min(wy + (uint32_t)kBlockItems, n_pad);
+    for (; y < yend; y += 32) {
+        if (y >= re) {
+            do {
+                ++q;
+                if (++ti == m) ti = 0;
+                rs = re;
+                re = offsets[q + 1];
+            } while (y >= re);
+            base = ti * t + srcb[q];
         }
-        s_rs[jj][TG] = acc;
-    }
-    __syncthreads();
-    for (uint32_t jj = warp; jj < nj; jj += T / 32) {
-        const uint32_t total = s_rs[jj][TG];
-        const uint64_t D = s_l[jj][0];
-        uint32_t i = 0;
-        {   // last i with s_rs[jj][i] <= lane (runs may be empty)
-            uint32_t lo = 0, hi = TG - 1;
-            while (lo < hi) {
-                uint32_t mid = (lo + hi + 1) >> 1;
-                if (s_rs[jj][mid] <= (uint32_t)lane) lo = mid;
-                else hi = mid - 1;
-            }
-            i = lo;
-        }
-        for (uint32_t q = lane; q < total; q += 32) {
-            while (s_rs[jj][i + 1] <= q) ++i;
-            const uint64_t src = (uint64_t)(i0 + i) * t + s_src[jj][i] + (q - s_rs[jj][i]);
-            reloc_k[D + q] = tiles_k[src];
-            if (val_bytes == 4)
-                static_cast<uint32_t *>(reloc_v)[D + q] = static_cast<const uint32_t *>(tiles_v)[src];
-            else if (val_bytes == 8)
-                static_cast<uint64_t *>(reloc_v)[D + q] = static_cast<const uint64_t *>(tiles_v)[src];
-        }
+        const uint32_t src = base + (y - rs);
+        reloc_k[y] = tiles_k[src];
+        if (val_bytes == 4)
+            static_cast<uint32_t *>(reloc_v)[y] = static_cast<const uint32_t *>(tiles_v)[src];
+        else if (val_bytes == 8)
+            static_cast<uint64_t *>(reloc_v)[y] = static_cast<const uint64_t *>(tiles_v)[src];
     }
 }
 
@@ -562,7 +567,6 @@ static cudaError_t set_smem(KernelT kern, int bytes)
 cudaError_t init_misc_kernels()
 {
     BSORT_TRY(set_smem(k_records_sort<1024, 16>, smem_bytes_for_cap(kRecordChunk, true)));
-    BSORT_TRY(set_smem(k_sample_index<256>, 96 * 1024));
     BSORT_TRY(set_smem(k_pack_units<1024>, 16 * 8193));
     return cudaSuccess;
 }
@@ -580,6 +584,10 @@ cudaError_t launch_records_chunk_sort(const uint64_t *src, uint64_t *dst, uint32
 cudaError_t launch_merge_pass(const uint64_t *src, uint64_t *dst, uint32_t n_pad, uint32_t L,
                               cudaStream_t st)
 {
+    // a CTA's outputs never span two pairs of runs: L and n_pad are
+    // multiples of kRecordChunk, itself a multiple of kMergeTile
+    static_assert(kRecordChunk % kMergeTile == 0, "merge tiles must divide record chunks");
+    if (n_pad % kRecordChunk != 0 || L % kRecordChunk != 0) return cudaErrorInvalidValue;
     k_merge_pass<256, 16><<<n_pad / kMergeTile, 256, 0, st>>>(src, dst, n_pad, L);
     return cudaGetLastError();
 }
@@ -596,9 +604,11 @@ cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples
                                 uint32_t *counts, uint32_t *cum, uint32_t *srcb,
                                 cudaStream_t st)
 {
-    const int sm = (int)(s * 12);
-    if (sm > 96 * 1024) return cudaErrorInvalidValue;
-    k_sample_index<256><<<m, 256, sm, st>>>(tiles_k, samples, spl, t, s, m, counts, cum, srcb);
+    constexpr int T = 128;
+    const uint32_t jb = s >= 8 * T ? 8 : (s + T - 1) / T;  // splitters per thread
+    const uint32_t gpt = (s + T * jb - 1) / (T * jb);
+    k_sample_index<T><<<m * gpt, T, 0, st>>>(tiles_k, samples, spl, t, s, m, counts, cum, srcb,
+                                             jb);
     return cudaGetLastError();
 }
 
@@ -610,16 +620,15 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
     return cudaGetLastError();
 }
 
-cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const uint32_t *cum,
-                            const uint32_t *offsets, uint32_t t, uint32_t s, uint32_t m,
-                            int val_bytes, uint32_t *reloc_k, void *reloc_v, int *err,
-                            cudaStream_t st)
+cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const uint32_t *offsets,
+                            const uint32_t *srcb, const uint32_t *blk, uint32_t t, uint32_t m,
+                            uint32_t runs, uint32_t n_pad, int val_bytes, uint32_t *reloc_k,
+                            void *reloc_v, cudaStream_t st)
 {
-    constexpr int TG = 32, BB = 32;
-    const dim3 grid((m + TG - 1) / TG, (s + BB - 1) / BB);
-    k_relocate<256, TG, BB><<<grid, 256, 0, st>>>(tiles_k, tiles_v, cum, offsets, t, s, m,
-                                                   (uint64_t)m * t, val_bytes, reloc_k, reloc_v,
-                                                   err);
+    constexpr int T = (kRelocPart / kBlockItems) * 32;
+    const uint32_t grid = (n_pad + kRelocPart - 1) / kRelocPart;
+    k_relocate<T><<<grid, T, 0, st>>>(tiles_k, tiles_v, offsets, srcb, blk, t, m, runs, n_pad,
+                                      val_bytes, reloc_k, reloc_v);
     return cudaGetLastError();
 }
 

@@ -250,3 +250,65 @@ def test_generators_numpy_torch_agree():
         fa = synth.keys_f32(d, 1024, 11)
         fb = synth.keys_f32_torch(d, 1024, 11).numpy()
         assert (fa.view(np.uint32) == fb.view(np.uint32)).all(), d
+
+
+# ---- decoupled bucket count b (extension: b global samples from the m*s samples)
+
+@pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 6])
+def test_bruteforce_tiny_decoupled_buckets(n):
+    inputs = [list(x) for x in itertools.product(range(3), repeat=n)]
+    inputs += [list(p) for p in itertools.permutations(range(n))][:60]
+    for keys in inputs:
+        perm = _stable_perm_bruteforce(keys)
+        for t, s in ((2, 1), (2, 2), (4, 2), (4, 4)):
+            m = -(-n // t)
+            for b in range(1, m * s + 1):
+                r = oracle.paper_sort(np.array(keys, np.uint32), t, s, "u32",
+                                      vals=np.arange(n, dtype=np.uint32), b=b)
+                assert list(r["vals"]) == perm, (keys, t, s, b)
+
+
+@pytest.mark.parametrize("kind", ["zero", "increasing", "decreasing"])
+@pytest.mark.parametrize("t,s,m,b", [(64, 8, 16, 5), (256, 16, 8, 37), (4096, 64, 4, 100),
+                                     (256, 16, 8, 128)])
+def test_closed_form_decoupled_buckets(kind, t, s, m, b):
+    """All-equal and strictly monotone keys: samples are every w-th item of
+    the global order, so bucket j holds exactly (r_j - r_{j-1}) * w items with
+    r_j = floor((j+1) m s / b) - 1."""
+    n = t * m
+    if kind == "zero":
+        keys = np.zeros(n, np.uint32)
+    else:
+        keys = (np.arange(n, dtype=np.uint64) * ((1 << 32) // n)).astype(np.uint32)
+        if kind == "decreasing":
+            keys = keys[::-1].copy()
+    r = oracle.paper_sort(keys, t, s, "u32", b=b)
+    w = t // s
+    ranks = [(j + 1) * m * s // b - 1 for j in range(b)]
+    want = [(ranks[j] - (ranks[j - 1] if j else -1)) * w for j in range(b)]
+    assert list(_bucket_sizes(r)) == want
+
+
+@pytest.mark.parametrize("dist", ["uniform", "staggered", "zero", "bucket"])
+@pytest.mark.parametrize("b", [3, 40, 250])
+def test_bound_and_partition_decoupled_buckets(dist, b):
+    t, s = 256, 16
+    n = 256 * 30 + 11
+    keys = synth.keys_u32(dist, n, synth.seed_for(1, 6))
+    r = oracle.paper_sort(keys, t, s, "u32", b=b)
+    m, npad = r["m"], r["n_padded"]
+    sizes = _bucket_sizes(r)
+    assert sizes.sum() == npad and len(sizes) == b
+    assert sizes.max() <= oracle.bucket_bound(npad, m, s, b)
+    samples = list(zip(r["samp_keys"].tolist(), r["samp_p"].tolist()))
+    spl = list(zip(r["spl_keys"].tolist(), r["spl_p"].tolist()))
+    for j, g in enumerate(spl):
+        assert sum(1 for x in samples if x <= g) == (j + 1) * m * s // b
+    tile_pos = r["tile_pos"]
+    spl_orig = [(int(k), int(tile_pos[p])) for k, p in spl]
+    rk, rp, bs = r["reloc_keys"], r["reloc_pos"], r["bucket_start"]
+    for j in range(b):
+        for x in range(int(bs[j]), int(bs[j + 1])):
+            item = (int(rk[x]), int(rp[x]))
+            assert item <= spl_orig[j] and (j == 0 or item > spl_orig[j - 1])
+    assert (r["keys"] == np.sort(keys)).all()
