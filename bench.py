@@ -6,6 +6,12 @@ uniformly (SplitMix64), keys only.  Prints ONE JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--n N] [--dist uniform] [--key-type u32|f32] [--dists]
+                  [--batch-arrays 20000] [--batch-cap 2^30]
+
+The line also carries "batched": the batched workload (20,000 independent
+uint32 arrays, sizes log-uniform in [2^7, 2^20], scaled to at most 2^30 keys
+in all, uniform keys) sorted by one bsort_sort_batch call, against the same
+arrays sorted by one plain bsort_sort_keys call each, on the same stream.
 
 --impl reference times the CPU oracle (a plain C statement of Algorithm 1)
 on the host cores, on a bounded sample of the same workload per step.
@@ -62,6 +68,13 @@ def _args():
                    help="keys per CPU-oracle sample")
     p.add_argument("--tile", type=int, default=0, help="force the sublist size t (0: planner)")
     p.add_argument("--samples", type=int, default=0, help="force s (0: planner)")
+    p.add_argument("--buckets", type=int, default=0,
+                   help="force the bucket count b (0: b = s if --samples, else planner)")
+    p.add_argument("--batch-arrays", type=int, default=20000,
+                   help="batched workload: number of arrays (0: skip the batched line)")
+    p.add_argument("--batch-cap", type=int, default=1 << 30,
+                   help="batched workload: total keys at most")
+    p.add_argument("--batch-steps", type=int, default=3)
     return p.parse_args()
 
 
@@ -283,7 +296,8 @@ def run_ours(args):
 
     keys = make_keys(args.dist)
     out = torch.empty_like(keys)
-    sorter = pkg.BucketSorter(device=local, timing=True, tile=args.tile, samples=args.samples)
+    sorter = pkg.BucketSorter(device=local, timing=True, tile=args.tile, samples=args.samples,
+                              buckets=args.buckets)
     plan = sorter.plan(args.n, args.key_type)
     stream = torch.cuda.current_stream(dev)
 
@@ -435,6 +449,10 @@ def run_ours(args):
                          "t=%d, s=%d, single-threaded C (host has %d cores)"
                          % (sample_n, len(rates), t_o, s_o, _cpu_cores())}
 
+    sorter.close()
+    del keys, out
+    batched = run_batched(args, pkg, synth, dev, stream, rank, world) if args.batch_arrays else None
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -445,16 +463,90 @@ def run_ours(args):
             "e2e": e2e, "gpu_launches": plan.num_kernels * args.steps,
             "clocks": clk, "per_kernel_ms": per_kernel,
             "plan": {k: v for k, v in plan.as_dict().items()
-                     if k in ("t", "s", "m", "w", "bucket_bound", "unit_capacity",
+                     if k in ("t", "s", "b", "m", "w", "bucket_bound", "unit_capacity",
                               "tile_ctas", "unit_ctas", "num_kernels")},
         }
         if dists is not None:
             line["distributions"] = dists
+        if batched is not None:
+            line["batched"] = batched
         print(json.dumps(line), flush=True)
-    sorter.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def run_batched(args, pkg, synth, dev, stream, rank, world):
+    """The batched workload: one bsort_sort_batch call per step against one
+    plain bsort_sort_keys call per array (same arrays, same stream)."""
+    import numpy as np
+    import torch
+
+    sizes = synth.batch_sizes(args.batch_arrays, synth.seed_for(4, 0, rank), cap=args.batch_cap)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    nb = int(off[-1])
+    keys = synth.keys_u32_torch("uniform", nb, synth.seed_for(4, 0, 1000 + rank), device=dev)
+    out = torch.empty_like(keys)
+    sorter = pkg.BucketSorter(device=dev.index, timing=True)
+    bplan = sorter.plan_batch(off)
+    for _ in range(3):
+        sorter.sort_batch(keys, off, out=out)
+    sorter.sync()
+    # correctness gate: nondecreasing inside every array, same multiset
+    o = out.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    starts = torch.zeros(nb, dtype=torch.bool, device=dev)
+    starts[torch.from_numpy(off[:-1].astype(np.int64)).to(dev)] = True
+    assert bool(((o[1:] >= o[:-1]) | starts[1:]).all()), "a batched array is not sorted"
+    kin = keys.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    assert int(kin.sum()) == int(o.sum()), "multiset changed"
+    del o, kin, starts
+    sorter.kernel_times()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.batch_steps):
+        sorter.sort_batch(keys, off, out=out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sorter.sync()
+    kt, kc = sorter.kernel_times()
+    per_kernel = {}
+    for name, ms in kt:
+        per_kernel[name] = round(per_kernel.get(name, 0.0) + ms / max(kc, 1), 4)
+    b_ms = job_time_ms(e0.elapsed_time(e1), world, dev) / args.batch_steps
+    sorter.close()
+
+    # the same arrays, one plain sort call each
+    plain = pkg.BucketSorter(device=dev.index)
+    plain._ensure(int(sizes.max()), "u32", 0)
+    h, st = plain.h, plain._stream()
+    kp, op = keys.data_ptr(), out.data_ptr()
+    bounds = [(int(off[q]) * 4, int(off[q + 1] - off[q])) for q in range(len(sizes))]
+
+    def sequential():
+        for a, n in bounds:
+            pkg.bsort_sort_keys(h, pkg.BSORT_U32, kp + a, op + a, n, st)
+
+    sequential()
+    plain.sync()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    sequential()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    plain.sync()
+    s_ms = job_time_ms(e0.elapsed_time(e1), world, dev)
+    plain.close()
+    return {"workload": "%d uint32 arrays, sizes log-uniform in [2^7, 2^20] scaled to <= %d "
+                        "keys in all, uniform keys, per GPU" % (len(sizes), args.batch_cap),
+            "keys": nb, "value": nb * world / (b_ms / 1e3) / 1e9, "unit": UNIT,
+            "ms_per_batch": b_ms, "steps": args.batch_steps,
+            "sequential": {"value": nb * world / (s_ms / 1e3) / 1e9, "unit": UNIT,
+                           "ms_per_batch": s_ms,
+                           "launch": "one bsort_sort_keys call per array, same stream"},
+            "speedup_vs_sequential": s_ms / b_ms, "gpu_launches": bplan.num_kernels,
+            "plan": bplan.as_dict(), "per_kernel_ms": per_kernel}
 
 
 def main():

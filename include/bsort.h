@@ -85,6 +85,16 @@ typedef struct {
     uint32_t tile;             /* t = n/m of Step 1 (0 = planner's choice) */
     uint32_t samples;          /* s of Step 3 (0 = planner's choice) */
     uint32_t flags;            /* BSORT_FLAG_* */
+    uint32_t buckets;          /* b, the number of buckets of Steps 5-9
+                                  (0 = b = s when samples is given, else the
+                                  planner's choice); the splitters are the
+                                  sorted samples of rank floor((j+1)ms/b) - 1,
+                                  which for b = s is the paper's S[(j+1)m - 1]
+                                  (Section 4, Step 5).  1 <= b <= m*s and
+                                  b <= 12288, else EINVAL / EUNSUPPORTED. */
+    uint32_t batch_direct_max; /* bsort_sort_batch: largest segment sorted
+                                  whole by one CTA or cluster (0 = 131072;
+                                  at most 262144) */
 } bsort_config;
 
 /* The plan of one job (Step 1 parameters and the Step-9 unit). */
@@ -92,17 +102,33 @@ typedef struct {
     uint64_t n;              /* items */
     uint64_t n_padded;       /* n' = m * t (the last sublist padded) */
     uint32_t t;              /* sublist size n/m (Step 1) */
-    uint32_t s;              /* samples per sublist = buckets (Steps 3, 5) */
+    uint32_t s;              /* samples per sublist (Step 3) */
     uint32_t m;              /* number of sublists */
     uint32_t w;              /* t / s, distance between samples (Step 3) */
-    uint64_t bucket_bound;   /* max |B_j| = n'/s + (m-1)(w-1) <= 2n'/s */
+    uint64_t bucket_bound;   /* max |B_j| = ceil(ms/b) w + (m-1)(w-1); for
+                                b = s this is n'/s + (m-1)(w-1) <= 2n'/s */
     uint32_t tile_ctas;      /* CTAs that sort one sublist (Step 2) */
     uint32_t unit_ctas;      /* CTAs that sort one bucket (Step 9) */
     uint64_t unit_capacity;  /* items one Step-9 unit holds (>= bucket_bound) */
     uint32_t single_tile;    /* 1: n fits one unit, sorted directly */
     uint32_t num_kernels;    /* kernel launches per call */
     uint64_t workspace_bytes;/* device workspace this job needs */
+    uint32_t b;              /* buckets (Steps 5-9); b = s is the paper's rule */
 } bsort_plan_info;
+
+/* The plan of one batch (bsort_plan_batch). */
+typedef struct {
+    uint64_t n;               /* keys in all segments */
+    uint32_t num_segs;
+    uint32_t direct_segs;     /* sorted whole by one CTA or cluster */
+    uint32_t sampled_segs;    /* sorted by segment-aware Algorithm 1 */
+    uint32_t large_segs;      /* above 524288 keys: one plain sort each */
+    uint32_t sublists;        /* sublists of the sampled segments */
+    uint32_t buckets;         /* buckets of the sampled segments */
+    uint32_t num_kernels;     /* kernel launches per call */
+    uint32_t pad_;
+    uint64_t workspace_bytes; /* device workspace the batch needs */
+} bsort_batch_info;
 
 /* Intermediates of the last call (for parity checks), see bsort_get_intermediate. */
 typedef enum {
@@ -110,10 +136,10 @@ typedef enum {
                                 key domain for F32), sublist-major */
     BSORT_IM_SAMPLES = 1,    /* Step 3: m*s records (key << 32 | p), p = i*t + r,
                                 sublist-major */
-    BSORT_IM_SPLITTERS = 2,  /* Step 5: s records g_0..g_{s-1} */
-    BSORT_IM_COUNTS = 3,     /* Step 6: a_ij, uint32, bucket-major a[j*m + i] */
-    BSORT_IM_OFFSETS = 4,    /* Step 7: l_ij, uint32, bucket-major */
-    BSORT_IM_RELOCATED = 5   /* Step 8: n' keys B_1 ... B_s (not with
+    BSORT_IM_SPLITTERS = 2,  /* Step 5: b records g_0..g_{b-1} */
+    BSORT_IM_COUNTS = 3,     /* Step 6: a_ij, uint32, bucket-major a[j*m + i], m*b */
+    BSORT_IM_OFFSETS = 4,    /* Step 7: l_ij, uint32, bucket-major, m*b */
+    BSORT_IM_RELOCATED = 5   /* Step 8: n' keys B_1 ... B_b (not with
                                 BSORT_FLAG_LOW_MEMORY) */
 } bsort_intermediate;
 
@@ -142,6 +168,28 @@ bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_i
                               const void *d_vals_in, void *d_keys_out,
                               void *d_vals_out, uint32_t val_bytes, uint64_t n,
                               void *cuda_stream);
+
+/* Batched sort (no counterpart in the paper, which sorts one array):
+ * num_segs independent arrays, segment q = keys [seg_offsets[q],
+ * seg_offsets[q+1]) of d_keys_in, each sorted on its own into the same
+ * range of d_keys_out (d_keys_out == d_keys_in allowed).  seg_offsets is
+ * HOST memory, num_segs + 1 nondecreasing values, the last below 2^32 -
+ * 2^16; keys outside every segment are left untouched.  Segments up to
+ * batch_direct_max keys are sorted whole by one CTA or thread-block cluster
+ * (as Step 9 sorts a bucket); larger ones up to 524288 keys by Algorithm 1
+ * (Section 4) with segment-aware sublists (32768 keys), s = 1024 samples
+ * per sublist and per-segment splitters, all segments together in one
+ * sequence of launches; larger ones by one plain sort each.  The segment
+ * table is copied to the device from pinned staging owned by the handle.
+ * kt: BSORT_U32 or BSORT_F32.  Errors: EINVAL (null pointers, decreasing
+ * offsets, partial overlap), EUNSUPPORTED (too many keys), ENOMEM. */
+bsort_status bsort_sort_batch(bsort_t h, bsort_key_type kt, const void *d_keys_in,
+                              void *d_keys_out, const uint64_t *seg_offsets,
+                              uint32_t num_segs, void *cuda_stream);
+
+/* The plan bsort_sort_batch would use for these segments.  Host-only. */
+bsort_status bsort_plan_batch(bsort_t h, bsort_key_type kt, const uint64_t *seg_offsets,
+                              uint32_t num_segs, bsort_batch_info *out);
 
 /* bsort_sort_keys on HOST buffers: copies h_keys_in to the device, sorts,
  * and copies the result back into h_keys_out, all on cuda_stream (the

@@ -11,6 +11,7 @@ bucket sizes, the bucket-size bound) live in ``tests/test_oracle_*.py``.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -26,45 +27,66 @@ _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 _lib = None
 
 
+def compile_to(src: str, out: str) -> str:
+    """Compile a C source of the oracle into the shared library ``out``."""
+    tmp = out + ".tmp.%d" % os.getpid()
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src])
+    os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle into ``oracle/_build/liboracle.so`` (plain gcc)."""
     os.makedirs(_BUILD, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
             and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
         return _LIB_PATH
-    tmp = _LIB_PATH + ".tmp.%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC",
-                           "-o", tmp, _SRC])
-    os.replace(tmp, _LIB_PATH)
-    return _LIB_PATH
+    return compile_to(_SRC, _LIB_PATH)
+
+
+@contextlib.contextmanager
+def use_library(path: str):
+    """Run the oracle functions on another build of the oracle source while
+    the context is open (the planted-mistake tests compile mutated copies of
+    ``bsort_oracle.c`` and check that the pins reject them)."""
+    global _lib
+    saved = _lib
+    _lib = _configure(ctypes.CDLL(path))
+    try:
+        yield
+    finally:
+        _lib = saved
 
 
 def _load():
     global _lib
     if _lib is None:
-        path = build()
-        lib = ctypes.CDLL(path)
-        u64p = ctypes.POINTER(ctypes.c_uint64)
-        lib.oracle_paper_sort.restype = ctypes.c_int
-        lib.oracle_paper_sort.argtypes = [u64p, u64p, ctypes.c_uint64,
-                                          ctypes.c_uint64, ctypes.c_uint64,
-                                          ctypes.c_uint64, ctypes.c_uint64] + [u64p] * 13
-        lib.oracle_textbook_sort.restype = ctypes.c_int
-        lib.oracle_textbook_sort.argtypes = [u64p, u64p, ctypes.c_uint64,
-                                             u64p, u64p]
-        lib.oracle_f32_to_key.restype = ctypes.c_uint32
-        lib.oracle_f32_to_key.argtypes = [ctypes.c_uint32]
-        lib.oracle_key_to_f32.restype = ctypes.c_uint32
-        lib.oracle_key_to_f32.argtypes = [ctypes.c_uint32]
-        u32p = ctypes.POINTER(ctypes.c_uint32)
-        lib.oracle_f32_to_key_array.restype = None
-        lib.oracle_f32_to_key_array.argtypes = [u32p, u32p, ctypes.c_uint64]
-        lib.oracle_key_to_f32_array.restype = None
-        lib.oracle_key_to_f32_array.argtypes = [u32p, u32p, ctypes.c_uint64]
-        lib.oracle_num_sublists.restype = ctypes.c_uint64
-        lib.oracle_num_sublists.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
-        _lib = lib
+        _lib = _configure(ctypes.CDLL(build()))
     return _lib
+
+
+def _configure(lib):
+    """Declare the argument and result types of the oracle's C functions."""
+    u64p = ctypes.POINTER(ctypes.c_uint64)
+    lib.oracle_paper_sort.restype = ctypes.c_int
+    lib.oracle_paper_sort.argtypes = [u64p, u64p, ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_uint64,
+                                      ctypes.c_uint64, ctypes.c_uint64] + [u64p] * 13
+    lib.oracle_textbook_sort.restype = ctypes.c_int
+    lib.oracle_textbook_sort.argtypes = [u64p, u64p, ctypes.c_uint64,
+                                         u64p, u64p]
+    lib.oracle_f32_to_key.restype = ctypes.c_uint32
+    lib.oracle_f32_to_key.argtypes = [ctypes.c_uint32]
+    lib.oracle_key_to_f32.restype = ctypes.c_uint32
+    lib.oracle_key_to_f32.argtypes = [ctypes.c_uint32]
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    lib.oracle_f32_to_key_array.restype = None
+    lib.oracle_f32_to_key_array.argtypes = [u32p, u32p, ctypes.c_uint64]
+    lib.oracle_key_to_f32_array.restype = None
+    lib.oracle_key_to_f32_array.argtypes = [u32p, u32p, ctypes.c_uint64]
+    lib.oracle_num_sublists.restype = ctypes.c_uint64
+    lib.oracle_num_sublists.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+    return lib
 
 
 def _ptr(a: Optional[np.ndarray]):

@@ -21,7 +21,7 @@ __all__ = [
     "bsort_sort_pairs", "bsort_sort_keys_host", "bsort_sync",
     "bsort_get_intermediate", "bsort_kernel_times", "bsort_kernel_name",
     "bsort_last_error", "bsort_status_string", "bsort_sort_keys_noalloc", "BucketSorter",
-    "EXPORTED_SYMBOLS",
+    "bsort_batch_info", "bsort_sort_batch", "bsort_plan_batch", "EXPORTED_SYMBOLS",
 ]
 
 BSORT_OK, BSORT_EINVAL, BSORT_ENOMEM, BSORT_ECUDA, BSORT_ETIMEOUT = 0, 1, 2, 3, 4
@@ -38,6 +38,7 @@ EXPORTED_SYMBOLS = (
     "bsort_sort_pairs", "bsort_sort_keys_host", "bsort_sync",
     "bsort_get_intermediate", "bsort_kernel_times", "bsort_kernel_name",
     "bsort_last_error", "bsort_status_string", "bsort_sort_keys_noalloc",
+    "bsort_sort_batch", "bsort_plan_batch",
 )
 
 
@@ -45,7 +46,8 @@ class bsort_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int), ("mem_budget_bytes", ctypes.c_uint64),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
                 ("tile", ctypes.c_uint32), ("samples", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("buckets", ctypes.c_uint32),
+                ("batch_direct_max", ctypes.c_uint32)]
 
 
 class bsort_plan_info(ctypes.Structure):
@@ -54,10 +56,22 @@ class bsort_plan_info(ctypes.Structure):
                 ("w", ctypes.c_uint32), ("bucket_bound", ctypes.c_uint64),
                 ("tile_ctas", ctypes.c_uint32), ("unit_ctas", ctypes.c_uint32),
                 ("unit_capacity", ctypes.c_uint64), ("single_tile", ctypes.c_uint32),
-                ("num_kernels", ctypes.c_uint32), ("workspace_bytes", ctypes.c_uint64)]
+                ("num_kernels", ctypes.c_uint32), ("workspace_bytes", ctypes.c_uint64),
+                ("b", ctypes.c_uint32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class bsort_batch_info(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("num_segs", ctypes.c_uint32),
+                ("direct_segs", ctypes.c_uint32), ("sampled_segs", ctypes.c_uint32),
+                ("large_segs", ctypes.c_uint32), ("sublists", ctypes.c_uint32),
+                ("buckets", ctypes.c_uint32), ("num_kernels", ctypes.c_uint32),
+                ("pad_", ctypes.c_uint32), ("workspace_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad_"}
 
 
 class BsortError(RuntimeError):
@@ -94,6 +108,9 @@ def load_library(rebuild: bool = False):
         "bsort_last_error": (ctypes.c_char_p, [H]),
         "bsort_status_string": (ctypes.c_char_p, [i32]),
         "bsort_sort_keys_noalloc": (i32, [i32, vp, vp, u64, vp, i32]),
+        "bsort_sort_batch": (i32, [H, i32, vp, vp, ctypes.POINTER(u64), u32, vp]),
+        "bsort_plan_batch": (i32, [H, i32, ctypes.POINTER(u64), u32,
+                                   ctypes.POINTER(bsort_batch_info)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -180,6 +197,26 @@ def bsort_sort_keys_noalloc(key_type, d_keys_in, d_keys_out, n, stream, wait=0):
                                                                n, stream, wait))
 
 
+def _offsets_arg(seg_offsets):
+    """Host uint64 array of num_segs + 1 offsets, kept alive by the caller."""
+    import numpy as np
+    arr = np.ascontiguousarray(seg_offsets, dtype=np.uint64)
+    return arr, arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), max(arr.size - 1, 0)
+
+
+def bsort_sort_batch(h, key_type, d_keys_in, d_keys_out, seg_offsets, stream):
+    arr, ptr, nseg = _offsets_arg(seg_offsets)
+    return _check(h, load_library().bsort_sort_batch(h, key_type, d_keys_in, d_keys_out, ptr,
+                                                     nseg, stream))
+
+
+def bsort_plan_batch(h, key_type, seg_offsets):
+    arr, ptr, nseg = _offsets_arg(seg_offsets)
+    info = bsort_batch_info()
+    _check(h, load_library().bsort_plan_batch(h, key_type, ptr, nseg, ctypes.byref(info)))
+    return info
+
+
 def bsort_kernel_name(h, index):
     return load_library().bsort_kernel_name(h, index).decode()
 
@@ -195,12 +232,14 @@ class BucketSorter:
     given as torch.int32 bit patterns) and run on the current torch stream."""
 
     def __init__(self, device: int = 0, tile: int = 0, samples: int = 0,
-                 timing: bool = False, workspace_bytes: int = 0, low_memory: bool = False):
+                 timing: bool = False, workspace_bytes: int = 0, low_memory: bool = False,
+                 buckets: int = 0, batch_direct_max: int = 0):
         import torch
         self.torch = torch
         self.device = device
         self.flags = (BSORT_FLAG_TIMING if timing else 0) | (BSORT_FLAG_LOW_MEMORY if low_memory else 0)
-        self.tile, self.samples = tile, samples
+        self.tile, self.samples, self.buckets = tile, samples, buckets
+        self.batch_direct_max = batch_direct_max
         self.ws = None
         self.h = None
         self._make(workspace_bytes)
@@ -211,7 +250,8 @@ class BucketSorter:
             bsort_destroy(self.h)
             self.h = None
         cfg = bsort_config(device=self.device, tile=self.tile, samples=self.samples,
-                           flags=self.flags)
+                           flags=self.flags, buckets=self.buckets,
+                           batch_direct_max=self.batch_direct_max)
         if nbytes:
             self.ws = torch.empty(int(nbytes), dtype=torch.uint8,
                                   device="cuda:%d" % self.device)
@@ -250,6 +290,21 @@ class BucketSorter:
         bsort_sort_pairs(self.h, _KEY_TYPES[key_type], keys.data_ptr(), vals.data_ptr(),
                          out_keys.data_ptr(), out_vals.data_ptr(), vb, n, self._stream())
         return out_keys, out_vals
+
+    def plan_batch(self, seg_offsets, key_type="u32"):
+        return bsort_plan_batch(self.h, _KEY_TYPES[key_type], seg_offsets)
+
+    def sort_batch(self, keys, seg_offsets, out=None, key_type="u32"):
+        """Sort every segment [seg_offsets[q], seg_offsets[q+1]) of keys on
+        its own (seg_offsets: host sequence of num_segs + 1 offsets)."""
+        if out is None:
+            out = self.torch.empty_like(keys)
+        need = self.plan_batch(seg_offsets, key_type).workspace_bytes
+        if self.ws is None or self.ws.numel() < need:
+            self._make(max(need, 256))
+        bsort_sort_batch(self.h, _KEY_TYPES[key_type], keys.data_ptr(), out.data_ptr(),
+                         seg_offsets, self._stream())
+        return out
 
     def sort_keys_host(self, h_keys, h_out, key_type="u32"):
         """Host tensors (pinned for asynchronous copies) in and out."""

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <utility>
 #include <vector>
 
 #include "../../include/bsort.h"
@@ -19,6 +20,14 @@ constexpr uint64_t kAlign = 256;
 constexpr uint64_t kMaxN = (1ull << 32) - (1ull << 16);
 constexpr uint64_t kMaxSamples = 8192;  // s per sublist (Step 6 keeps 12*s bytes in SMEM)
 constexpr int kMaxTimed = 40;   // launches recorded per call
+// Batches: segments up to kBatchDirectMax keys (default) are sorted whole by
+// one unit; up to kBatchSampledMax by segment-aware sampling with sublists
+// of kSegTile keys and s = kBatchSamples (m*s <= kRecordChunk); larger ones
+// by one plain sort each.
+constexpr uint32_t kBatchDirectMax = 131072;
+constexpr uint32_t kBatchSampledMax = (uint32_t)kRecordChunk / 1024 * (uint32_t)kSegTile;
+constexpr uint32_t kBatchSamples = 1024;
+constexpr uint32_t kBatchUnit = 32768;  // Step-9 unit of sampled segments
 constexpr int kRing = 64;       // calls kept for bsort_kernel_times
 
 uint64_t align_up(uint64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -31,6 +40,7 @@ struct Plan {
     int tile_chunk;  // items per CTA in Step 2 (t = tile_ctas * tile_chunk)
     int unit_chunk;  // items per CTA in Step 9 (capacity = unit_ctas * unit_chunk)
     uint32_t n_rec;      // m*s sample records
+    uint32_t n_runs;     // m*b runs A_ij (counts, offsets)
     uint32_t n_rec_pad;  // rounded up to kRecordChunk
     uint32_t scan_chunks;
     // workspace offsets (bytes)
@@ -45,7 +55,7 @@ struct Plan {
 struct bsort_ctx {
     int device = 0;
     uint32_t flags = 0;
-    uint32_t force_t = 0, force_s = 0;
+    uint32_t force_t = 0, force_s = 0, force_b = 0;
     void *ws = nullptr;
     uint64_t ws_bytes = 0;
     bool ws_owned = false;
@@ -58,6 +68,11 @@ struct bsort_ctx {
     cudaEvent_t ev[kRing][kMaxTimed + 1] = {};
     const char *ev_name[kMaxTimed] = {};
     int n_ev[kRing] = {};
+    uint32_t direct_max = kBatchDirectMax;  // batches: largest segment sorted whole
+    void *stage = nullptr;           // pinned staging of batch descriptors
+    uint64_t stage_bytes = 0;
+    cudaEvent_t stage_ev = nullptr;  // last copy out of stage
+    bool stage_pending = false;
     uint64_t calls_recorded = 0;  // calls since the last bsort_kernel_times
     uint64_t call_seq = 0;
     bool events_made = false;
@@ -81,11 +96,35 @@ bsort_status cuda_fail(bsort_t h, cudaError_t e, const char *what)
     return fail(h, BSORT_ECUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-uint64_t bound_for(uint64_t n_pad, uint64_t m, uint64_t s)
+// Largest bucket with b splitters taken from the m*s samples: a bucket
+// spans at most ceil(m*s/b) sample ranks, w items each, plus w-1 items of
+// every other sublist (for b = s: n'/s + (m-1)(w-1), Lemma 1).
+uint64_t bound_for(uint64_t n_pad, uint64_t m, uint64_t s, uint64_t b)
 {
     const uint64_t t = n_pad / m;
     const uint64_t w = t / s;
-    return n_pad / s + (m - 1) * (w - 1);
+    return (m * s + b - 1) / b * w + (m - 1) * (w - 1);
+}
+
+// Bucket count for a plan whose units hold Q items: at least the smallest b
+// whose bound fits Q, else about (k + 0.1) buckets per unit for the smallest
+// whole k that allows it, so that greedy packing fills units to ~k/(k+0.1)
+// instead of leaving a unit with one bucket when two nearly fit.  Returns 0
+// when no b <= bmax keeps every bucket within Q.
+uint64_t choose_buckets(uint64_t np, uint64_t m, uint64_t s, uint64_t Q, uint64_t bmax)
+{
+    if (bound_for(np, m, s, bmax) > Q) return 0;
+    uint64_t lo = 1, hi = bmax;  // smallest b with bound <= Q (bound falls with b)
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if (bound_for(np, m, s, mid) <= Q) hi = mid;
+        else lo = mid + 1;
+    }
+    for (uint64_t k = 1;; ++k) {
+        const uint64_t b = ((10 * k + 1) * np + 10 * Q - 1) / (10 * Q);
+        if (b >= bmax) return bmax;
+        if (b >= lo) return b;
+    }
 }
 
 // Sort-unit shapes (items per CTA) and cluster sizes the kernels provide.
@@ -177,15 +216,20 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
     I.n = n;
     const uint64_t forced_t = h ? h->force_t : 0;
     const uint64_t forced_s = h ? h->force_s : 0;
+    const uint64_t forced_b = h ? h->force_b : 0;
+    if (forced_b > (uint64_t)kMaxBuckets)
+        return fail(h, BSORT_EUNSUPPORTED, "b = %llu exceeds %d buckets",
+                    (unsigned long long)forced_b, kMaxBuckets);
     int uchunk = 0, uctas = 0;
 
-    if (forced_t == 0 && forced_s == 0 && unit_for(n, pairs, &uchunk, &uctas) ||
+    if (forced_t == 0 && forced_s == 0 && forced_b == 0 && unit_for(n, pairs, &uchunk, &uctas) ||
         (forced_t && n <= forced_t && unit_for(n, pairs, &uchunk, &uctas))) {
         // c7: n fits one Step-9 unit; the sort needs no sampling.
         I.single_tile = 1;
         I.n_padded = n;
         I.t = (uint32_t)n;
         I.s = 1;
+        I.b = 1;
         I.m = n ? 1 : 0;
         I.w = (uint32_t)n;
         I.bucket_bound = n;
@@ -196,7 +240,8 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         I.num_kernels = n > 1 ? 1 : 0;
     } else {
         // candidates: forced t or every sublist shape; forced s or every
-        // power of two with w = t/s >= 16 and s <= 4096
+        // power of two with w = t/s >= 16 and s <= kMaxSamples.  The unit is
+        // sized for b = s (or the forced b); the bucket count is chosen after.
         double best = -1.0;
         uint64_t bt = 0, bs = 0;
         int btc = 0, btk = 0, buc = 0, buk = 0;
@@ -211,7 +256,9 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
             if (np >= kMaxN) continue;
             for (uint64_t sv = 1; sv <= t; sv <<= 1) {
                 if (forced_s ? sv != forced_s : (sv > kMaxSamples || t / sv < 16)) continue;
-                const uint64_t bound = bound_for(np, m, sv);
+                const uint64_t bv = forced_b ? forced_b : sv;
+                if (bv > m * sv) continue;
+                const uint64_t bound = bound_for(np, m, sv, bv);
                 int uc, uk;
                 if (!unit_for(bound, pairs, &uc, &uk)) continue;
                 const double c = plan_cost(np, sv, tc, tk, uc, uk);
@@ -235,9 +282,13 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         if (!bt) {
             if (forced_t && forced_s) {
                 const uint64_t m = (n + forced_t - 1) / forced_t;
+                const uint64_t bv = forced_b ? forced_b : forced_s;
+                if (bv > m * forced_s)
+                    return fail(h, BSORT_EINVAL, "b = %llu exceeds the m*s = %llu samples",
+                                (unsigned long long)bv, (unsigned long long)(m * forced_s));
                 return fail(h, BSORT_EUNSUPPORTED,
                             "bucket bound %llu exceeds the largest Step-9 unit (%d items)",
-                            (unsigned long long)bound_for(m * forced_t, m, forced_s), 8 * cm);
+                            (unsigned long long)bound_for(m * forced_t, m, forced_s, bv), 8 * cm);
             }
             return fail(h, BSORT_EUNSUPPORTED, "no plan keeps every bucket within a Step-9 unit");
         }
@@ -248,15 +299,25 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         I.s = (uint32_t)bs;
         I.m = (uint32_t)m;
         I.w = (uint32_t)(bt / bs);
-        I.bucket_bound = bound_for(I.n_padded, m, bs);
         I.tile_ctas = (uint32_t)btk;
         I.unit_ctas = (uint32_t)buk;
         P->tile_chunk = btc;
         P->unit_chunk = buc;
         I.unit_capacity = (uint64_t)buc * buk;
+        uint64_t b = bs;  // the paper's rule, kept when s is given
+        if (forced_b) {
+            b = forced_b;
+        } else if (!forced_s) {
+            const uint64_t bmax = m * bs < (uint64_t)kMaxBuckets ? m * bs : (uint64_t)kMaxBuckets;
+            const uint64_t bc = choose_buckets(I.n_padded, m, bs, I.unit_capacity, bmax);
+            if (bc) b = bc;
+        }
+        I.b = (uint32_t)b;
+        I.bucket_bound = bound_for(I.n_padded, m, bs, b);
         P->n_rec = (uint32_t)(m * bs);
+        P->n_runs = (uint32_t)(m * b);
         P->n_rec_pad = (uint32_t)((P->n_rec + kRecordChunk - 1) / kRecordChunk * kRecordChunk);
-        P->scan_chunks = (P->n_rec + kScanChunk - 1) / kScanChunk;
+        P->scan_chunks = (P->n_runs + kScanChunk - 1) / kScanChunk;
         uint32_t merges = 0;
         for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
         const bool reloc = !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
@@ -283,13 +344,13 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->off_samples = take((uint64_t)P->n_rec * 8);
         P->off_rec_a = take((uint64_t)P->n_rec_pad * 8);
         P->off_rec_b = take(P->n_rec_pad > (uint32_t)kRecordChunk ? (uint64_t)P->n_rec_pad * 8 : 0);
-        P->off_spl = take((uint64_t)I.s * 8);
-        P->off_counts = take((uint64_t)P->n_rec * 4);
-        P->off_cum = take((uint64_t)P->n_rec * 4);
-        P->off_offsets = take(((uint64_t)P->n_rec + 1) * 4);
+        P->off_spl = take((uint64_t)I.b * 8);
+        P->off_counts = take((uint64_t)P->n_runs * 4);
+        P->off_cum = take((uint64_t)P->n_runs * 4);
+        P->off_offsets = take(((uint64_t)P->n_runs + 1) * 4);
         P->off_status = take((uint64_t)P->scan_chunks * 8);
-        P->off_units = take((1 + 2 * (uint64_t)I.s) * 4);
-        P->off_srcb = take((uint64_t)P->n_rec * 4);
+        P->off_units = take((1 + 2 * (uint64_t)I.b) * 4);
+        P->off_srcb = take((uint64_t)P->n_runs * 4);
         P->off_blk = take((np + kBlockItems - 1) / kBlockItems * 4);
     }
     P->total = o;
@@ -451,7 +512,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     // Steps 4-5
     const bool one_chunk = P.n_rec_pad == (uint32_t)kRecordChunk;
     SEQ(launch_records_chunk_sort(samples, rec_a, P.n_rec, P.n_rec_pad, one_chunk ? spl : nullptr,
-                                  I.m, I.s, st),
+                                  I.s, I.b, st),
         "step4_sample_chunks");
     if (!one_chunk) {
         uint64_t *src = rec_a, *dst = rec_b;
@@ -461,45 +522,306 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
             src = dst;
             dst = tmp;
         }
-        SEQ(launch_select_splitters(src, I.m, I.s, spl, st), "step5_splitters");
+        SEQ(launch_select_splitters(src, P.n_rec, I.b, spl, st), "step5_splitters");
     }
     uint32_t *srcb = reinterpret_cast<uint32_t *>(ws + P.off_srcb);
     uint32_t *blk = reinterpret_cast<uint32_t *>(ws + P.off_blk);
     // Step 6
-    SEQ(launch_sample_index(tiles_k, samples, spl, I.t, I.s, I.m, counts, cum, srcb, st),
+    SEQ(launch_sample_index(tiles_k, samples, spl, I.t, I.s, I.b, I.m, counts, cum, srcb, st),
         "step6_sample_index");
     // Step 7
-    SEQ(launch_scan(counts, offsets, P.n_rec, status, ticket, err, st), "step7_prefix_sum");
+    SEQ(launch_scan(counts, offsets, P.n_runs, status, ticket, err, st), "step7_prefix_sum");
     // Step 8: materialised, unless BSORT_FLAG_LOW_MEMORY fuses it into the
     // load of Step 9, which then gathers every unit from the runs A_ij
     GatherSrc g;
-    SEQ(launch_block_index(offsets, P.n_rec, (uint32_t)I.n_padded, blk, st), "step8_run_index");
+    SEQ(launch_block_index(offsets, P.n_runs, (uint32_t)I.n_padded, blk, st), "step8_run_index");
     if (P.relocate) {
-        SEQ(launch_relocate(tiles_k, tiles_v, offsets, srcb, blk, I.t, I.m, P.n_rec,
+        SEQ(launch_relocate(tiles_k, tiles_v, offsets, srcb, blk, P.n_runs,
                             (uint32_t)I.n_padded, (int)vb, reloc_k, reloc_v, st),
             "step8_relocate");
     }
     // Step 9: buckets packed into units of at most unit_capacity items
     uint32_t *units = reinterpret_cast<uint32_t *>(ws + P.off_units);
-    SEQ(launch_pack_units(offsets, I.m, I.s, (uint32_t)I.n_padded, (uint32_t)I.unit_capacity,
+    SEQ(launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, (uint32_t)I.unit_capacity,
                           units, err, st),
         "step9_pack_units");
     if (!P.relocate) {
         g.offsets = offsets;
         g.srcb = srcb;
         g.blk = blk;
-        g.m = I.m;
-        g.t = I.t;
-        g.runs = P.n_rec;
+        g.runs = P.n_runs;
     }
     const void *s9k = P.relocate ? (const void *)reloc_k : (const void *)tiles_k;
     const void *s9v = P.relocate ? (const void *)reloc_v : (const void *)tiles_v;
-    SEQ(P.pairs ? launch_bucket_sort_pairs(P.unit_chunk, (int)I.unit_ctas, s9k, s9v, units, I.s,
+    SEQ(P.pairs ? launch_bucket_sort_pairs(P.unit_chunk, (int)I.unit_ctas, s9k, s9v, units, I.b,
                                            n, I.n_padded, is_f32, (int)vb, kout, vout, err, g,
                                            st)
-                : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, s9k, units, I.s, n,
+                : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, s9k, units, I.b, n,
                                           I.n_padded, is_f32, kout, err, g, st),
         "step9_bucket_sort");
+    return BSORT_OK;
+}
+
+// ---------------------------------------------------------------- batches
+// Direct unit shapes, smallest first: (chunk, ctas).
+const int kDirectShapes[][2] = {{2048, 1}, {4096, 1}, {8192, 1}, {16384, 1}, {32768, 1},
+                                {32768, 2}, {32768, 4}, {32768, 8}};
+constexpr int kNumDirect = 8;
+const char *const kDirectNames[kNumDirect] = {
+    "batch_direct_2048", "batch_direct_4096", "batch_direct_8192", "batch_direct_16384",
+    "batch_direct_32768", "batch_direct_2x32768", "batch_direct_4x32768", "batch_direct_8x32768"};
+
+// Host plan of one batch: direct lists per shape, sampled segments with
+// their sublists and buckets, plain-sorted large segments, and the
+// workspace layout (descriptors first, copied from pinned staging).
+struct BatchPlan {
+    bsort_batch_info info;
+    std::vector<uint32_t> direct[kNumDirect];  // (begin, end) pairs per shape
+    std::vector<SegInfo> segs;
+    std::vector<uint32_t> sub_seg;
+    std::vector<uint32_t> units;               // (segment, bucket) pairs
+    std::vector<std::pair<uint64_t, uint64_t>> large;  // (begin, n)
+    uint64_t large_ws = 0;
+    uint32_t nrec = 0, nspl = 0, runs = 0, scan_chunks = 0;
+    uint64_t n_pad = 0;
+    // descriptor words (uint32) and their offsets in it
+    uint64_t d_direct[kNumDirect] = {}, d_sub = 0, d_segs = 0, d_units = 0, d_words = 0;
+    // workspace offsets (bytes)
+    uint64_t off_desc = 0, off_tiles = 0, off_reloc = 0, off_samples = 0, off_spl = 0,
+             off_counts = 0, off_offsets = 0, off_srcb = 0, off_status = 0, off_blk = 0,
+             total = 0;
+};
+
+bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const uint64_t *segoff,
+                             uint32_t nsegs, BatchPlan *B)
+{
+    if (kt == BSORT_U64) return fail(h, BSORT_EUNSUPPORTED, "64-bit keys are not served by this build");
+    if (kt != BSORT_U32 && kt != BSORT_F32) return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
+    if (nsegs && !segoff) return fail(h, BSORT_EINVAL, "null segment offsets");
+    bsort_batch_info &I = B->info;
+    memset(&I, 0, sizeof(I));
+    I.num_segs = nsegs;
+    if (nsegs == 0) return BSORT_OK;
+    if (segoff[nsegs] >= kMaxN)
+        return fail(h, BSORT_EUNSUPPORTED, "segment end %llu exceeds 2^32 - 2^16",
+                    (unsigned long long)segoff[nsegs]);
+    const uint32_t dmax = h->direct_max;
+    uint64_t g = 0;  // sublists so far
+    for (uint32_t q = 0; q < nsegs; ++q) {
+        if (segoff[q + 1] < segoff[q])
+            return fail(h, BSORT_EINVAL, "segment offsets decrease at %u", q);
+        const uint64_t a = segoff[q], n = segoff[q + 1] - segoff[q];
+        I.n += n;
+        if (n <= 1) continue;  // nothing to order (a copy when out != in)
+        if (n <= dmax) {
+            int c = 0;
+            while ((uint64_t)kDirectShapes[c][0] * kDirectShapes[c][1] < n) ++c;
+            B->direct[c].push_back((uint32_t)a);
+            B->direct[c].push_back((uint32_t)(a + n));
+            ++I.direct_segs;
+        } else if (n <= kBatchSampledMax) {
+            SegInfo sg = {};
+            sg.g0 = (uint32_t)g;
+            sg.m = (uint32_t)((n + kSegTile - 1) / kSegTile);
+            sg.s = kBatchSamples;
+            const uint64_t np = (uint64_t)sg.m * kSegTile;
+            uint64_t lo = 1, hi = (uint64_t)sg.m * sg.s;  // smallest b whose bound fits a unit
+            while (lo < hi) {
+                const uint64_t mid = (lo + hi) / 2;
+                if (bound_for(np, sg.m, sg.s, mid) <= kBatchUnit) hi = mid;
+                else lo = mid + 1;
+            }
+            sg.b = (uint32_t)lo;
+            sg.rec = B->nrec;
+            sg.spl = B->nspl;
+            sg.run0 = B->runs;
+            sg.out = (uint32_t)a;
+            sg.n = (uint32_t)n;
+            for (uint32_t i = 0; i < sg.m; ++i) B->sub_seg.push_back((uint32_t)B->segs.size());
+            for (uint32_t j = 0; j < sg.b; ++j) {
+                B->units.push_back((uint32_t)B->segs.size());
+                B->units.push_back(j);
+            }
+            B->nrec += sg.m * sg.s;
+            B->nspl += sg.b;
+            B->runs += sg.m * sg.b;
+            g += sg.m;
+            B->segs.push_back(sg);
+        } else {
+            B->large.push_back({a, n});
+        }
+    }
+    if (g * kSegTile >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "padded sampled segments exceed 2^32");
+    B->n_pad = g * kSegTile;
+    I.sampled_segs = (uint32_t)B->segs.size();
+    I.large_segs = (uint32_t)B->large.size();
+    I.sublists = (uint32_t)g;
+    I.buckets = B->nspl;
+    B->scan_chunks = (B->runs + kScanChunk - 1) / kScanChunk;
+    // plain sorts of the large segments reuse the workspace after the batch
+    for (const auto &lg : B->large) {
+        Plan P;
+        bsort_status st = make_plan(h, kt, 0, lg.second, &P);
+        if (st != BSORT_OK) return st;
+        if (P.total > B->large_ws) B->large_ws = P.total;
+        I.num_kernels += P.info.num_kernels;
+    }
+    // descriptor words
+    uint64_t wds = 0;
+    auto words = [&](uint64_t n) {
+        const uint64_t at = wds;
+        wds += (n + 3) / 4 * 4;  // 16-byte aligned pieces
+        return at;
+    };
+    for (int c = 0; c < kNumDirect; ++c) {
+        B->d_direct[c] = words(B->direct[c].size());
+        if (!B->direct[c].empty()) ++I.num_kernels;
+    }
+    B->d_sub = words(B->sub_seg.size());
+    B->d_segs = words(B->segs.size() * (sizeof(SegInfo) / 4));
+    B->d_units = words(B->units.size());
+    B->d_words = wds;
+    if (!B->segs.empty()) I.num_kernels += 7;  // Steps 1-3, 4-5, 6, 7, run index, 8, 9
+    // workspace
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) {
+        const uint64_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    take(kAlign);  // error word + scan ticket
+    B->off_desc = take(wds * 4);
+    if (!B->segs.empty()) {
+        B->off_tiles = take(B->n_pad * 4);
+        B->off_reloc = take(B->n_pad * 4);
+        B->off_samples = take((uint64_t)B->nrec * 8);
+        B->off_spl = take((uint64_t)B->nspl * 8);
+        B->off_counts = take((uint64_t)B->runs * 4);
+        B->off_offsets = take(((uint64_t)B->runs + 1) * 4);
+        B->off_srcb = take((uint64_t)B->runs * 4);
+        B->off_status = take((uint64_t)B->scan_chunks * 8);
+        B->off_blk = take((B->n_pad + kBlockItems - 1) / kBlockItems * 4);
+    }
+    B->total = o > B->large_ws ? o : B->large_ws;
+    I.workspace_bytes = B->total;
+    return BSORT_OK;
+}
+
+bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout,
+                       const uint64_t *segoff, uint32_t nsegs, cudaStream_t st)
+{
+    bsort_status rs = prepare(h);
+    if (rs != BSORT_OK) return rs;
+    BatchPlan B;
+    rs = make_batch_plan(h, kt, segoff, nsegs, &B);
+    if (rs != BSORT_OK) return rs;
+    if (B.info.n == 0) return BSORT_OK;
+    rs = ensure_workspace(h, B.total);
+    if (rs != BSORT_OK) return rs;
+    cudaError_t e;
+    // segments of one key: copies
+    if (kout != kin)
+        for (uint32_t q = 0; q < nsegs; ++q)
+            if (segoff[q + 1] - segoff[q] == 1) {
+                e = cudaMemcpyAsync(static_cast<uint32_t *>(kout) + segoff[q],
+                                    static_cast<const uint32_t *>(kin) + segoff[q], 4,
+                                    cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "copy of a one-key segment");
+            }
+    unsigned char *ws = static_cast<unsigned char *>(h->ws);
+    int *err = reinterpret_cast<int *>(ws);
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(ws + 64);
+    uint32_t *desc = reinterpret_cast<uint32_t *>(ws + B.off_desc);
+    const int is_f32 = kt == BSORT_F32;
+    const uint32_t *ki = static_cast<const uint32_t *>(kin);
+    uint32_t *ko = static_cast<uint32_t *>(kout);
+    Seq seq(h, st);
+    if (B.d_words) {
+        // descriptors: pinned staging -> workspace (the staging is reused
+        // only after the previous copy out of it has completed)
+        const uint64_t bytes = B.d_words * 4;
+        if (h->stage_pending) {
+            e = cudaEventSynchronize(h->stage_ev);
+            if (e != cudaSuccess) return cuda_fail(h, e, "wait for the staging copy");
+            h->stage_pending = false;
+        }
+        if (bytes > h->stage_bytes) {
+            if (h->stage) cudaFreeHost(h->stage);
+            h->stage = nullptr;
+            h->stage_bytes = 0;
+            e = cudaHostAlloc(&h->stage, bytes, cudaHostAllocDefault);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                return fail(h, BSORT_ENOMEM, "pinned staging of %llu bytes: %s",
+                            (unsigned long long)bytes, cudaGetErrorString(e));
+            }
+            h->stage_bytes = bytes;
+        }
+        if (!h->stage_ev) {
+            e = cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming);
+            if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate");
+        }
+        uint32_t *hw = static_cast<uint32_t *>(h->stage);
+        memset(hw, 0, bytes);
+        for (int c = 0; c < kNumDirect; ++c)
+            if (!B.direct[c].empty())
+                memcpy(hw + B.d_direct[c], B.direct[c].data(), B.direct[c].size() * 4);
+        if (!B.sub_seg.empty()) memcpy(hw + B.d_sub, B.sub_seg.data(), B.sub_seg.size() * 4);
+        if (!B.segs.empty()) memcpy(hw + B.d_segs, B.segs.data(), B.segs.size() * sizeof(SegInfo));
+        if (!B.units.empty()) memcpy(hw + B.d_units, B.units.data(), B.units.size() * 4);
+        e = cudaMemcpyAsync(desc, hw, bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of the batch descriptors");
+        e = cudaEventRecord(h->stage_ev, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventRecord");
+        h->stage_pending = true;
+    }
+    // direct segments: one launch per unit shape
+    for (int c = 0; c < kNumDirect; ++c) {
+        const uint32_t cnt = (uint32_t)(B.direct[c].size() / 2);
+        if (!cnt) continue;
+        SEQ(launch_seg_sort(kDirectShapes[c][0], kDirectShapes[c][1], ki, ko, desc + B.d_direct[c],
+                            cnt, is_f32, err, st),
+            kDirectNames[c]);
+    }
+    // sampled segments: Algorithm 1, segment-aware
+    if (!B.segs.empty()) {
+        const uint32_t nsub = B.info.sublists;
+        const uint32_t *sub_seg = desc + B.d_sub;
+        const SegInfo *segs = reinterpret_cast<const SegInfo *>(desc + B.d_segs);
+        const uint32_t *units = desc + B.d_units;
+        uint32_t *tiles = reinterpret_cast<uint32_t *>(ws + B.off_tiles);
+        uint32_t *reloc = reinterpret_cast<uint32_t *>(ws + B.off_reloc);
+        uint64_t *samples = reinterpret_cast<uint64_t *>(ws + B.off_samples);
+        uint64_t *spl = reinterpret_cast<uint64_t *>(ws + B.off_spl);
+        uint32_t *counts = reinterpret_cast<uint32_t *>(ws + B.off_counts);
+        uint32_t *offsets = reinterpret_cast<uint32_t *>(ws + B.off_offsets);
+        uint32_t *srcb = reinterpret_cast<uint32_t *>(ws + B.off_srcb);
+        unsigned long long *status = reinterpret_cast<unsigned long long *>(ws + B.off_status);
+        uint32_t *blk = reinterpret_cast<uint32_t *>(ws + B.off_blk);
+        e = cudaMemsetAsync(status, 0, (size_t)B.scan_chunks * 8, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan status)");
+        e = cudaMemsetAsync(ticket, 0, 4, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan ticket)");
+        SEQ(launch_seg_sublist_sort(ki, is_f32, sub_seg, nsub, segs, tiles, samples, st),
+            "batch_step1_3_sublist_sort");
+        SEQ(launch_seg_records(samples, segs, B.info.sampled_segs, spl, st),
+            "batch_step4_5_samples");
+        SEQ(launch_seg_sample_index(tiles, samples, spl, sub_seg, nsub, segs, counts, srcb, st),
+            "batch_step6_sample_index");
+        SEQ(launch_scan(counts, offsets, B.runs, status, ticket, err, st), "batch_step7_prefix_sum");
+        SEQ(launch_block_index(offsets, B.runs, (uint32_t)B.n_pad, blk, st), "batch_step8_run_index");
+        SEQ(launch_relocate(tiles, nullptr, offsets, srcb, blk, B.runs, (uint32_t)B.n_pad, 0,
+                            reloc, nullptr, st),
+            "batch_step8_relocate");
+        SEQ(launch_seg_bucket_sort((int)kBatchUnit, reloc, units, B.info.buckets, segs, offsets,
+                                   is_f32, ko, err, st),
+            "batch_step9_bucket_sort");
+    }
+    // large segments: one plain sort each, after the batch (same stream)
+    for (const auto &lg : B.large) {
+        rs = run_sort(h, kt, ki + lg.first, nullptr, ko + lg.first, nullptr, 0, lg.second, st);
+        if (rs != BSORT_OK) return rs;
+    }
     return BSORT_OK;
 }
 
@@ -541,6 +863,14 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
         h->flags = cfg->flags;
         h->force_t = cfg->tile;
         h->force_s = cfg->samples;
+        h->force_b = cfg->buckets;
+        if (cfg->batch_direct_max) {
+            if (cfg->batch_direct_max > 8u * (uint32_t)kMaxCapKeys) {
+                delete h;
+                return BSORT_EINVAL;
+            }
+            h->direct_max = cfg->batch_direct_max;
+        }
         if (cfg->flags & ~(uint32_t)(BSORT_FLAG_TIMING | BSORT_FLAG_LOW_MEMORY)) {
             delete h;
             return BSORT_EINVAL;
@@ -585,6 +915,8 @@ bsort_status bsort_destroy(bsort_t h)
         cudaSetDevice(h->device);
         cudaFree(h->ws);
     }
+    if (h->stage_ev) cudaEventDestroy(h->stage_ev);
+    if (h->stage) cudaFreeHost(h->stage);
     if (h->events_made)
         for (int r = 0; r < kRing; ++r)
             for (int i = 0; i <= kMaxTimed; ++i) cudaEventDestroy(h->ev[r][i]);
@@ -629,6 +961,31 @@ bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_i
         return fail(h, BSORT_EINVAL, "value input and output overlap partially");
     return run_sort(h, kt, d_keys_in, d_vals_in, d_keys_out, d_vals_out, val_bytes, n,
                     static_cast<cudaStream_t>(cuda_stream));
+}
+
+bsort_status bsort_plan_batch(bsort_t h, bsort_key_type kt, const uint64_t *seg_offsets,
+                              uint32_t num_segs, bsort_batch_info *out)
+{
+    if (!h || !out) return BSORT_EINVAL;
+    BatchPlan B;
+    bsort_status st = make_batch_plan(h, kt, seg_offsets, num_segs, &B);
+    if (st != BSORT_OK) return st;
+    *out = B.info;
+    return BSORT_OK;
+}
+
+bsort_status bsort_sort_batch(bsort_t h, bsort_key_type kt, const void *d_keys_in,
+                              void *d_keys_out, const uint64_t *seg_offsets, uint32_t num_segs,
+                              void *cuda_stream)
+{
+    if (!h) return BSORT_EINVAL;
+    if (num_segs && !seg_offsets) return fail(h, BSORT_EINVAL, "null segment offsets");
+    const uint64_t end = num_segs ? seg_offsets[num_segs] : 0;
+    if (end && (!d_keys_in || !d_keys_out)) return fail(h, BSORT_EINVAL, "null key pointer");
+    if (end && d_keys_in != d_keys_out && overlaps(d_keys_in, end * 4, d_keys_out, end * 4))
+        return fail(h, BSORT_EINVAL, "input and output overlap partially");
+    return run_batch(h, kt, d_keys_in, d_keys_out, seg_offsets, num_segs,
+                     static_cast<cudaStream_t>(cuda_stream));
 }
 
 bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_keys_in,
@@ -687,9 +1044,9 @@ bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which, void *h
     switch (which) {
     case BSORT_IM_TILES: off = P.off_tiles_k; size = P.info.n_padded * 4; break;
     case BSORT_IM_SAMPLES: off = P.off_samples; size = (uint64_t)P.n_rec * 8; break;
-    case BSORT_IM_SPLITTERS: off = P.off_spl; size = (uint64_t)P.info.s * 8; break;
-    case BSORT_IM_COUNTS: off = P.off_counts; size = (uint64_t)P.n_rec * 4; break;
-    case BSORT_IM_OFFSETS: off = P.off_offsets; size = (uint64_t)P.n_rec * 4; break;
+    case BSORT_IM_SPLITTERS: off = P.off_spl; size = (uint64_t)P.info.b * 8; break;
+    case BSORT_IM_COUNTS: off = P.off_counts; size = (uint64_t)P.n_runs * 4; break;
+    case BSORT_IM_OFFSETS: off = P.off_offsets; size = (uint64_t)P.n_runs * 4; break;
     case BSORT_IM_RELOCATED:
         if (!P.relocate)
             return fail(h, BSORT_ENOTREADY,

@@ -1,0 +1,396 @@
+// bsort_batch.cu -- batched sorting of many independent arrays (segments)
+// of uint32 / float32 keys in one launch sequence.  The paper sorts one
+// array (Section 4, Algorithm 1); here each segment gets the part of the
+// method its size calls for:
+//
+//   direct segments (up to one Step-9 unit): sorted whole by one CTA or one
+//     thread-block cluster, as Step 9 sorts a bucket (k_seg_sort, one launch
+//     per unit shape);
+//   sampled segments (larger): Algorithm 1 with segment-aware sublists,
+//     samples and splitters.  Every sublist lies in one segment (the last
+//     sublist of a segment is padded), every segment sorts its own m*s
+//     samples and picks its own b splitters, buckets never cross segments,
+//     and Step 9 writes each bucket back into its segment's output range.
+//
+// Sublists of all sampled segments are numbered globally (g); sublist g
+// occupies positions [g*t, (g+1)*t) of the padded sublist space, so the
+// composite position p = g*t + r orders each segment's items by index, as
+// p = i*t + r does for one array.  Runs A_ij of all segments are numbered
+// segment by segment (bucket-major inside a segment), so one exclusive scan
+// over all counts gives every run its place in the padded space.
+#include "bsort_device.cuh"
+#include "bsort_internal.h"
+
+namespace bsort {
+
+// ============================================================ direct segments
+// Cluster u sorts segment u = [seg[2u], seg[2u+1]) of the input (at most
+// C*T*E keys, guaranteed by the host) into the same range of the output.
+template <int T, int E, int C>
+__global__ void __launch_bounds__(T, 1)
+k_seg_sort(const uint32_t *__restrict__ keys_in, uint32_t *__restrict__ keys_out,
+           const uint32_t *__restrict__ seg, int is_f32, int *err)
+{
+    constexpr int CH = T * E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sm = reinterpret_cast<uint32_t *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t u = blockIdx.x / C;
+    const int r = (int)(blockIdx.x % C);
+    const uint32_t L = seg[2 * u], R = seg[2 * u + 1];
+    if (R < L || R - L > (uint32_t)(C * CH)) {
+        if (tid == 0) set_error(err, DEV_INTERNAL);
+        return;  // uniform per cluster
+    }
+    const int len = (int)(R - L);
+    if (len == 0) return;
+    const int per = C == 1 ? CH : (len + C - 1) / C;
+    const int ustart = r * per;
+    const int uend = min(ustart + per, len);
+    uint32_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int x = ustart + wb_pos<E>(warp, lane, k);
+        uint32_t key = 0xFFFFFFFFu;
+        if (x < uend) {
+            key = keys_in[L + x];
+            if (is_f32) key = f32_encode(key);
+        }
+        v[k] = key;
+    }
+    cta_sort<uint32_t, T, E>(v, sm, uend > ustart ? uend - ustart : 0);
+    cluster_merge<uint32_t, T, E, C>(sm, len, per);
+    const int off = r * CH;
+#pragma unroll 4
+    for (int k = 0; k < E; ++k) {
+        const int x = k * T + tid;
+        if (off + x < len) {
+            uint32_t key = sm[pidx<uint32_t>(x)];
+            if (is_f32) key = f32_decode(key);
+            keys_out[L + off + x] = key;
+        }
+    }
+}
+
+// ============================================================ Steps 1-3
+// CTA g sorts sublist g (kSegTile keys): items [i*t, min((i+1)*t, n)) of its
+// segment, i = g - g0, padded with the maximal key; writes the sorted
+// sublist to tiles[g*t ...] and its s samples (ranks (k+1)w - 1) as
+// key << 32 | (g*t + rank) to the segment's record array.
+template <int T, int E>
+__global__ void __launch_bounds__(T, 1)
+k_seg_sublist_sort(const uint32_t *__restrict__ keys_in, int is_f32,
+                   const uint32_t *__restrict__ sub_seg, const SegInfo *__restrict__ segs,
+                   uint32_t *__restrict__ tiles_k, uint64_t *__restrict__ samples)
+{
+    constexpr int TT = T * E;  // t
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sm = reinterpret_cast<uint32_t *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t g = blockIdx.x;
+    const SegInfo sg = segs[sub_seg[g]];
+    const uint32_t i = g - sg.g0;
+    const uint32_t first = i * (uint32_t)TT;  // item offset inside the segment
+    const int len = sg.n - first < (uint32_t)TT ? (int)(sg.n - first) : TT;
+    const uint64_t src = (uint64_t)sg.out + first;
+    uint32_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int x = wb_pos<E>(warp, lane, k);
+        uint32_t key = 0xFFFFFFFFu;
+        if (x < len) {
+            key = keys_in[src + x];
+            if (is_f32) key = f32_encode(key);
+        }
+        v[k] = key;
+    }
+    cta_sort<uint32_t, T, E>(v, sm, len);
+    const uint64_t base = (uint64_t)g * TT;
+#pragma unroll 4
+    for (int k = 0; k < E; ++k) {
+        const int x = k * T + tid;
+        tiles_k[base + x] = sm[pidx<uint32_t>(x)];
+    }
+    const uint32_t w = (uint32_t)TT / sg.s;
+    uint64_t *rec = samples + sg.rec + (uint64_t)i * sg.s;
+    for (uint32_t k = tid; k < sg.s; k += T) {
+        const uint32_t rank = (k + 1) * w - 1;
+        rec[k] = ((uint64_t)sm[pidx<uint32_t>((int)rank)] << 32) | (uint32_t)(base + rank);
+    }
+}
+
+// ============================================================ Steps 4-5
+// CTA q sorts the m*s sample records of sampled segment q (at most T*E;
+// every sublist's s records are already a sorted run) and writes its b
+// splitters g_j = S[floor((j+1) m s / b) - 1].
+template <int T, int E>
+__global__ void __launch_bounds__(T, 1)
+k_seg_records(const uint64_t *__restrict__ samples, const SegInfo *__restrict__ segs,
+              uint64_t *__restrict__ spl)
+{
+    constexpr int CAP = T * E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sm = reinterpret_cast<uint64_t *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const SegInfo sg = segs[blockIdx.x];
+    const uint32_t nrec = sg.m * sg.s;
+    const uint64_t *src = samples + sg.rec;
+    if (sg.s >= 32u * E && sg.s < (uint32_t)CAP) {
+        const int s = (int)sg.s;
+        for (int x = tid; x < CAP; x += T) {
+            const uint64_t r = (uint32_t)x < nrec ? src[x] : 0xFFFFFFFFFFFFFFFFull;
+            const int q = x / s, o = x % s;
+            const int pos = (q & 1) ? q * s + s - 1 - o : x;
+            sm[pidx<uint64_t>(pos)] = r;
+        }
+        __syncthreads();
+        cta_merge_runs<uint64_t, T, E>(sm, s);
+    } else {
+        uint64_t v[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const uint32_t x = (uint32_t)wb_pos<E>(warp, lane, k);
+            v[k] = x < nrec ? src[x] : 0xFFFFFFFFFFFFFFFFull;
+        }
+        cta_sort<uint64_t, T, E>(v, sm);
+    }
+    for (uint32_t j = tid; j < sg.b; j += T)
+        spl[sg.spl + j] = sm[pidx<uint64_t>((int)((uint64_t)(j + 1) * nrec / sg.b - 1))];
+}
+
+// ============================================================ Step 6
+// CTA g locates its segment's b splitters in sorted sublist g: c_j = #items
+// <= g_j (binary search over the sublist's s samples, then its w-item
+// window), T splitters per round, and writes for run (j, i) of the segment
+// the count a_ij = c_j - c_{j-1} and the run's first position g*t + c_{j-1}.
+template <int T>
+__global__ void __launch_bounds__(T)
+k_seg_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ samples,
+                   const uint64_t *__restrict__ spl, const uint32_t *__restrict__ sub_seg,
+                   const SegInfo *__restrict__ segs, uint32_t t, uint32_t *__restrict__ counts,
+                   uint32_t *__restrict__ srcb)
+{
+    __shared__ uint32_t c[T + 1];
+    const int tid = threadIdx.x;
+    const uint32_t g = blockIdx.x;
+    const SegInfo sg = segs[sub_seg[g]];
+    const uint32_t i = g - sg.g0;
+    const uint32_t s = sg.s, w = t / s;
+    const uint64_t base = (uint64_t)g * t;
+    const uint64_t *smp = samples + sg.rec + (uint64_t)i * s;
+    const uint64_t *gs = spl + sg.spl;
+    if (tid == 0) c[0] = 0;
+    for (uint32_t j0 = 0; j0 < sg.b; j0 += T) {
+        const uint32_t j = j0 + tid;
+        uint32_t cj = t;
+        if (j < sg.b) {
+            const uint64_t gj = gs[j];
+            uint32_t lo = 0, hi = s;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (smp[mid] <= gj) lo = mid + 1;
+                else hi = mid;
+            }
+            cj = window_count(tiles_k, base, lo, w, t, s, gj);
+        }
+        c[tid + 1] = cj;
+        __syncthreads();
+        if (j < sg.b) {
+            const uint64_t q = sg.run0 + (uint64_t)j * sg.m + i;
+            counts[q] = cj - c[tid];
+            srcb[q] = (uint32_t)base + c[tid];
+        }
+        const uint32_t carry = c[T];  // c of the round's last splitter
+        __syncthreads();
+        if (tid == 0) c[0] = carry;
+    }
+}
+
+// ============================================================ Step 9
+// CTA u sorts bucket j of sampled segment q (units[2u] = q, units[2u+1] =
+// j): positions [offsets[run0 + j*m], next bucket's first position) of the
+// relocated array, and writes its ranks that hold real items (position -
+// g0*t < n) to the segment's output range.
+template <int T, int E>
+__global__ void __launch_bounds__(T, 1)
+k_seg_bucket_sort(const uint32_t *__restrict__ reloc_k, const uint32_t *__restrict__ units,
+                  const SegInfo *__restrict__ segs, const uint32_t *__restrict__ offsets,
+                  uint32_t t, int is_f32, uint32_t *__restrict__ keys_out, int *err)
+{
+    constexpr int CH = T * E;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *sm = reinterpret_cast<uint32_t *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t u = blockIdx.x;
+    const SegInfo sg = segs[units[2 * u]];
+    const uint32_t j = units[2 * u + 1];
+    const uint32_t P = sg.g0 * t;  // the segment's first padded position
+    const uint32_t L = offsets[sg.run0 + j * sg.m];
+    const uint32_t R = j + 1 < sg.b ? offsets[sg.run0 + (j + 1) * sg.m] : P + sg.m * t;
+    if (R < L || R - L > (uint32_t)CH) {
+        if (tid == 0) set_error(err, DEV_INTERNAL);
+        return;
+    }
+    const int len = (int)(R - L);
+    if (len == 0) return;
+    uint32_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int x = wb_pos<E>(warp, lane, k);
+        v[k] = x < len ? reloc_k[L + x] : 0xFFFFFFFFu;
+    }
+    cta_sort<uint32_t, T, E>(v, sm, len);
+    // ranks below lim hold real items of the segment (its padding sorts last)
+    const uint32_t rel = L - P;
+    const int lim = rel >= sg.n ? 0 : (sg.n - rel < (uint32_t)len ? (int)(sg.n - rel) : len);
+    const uint64_t dst = (uint64_t)sg.out + rel;
+#pragma unroll 4
+    for (int k = 0; k < E; ++k) {
+        const int x = k * T + tid;
+        if (x < lim) {
+            uint32_t key = sm[pidx<uint32_t>(x)];
+            if (is_f32) key = f32_decode(key);
+            keys_out[dst + x] = key;
+        }
+    }
+}
+
+// ============================================================ launching
+namespace {
+
+template <typename KernelT>
+cudaError_t set_smem_attr(KernelT k, int bytes, bool nonportable = false)
+{
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && nonportable)
+        e = cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return e;
+}
+
+template <int T, int E, int C>
+cudaError_t launch_seg_sort_t(const uint32_t *keys_in, uint32_t *keys_out, const uint32_t *seg,
+                              uint32_t nseg, int is_f32, int *err, cudaStream_t st)
+{
+    const int sm = padded_elems<uint32_t>(T * E) * 4;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nseg * C, 1, 1);
+    cfg.blockDim = dim3(T, 1, 1);
+    cfg.dynamicSmemBytes = (size_t)sm;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = C > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_seg_sort<T, E, C>, keys_in, keys_out, seg, is_f32, err);
+}
+
+template <int T, int E, int C>
+cudaError_t init_seg_sort_t()
+{
+    return set_smem_attr(k_seg_sort<T, E, C>, padded_elems<uint32_t>(T * E) * 4);
+}
+
+}  // namespace
+
+cudaError_t init_batch_kernels()
+{
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = init_seg_sort_t<128, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<256, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<512, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<1024, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<1024, 32, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<1024, 32, 2>();
+    if (e == cudaSuccess) e = init_seg_sort_t<1024, 32, 4>();
+    if (e == cudaSuccess) e = init_seg_sort_t<1024, 32, 8>();
+    if (e == cudaSuccess)
+        e = set_smem_attr(k_seg_sublist_sort<1024, 32>, padded_elems<uint32_t>(kSegTile) * 4);
+    if (e == cudaSuccess)
+        e = set_smem_attr(k_seg_records<1024, 16>, padded_elems<uint64_t>(kRecordChunk) * 8);
+    if (e == cudaSuccess)
+        e = set_smem_attr(k_seg_bucket_sort<1024, 16>, padded_elems<uint32_t>(16384) * 4);
+    if (e == cudaSuccess)
+        e = set_smem_attr(k_seg_bucket_sort<1024, 32>, padded_elems<uint32_t>(32768) * 4);
+    return e;
+}
+
+cudaError_t launch_seg_sort(int chunk, int ctas, const uint32_t *keys_in, uint32_t *keys_out,
+                            const uint32_t *seg, uint32_t nseg, int is_f32, int *err,
+                            cudaStream_t st)
+{
+    if (nseg == 0) return cudaSuccess;
+    if (ctas == 1) {
+        switch (chunk) {
+        case 2048: return launch_seg_sort_t<128, 16, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
+        case 4096: return launch_seg_sort_t<256, 16, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
+        case 8192: return launch_seg_sort_t<512, 16, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
+        case 16384: return launch_seg_sort_t<1024, 16, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
+        case 32768: return launch_seg_sort_t<1024, 32, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
+        default: return cudaErrorInvalidValue;
+        }
+    }
+    if (chunk != 32768) return cudaErrorInvalidValue;
+    switch (ctas) {
+    case 2: return launch_seg_sort_t<1024, 32, 2>(keys_in, keys_out, seg, nseg, is_f32, err, st);
+    case 4: return launch_seg_sort_t<1024, 32, 4>(keys_in, keys_out, seg, nseg, is_f32, err, st);
+    case 8: return launch_seg_sort_t<1024, 32, 8>(keys_in, keys_out, seg, nseg, is_f32, err, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_seg_sublist_sort(const uint32_t *keys_in, int is_f32, const uint32_t *sub_seg,
+                                    uint32_t nsub, const SegInfo *segs, uint32_t *tiles_k,
+                                    uint64_t *samples, cudaStream_t st)
+{
+    if (nsub == 0) return cudaSuccess;
+    const int sm = padded_elems<uint32_t>(kSegTile) * 4;
+    k_seg_sublist_sort<1024, 32><<<nsub, 1024, sm, st>>>(keys_in, is_f32, sub_seg, segs, tiles_k,
+                                                         samples);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_records(const uint64_t *samples, const SegInfo *segs, uint32_t nsegs,
+                               uint64_t *spl, cudaStream_t st)
+{
+    if (nsegs == 0) return cudaSuccess;
+    const int sm = padded_elems<uint64_t>(kRecordChunk) * 8;
+    k_seg_records<1024, 16><<<nsegs, 1024, sm, st>>>(samples, segs, spl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
+                                    const uint64_t *spl, const uint32_t *sub_seg, uint32_t nsub,
+                                    const SegInfo *segs, uint32_t *counts, uint32_t *srcb,
+                                    cudaStream_t st)
+{
+    if (nsub == 0) return cudaSuccess;
+    k_seg_sample_index<128><<<nsub, 128, 0, st>>>(tiles_k, samples, spl, sub_seg, segs,
+                                                  (uint32_t)kSegTile, counts, srcb);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_seg_bucket_sort(int chunk, const uint32_t *reloc_k, const uint32_t *units,
+                                   uint32_t nunits, const SegInfo *segs, const uint32_t *offsets,
+                                   int is_f32, uint32_t *keys_out, int *err, cudaStream_t st)
+{
+    if (nunits == 0) return cudaSuccess;
+    if (chunk == 16384) {
+        k_seg_bucket_sort<1024, 16><<<nunits, 1024, padded_elems<uint32_t>(16384) * 4, st>>>(
+            reloc_k, units, segs, offsets, (uint32_t)kSegTile, is_f32, keys_out, err);
+    } else if (chunk == 32768) {
+        k_seg_bucket_sort<1024, 32><<<nunits, 1024, padded_elems<uint32_t>(32768) * 4, st>>>(
+            reloc_k, units, segs, offsets, (uint32_t)kSegTile, is_f32, keys_out, err);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace bsort

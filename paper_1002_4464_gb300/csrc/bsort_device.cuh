@@ -550,4 +550,76 @@ __device__ __forceinline__ void cluster_merge(K *sm, int len, int per = T * E)
     }
 }
 
+// ---------------------------------------------------------------- run walking
+// The runs of the relocated order are position ranges [offsets[q],
+// offsets[q+1]) (offsets[runs] = n_pad), often short and sometimes long
+// stretches of empty ones; blk[b] is the run holding position b*BI.  A
+// walker at position y in run q with re = offsets[q+1] <= y steps over up to
+// kRunSteps runs one by one, then finds the run holding y (< n_pad) by a
+// binary search bounded by y's block.
+constexpr int kRunSteps = 4;
+
+template <int BI>
+__device__ __forceinline__ void run_advance(const uint32_t *__restrict__ offsets,
+                                            const uint32_t *__restrict__ blk, uint32_t nblk,
+                                            uint32_t runs, uint32_t y, uint32_t &q,
+                                            uint32_t &rs, uint32_t &re)
+{
+    int steps = 0;
+    do {
+        ++q;
+        rs = re;
+        re = offsets[q + 1];
+    } while (y >= re && ++steps < kRunSteps);
+    if (y < re) return;
+    // offsets[q + 1] <= y: the run holding y is after q
+    const uint32_t b = y / (uint32_t)BI;
+    uint32_t lo = max(q + 1, blk[b]);
+    uint32_t hi = b + 1 < nblk ? blk[b + 1] : runs - 1;
+    while (lo < hi) {  // last run with offsets[run] <= y
+        const uint32_t mid = (lo + hi + 1) >> 1;
+        if (offsets[mid] <= y) lo = mid;
+        else hi = mid - 1;
+    }
+    q = lo;
+    rs = offsets[q];
+    re = offsets[q + 1];
+}
+
+// ---------------------------------------------------------------- Step 6 window
+// c = #items of the sorted sublist at base (t items) that are <= g in
+// composite order (key << 32 | position), given q = #samples <= g (sample k
+// is rank (k+1)w - 1): c lies in [q*w, q*w + w - 1] and only that window of
+// w items is read.
+__device__ __forceinline__ uint32_t window_count(const uint32_t *__restrict__ tiles_k,
+                                                 uint64_t base, uint32_t q, uint32_t w,
+                                                 uint32_t t, uint32_t s, uint64_t g)
+{
+    if (q >= s) return t;
+    const uint32_t r0 = q * w;
+    const uint32_t gk = (uint32_t)(g >> 32);
+    const uint32_t gp = (uint32_t)g;
+    uint32_t cnt = 0;
+    if (w <= 64 && (w & 3) == 0) {  // 16-byte aligned: base and q*w are multiples of 4
+        const uint4 *p = reinterpret_cast<const uint4 *>(tiles_k + base + r0);
+        for (uint32_t v = 0; v < w / 4; ++v) {
+            const uint4 x = p[v];
+            const uint32_t pos = (uint32_t)(base + r0 + 4 * v);
+            cnt += (x.x < gk || (x.x == gk && pos + 0 <= gp)) ? 1u : 0u;
+            cnt += (x.y < gk || (x.y == gk && pos + 1 <= gp)) ? 1u : 0u;
+            cnt += (x.z < gk || (x.z == gk && pos + 2 <= gp)) ? 1u : 0u;
+            cnt += (x.w < gk || (x.w == gk && pos + 3 <= gp)) ? 1u : 0u;
+        }
+        return r0 + cnt;
+    }
+    uint32_t a = r0, b = r0 + w - 1;  // the item at rank b is > g
+    while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        const uint64_t item = ((uint64_t)tiles_k[base + mid] << 32) | (uint32_t)(base + mid);
+        if (item <= g) a = mid + 1;
+        else b = mid;
+    }
+    return a;
+}
+
 }  // namespace bsort

@@ -47,9 +47,9 @@ cudaError_t launch_sublist_sort_pairs(int chunk, int ctas, const void *keys_in,
 // at rank srcb[q] + (y - offsets[q]).
 struct GatherSrc {
     const uint32_t *offsets = nullptr;  // l_q, runs + 1 words
-    const uint32_t *srcb = nullptr;     // c_i(j-1) per run q = j*m + i
+    const uint32_t *srcb = nullptr;     // sorted-sublist position of run q's first item
     const uint32_t *blk = nullptr;      // run index per kBlockItems positions
-    uint32_t m = 0, t = 0, runs = 0;
+    uint32_t runs = 0;
 };
 
 cudaError_t launch_bucket_sort_keys(int chunk, int ctas, const void *src_k, const uint32_t *units,
@@ -60,24 +60,27 @@ cudaError_t launch_bucket_sort_pairs(int chunk, int ctas, const void *src_k, con
                                      uint64_t n_pad, int is_f32, int val_bytes, void *out_k,
                                      void *out_v, int *err, const GatherSrc &g, cudaStream_t st);
 
+constexpr int kMaxBuckets = 12288;  // b (Step-9 unit packing keeps 16 b bytes in SMEM)
+
 // Step 4 (chunks): sort the n_rec records of src in chunks of kRecordChunk
 // into dst (which holds n_pad = chunks * kRecordChunk records, the tail
-// filled with all-ones); if the whole array is one chunk and spl != nullptr,
-// also writes the splitters (Step 5).
+// filled with all-ones); runs of s records are already sorted.  If the whole
+// array is one chunk and spl != nullptr, also writes the b splitters (Step 5).
 cudaError_t launch_records_chunk_sort(const uint64_t *src, uint64_t *dst, uint32_t n_rec,
-                                      uint32_t n_pad, uint64_t *spl, uint32_t m,
-                                      uint32_t s, cudaStream_t st);
+                                      uint32_t n_pad, uint64_t *spl, uint32_t s,
+                                      uint32_t b, cudaStream_t st);
 // Step 4 (merges): merge sorted runs of length L of src into dst.
 cudaError_t launch_merge_pass(const uint64_t *src, uint64_t *dst, uint32_t n_pad,
                               uint32_t L, cudaStream_t st);
-// Step 5: splitters g_j = sorted[(j+1)m - 1].
-cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t m, uint32_t s,
+// Step 5: b splitters g_j = sorted[floor((j+1) n_rec / b) - 1].
+cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint32_t b,
                                     uint64_t *spl, cudaStream_t st);
 
-// Step 6: counts a_ij (bucket-major) and cumulative counts c_ij
-// (sublist-major, c[i*s + j] = items of sublist i <= g_j).
+// Step 6: for the b splitters, counts a_ij (bucket-major), cumulative counts
+// c_ij (sublist-major, c[i*b + j] = items of sublist i <= g_j) and run starts
+// srcb[j*m + i] = i*t + c_i(j-1); s samples per sublist index the sublist.
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
-                                const uint64_t *spl, uint32_t t, uint32_t s,
+                                const uint64_t *spl, uint32_t t, uint32_t s, uint32_t b,
                                 uint32_t m, uint32_t *counts, uint32_t *cum,
                                 uint32_t *srcb, cudaStream_t st);
 
@@ -91,13 +94,14 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
 constexpr int kRelocateSmemMax = 220 * 1024;
 constexpr int kRelocPart = 8192;  // sublist items per Step-8 CTA
 
-// Step 8: fill the relocated array B_1 ... B_s position by position from
-// the runs A_ij (offsets: l in bucket-major order with the sentinel
-// offsets[runs] = n_pad; srcb: run starts c_i(j-1); blk: run index).
+// Step 8: fill the relocated array B_1 ... B_b position by position from
+// the runs A_ij (offsets: l in run order with the sentinel offsets[runs] =
+// n_pad; srcb: sorted-sublist position of each run's first item, i*t +
+// c_i(j-1); blk: run index).
 cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const uint32_t *offsets,
-                            const uint32_t *srcb, const uint32_t *blk, uint32_t t, uint32_t m,
-                            uint32_t runs, uint32_t n_pad, int val_bytes, uint32_t *reloc_k,
-                            void *reloc_v, cudaStream_t st);
+                            const uint32_t *srcb, const uint32_t *blk, uint32_t runs,
+                            uint32_t n_pad, int val_bytes, uint32_t *reloc_k, void *reloc_v,
+                            cudaStream_t st);
 
 // Positions per entry of the run index used by Step 9's gathering load.
 constexpr int kBlockItems = 1024;
@@ -109,9 +113,44 @@ cudaError_t launch_block_index(uint32_t *offsets, uint32_t runs, uint32_t n_pad,
                                cudaStream_t st);
 
 // Step 9 units: pack consecutive buckets into units of at most Q items;
-// units holds 1 + 2*s words (count, then begin/end pairs).
-cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t s,
+// units holds 1 + 2*b words (count, then begin/end pairs).
+cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t b,
                               uint32_t n_pad, uint32_t Q, uint32_t *units, int *err,
                               cudaStream_t st);
+
+// ---------------------------------------------------------------- batches
+// Sublist size of sampled segments (one 1024 x 32 CTA per sublist).
+constexpr int kSegTile = 32768;
+
+// One sampled segment of a batch: sublists g0 .. g0+m-1 (padded positions
+// [g0*t, (g0+m)*t)), s samples per sublist at records [rec, rec + m*s),
+// b splitters at spl, runs (bucket-major) at [run0, run0 + m*b), n items at
+// input / output offset out.
+struct SegInfo {
+    uint32_t g0, m, s, b, rec, spl, run0, out, n, pad;
+};
+
+cudaError_t init_batch_kernels();
+// Direct segments: unit u = [seg[2u], seg[2u+1]) sorted by one unit of
+// `ctas` CTAs of `chunk` keys.
+cudaError_t launch_seg_sort(int chunk, int ctas, const uint32_t *keys_in, uint32_t *keys_out,
+                            const uint32_t *seg, uint32_t nseg, int is_f32, int *err,
+                            cudaStream_t st);
+// Sampled segments, Steps 1-3 (sub_seg[g] = segment of sublist g).
+cudaError_t launch_seg_sublist_sort(const uint32_t *keys_in, int is_f32, const uint32_t *sub_seg,
+                                    uint32_t nsub, const SegInfo *segs, uint32_t *tiles_k,
+                                    uint64_t *samples, cudaStream_t st);
+// Steps 4-5, one CTA per segment (m*s <= kRecordChunk).
+cudaError_t launch_seg_records(const uint64_t *samples, const SegInfo *segs, uint32_t nsegs,
+                               uint64_t *spl, cudaStream_t st);
+// Step 6: counts a_ij and run starts for every run of every segment.
+cudaError_t launch_seg_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
+                                    const uint64_t *spl, const uint32_t *sub_seg, uint32_t nsub,
+                                    const SegInfo *segs, uint32_t *counts, uint32_t *srcb,
+                                    cudaStream_t st);
+// Step 9: unit u = bucket units[2u+1] of segment units[2u], `chunk` keys max.
+cudaError_t launch_seg_bucket_sort(int chunk, const uint32_t *reloc_k, const uint32_t *units,
+                                   uint32_t nunits, const SegInfo *segs, const uint32_t *offsets,
+                                   int is_f32, uint32_t *keys_out, int *err, cudaStream_t st);
 
 }  // namespace bsort

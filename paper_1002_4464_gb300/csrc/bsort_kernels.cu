@@ -4,8 +4,8 @@
 //   Steps 1-3  k_sublist_sort      (bsort_sort.cuh) sort each sublist, emit samples
 //   Step 4     k_records_sort      sort the s*m samples (chunks of 16K) ...
 //              k_merge_pass        ... then merge-path passes through L2
-//   Step 5     k_select_splitters  every m-th sorted sample
-//   Step 6     k_sample_index      locate the s splitters in every sublist
+//   Step 5     k_select_splitters  b evenly spaced sorted samples
+//   Step 6     k_sample_index      locate the b splitters in every sublist
 //   Step 7     k_scan              bucket-major exclusive scan (look-back)
 //   Step 8     k_relocate          move each run A_ij to l_ij
 //   Step 9     k_pack_units        pack consecutive buckets into Step-9 units
@@ -27,7 +27,7 @@ namespace bsort {
 template <int T, int E>
 __global__ void __launch_bounds__(T, 1)
 k_records_sort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uint32_t n_rec,
-               uint64_t *__restrict__ spl, uint32_t m, uint32_t s)
+               uint64_t *__restrict__ spl, uint32_t s, uint32_t b)
 {
     constexpr int CAP = T * E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -60,7 +60,8 @@ k_records_sort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uin
         dst[base + x] = sm[pidx<uint64_t>(x)];
     }
     if (spl != nullptr) {  // whole sample array in this one chunk: Step 5
-        for (uint32_t j = tid; j < s; j += T) spl[j] = sm[pidx<uint64_t>((j + 1) * m - 1)];
+        for (uint32_t j = tid; j < b; j += T)
+            spl[j] = sm[pidx<uint64_t>((int)((uint64_t)(j + 1) * n_rec / b - 1))];
     }
 }
 
@@ -160,66 +161,38 @@ k_merge_pass(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uint3
 }
 
 // ============================================================ Step 5
-__global__ void k_select_splitters(const uint64_t *__restrict__ sorted, uint32_t m,
-                                   uint32_t s, uint64_t *__restrict__ spl)
+// g_j = S[r_j], r_j = floor((j+1) * n_rec / b) - 1 (n_rec = m*s; with b = s
+// this is the paper's S[(j+1)m - 1]).
+__global__ void k_select_splitters(const uint64_t *__restrict__ sorted, uint32_t n_rec,
+                                   uint32_t b, uint64_t *__restrict__ spl)
 {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < s) spl[j] = sorted[(uint64_t)(j + 1) * m - 1];
+    if (j < b) spl[j] = sorted[(uint64_t)(j + 1) * n_rec / b - 1];
 }
 
 // ============================================================ Step 6
-// CTA x handles sublist i = x / gpt for a block of splitters; thread k of it
-// a contiguous run of JB splitters j0 .. j0+JB-1 (and j0-1 for the count of
-// the first).  The sublist's own s samples (every w-th item, sorted) index
+// CTA x handles sublist i = x / gpt for a block of the b splitters; thread
+// k of it a contiguous run of jb splitters j0 .. j0+jb-1 (and j0-1 for the
+// count of the first).  The sublist's own s samples (every w-th item, sorted) index
 // the sorted sublist: q = #samples <= g_j (found by a binary search for j0,
 // then a forward walk, since q grows with j) gives c_ij in
 // [q*w, q*w + w - 1]; for w <= 64 the w items of that window (16-byte
 // aligned when w is a multiple of 4) are read with independent 16-byte
 // loads and the ones <= g_j counted, otherwise a binary search over the
 // window finds the count.  Items compare as key << 32 | (i*t + r).
-__device__ __forceinline__ uint32_t window_count(const uint32_t *__restrict__ tiles_k,
-                                                 uint64_t base, uint32_t q, uint32_t w,
-                                                 uint32_t t, uint32_t s, uint64_t g)
-{
-    if (q >= s) return t;
-    const uint32_t r0 = q * w;
-    const uint32_t gk = (uint32_t)(g >> 32);
-    const uint32_t gp = (uint32_t)g;
-    uint32_t cnt = 0;
-    if (w <= 64 && (w & 3) == 0) {  // 16-byte aligned: base and q*w are multiples of 4
-        const uint4 *p = reinterpret_cast<const uint4 *>(tiles_k + base + r0);
-        for (uint32_t v = 0; v < w / 4; ++v) {
-            const uint4 x = p[v];
-            const uint32_t pos = (uint32_t)(base + r0 + 4 * v);
-            cnt += (x.x < gk || (x.x == gk && pos + 0 <= gp)) ? 1u : 0u;
-            cnt += (x.y < gk || (x.y == gk && pos + 1 <= gp)) ? 1u : 0u;
-            cnt += (x.z < gk || (x.z == gk && pos + 2 <= gp)) ? 1u : 0u;
-            cnt += (x.w < gk || (x.w == gk && pos + 3 <= gp)) ? 1u : 0u;
-        }
-        return r0 + cnt;
-    }
-    uint32_t a = r0, b = r0 + w - 1;  // the item at rank b is > g
-    while (a < b) {
-        const uint32_t mid = (a + b) >> 1;
-        const uint64_t item = ((uint64_t)tiles_k[base + mid] << 32) | (uint32_t)(base + mid);
-        if (item <= g) a = mid + 1;
-        else b = mid;
-    }
-    return a;
-}
 
 template <int T>
 __global__ void __launch_bounds__(T)
 k_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ samples,
-               const uint64_t *__restrict__ spl, uint32_t t, uint32_t s, uint32_t m,
-               uint32_t *__restrict__ counts, uint32_t *__restrict__ cum,
+               const uint64_t *__restrict__ spl, uint32_t t, uint32_t s, uint32_t b,
+               uint32_t m, uint32_t *__restrict__ counts, uint32_t *__restrict__ cum,
                uint32_t *__restrict__ srcb, uint32_t jb)
 {
-    const uint32_t gpt = (s + T * jb - 1) / (T * jb);  // CTAs per sublist
+    const uint32_t gpt = (b + T * jb - 1) / (T * jb);  // CTAs per sublist
     const uint32_t i = blockIdx.x / gpt;
     const uint32_t j0 = ((blockIdx.x % gpt) * T + threadIdx.x) * jb;
-    if (j0 >= s) return;
-    const uint32_t j1 = min(j0 + jb, s);
+    if (j0 >= b) return;
+    const uint32_t j1 = min(j0 + jb, b);
     const uint64_t base = (uint64_t)i * t;
     const uint32_t w = t / s;
     const uint64_t *smp = samples + (uint64_t)i * s;
@@ -253,8 +226,8 @@ k_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict_
         }
         const uint32_t c = window_count(tiles_k, base, q, w, t, s, g);
         counts[(uint64_t)j * m + i] = c - prev;
-        cum[(uint64_t)i * s + j] = c;
-        srcb[(uint64_t)j * m + i] = prev;  // run A_ij starts at rank c_i(j-1)
+        cum[(uint64_t)i * b + j] = c;
+        srcb[(uint64_t)j * m + i] = (uint32_t)base + prev;  // A_ij starts at rank c_i(j-1)
         prev = c;
     }
 }
@@ -368,16 +341,17 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 // Relocation by destination: CTA c fills positions [c*kRelocPart,
 // (c+1)*kRelocPart) of the relocated array, so every CTA moves the same
 // number of items whatever the key distribution.  Position y lies in the
-// bucket-major run q = j*m + i (offsets[q] <= y < offsets[q+1]) of sublist
-// i, at rank srcb[q] + (y - offsets[q]).  Each warp covers kBlockItems
+// run q (offsets[q] <= y < offsets[q+1]) and comes from position srcb[q] +
+// (y - offsets[q]) of the sorted sublists.  Each warp covers kBlockItems
 // consecutive positions with its lanes on consecutive positions (coalesced
 // stores); a lane finds its first run from the run index of its block and
-// then advances its run as its position grows.
+// then advances its run as its position grows (skipping empty runs by a
+// search bounded by the run index, not one by one).
 template <int T>
 __global__ void __launch_bounds__(T, 4)
 k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_v,
            const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ srcb,
-           const uint32_t *__restrict__ blk, uint32_t t, uint32_t m, uint32_t runs,
+           const uint32_t *__restrict__ blk, uint32_t runs,
            uint32_t n_pad, int val_bytes, uint32_t *__restrict__ reloc_k,
            void *__restrict__ reloc_v)
 {
@@ -395,19 +369,13 @@ k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_
         else hi = mid - 1;
     }
     uint32_t q = lo;
-    uint32_t ti = q % m;
     uint32_t rs = offsets[q], re = offsets[q + 1];
-    uint32_t base = ti * t + srcb[q];
+    uint32_t base = srcb[q];
     const uint32_t yend = min(wy + (uint32_t)kBlockItems, n_pad);
     for (; y < yend; y += 32) {
         if (y >= re) {
-            do {
-                ++q;
-                if (++ti == m) ti = 0;
-                rs = re;
-                re = offsets[q + 1];
-            } while (y >= re);
-            base = ti * t + srcb[q];
+            run_advance<kBlockItems>(offsets, blk, nblk, runs, y, q, rs, re);
+            base = srcb[q];
         }
         const uint32_t src = base + (y - rs);
         reloc_k[y] = tiles_k[src];
@@ -425,26 +393,26 @@ k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_
 // doubling), and a scan numbers them.  units[0] = U, then (begin, end) pairs.
 template <int T>
 __global__ void __launch_bounds__(T, 1)
-k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t s, uint32_t n_pad,
+k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t b, uint32_t n_pad,
              uint32_t Q, uint32_t *__restrict__ units, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem_raw);  // s + 1
-    uint32_t *nxt = Lb + (s + 1);                             // s + 1
-    uint32_t *jmp = nxt + (s + 1);                            // s + 1
-    uint32_t *on = jmp + (s + 1);                             // s + 1
+    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem_raw);  // b + 1
+    uint32_t *nxt = Lb + (b + 1);                             // b + 1
+    uint32_t *jmp = nxt + (b + 1);                            // b + 1
+    uint32_t *on = jmp + (b + 1);                             // b + 1
     __shared__ uint32_t s_warp[T / 32];
     __shared__ uint32_t s_total;
     const int tid = threadIdx.x;
-    for (uint32_t j = tid; j <= s; j += T) {
-        Lb[j] = j < s ? offsets[(uint64_t)j * m] : n_pad;
+    for (uint32_t j = tid; j <= b; j += T) {
+        Lb[j] = j < b ? offsets[(uint64_t)j * m] : n_pad;
         on[j] = j == 0 ? 1u : 0u;
     }
     __syncthreads();
-    for (uint32_t j = tid; j <= s; j += T) {
+    for (uint32_t j = tid; j <= b; j += T) {
         uint32_t e = j;
-        if (j < s) {
-            uint32_t lo = j + 1, hi = s;  // largest e in [j+1, s] with Lb[e] - Lb[j] <= Q
+        if (j < b) {
+            uint32_t lo = j + 1, hi = b;  // largest e in [j+1, b] with Lb[e] - Lb[j] <= Q
             const uint32_t lim = Lb[j] + Q;
             while (lo < hi) {
                 uint32_t mid = (lo + hi + 1) >> 1;
@@ -458,23 +426,23 @@ k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t s, uint3
         jmp[j] = e;
     }
     __syncthreads();
-    for (uint32_t span = 1; span <= s; span <<= 1) {
-        for (uint32_t j = tid; j <= s; j += T)
+    for (uint32_t span = 1; span <= b; span <<= 1) {
+        for (uint32_t j = tid; j <= b; j += T)
             if (on[j]) on[jmp[j]] = 1u;
         __syncthreads();
-        for (uint32_t j = tid; j <= s; j += T) {
+        for (uint32_t j = tid; j <= b; j += T) {
             const uint32_t a = jmp[j];
             nxt[j] = jmp[a];  // use nxt as scratch for the doubled jump
         }
         __syncthreads();
-        for (uint32_t j = tid; j <= s; j += T) jmp[j] = nxt[j];
+        for (uint32_t j = tid; j <= b; j += T) jmp[j] = nxt[j];
         __syncthreads();
     }
     // recompute the single-step successor (nxt was used as scratch)
-    for (uint32_t j = tid; j <= s; j += T) {
+    for (uint32_t j = tid; j <= b; j += T) {
         uint32_t e = j;
-        if (j < s) {
-            uint32_t lo = j + 1, hi = s;
+        if (j < b) {
+            uint32_t lo = j + 1, hi = b;
             const uint32_t lim = Lb[j] + Q;
             while (lo < hi) {
                 uint32_t mid = (lo + hi + 1) >> 1;
@@ -486,12 +454,12 @@ k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t s, uint3
         nxt[j] = e;
     }
     __syncthreads();
-    // number the unit starts (chain members j < s) in order: block scan
-    const uint32_t per = (s + T - 1) / T;
+    // number the unit starts (chain members j < b) in order: block scan
+    const uint32_t per = (b + T - 1) / T;
     const uint32_t j0 = tid * per;
     uint32_t cnt = 0;
     for (uint32_t q = 0; q < per; ++q)
-        if (j0 + q < s && on[j0 + q]) ++cnt;
+        if (j0 + q < b && on[j0 + q]) ++cnt;
     const int lane = tid & 31, warp = tid >> 5;
     uint32_t incl = cnt;
 #pragma unroll
@@ -516,7 +484,7 @@ k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t s, uint3
     uint32_t u = s_warp[warp] + incl - cnt;
     for (uint32_t q = 0; q < per; ++q) {
         const uint32_t j = j0 + q;
-        if (j < s && on[j]) {
+        if (j < b && on[j]) {
             units[1 + 2 * u] = Lb[j];
             units[2 + 2 * u] = Lb[nxt[j]];
             ++u;
@@ -567,17 +535,17 @@ static cudaError_t set_smem(KernelT kern, int bytes)
 cudaError_t init_misc_kernels()
 {
     BSORT_TRY(set_smem(k_records_sort<1024, 16>, smem_bytes_for_cap(kRecordChunk, true)));
-    BSORT_TRY(set_smem(k_pack_units<1024>, 16 * 8193));
+    BSORT_TRY(set_smem(k_pack_units<1024>, 16 * (kMaxBuckets + 1)));
     return cudaSuccess;
 }
 
 cudaError_t launch_records_chunk_sort(const uint64_t *src, uint64_t *dst, uint32_t n_rec,
-                                      uint32_t n_pad, uint64_t *spl, uint32_t m, uint32_t s,
+                                      uint32_t n_pad, uint64_t *spl, uint32_t s, uint32_t b,
                                       cudaStream_t st)
 {
     const uint32_t chunks = n_pad / kRecordChunk;
     k_records_sort<1024, 16><<<chunks, 1024, smem_bytes_for_cap(kRecordChunk, true), st>>>(
-        src, dst, n_rec, chunks == 1 ? spl : nullptr, m, s);
+        src, dst, n_rec, chunks == 1 ? spl : nullptr, s, b);
     return cudaGetLastError();
 }
 
@@ -592,23 +560,23 @@ cudaError_t launch_merge_pass(const uint64_t *src, uint64_t *dst, uint32_t n_pad
     return cudaGetLastError();
 }
 
-cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t m, uint32_t s,
+cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint32_t b,
                                     uint64_t *spl, cudaStream_t st)
 {
-    k_select_splitters<<<(s + 255) / 256, 256, 0, st>>>(sorted, m, s, spl);
+    k_select_splitters<<<(b + 255) / 256, 256, 0, st>>>(sorted, n_rec, b, spl);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
-                                const uint64_t *spl, uint32_t t, uint32_t s, uint32_t m,
-                                uint32_t *counts, uint32_t *cum, uint32_t *srcb,
+                                const uint64_t *spl, uint32_t t, uint32_t s, uint32_t b,
+                                uint32_t m, uint32_t *counts, uint32_t *cum, uint32_t *srcb,
                                 cudaStream_t st)
 {
     constexpr int T = 128;
-    const uint32_t jb = s >= 8 * T ? 8 : (s + T - 1) / T;  // splitters per thread
-    const uint32_t gpt = (s + T * jb - 1) / (T * jb);
-    k_sample_index<T><<<m * gpt, T, 0, st>>>(tiles_k, samples, spl, t, s, m, counts, cum, srcb,
-                                             jb);
+    const uint32_t jb = b >= 8 * T ? 8 : (b + T - 1) / T;  // splitters per thread
+    const uint32_t gpt = (b + T * jb - 1) / (T * jb);
+    k_sample_index<T><<<m * gpt, T, 0, st>>>(tiles_k, samples, spl, t, s, b, m, counts, cum,
+                                             srcb, jb);
     return cudaGetLastError();
 }
 
@@ -621,13 +589,13 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
 }
 
 cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const uint32_t *offsets,
-                            const uint32_t *srcb, const uint32_t *blk, uint32_t t, uint32_t m,
-                            uint32_t runs, uint32_t n_pad, int val_bytes, uint32_t *reloc_k,
-                            void *reloc_v, cudaStream_t st)
+                            const uint32_t *srcb, const uint32_t *blk, uint32_t runs,
+                            uint32_t n_pad, int val_bytes, uint32_t *reloc_k, void *reloc_v,
+                            cudaStream_t st)
 {
     constexpr int T = (kRelocPart / kBlockItems) * 32;
     const uint32_t grid = (n_pad + kRelocPart - 1) / kRelocPart;
-    k_relocate<T><<<grid, T, 0, st>>>(tiles_k, tiles_v, offsets, srcb, blk, t, m, runs, n_pad,
+    k_relocate<T><<<grid, T, 0, st>>>(tiles_k, tiles_v, offsets, srcb, blk, runs, n_pad,
                                       val_bytes, reloc_k, reloc_v);
     return cudaGetLastError();
 }
@@ -640,11 +608,11 @@ cudaError_t launch_block_index(uint32_t *offsets, uint32_t runs, uint32_t n_pad,
     return cudaGetLastError();
 }
 
-cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t s, uint32_t n_pad,
+cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t b, uint32_t n_pad,
                               uint32_t Q, uint32_t *units, int *err, cudaStream_t st)
 {
-    const int sm = (int)(4 * (s + 1) * 4);
-    k_pack_units<1024><<<1, 1024, sm, st>>>(offsets, m, s, n_pad, Q, units, err);
+    const int sm = (int)(4 * (b + 1) * 4);
+    k_pack_units<1024><<<1, 1024, sm, st>>>(offsets, m, b, n_pad, Q, units, err);
     return cudaGetLastError();
 }
 
@@ -653,6 +621,7 @@ cudaError_t init_kernels()
     cudaError_t e = init_misc_kernels();
     if (e == cudaSuccess) e = init_sort_keys_kernels();
     if (e == cudaSuccess) e = init_sort_pairs_kernels();
+    if (e == cudaSuccess) e = init_batch_kernels();
     return e;
 }
 

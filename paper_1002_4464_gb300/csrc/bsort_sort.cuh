@@ -160,9 +160,9 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
         // of its block and the next (positions of a warp span < 2 blocks)
         const uint32_t y0 = (uint32_t)(L + ustart + wb_pos<E>(warp, lane, 0));
         uint32_t q = 0;
+        const uint32_t nblk = (uint32_t)((n_pad + kBlockItems - 1) / kBlockItems);
         if (ustart + wb_pos<E>(warp, 0, 0) < uend) {  // the warp holds real items
             const uint32_t wy = (uint32_t)(L + ustart + wb_pos<E>(warp, 0, 0));
-            const uint32_t nblk = (uint32_t)((n_pad + kBlockItems - 1) / kBlockItems);
             const uint32_t b = wy / (uint32_t)kBlockItems;  // < nblk since wy < R <= n_pad
             uint32_t lo = g.blk[b];
             uint32_t hi = b + 2 < nblk ? g.blk[b + 2] : g.runs - 1;
@@ -173,9 +173,8 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
             }
             q = lo;
         }
-        uint32_t ti = q % g.m;  // sublist of run q
         uint32_t rs = g.offsets[q], re = g.offsets[q + 1];
-        uint32_t base = ti * g.t + g.srcb[q];  // position of run q's first item
+        uint32_t base = g.srcb[q];  // position of run q's first item
 #pragma unroll
         for (int k = 0; k < E; ++k) {
             const int x = ustart + wb_pos<E>(warp, lane, k);
@@ -184,13 +183,8 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
             uint32_t pos = 0xFFFFFFFFu;  // pads sort after every real item
             if (x < uend) {
                 if (y >= re) {
-                    do {
-                        ++q;
-                        if (++ti == g.m) ti = 0;
-                        rs = re;
-                        re = g.offsets[q + 1];
-                    } while (y >= re);
-                    base = ti * g.t + g.srcb[q];
+                    run_advance<kBlockItems>(g.offsets, g.blk, nblk, g.runs, y, q, rs, re);
+                    base = g.srcb[q];
                 }
                 pos = base + (y - rs);
                 key = src_k[pos];

@@ -131,6 +131,26 @@ def keys_16distinct(n: int, seed: int) -> np.ndarray:
     return draws32(seed, n) & np.uint32(0xF0000000)
 
 
+def batch_sizes(num: int, seed: int, lo_log2: int = 7, hi_log2: int = 20,
+                cap: int = 1 << 30) -> np.ndarray:
+    """Sizes of the arrays of a batched workload, log-uniform in
+    [2^lo, 2^hi]: size_k = floor(2^(lo + (hi - lo) x_k)) with x_k =
+    (x_k64 >> 11) * 2^-53 in [0, 1).  If they sum to more than cap, every
+    size is scaled by one factor f (floor(size * f), at least 2^lo), f the
+    largest of cap/sum, cap/sum * (1 - 2^-10), ... that keeps the sum <= cap."""
+    x = (draws64(seed, num) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    sizes = np.floor(2.0 ** (lo_log2 + (hi_log2 - lo_log2) * x)).astype(np.int64)
+    total = int(sizes.sum())
+    if total <= cap:
+        return sizes
+    f = cap / total
+    while True:
+        scaled = np.maximum(np.floor(sizes * f).astype(np.int64), 1 << lo_log2)
+        if int(scaled.sum()) <= cap:
+            return scaled
+        f *= 1.0 - 2.0 ** -10
+
+
 def keys_u64(n: int, seed: int) -> np.ndarray:
     return draws64(seed, n)
 

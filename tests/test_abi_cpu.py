@@ -6,9 +6,12 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
+import oracle
 import paper_1002_4464_gb300 as pkg
+import synth
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "bsort.h")
@@ -40,8 +43,9 @@ def test_status_strings():
     assert pkg.bsort_status_string(pkg.BSORT_ETIMEOUT) == "BSORT_ETIMEOUT"
 
 
-def _handle(tile=0, samples=0):
-    return pkg.bsort_create(pkg.bsort_config(device=0, tile=tile, samples=samples))
+def _handle(tile=0, samples=0, buckets=0):
+    return pkg.bsort_create(pkg.bsort_config(device=0, tile=tile, samples=samples,
+                                             buckets=buckets))
 
 
 def test_plan_config1():
@@ -66,9 +70,47 @@ def test_plan_auto_bound_fits_unit(n):
     else:
         assert p.t % p.s == 0 and p.m * p.t == p.n_padded >= n > p.n_padded - p.t
         w = p.t // p.s
-        assert p.bucket_bound == p.n_padded // p.s + (p.m - 1) * (w - 1)
-        assert p.bucket_bound <= 2 * p.n_padded // p.s
+        # b buckets from the m*s samples: ceil(ms/b) sample ranks of w items
+        # plus w-1 items of every other sublist
+        assert 1 <= p.b <= p.m * p.s
+        assert p.bucket_bound == -(-p.m * p.s // p.b) * w + (p.m - 1) * (w - 1)
+        assert p.bucket_bound == oracle.bucket_bound(p.n_padded, p.m, p.s, p.b)
         assert p.unit_capacity >= p.bucket_bound
+        # about (k + 0.1) average buckets per unit for a whole k
+        per_unit = p.unit_capacity * p.b / p.n_padded
+        assert per_unit >= 1.0
+    pkg.bsort_destroy(h)
+
+
+def test_plan_bucket_count():
+    """b = s when s is given (Section 4, Step 5); a forced b is kept and its
+    bound is ceil(ms/b) w + (m-1)(w-1); b beyond m*s or 12288 is refused."""
+    h = _handle(4096, 64)
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 20)
+    assert p.b == p.s == 64 and p.bucket_bound == 32449
+    pkg.bsort_destroy(h)
+    h = _handle(4096, 64, 100)
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 20)
+    assert p.b == 100
+    assert p.bucket_bound == -(-256 * 64 // 100) * 64 + 255 * 63 == 26561
+    pkg.bsort_destroy(h)
+    h = _handle(4096, 64, 40)  # fewer buckets than samples: bound 41*64 + 16065
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 20)
+    assert p.b == 40 and p.bucket_bound == 410 * 64 + 255 * 63
+    pkg.bsort_destroy(h)
+    h = _handle(4096, 64, 256 * 64 + 1)
+    with pytest.raises(pkg.BsortError) as e:
+        pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 20)
+    assert e.value.status in (pkg.BSORT_EINVAL, pkg.BSORT_EUNSUPPORTED)
+    pkg.bsort_destroy(h)
+    h = _handle(0, 0, 12289)
+    with pytest.raises(pkg.BsortError) as e:
+        pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 24)
+    assert e.value.status == pkg.BSORT_EUNSUPPORTED
+    pkg.bsort_destroy(h)
+    h = _handle(0, 0, 3000)  # forced b, planner's t and s
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 24)
+    assert p.b == 3000 and p.unit_capacity >= p.bucket_bound
     pkg.bsort_destroy(h)
 
 
@@ -100,3 +142,59 @@ def test_plan_paper_worked_parameters():
     assert e.value.status == pkg.BSORT_EUNSUPPORTED
     assert "1032161" in pkg.bsort_last_error(h)  # 2^25/64 + (2^14-1)(32-1)
     pkg.bsort_destroy(h)
+
+
+def test_plan_batch_classes():
+    """Segments up to batch_direct_max keys are sorted whole, larger ones up to
+    524288 by the segment-aware sample sort (sublists of 32768, s = 1024, b
+    buckets whose bound fits a 32768-key unit), larger ones by a plain sort."""
+    sizes = [0, 1, 2, 100, 2048, 2049, 32768, 131072, 131073, 200000, 524288, 524289, 3]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    h = _handle()
+    p = pkg.bsort_plan_batch(h, pkg.BSORT_U32, off)
+    assert p.num_segs == len(sizes) and p.n == sum(sizes)
+    assert p.direct_segs == 7  # 2 .. 131072 (0 and 1 need no sort)
+    assert p.sampled_segs == 3 and p.large_segs == 1
+    assert p.sublists == 5 + 7 + 16
+    b_expect = 0
+    for n in (131073, 200000, 524288):
+        m = -(-n // 32768)
+        b = next(b for b in range(1, m * 1024 + 1)
+                 if oracle.bucket_bound(m * 32768, m, 1024, b) <= 32768)
+        b_expect += b
+    assert p.buckets == b_expect
+    pkg.bsort_destroy(h)
+    h = pkg.bsort_create(pkg.bsort_config(device=0, batch_direct_max=32768))
+    p = pkg.bsort_plan_batch(h, pkg.BSORT_U32, off)
+    assert p.direct_segs == 6 and p.sampled_segs == 4
+    pkg.bsort_destroy(h)
+    with pytest.raises(pkg.BsortError):
+        pkg.bsort_create(pkg.bsort_config(device=0, batch_direct_max=262145))
+
+
+def test_plan_batch_errors():
+    h = _handle()
+    with pytest.raises(pkg.BsortError) as e:
+        pkg.bsort_plan_batch(h, pkg.BSORT_U32, np.array([0, 10, 5], np.uint64))
+    assert e.value.status == pkg.BSORT_EINVAL
+    with pytest.raises(pkg.BsortError) as e:
+        pkg.bsort_plan_batch(h, pkg.BSORT_U64, np.array([0, 10], np.uint64))
+    assert e.value.status == pkg.BSORT_EUNSUPPORTED
+    with pytest.raises(pkg.BsortError) as e:
+        pkg.bsort_plan_batch(h, pkg.BSORT_U32, np.array([0, 1 << 32], np.uint64))
+    assert e.value.status == pkg.BSORT_EUNSUPPORTED
+    p = pkg.bsort_plan_batch(h, pkg.BSORT_U32, np.array([0], np.uint64))
+    assert p.num_segs == 0 and p.n == 0 and p.num_kernels == 0
+    pkg.bsort_destroy(h)
+
+
+def test_batch_sizes_generator():
+    """Log-uniform sizes in [2^7, 2^20], scaled to at most 2^30 keys in all."""
+    s = synth.batch_sizes(20000, synth.seed_for(4, 0))
+    assert s.size == 20000 and s.min() >= 128 and s.max() <= 1 << 20
+    assert s.sum() <= 1 << 30 and s.sum() > 0.99 * (1 << 30)
+    small = synth.batch_sizes(100, synth.seed_for(4, 1), cap=1 << 40)
+    assert small.min() >= 128 and small.max() < 1 << 20
+    # the scaling keeps the order of the sizes
+    raw = synth.batch_sizes(20000, synth.seed_for(4, 0), cap=1 << 40)
+    assert np.all(np.diff(s[np.argsort(raw, kind="stable")]) >= 0)

@@ -1,0 +1,119 @@
+"""GPU parity of the batched sort (bsort_sort_batch): every segment of the
+output equals the textbook sort of that segment of the input, bit for bit,
+and keys outside every segment are left untouched."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_1002_4464_gb300 as pkg  # noqa: E402
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).cuda()
+
+
+def _expect(keys, off, key_type="u32"):
+    """Per-segment textbook sort (oracle); keys outside segments unchanged."""
+    want = keys.copy()
+    for q in range(len(off) - 1):
+        a, b = int(off[q]), int(off[q + 1])
+        if b > a:
+            want[a:b] = oracle.textbook_sort(keys[a:b], key_type)
+    return want
+
+
+def _run(sorter, keys, off, key_type="u32", out=None):
+    d_in = _dev(keys)
+    if out is None:
+        d_out = sorter.sort_batch(d_in, off, key_type=key_type)
+    else:
+        d_out = _dev(out)
+        sorter.sort_batch(d_in, off, out=d_out, key_type=key_type)
+    sorter.sync()
+    return d_out.cpu().numpy().view(np.uint32)
+
+
+# one segment of every class: empty, one key, direct shapes 2048 .. 8 x 32768,
+# sampled segments (ragged last sublist, exact multiples), a plain-sorted one
+EDGE_SIZES = [0, 1, 2, 3, 127, 2047, 2048, 2049, 4096, 8191, 16384, 16385, 32768, 32769,
+              65536, 65537, 131072, 131073, 163840, 200001, 262144, 300000, 524288, 524289,
+              1, 0, 5]
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zero", "sorted", "reverse", "staggered"])
+def test_batch_every_class(dist):
+    sizes = np.array(EDGE_SIZES, np.int64)
+    off = np.concatenate([[7], 7 + np.cumsum(sizes)]).astype(np.uint64)  # keys 0..6 outside
+    n = int(off[-1]) + 11                                                # and 11 after
+    keys = synth.keys_u32(dist, n, synth.seed_for(4, synth.DISTRIBUTIONS.index(dist)))
+    sorter = pkg.BucketSorter()
+    p = sorter.plan_batch(off)
+    assert p.direct_segs > 0 and p.sampled_segs > 0 and p.large_segs == 1
+    sentinel = np.full(n, 0xA5A5A5A5, np.uint32)
+    got = _run(sorter, keys, off, out=sentinel)
+    want = _expect(keys, off)
+    want[:7] = 0xA5A5A5A5
+    want[int(off[-1]):] = 0xA5A5A5A5
+    assert np.array_equal(got, want)
+    sorter.close()
+
+
+@pytest.mark.parametrize("direct_max", [2048, 32768, 131072, 262144])
+def test_batch_log_uniform(direct_max):
+    """A scaled-down batched workload: 400 arrays, log-uniform sizes in
+    [2^7, 2^20] (about 2^25 keys in all), uniform keys."""
+    sizes = synth.batch_sizes(400, synth.seed_for(4, 0, 1), cap=1 << 27)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    keys = synth.keys_u32("uniform", n, synth.seed_for(4, 0, 2))
+    sorter = pkg.BucketSorter(batch_direct_max=direct_max)
+    got = _run(sorter, keys, off)
+    seg = np.repeat(np.arange(len(sizes)), sizes)
+    want = keys[np.lexsort((keys, seg))]  # library sort, segment-major
+    assert np.array_equal(got, want)
+    sorter.close()
+
+
+def test_batch_f32_and_in_place():
+    sizes = np.array([3000, 140000, 40000, 260000, 9], np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    f = synth.keys_f32("gaussian", n, synth.seed_for(4, 3))
+    f[:8] = np.array([np.inf, -np.inf, np.nan, -0.0, 0.0, 1e-45, -1e-45, -np.nan], np.float32)
+    f[140000:140008] = f[:8]
+    sorter = pkg.BucketSorter()
+    d = torch.from_numpy(f.copy()).cuda()
+    sorter.sort_batch(d, off, out=d, key_type="f32")
+    sorter.sync()
+    got = d.cpu().numpy().view(np.uint32)
+    want = _expect(f, off, "f32").view(np.uint32)
+    assert np.array_equal(got, want)
+    sorter.close()
+
+
+def test_batch_equals_one_at_a_time():
+    """Each segment's result is the same sorted alone and in the batch."""
+    sizes = synth.batch_sizes(200, synth.seed_for(4, 4), cap=1 << 24)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    keys = synth.keys_zipf(int(off[-1]), synth.seed_for(4, 5))
+    sorter = pkg.BucketSorter()
+    got = _run(sorter, keys, off)
+    d_in = _dev(keys)
+    alone = np.empty_like(keys)
+    for q in range(len(sizes)):
+        a, b = int(off[q]), int(off[q + 1])
+        o = sorter.sort_keys(d_in[a:b])
+        sorter.sync()
+        alone[a:b] = o.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, alone)
+    # and again: the batch is deterministic
+    assert np.array_equal(_run(sorter, keys, off), got)
+    sorter.close()

@@ -31,17 +31,18 @@ def _gpu_sort_keys(sorter, keys, key_type="u32"):
     return d_out.cpu().numpy().view(np.uint32)
 
 
-def _check_intermediates(sorter, want, n_pad, m, s):
+def _check_intermediates(sorter, want, n_pad, m, s, b=0):
+    b = b or s
     im = pkg
     got_t = sorter.intermediate(im.BSORT_IM_TILES, n_pad * 4, np.uint32)
     assert np.array_equal(got_t, want["tile_keys"].astype(np.uint32)), "Step 2 sublists"
     got_s = sorter.intermediate(im.BSORT_IM_SAMPLES, m * s * 8, np.uint64)
     assert np.array_equal(got_s, _rec(want["samp_keys"], want["samp_p"])), "Step 3 samples"
-    got_g = sorter.intermediate(im.BSORT_IM_SPLITTERS, s * 8, np.uint64)
+    got_g = sorter.intermediate(im.BSORT_IM_SPLITTERS, b * 8, np.uint64)
     assert np.array_equal(got_g, _rec(want["spl_keys"], want["spl_p"])), "Step 5 splitters"
-    got_a = sorter.intermediate(im.BSORT_IM_COUNTS, m * s * 4, np.uint32)
+    got_a = sorter.intermediate(im.BSORT_IM_COUNTS, m * b * 4, np.uint32)
     assert np.array_equal(got_a, want["counts"].astype(np.uint32)), "Step 6 counts"
-    got_l = sorter.intermediate(im.BSORT_IM_OFFSETS, m * s * 4, np.uint32)
+    got_l = sorter.intermediate(im.BSORT_IM_OFFSETS, m * b * 4, np.uint32)
     assert np.array_equal(got_l, want["offsets"].astype(np.uint32)), "Step 7 offsets"
     got_r = sorter.intermediate(im.BSORT_IM_RELOCATED, n_pad * 4, np.uint32)
     assert np.array_equal(got_r, want["reloc_keys"].astype(np.uint32)), "Step 8 relocation"
@@ -57,6 +58,52 @@ def test_config1_all_intermediates(dist):
     got = _gpu_sort_keys(sorter, keys)
     assert np.array_equal(got, want["keys"])
     _check_intermediates(sorter, want, want["n_padded"], want["m"], s)
+    sorter.close()
+
+
+@pytest.mark.parametrize("n,t,s,b", [
+    (1 << 20, 4096, 64, 67),        # b > s, not a divisor of m*s
+    (1 << 20, 4096, 64, 40),        # b < s
+    (1 << 18, 4096, 64, 64 * 64),   # every sample a splitter (b = m*s)
+    (50000, 4096, 64, 1),           # one bucket: Step 9 sorts everything
+    (3 * 4096 + 1000, 4096, 16, 23),
+    (200003, 16384, 256, 3001),
+])
+@pytest.mark.parametrize("dist", ["uniform", "zero", "staggered"])
+def test_decoupled_buckets_intermediates(n, t, s, b, dist):
+    """b splitters taken from the m*s sorted samples at ranks
+    floor((j+1)ms/b) - 1 (b = s is the paper's Step 5), Steps 6-9 over b
+    buckets: every intermediate equals the oracle's."""
+    m = -(-n // t)
+    if oracle.bucket_bound(m * t, m, s, b) > 8 * 32768:
+        pytest.skip("bound beyond the largest Step-9 unit")
+    keys = synth.keys_u32(dist, n, synth.seed_for(2, 11, b))
+    want = oracle.paper_sort(keys, t, s, "u32", b=b)
+    sorter = pkg.BucketSorter(tile=t, samples=s, buckets=b)
+    p = sorter.plan(n)
+    assert (p.t, p.s, p.b) == (t, s, b)
+    assert p.bucket_bound == oracle.bucket_bound(m * t, m, s, b)
+    got = _gpu_sort_keys(sorter, keys)
+    assert np.array_equal(got, want["keys"])
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], s, b)
+    sorter.close()
+    low = pkg.BucketSorter(tile=t, samples=s, buckets=b, low_memory=True)
+    assert np.array_equal(_gpu_sort_keys(low, keys), want["keys"])
+    low.close()
+
+
+def test_auto_buckets_intermediates():
+    """The planner's own b (not s) at n = 2^22: intermediates against the
+    oracle run with the same t, s and b."""
+    n = 1 << 22
+    keys = synth.keys_u32("gaussian", n, synth.seed_for(2, 12))
+    sorter = pkg.BucketSorter()
+    p = sorter.plan(n)
+    assert p.b != p.s and not p.single_tile
+    want = oracle.paper_sort(keys, p.t, p.s, "u32", b=p.b)
+    got = _gpu_sort_keys(sorter, keys)
+    assert np.array_equal(got, want["keys"])
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], p.s, p.b)
     sorter.close()
 
 
@@ -133,17 +180,18 @@ def test_pairs_stable(kind, vdtype):
     sorter.close()
 
 
-def test_pairs_intermediates_forced_plan():
+@pytest.mark.parametrize("b", [0, 97])
+def test_pairs_intermediates_forced_plan(b):
     n, t, s = 100000, 4096, 64
     keys = synth.keys_zipf(n, synth.seed_for(3, 2))
     vals = np.arange(n, dtype=np.uint32)
-    want = oracle.paper_sort(keys, t, s, "u32", vals=vals)
-    sorter = pkg.BucketSorter(tile=t, samples=s)
+    want = oracle.paper_sort(keys, t, s, "u32", vals=vals, b=b)
+    sorter = pkg.BucketSorter(tile=t, samples=s, buckets=b)
     ok, ov = sorter.sort_pairs(_to_dev_u32(keys), _to_dev_u32(vals))
     sorter.sync()
     assert np.array_equal(ok.cpu().numpy().view(np.uint32), want["keys"])
     assert np.array_equal(ov.cpu().numpy().view(np.uint32), want["vals"])
-    _check_intermediates(sorter, want, want["n_padded"], want["m"], s)
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], s, b)
     sorter.close()
 
 
