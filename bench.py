@@ -8,7 +8,14 @@ uniformly (SplitMix64), keys only.  Prints ONE JSON line on rank 0.
                   [--n N] [--dist uniform] [--key-type u32|f32] [--dists]
                   [--batch-arrays 20000] [--batch-cap 2^30]
 
-The line also carries "batched": the batched workload (20,000 independent
+The line also carries "served": a Poisson stream of sort jobs (2,000 per
+second for 60 s, 50/50 uint32/uint64, sizes log-uniform in [2^10, 2^24],
+50/50 uniform/Zipf keys, pinned host buffers in and out, 40 GB device
+budget) through bsort_submit/bsort_poll, against the same arrivals sorted
+one at a time (bsort_sort_keys_host, then a wait); latency = the time the
+sorted keys are in host memory minus the scheduled arrival.
+
+And "batched": the batched workload (20,000 independent
 uint32 arrays, sizes log-uniform in [2^7, 2^20], scaled to at most 2^30 keys
 in all, uniform keys) sorted by one bsort_sort_batch call, against the same
 arrays sorted by one plain bsort_sort_keys call each, on the same stream.
@@ -60,7 +67,8 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=1 << 28)
     p.add_argument("--dist", default="uniform")
-    p.add_argument("--key-type", default="u32", choices=["u32", "f32"])
+    p.add_argument("--key-type", default="u32", choices=["u32", "f32", "u64"],
+                   help="u64: uniform 64-bit keys (the --dist option is ignored)")
     p.add_argument("--dists", action="store_true",
                    help="also time every distribution (spread across distributions)")
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -75,6 +83,10 @@ def _args():
     p.add_argument("--batch-cap", type=int, default=1 << 30,
                    help="batched workload: total keys at most")
     p.add_argument("--batch-steps", type=int, default=3)
+    p.add_argument("--serve-seconds", type=float, default=60.0,
+                   help="served stream: seconds of Poisson arrivals (0: skip the served line)")
+    p.add_argument("--serve-rate", type=float, default=2000.0, help="arrivals per second")
+    p.add_argument("--serve-budget", type=int, default=40 << 30, help="device bytes")
     return p.parse_args()
 
 
@@ -207,7 +219,14 @@ def _sample_keys(args, rank, count):
     import synth
     if args.key_type == "f32":
         return synth.keys_f32(args.dist, count, synth.seed_for(2, _dist_index(args.dist), rank))
+    if args.key_type == "u64":
+        return synth.keys_u64(count, synth.seed_for(2, _dist_index(args.dist), rank))
     return synth.keys_u32(args.dist, count, synth.seed_for(2, _dist_index(args.dist), rank))
+
+
+def _kb(args):
+    """Key bytes of the workload."""
+    return 8 if args.key_type == "u64" else 4
 
 
 def _dist_index(name):
@@ -270,8 +289,8 @@ def _config(args, world):
             else "%s %s keys-only sort, n=%d per GPU" % (args.dist, args.key_type, args.n),
             "n": args.n, "key_type": args.key_type, "distribution": args.dist,
             "global_keys": args.n * world, "parallelism": "replicas x%d" % world,
-            "l2_policy": "input (%d MB) larger than the 129 MB L2; no flush" % (args.n * 4 >> 20)
-            if args.n * 4 > 129 * 2 ** 20 else "input smaller than L2 (resident)"}
+            "l2_policy": "input (%d MB) larger than the 129 MB L2; no flush" % (args.n * _kb(args) >> 20)
+            if args.n * _kb(args) > 129 * 2 ** 20 else "input smaller than L2 (resident)"}
 
 
 def run_ours(args):
@@ -292,6 +311,8 @@ def run_ours(args):
         seed = synth.seed_for(2, _dist_index(dname), rank)
         if args.key_type == "f32":
             return synth.keys_f32_torch(dname, args.n, seed, device=dev)
+        if args.key_type == "u64":
+            return synth.draws64_torch(seed, args.n, device=dev)
         return synth.keys_u32_torch(dname, args.n, seed, device=dev)
 
     keys = make_keys(args.dist)
@@ -314,6 +335,10 @@ def run_ours(args):
         kin = keys.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
         assert int(kin.sum()) == int(o.sum()), "multiset changed"
         del kin
+    if args.key_type == "u64":  # unsigned order = signed order with the top bit flipped
+        o = out ^ torch.tensor(-(1 << 63), dtype=torch.int64, device=dev)
+        assert bool((o[1:] >= o[:-1]).all()), "output not sorted"
+        assert int(keys.sum()) == int(out.sum()), "multiset changed"
     del o
     sorter.kernel_times()  # reset the timing ring
 
@@ -366,7 +391,7 @@ def run_ours(args):
                         "alg_ops_per_launch": alg, "merge_levels": levels,
                         "ms_per_launch": dom_ms}
         else:
-            alg = 2 * plan.n_padded * 4
+            alg = 2 * plan.n_padded * _kb(args)
             achieved = alg / (dom_ms / 1e3) / 1e9
             roofline = {"bound": "hbm", "kernel": KERNEL_FN.get(dom, dom), "achieved": achieved,
                         "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
@@ -374,7 +399,7 @@ def run_ours(args):
                         "ms_per_launch": dom_ms}
         roofline["traffic"] = _traffic_for(KERNEL_FN.get(dom, dom), _config(args, 1)["workload"])
         # whole-step HBM roofline: three read+write passes (Steps 2, 8, 9)
-        whole = 6 * args.n * 4 / (ms_step / 1e3) / 1e9
+        whole = 6 * args.n * _kb(args) / (ms_step / 1e3) / 1e9
         roofline["step_hbm_achieved_gbs"] = whole
         roofline["step_hbm_peak_gbs"] = hbm_peak
         roofline["step_hbm_frac"] = whole / hbm_peak
@@ -397,7 +422,8 @@ def run_ours(args):
         sorter.sync()
         ems = e0.elapsed_time(e1) / args.e2e_steps
         e2e = {"value": args.n / (ems / 1e3) / 1e9 * world, "unit": UNIT,
-               "h2d_bytes_per_step": args.n * 4, "d2h_bytes_per_step": args.n * 4,
+               "h2d_bytes_per_step": args.n * _kb(args),
+               "d2h_bytes_per_step": args.n * _kb(args),
                "ms_per_step": ems}
         del h_in, h_out
 
@@ -438,6 +464,8 @@ def run_ours(args):
         keys_np = keys[:sample_n].cpu().numpy()
         if args.key_type == "u32":
             keys_np = keys_np.view(np.uint32)
+        elif args.key_type == "u64":
+            keys_np = keys_np.view(np.uint64)
         rates = []
         t_spent = 0.0
         while t_spent < 10.0 and len(rates) < 8:
@@ -452,6 +480,7 @@ def run_ours(args):
     sorter.close()
     del keys, out
     batched = run_batched(args, pkg, synth, dev, stream, rank, world) if args.batch_arrays else None
+    served = run_served(args, pkg, synth, dev, rank) if args.serve_seconds > 0 else None
 
     if rank == 0:
         line = {
@@ -470,6 +499,8 @@ def run_ours(args):
             line["distributions"] = dists
         if batched is not None:
             line["batched"] = batched
+        if served is not None:
+            line["served"] = served
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
@@ -547,6 +578,133 @@ def run_batched(args, pkg, synth, dev, stream, rank, world):
                            "launch": "one bsort_sort_keys call per array, same stream"},
             "speedup_vs_sequential": s_ms / b_ms, "gpu_launches": bplan.num_kernels,
             "plan": bplan.as_dict(), "per_kernel_ms": per_kernel}
+
+
+def run_served(args, pkg, synth, dev, rank):
+    """The served workload: a Poisson stream of jobs through the request loop
+    (bsort_submit / bsort_poll) and, for comparison, the same arrivals sorted
+    one at a time.  Inputs come from pinned pools (each job sorts the first
+    n keys of the pool of its key width and distribution); each job in
+    flight owns one of a ring of pinned output buffers."""
+    import numpy as np
+    import torch
+
+    rate, secs = args.serve_rate, args.serve_seconds
+    cap = int(secs * rate * 1.5) + 16
+    arr = synth.poisson_arrivals(cap, rate, synth.seed_for(5, 0, rank))
+    njobs = int((arr < secs).sum())
+    arr = arr[:njobs]
+    sizes = synth.batch_sizes(njobs, synth.seed_for(5, 1, rank), lo_log2=10, hi_log2=24,
+                              cap=1 << 62)
+    bits = synth.draws64(synth.seed_for(5, 2, rank), njobs)
+    wide = (bits & np.uint64(1)) != 0          # 64-bit keys
+    zipf = (bits & np.uint64(2)) != 0          # Zipf(1.1) keys
+    maxn = 1 << 24
+    pools = {}
+    for w in (False, True):
+        for z in (False, True):
+            seed = synth.seed_for(5, 3 + 2 * int(w) + int(z), rank)
+            if w:
+                a = synth.keys_zipf_u64(maxn, seed) if z else synth.keys_u64(maxn, seed)
+                pools[(w, z)] = torch.from_numpy(a.view(np.int64)).pin_memory()
+            else:
+                a = synth.keys_zipf(maxn, seed) if z else synth.keys_u32("uniform", maxn, seed)
+                pools[(w, z)] = torch.from_numpy(a.view(np.int32)).pin_memory()
+    ring = 32
+    slots = [torch.empty(maxn, dtype=torch.int64).pin_memory() for _ in range(ring)]
+    kt_of = {False: pkg.BSORT_U32, True: pkg.BSORT_U64}
+
+    def job(k, slot):
+        w, z, n = bool(wide[k]), bool(zipf[k]), int(sizes[k])
+        src = pools[(w, z)]
+        dst = slots[slot] if w else slots[slot].view(torch.int32)
+        return kt_of[w], src.data_ptr(), dst.data_ptr(), n, src, dst
+
+    def check(k, slot):
+        kt, _, _, n, src, dst = job(k, slot)
+        if kt == pkg.BSORT_U64:
+            flip = torch.tensor(-(1 << 63), dtype=torch.int64)
+            want = torch.sort(src[:n] ^ flip).values ^ flip
+        else:
+            want = (torch.sort(src[:n].to(torch.int64) & 0xFFFFFFFF).values).to(torch.int32)
+        return torch.equal(dst[:n], want)
+
+    # served: arrivals submitted at their scheduled times, results polled
+    srv = pkg.SortServer(device=dev.index, budget_bytes=args.serve_budget)
+    kt, a, b, n, _, _ = job(0, 0)
+    w0 = pkg.bsort_submit(srv.h, kt, a, b, min(n, 4096))  # starts the loop (warm-up)
+    while pkg.bsort_poll(srv.h, w0) is None:
+        time.sleep(1e-4)
+    lat = np.zeros(njobs)
+    done_at = np.zeros(njobs, np.int64)
+    free, inflight = list(range(ring)), {}
+    checked = 0
+    t0 = pkg.bsort_clock_ns() + 50_000_000
+    nxt = done = 0
+    while done < njobs:
+        now = pkg.bsort_clock_ns()
+        while nxt < njobs and t0 + int(arr[nxt] * 1e9) <= now and free:
+            slot = free.pop()
+            kt, a, b, n, _, _ = job(nxt, slot)
+            inflight[pkg.bsort_submit(srv.h, kt, a, b, n)] = (nxt, slot)
+            nxt += 1
+        progressed = False
+        for t in list(inflight):
+            r = pkg.bsort_poll(srv.h, t)
+            if r is None:
+                continue
+            k, slot = inflight.pop(t)
+            assert r.status == pkg.BSORT_OK, "served job failed"
+            if k % 97 == 0 and checked < 24:  # spot checks against torch.sort
+                assert check(k, slot), "served job %d not sorted" % k
+                checked += 1
+            free.append(slot)
+            lat[k] = (r.done_ns - (t0 + int(arr[k] * 1e9))) / 1e6
+            done_at[k] = r.done_ns
+            done += 1
+            progressed = True
+        if not progressed:
+            time.sleep(2e-5)
+    st = srv.stats()
+    srv.close()
+    span = (int(done_at.max()) - t0) / 1e9
+    keys_total = int(sizes.sum())
+
+    # one at a time: the same arrivals, each sorted and copied back before the next
+    one = pkg.BucketSorter(device=dev.index)
+    one._ensure(maxn, "u64", 0, extra=maxn * 8)
+    lat1 = np.zeros(njobs)
+    t1 = pkg.bsort_clock_ns() + 50_000_000
+    last = t1
+    strm = one._stream()
+    for k in range(njobs):
+        at = t1 + int(arr[k] * 1e9)
+        while pkg.bsort_clock_ns() < at:
+            pass
+        kt, a, b, n, _, _ = job(k, 0)
+        pkg.bsort_sort_keys_host(one.h, kt, a, b, n, strm)
+        one.sync()
+        last = pkg.bsort_clock_ns()
+        lat1[k] = (last - at) / 1e6
+    one.close()
+    span1 = (last - t1) / 1e9
+
+    def pct(x, q):
+        return float(np.percentile(x, q))
+
+    return {"workload": "Poisson arrivals %.0f/s for %.0f s, %d jobs, 50/50 uint32/uint64, "
+                        "sizes log-uniform in [2^10, 2^24], 50/50 uniform/Zipf(1.1), pinned host "
+                        "buffers, %d GB budget" % (rate, secs, njobs, args.serve_budget >> 30),
+            "jobs": njobs, "keys": keys_total,
+            "value": keys_total / span / 1e9, "unit": UNIT,
+            "p50_ms": pct(lat, 50), "p99_ms": pct(lat, 99), "mean_ms": float(lat.mean()),
+            "jobs_per_s": njobs / span, "batches": st["batches"],
+            "mean_batch": njobs / max(st["batches"], 1), "max_batch": st["max_batch"],
+            "arena_peak_bytes": st["arena_peak_bytes"],
+            "one_at_a_time": {"value": keys_total / span1 / 1e9, "unit": UNIT,
+                              "p50_ms": pct(lat1, 50), "p99_ms": pct(lat1, 99),
+                              "mean_ms": float(lat1.mean()), "jobs_per_s": njobs / span1},
+            "latency": "sorted keys in host memory minus scheduled arrival"}
 
 
 def main():

@@ -57,7 +57,9 @@ typedef enum {
     BSORT_F32 = 1,  /* IEEE binary32 keys, total order
                        -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN;
                        bit patterns are preserved */
-    BSORT_U64 = 2   /* unsigned 64-bit keys (not served by this build) */
+    BSORT_U64 = 2   /* unsigned 64-bit keys: keys-only sorts (bsort_sort_keys,
+                       bsort_sort_keys_host); not pairs, batches or the
+                       no-allocation entry (BSORT_EUNSUPPORTED) */
 } bsort_key_type;
 
 /* Flags for bsort_config.flags. */
@@ -95,6 +97,12 @@ typedef struct {
     uint32_t batch_direct_max; /* bsort_sort_batch: largest segment sorted
                                   whole by one CTA or cluster (0 = 131072;
                                   at most 262144) */
+    uint32_t pad_;
+    uint64_t serve_budget_bytes; /* bsort_submit: device memory of the request
+                                  loop (0 = 4 GiB): half (at most 15 GiB)
+                                  holds admitted requests' keys, the rest is
+                                  split between the workspaces of its two
+                                  lanes */
 } bsort_config;
 
 /* The plan of one job (Step 1 parameters and the Step-9 unit). */
@@ -135,8 +143,9 @@ typedef enum {
     BSORT_IM_TILES = 0,      /* Step 2: sorted sublists, n' keys (transformed
                                 key domain for F32), sublist-major */
     BSORT_IM_SAMPLES = 1,    /* Step 3: m*s records (key << 32 | p), p = i*t + r,
-                                sublist-major */
-    BSORT_IM_SPLITTERS = 2,  /* Step 5: b records g_0..g_{b-1} */
+                                sublist-major; for BSORT_U64 two uint64 words
+                                per record (key, p) */
+    BSORT_IM_SPLITTERS = 2,  /* Step 5: b records g_0..g_{b-1} (same format) */
     BSORT_IM_COUNTS = 3,     /* Step 6: a_ij, uint32, bucket-major a[j*m + i], m*b */
     BSORT_IM_OFFSETS = 4,    /* Step 7: l_ij, uint32, bucket-major, m*b */
     BSORT_IM_RELOCATED = 5   /* Step 8: n' keys B_1 ... B_b (not with
@@ -181,11 +190,71 @@ bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_i
  * per sublist and per-segment splitters, all segments together in one
  * sequence of launches; larger ones by one plain sort each.  The segment
  * table is copied to the device from pinned staging owned by the handle.
- * kt: BSORT_U32 or BSORT_F32.  Errors: EINVAL (null pointers, decreasing
- * offsets, partial overlap), EUNSUPPORTED (too many keys), ENOMEM. */
+ * kt: BSORT_U32, BSORT_F32 or BSORT_U64 (64-bit keys: segments up to
+ * min(batch_direct_max, 131072) keys sorted whole, larger ones one plain
+ * sort each).  Errors: EINVAL (null pointers, decreasing offsets, partial
+ * overlap), EUNSUPPORTED (too many keys), ENOMEM. */
 bsort_status bsort_sort_batch(bsort_t h, bsort_key_type kt, const void *d_keys_in,
                               void *d_keys_out, const uint64_t *seg_offsets,
                               uint32_t num_segs, void *cuda_stream);
+
+/* ---- Served stream (no counterpart in the paper) ------------------------
+ * bsort_submit queues one independent sort job; a request loop owned by the
+ * handle (one worker thread, started by the first submit) admits queued
+ * jobs in arrival order while its device arena has room (the serving budget,
+ * bsort_config.serve_budget_bytes) and copies their keys in.  Small jobs
+ * (up to 524288 32-bit or 131072 64-bit keys) are sorted together as a
+ * batch (bsort_sort_batch's path) as soon as the previous small batch has
+ * finished sorting, on a high-priority stream; jobs that arrive meanwhile
+ * are copied in and form the next batch (continuous batching).  Larger jobs
+ * are sorted one at a time on a low-priority stream with a workspace of
+ * their own, so small jobs are not held behind them.  Every job's result is
+ * exactly the sort of its keys.  Once a handle has served a request its
+ * plain sort calls return BSORT_EBUSY. */
+typedef struct {
+    bsort_key_type key_type;  /* BSORT_U32, BSORT_F32 or BSORT_U64 */
+    uint32_t pad_;
+    uint64_t n;               /* keys */
+    const void *h_keys_in;    /* host memory (pinned for asynchronous copies);
+                                 must stay valid until the job is polled */
+    void *h_keys_out;         /* host memory for the sorted keys (may equal
+                                 h_keys_in) */
+} bsort_request;
+
+typedef struct {
+    bsort_status status;      /* BSORT_OK, or the failure of the job */
+    uint32_t batch_size;      /* jobs sorted in the same batch */
+    uint64_t submit_ns;       /* bsort_clock_ns() at bsort_submit */
+    uint64_t start_ns;        /* when its batch was launched */
+    uint64_t done_ns;         /* when its sorted keys were in h_keys_out */
+} bsort_result;
+
+typedef struct {
+    uint64_t arena_bytes;      /* device bytes for admitted jobs' keys */
+    uint64_t workspace_bytes;  /* workspace of the batches */
+    uint64_t arena_used_bytes; /* in use now */
+    uint64_t arena_peak_bytes; /* most ever in use (<= arena_bytes) */
+    uint64_t queued;           /* submitted, waiting for arena room */
+    uint64_t completed;        /* jobs finished */
+    uint64_t batches;          /* batches launched */
+    uint64_t max_batch;        /* most jobs in one batch */
+} bsort_serve_info;
+
+/* Queue one job; *ticket identifies it for bsort_poll.  Errors: EINVAL,
+ * ENOMEM (the job alone exceeds the arena or the workspace), and the
+ * errors of starting the loop (ENOMEM, ECUDA). */
+bsort_status bsort_submit(bsort_t h, const bsort_request *req, uint64_t *ticket);
+
+/* Non-blocking: BSORT_ENOTREADY while the job runs; BSORT_OK once its keys
+ * are in h_keys_out, with *out filled (the ticket is then released);
+ * BSORT_EINVAL for an unknown ticket. */
+bsort_status bsort_poll(bsort_t h, uint64_t ticket, bsort_result *out);
+
+/* Counters of the request loop (all zero before the first submit). */
+bsort_status bsort_serve_stats(bsort_t h, bsort_serve_info *out);
+
+/* The clock of bsort_result (a monotonic clock, nanoseconds). */
+uint64_t bsort_clock_ns(void);
 
 /* The plan bsort_sort_batch would use for these segments.  Host-only. */
 bsort_status bsort_plan_batch(bsort_t h, bsort_key_type kt, const uint64_t *seg_offsets,

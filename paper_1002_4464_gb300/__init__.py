@@ -22,6 +22,8 @@ __all__ = [
     "bsort_get_intermediate", "bsort_kernel_times", "bsort_kernel_name",
     "bsort_last_error", "bsort_status_string", "bsort_sort_keys_noalloc", "BucketSorter",
     "bsort_batch_info", "bsort_sort_batch", "bsort_plan_batch", "EXPORTED_SYMBOLS",
+    "bsort_request", "bsort_result", "bsort_serve_info", "bsort_submit", "bsort_poll",
+    "bsort_serve_stats", "bsort_clock_ns", "SortServer",
 ]
 
 BSORT_OK, BSORT_EINVAL, BSORT_ENOMEM, BSORT_ECUDA, BSORT_ETIMEOUT = 0, 1, 2, 3, 4
@@ -38,7 +40,8 @@ EXPORTED_SYMBOLS = (
     "bsort_sort_pairs", "bsort_sort_keys_host", "bsort_sync",
     "bsort_get_intermediate", "bsort_kernel_times", "bsort_kernel_name",
     "bsort_last_error", "bsort_status_string", "bsort_sort_keys_noalloc",
-    "bsort_sort_batch", "bsort_plan_batch",
+    "bsort_sort_batch", "bsort_plan_batch", "bsort_submit", "bsort_poll", "bsort_serve_stats",
+    "bsort_clock_ns",
 )
 
 
@@ -47,7 +50,8 @@ class bsort_config(ctypes.Structure):
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
                 ("tile", ctypes.c_uint32), ("samples", ctypes.c_uint32),
                 ("flags", ctypes.c_uint32), ("buckets", ctypes.c_uint32),
-                ("batch_direct_max", ctypes.c_uint32)]
+                ("batch_direct_max", ctypes.c_uint32), ("pad_", ctypes.c_uint32),
+                ("serve_budget_bytes", ctypes.c_uint64)]
 
 
 class bsort_plan_info(ctypes.Structure):
@@ -72,6 +76,26 @@ class bsort_batch_info(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_ if name != "pad_"}
+
+
+class bsort_request(ctypes.Structure):
+    _fields_ = [("key_type", ctypes.c_int), ("pad_", ctypes.c_uint32), ("n", ctypes.c_uint64),
+                ("h_keys_in", ctypes.c_void_p), ("h_keys_out", ctypes.c_void_p)]
+
+
+class bsort_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("batch_size", ctypes.c_uint32),
+                ("submit_ns", ctypes.c_uint64), ("start_ns", ctypes.c_uint64),
+                ("done_ns", ctypes.c_uint64)]
+
+
+class bsort_serve_info(ctypes.Structure):
+    _fields_ = [(name, ctypes.c_uint64) for name in (
+        "arena_bytes", "workspace_bytes", "arena_used_bytes", "arena_peak_bytes", "queued",
+        "completed", "batches", "max_batch")]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class BsortError(RuntimeError):
@@ -111,6 +135,10 @@ def load_library(rebuild: bool = False):
         "bsort_sort_batch": (i32, [H, i32, vp, vp, ctypes.POINTER(u64), u32, vp]),
         "bsort_plan_batch": (i32, [H, i32, ctypes.POINTER(u64), u32,
                                    ctypes.POINTER(bsort_batch_info)]),
+        "bsort_submit": (i32, [H, ctypes.POINTER(bsort_request), ctypes.POINTER(u64)]),
+        "bsort_poll": (i32, [H, u64, ctypes.POINTER(bsort_result)]),
+        "bsort_serve_stats": (i32, [H, ctypes.POINTER(bsort_serve_info)]),
+        "bsort_clock_ns": (u64, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -217,6 +245,33 @@ def bsort_plan_batch(h, key_type, seg_offsets):
     return info
 
 
+def bsort_submit(h, key_type, h_keys_in, h_keys_out, n):
+    req = bsort_request(key_type=key_type, n=n, h_keys_in=h_keys_in, h_keys_out=h_keys_out)
+    ticket = ctypes.c_uint64()
+    _check(h, load_library().bsort_submit(h, ctypes.byref(req), ctypes.byref(ticket)))
+    return ticket.value
+
+
+def bsort_poll(h, ticket):
+    """bsort_result once the job is done, else None."""
+    res = bsort_result()
+    st = load_library().bsort_poll(h, ticket, ctypes.byref(res))
+    if st == BSORT_ENOTREADY:
+        return None
+    _check(h, st)
+    return res
+
+
+def bsort_serve_stats(h):
+    info = bsort_serve_info()
+    _check(h, load_library().bsort_serve_stats(h, ctypes.byref(info)))
+    return info
+
+
+def bsort_clock_ns():
+    return load_library().bsort_clock_ns()
+
+
 def bsort_kernel_name(h, index):
     return load_library().bsort_kernel_name(h, index).decode()
 
@@ -309,7 +364,7 @@ class BucketSorter:
     def sort_keys_host(self, h_keys, h_out, key_type="u32"):
         """Host tensors (pinned for asynchronous copies) in and out."""
         n = h_keys.numel()
-        self._ensure(n, key_type, 0, extra=((n * 4 + 255) // 256) * 256)
+        self._ensure(n, key_type, 0, extra=((n * h_keys.element_size() + 255) // 256) * 256)
         bsort_sort_keys_host(self.h, _KEY_TYPES[key_type], h_keys.data_ptr(),
                              h_out.data_ptr(), n, self._stream())
         return h_out
@@ -331,6 +386,52 @@ class BucketSorter:
             bsort_destroy(self.h)
             self.h = None
         self.ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SortServer:
+    """A handle that serves sort jobs (bsort_submit / bsort_poll): host
+    tensors in and out (pinned for asynchronous copies), results polled by
+    ticket.  The handle's device memory is the serving budget."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 4 << 30, batch_direct_max: int = 0):
+        self.h = bsort_create(bsort_config(device=device, serve_budget_bytes=int(budget_bytes),
+                                           batch_direct_max=batch_direct_max))
+        self._alive = {}
+
+    def submit(self, h_keys, h_out, key_type="u32"):
+        t = bsort_submit(self.h, _KEY_TYPES[key_type], h_keys.data_ptr(), h_out.data_ptr(),
+                         h_keys.numel())
+        self._alive[t] = (h_keys, h_out)  # keep the buffers alive until polled
+        return t
+
+    def poll(self, ticket):
+        res = bsort_poll(self.h, ticket)
+        if res is not None:
+            self._alive.pop(ticket, None)
+        return res
+
+    def wait(self, ticket, sleep_s=20e-6):
+        import time
+        while True:
+            res = self.poll(ticket)
+            if res is not None:
+                return res
+            time.sleep(sleep_s)
+
+    def stats(self):
+        return bsort_serve_stats(self.h).as_dict()
+
+    def close(self):
+        if self.h is not None:
+            bsort_destroy(self.h)
+            self.h = None
+        self._alive.clear()
 
     def __del__(self):
         try:

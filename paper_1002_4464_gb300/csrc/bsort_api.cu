@@ -4,7 +4,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
 #include <mutex>
+#include <thread>
+#include <unordered_map>
 #include <new>
 #include <utility>
 #include <vector>
@@ -36,6 +42,8 @@ uint64_t align_up(uint64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Plan {
     bsort_plan_info info;
     bool pairs;
+    bool wide;       // 64-bit keys
+    int kb;          // key bytes (4 or 8)
     int vb;          // value bytes (0 keys only)
     int tile_chunk;  // items per CTA in Step 2 (t = tile_ctas * tile_chunk)
     int unit_chunk;  // items per CTA in Step 9 (capacity = unit_ctas * unit_chunk)
@@ -51,6 +59,8 @@ struct Plan {
 };
 
 }  // namespace
+
+struct bsort_server;  // the request loop of bsort_submit (below)
 
 struct bsort_ctx {
     int device = 0;
@@ -76,6 +86,8 @@ struct bsort_ctx {
     uint64_t calls_recorded = 0;  // calls since the last bsort_kernel_times
     uint64_t call_seq = 0;
     bool events_made = false;
+    uint64_t serve_budget = 0;        // bytes for served requests (0: 4 GiB)
+    bsort_server *server = nullptr;   // started by the first bsort_submit
 };
 
 namespace {
@@ -204,13 +216,18 @@ double plan_cost(uint64_t np, uint64_t s, int tchunk, int tctas, int uchunk, int
 bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P)
 {
     memset(P, 0, sizeof(*P));
-    if (kt == BSORT_U64) return fail(h, BSORT_EUNSUPPORTED, "64-bit keys are not served by this build");
-    if (kt != BSORT_U32 && kt != BSORT_F32) return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
+    if (kt != BSORT_U32 && kt != BSORT_F32 && kt != BSORT_U64)
+        return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
     if (vb != 0 && vb != 4 && vb != 8) return fail(h, BSORT_EINVAL, "val_bytes must be 0, 4 or 8");
+    if (kt == BSORT_U64 && vb != 0)
+        return fail(h, BSORT_EUNSUPPORTED, "64-bit keys are sorted keys-only by this build");
     if (n >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "n = %llu exceeds 2^32 - 2^16", (unsigned long long)n);
-    const bool pairs = vb != 0;
+    // 64-bit keys and pairs sort 64-bit words: the smaller chunk shapes
+    const bool pairs = vb != 0 || kt == BSORT_U64;
     const int cm = max_chunk(pairs);
-    P->pairs = pairs;
+    P->pairs = vb != 0;
+    P->wide = kt == BSORT_U64;
+    P->kb = P->wide ? 8 : 4;
     P->vb = (int)vb;
     bsort_plan_info &I = P->info;
     I.n = n;
@@ -318,12 +335,21 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->n_runs = (uint32_t)(m * b);
         P->n_rec_pad = (uint32_t)((P->n_rec + kRecordChunk - 1) / kRecordChunk * kRecordChunk);
         P->scan_chunks = (P->n_runs + kScanChunk - 1) / kScanChunk;
-        uint32_t merges = 0;
-        for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
-        const bool reloc = !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
-        I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
-                        1 /*S6*/ + 1 /*S7*/ + 1 /*run index*/ + (reloc ? 1 : 0) /*S8*/ +
-                        1 /*units*/ + 1 /*S9*/;
+        const bool reloc = P->wide || !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
+        if (P->wide) {
+            // records (16 bytes) merged from runs of s: ceil(log2 m) passes
+            P->n_rec_pad = P->n_rec;
+            uint32_t merges = 0;
+            for (uint64_t L = bs; L < P->n_rec; L <<= 1) ++merges;
+            I.num_kernels = 1 /*S2-3*/ + merges + 1 /*S5*/ + 1 /*S6*/ + 1 /*S7*/ +
+                            1 /*run index*/ + 1 /*S8*/ + 1 /*units*/ + 1 /*S9*/;
+        } else {
+            uint32_t merges = 0;
+            for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
+            I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
+                            1 /*S6*/ + 1 /*S7*/ + 1 /*run index*/ + (reloc ? 1 : 0) /*S8*/ +
+                            1 /*units*/ + 1 /*S9*/;
+        }
     }
 
     // workspace layout
@@ -333,18 +359,21 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         o = align_up(o + bytes);
         return at;
     };
-    P->relocate = !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
+    P->relocate = P->wide || !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
     P->off_hdr = take(kAlign);  // error word (int) + scan ticket (uint32)
     if (!I.single_tile) {
         const uint64_t np = I.n_padded;
-        P->off_tiles_k = take(np * 4);
+        const uint64_t kb = (uint64_t)P->kb;
+        const uint64_t rb = P->wide ? 16 : 8;  // sample record bytes
+        P->off_tiles_k = take(np * kb);
         P->off_tiles_v = take(np * (uint64_t)vb);
-        P->off_reloc_k = take(P->relocate ? np * 4 : 0);
+        P->off_reloc_k = take(P->relocate ? np * kb : 0);
         P->off_reloc_v = take(P->relocate ? np * (uint64_t)vb : 0);
-        P->off_samples = take((uint64_t)P->n_rec * 8);
-        P->off_rec_a = take((uint64_t)P->n_rec_pad * 8);
-        P->off_rec_b = take(P->n_rec_pad > (uint32_t)kRecordChunk ? (uint64_t)P->n_rec_pad * 8 : 0);
-        P->off_spl = take((uint64_t)I.b * 8);
+        P->off_samples = take((uint64_t)P->n_rec * rb);
+        P->off_rec_a = take((uint64_t)P->n_rec_pad * rb);
+        P->off_rec_b = take(P->wide || P->n_rec_pad > (uint32_t)kRecordChunk
+                                ? (uint64_t)P->n_rec_pad * rb : 0);
+        P->off_spl = take((uint64_t)I.b * rb);
         P->off_counts = take((uint64_t)P->n_runs * 4);
         P->off_cum = take((uint64_t)P->n_runs * 4);
         P->off_offsets = take(((uint64_t)P->n_runs + 1) * 4);
@@ -444,6 +473,77 @@ struct Seq {
         if (s_ != BSORT_OK) return s_;                   \
     } while (0)
 
+// Algorithm 1 on 64-bit keys (keys only): the same steps with 64-bit sorted
+// sublists and buckets and 16-byte sample records merged in L2 (Step 4).
+bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout, uint64_t n,
+                          cudaStream_t st, Seq &seq)
+{
+    const bsort_plan_info &I = P.info;
+    unsigned char *ws = static_cast<unsigned char *>(h->ws);
+    int *err = reinterpret_cast<int *>(ws + P.off_hdr);
+    uint32_t *ticket = reinterpret_cast<uint32_t *>(ws + P.off_hdr + 64);
+    if (I.single_tile) {
+        if (n == 1) {
+            if (kout != kin) {
+                cudaError_t e = cudaMemcpyAsync(kout, kin, 8, cudaMemcpyDeviceToDevice, st);
+                if (e != cudaSuccess) return cuda_fail(h, e, "copy n=1");
+            }
+            return BSORT_OK;
+        }
+        SEQ(launch_bucket_sort_u64(P.unit_chunk, (int)I.unit_ctas, kin, nullptr, 1, n, n, kout,
+                                   err, st),
+            "step9_single_unit");
+        return BSORT_OK;
+    }
+    uint64_t *tiles = reinterpret_cast<uint64_t *>(ws + P.off_tiles_k);
+    uint64_t *reloc = reinterpret_cast<uint64_t *>(ws + P.off_reloc_k);
+    Rec128 *samples = reinterpret_cast<Rec128 *>(ws + P.off_samples);
+    Rec128 *rec_a = reinterpret_cast<Rec128 *>(ws + P.off_rec_a);
+    Rec128 *rec_b = reinterpret_cast<Rec128 *>(ws + P.off_rec_b);
+    Rec128 *spl = reinterpret_cast<Rec128 *>(ws + P.off_spl);
+    uint32_t *counts = reinterpret_cast<uint32_t *>(ws + P.off_counts);
+    uint32_t *offsets = reinterpret_cast<uint32_t *>(ws + P.off_offsets);
+    uint32_t *srcb = reinterpret_cast<uint32_t *>(ws + P.off_srcb);
+    uint32_t *blk = reinterpret_cast<uint32_t *>(ws + P.off_blk);
+    uint32_t *units = reinterpret_cast<uint32_t *>(ws + P.off_units);
+    unsigned long long *status = reinterpret_cast<unsigned long long *>(ws + P.off_status);
+    cudaError_t e = cudaMemsetAsync(status, 0, (size_t)P.scan_chunks * 8, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan status)");
+    e = cudaMemsetAsync(ticket, 0, 4, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan ticket)");
+    // Steps 1-3
+    SEQ(launch_sublist_sort_u64(P.tile_chunk, (int)I.tile_ctas, kin, n, I.m, I.s, tiles, samples,
+                                st),
+        "step1_3_sublist_sort");
+    // Step 4: merge the m sorted runs of s records (the samples stay intact)
+    const Rec128 *src = samples;
+    Rec128 *dst = rec_a;
+    for (uint64_t L = I.s; L < P.n_rec; L <<= 1) {
+        SEQ(launch_rec_merge(src, dst, P.n_rec, (uint32_t)L, st), "step4_sample_merge");
+        src = dst;
+        dst = dst == rec_a ? rec_b : rec_a;
+    }
+    // Step 5
+    SEQ(launch_select_splitters_u64(src, P.n_rec, I.b, spl, st), "step5_splitters");
+    // Step 6
+    SEQ(launch_sample_index_u64(tiles, samples, spl, I.t, I.s, I.b, I.m, counts, srcb, st),
+        "step6_sample_index");
+    // Step 7
+    SEQ(launch_scan(counts, offsets, P.n_runs, status, ticket, err, st), "step7_prefix_sum");
+    // Step 8
+    SEQ(launch_block_index(offsets, P.n_runs, (uint32_t)I.n_padded, blk, st), "step8_run_index");
+    SEQ(launch_relocate_u64(tiles, offsets, srcb, blk, P.n_runs, (uint32_t)I.n_padded, reloc, st),
+        "step8_relocate");
+    // Step 9
+    SEQ(launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, (uint32_t)I.unit_capacity,
+                          units, err, st),
+        "step9_pack_units");
+    SEQ(launch_bucket_sort_u64(P.unit_chunk, (int)I.unit_ctas, reloc, units, I.b, n, I.n_padded,
+                               kout, err, st),
+        "step9_bucket_sort");
+    return BSORT_OK;
+}
+
 bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void *vin, void *kout,
                       void *vout, uint32_t vb, uint64_t n, cudaStream_t st)
 {
@@ -463,6 +563,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     const bsort_plan_info &I = P.info;
     Seq seq(h, st);
     if (n == 0) return BSORT_OK;
+    if (P.wide) return run_sort_u64(h, P, kin, kout, n, st, seq);
     if (I.single_tile) {
         if (n == 1) {
             if (kout != kin) {
@@ -563,19 +664,28 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
 }
 
 // ---------------------------------------------------------------- batches
-// Direct unit shapes, smallest first: (chunk, ctas).
-const int kDirectShapes[][2] = {{2048, 1}, {4096, 1}, {8192, 1}, {16384, 1}, {32768, 1},
-                                {32768, 2}, {32768, 4}, {32768, 8}};
+// Direct unit shapes, smallest first: (chunk, ctas); 64-bit keys use CTAs
+// of at most 16384 keys.
 constexpr int kNumDirect = 8;
+const int kDirectShapes[kNumDirect][2] = {{2048, 1},  {4096, 1},  {8192, 1},  {16384, 1},
+                                          {32768, 1}, {32768, 2}, {32768, 4}, {32768, 8}};
 const char *const kDirectNames[kNumDirect] = {
     "batch_direct_2048", "batch_direct_4096", "batch_direct_8192", "batch_direct_16384",
     "batch_direct_32768", "batch_direct_2x32768", "batch_direct_4x32768", "batch_direct_8x32768"};
+constexpr int kNumDirectWide = 7;
+const int kDirectShapesWide[kNumDirectWide][2] = {{2048, 1},  {4096, 1},  {8192, 1}, {16384, 1},
+                                                  {16384, 2}, {16384, 4}, {16384, 8}};
+const char *const kDirectNamesWide[kNumDirectWide] = {
+    "batch_direct_u64_2048", "batch_direct_u64_4096", "batch_direct_u64_8192",
+    "batch_direct_u64_16384", "batch_direct_u64_2x16384", "batch_direct_u64_4x16384",
+    "batch_direct_u64_8x16384"};
 
 // Host plan of one batch: direct lists per shape, sampled segments with
 // their sublists and buckets, plain-sorted large segments, and the
 // workspace layout (descriptors first, copied from pinned staging).
 struct BatchPlan {
     bsort_batch_info info;
+    bool wide = false;  // 64-bit keys: direct units and plain sorts only
     std::vector<uint32_t> direct[kNumDirect];  // (begin, end) pairs per shape
     std::vector<SegInfo> segs;
     std::vector<uint32_t> sub_seg;
@@ -592,34 +702,58 @@ struct BatchPlan {
              total = 0;
 };
 
-bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const uint64_t *segoff,
+// One array of a batch: keys [begin, begin + n) of the input and output.
+struct SegSpan {
+    uint64_t begin, n;
+};
+
+// Segments q = [segoff[q], segoff[q+1]) of the public offsets table.
+bsort_status spans_from_offsets(bsort_t h, const uint64_t *segoff, uint32_t nsegs,
+                                std::vector<SegSpan> *out)
+{
+    out->clear();
+    if (nsegs == 0) return BSORT_OK;
+    if (!segoff) return fail(h, BSORT_EINVAL, "null segment offsets");
+    out->reserve(nsegs);
+    for (uint32_t q = 0; q < nsegs; ++q) {
+        if (segoff[q + 1] < segoff[q])
+            return fail(h, BSORT_EINVAL, "segment offsets decrease at %u", q);
+        out->push_back({segoff[q], segoff[q + 1] - segoff[q]});
+    }
+    return BSORT_OK;
+}
+
+bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const SegSpan *spans,
                              uint32_t nsegs, BatchPlan *B)
 {
-    if (kt == BSORT_U64) return fail(h, BSORT_EUNSUPPORTED, "64-bit keys are not served by this build");
-    if (kt != BSORT_U32 && kt != BSORT_F32) return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
-    if (nsegs && !segoff) return fail(h, BSORT_EINVAL, "null segment offsets");
+    if (kt != BSORT_U32 && kt != BSORT_F32 && kt != BSORT_U64)
+        return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
+    B->wide = kt == BSORT_U64;
+    const int(*shapes)[2] = B->wide ? kDirectShapesWide : kDirectShapes;
+    const int nshapes = B->wide ? kNumDirectWide : kNumDirect;
+    const uint64_t largest = (uint64_t)shapes[nshapes - 1][0] * shapes[nshapes - 1][1];
+    if (nsegs && !spans) return fail(h, BSORT_EINVAL, "null segment list");
     bsort_batch_info &I = B->info;
     memset(&I, 0, sizeof(I));
     I.num_segs = nsegs;
     if (nsegs == 0) return BSORT_OK;
-    if (segoff[nsegs] >= kMaxN)
-        return fail(h, BSORT_EUNSUPPORTED, "segment end %llu exceeds 2^32 - 2^16",
-                    (unsigned long long)segoff[nsegs]);
-    const uint32_t dmax = h->direct_max;
+    for (uint32_t q = 0; q < nsegs; ++q)
+        if (spans[q].begin + spans[q].n >= kMaxN)
+            return fail(h, BSORT_EUNSUPPORTED, "segment end %llu exceeds 2^32 - 2^16",
+                        (unsigned long long)(spans[q].begin + spans[q].n));
+    const uint64_t dmax = h->direct_max < largest ? h->direct_max : largest;
     uint64_t g = 0;  // sublists so far
     for (uint32_t q = 0; q < nsegs; ++q) {
-        if (segoff[q + 1] < segoff[q])
-            return fail(h, BSORT_EINVAL, "segment offsets decrease at %u", q);
-        const uint64_t a = segoff[q], n = segoff[q + 1] - segoff[q];
+        const uint64_t a = spans[q].begin, n = spans[q].n;
         I.n += n;
         if (n <= 1) continue;  // nothing to order (a copy when out != in)
         if (n <= dmax) {
             int c = 0;
-            while ((uint64_t)kDirectShapes[c][0] * kDirectShapes[c][1] < n) ++c;
+            while ((uint64_t)shapes[c][0] * shapes[c][1] < n) ++c;
             B->direct[c].push_back((uint32_t)a);
             B->direct[c].push_back((uint32_t)(a + n));
             ++I.direct_segs;
-        } else if (n <= kBatchSampledMax) {
+        } else if (n <= kBatchSampledMax && !B->wide) {
             SegInfo sg = {};
             sg.g0 = (uint32_t)g;
             sg.m = (uint32_t)((n + kSegTile - 1) / kSegTile);
@@ -708,23 +842,24 @@ bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const uint64_t *segof
 }
 
 bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout,
-                       const uint64_t *segoff, uint32_t nsegs, cudaStream_t st)
+                       const SegSpan *spans, uint32_t nsegs, cudaStream_t st)
 {
     bsort_status rs = prepare(h);
     if (rs != BSORT_OK) return rs;
     BatchPlan B;
-    rs = make_batch_plan(h, kt, segoff, nsegs, &B);
+    rs = make_batch_plan(h, kt, spans, nsegs, &B);
     if (rs != BSORT_OK) return rs;
     if (B.info.n == 0) return BSORT_OK;
     rs = ensure_workspace(h, B.total);
     if (rs != BSORT_OK) return rs;
     cudaError_t e;
     // segments of one key: copies
+    const uint64_t kb = B.wide ? 8 : 4;
     if (kout != kin)
         for (uint32_t q = 0; q < nsegs; ++q)
-            if (segoff[q + 1] - segoff[q] == 1) {
-                e = cudaMemcpyAsync(static_cast<uint32_t *>(kout) + segoff[q],
-                                    static_cast<const uint32_t *>(kin) + segoff[q], 4,
+            if (spans[q].n == 1) {
+                e = cudaMemcpyAsync(static_cast<char *>(kout) + spans[q].begin * kb,
+                                    static_cast<const char *>(kin) + spans[q].begin * kb, kb,
                                     cudaMemcpyDeviceToDevice, st);
                 if (e != cudaSuccess) return cuda_fail(h, e, "copy of a one-key segment");
             }
@@ -779,9 +914,10 @@ bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout
     for (int c = 0; c < kNumDirect; ++c) {
         const uint32_t cnt = (uint32_t)(B.direct[c].size() / 2);
         if (!cnt) continue;
-        SEQ(launch_seg_sort(kDirectShapes[c][0], kDirectShapes[c][1], ki, ko, desc + B.d_direct[c],
+        const int(*shapes)[2] = B.wide ? kDirectShapesWide : kDirectShapes;
+        SEQ(launch_seg_sort(shapes[c][0], shapes[c][1], B.wide, kin, kout, desc + B.d_direct[c],
                             cnt, is_f32, err, st),
-            kDirectNames[c]);
+            B.wide ? kDirectNamesWide[c] : kDirectNames[c]);
     }
     // sampled segments: Algorithm 1, segment-aware
     if (!B.segs.empty()) {
@@ -819,10 +955,424 @@ bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout
     }
     // large segments: one plain sort each, after the batch (same stream)
     for (const auto &lg : B.large) {
-        rs = run_sort(h, kt, ki + lg.first, nullptr, ko + lg.first, nullptr, 0, lg.second, st);
+        rs = run_sort(h, kt, static_cast<const char *>(kin) + lg.first * kb, nullptr,
+                      static_cast<char *>(kout) + lg.first * kb, nullptr, 0, lg.second, st);
         if (rs != BSORT_OK) return rs;
     }
     return BSORT_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- serving
+// The request loop behind bsort_submit / bsort_poll: continuous batching of
+// independent sort jobs.  One worker thread per serving handle owns a
+// device arena for admitted jobs' keys (part of the serving budget) and two
+// lanes, each with its own streams (copy in, sort, copy out) and workspace:
+//   lane A (small jobs: those a batch sorts with one CTA, one cluster or
+//       the segment-aware sample sort) sorts everything admitted as one
+//       batch (bsort_sort_batch's path, in place in the arena) as soon as
+//       its previous batch has finished sorting, on a high-priority stream;
+//   lane B (large jobs) sorts them one at a time, in arrival order, on a
+//       low-priority stream, so that small jobs are not held behind them.
+// Each turn of the loop retires jobs whose results are back in host memory
+// (freeing their arena ranges), admits queued jobs in arrival order while
+// the arena has room (first fit), and launches lane A's next batch.  Jobs
+// that arrive while a batch sorts are copied in meanwhile and form the next
+// batch.
+struct bsort_server {
+    struct Req {
+        uint64_t ticket = 0;
+        bsort_key_type kt = BSORT_U32;
+        const void *in = nullptr;
+        void *out = nullptr;
+        uint64_t n = 0, bytes = 0, off = 0;
+        uint64_t submit_ns = 0, start_ns = 0, done_ns = 0;
+        uint32_t batch_size = 0;
+        int lane = 0;
+        bsort_status status = BSORT_ENOTREADY;
+        cudaEvent_t ev = nullptr;  // its result is in host memory
+        bool done = false;
+    };
+    struct Batch {
+        std::vector<Req *> reqs;
+        cudaEvent_t sorted = nullptr;
+        int *err_host = nullptr;  // pinned copy of the lane's device error word
+    };
+    struct Lane {
+        bsort_t ctx = nullptr;  // workspace and error word of the lane
+        cudaStream_t s_in = nullptr, s_run = nullptr, s_out = nullptr;
+        std::deque<Batch> running;
+    };
+    bsort_t h = nullptr;
+    bsort_t hb = nullptr;  // lane B's own context
+    Lane lane[2];
+    uint64_t arena_bytes = 0;
+    unsigned char *arena = nullptr;
+    std::map<uint64_t, uint64_t> free_list;  // offset -> bytes, coalesced
+    std::thread worker;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool stop = false;
+    std::deque<Req *> queue;                    // submitted, not admitted
+    std::unordered_map<uint64_t, Req *> tickets;
+    uint64_t next_ticket = 1;
+    std::vector<Req *> staged;   // lane A: keys copied in (or on their way)
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int *> err_pool;
+    // statistics
+    uint64_t used = 0, peak = 0, batches = 0, done_count = 0, max_batch = 0;
+};
+
+namespace {
+
+uint64_t clock_ns()
+{
+    return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+constexpr uint64_t kServeAlign = 256;
+// arena positions of a batch are key indices below 2^32 - 2^16
+constexpr uint64_t kServeArenaMax = 15ull << 30;
+constexpr uint64_t kServeDefaultBudget = 4ull << 30;
+
+uint64_t key_bytes(bsort_key_type kt) { return kt == BSORT_U64 ? 8 : 4; }
+
+// Lane of a job: 0 when a batch sorts it as a direct or sampled segment.
+int lane_of(const bsort_t h, bsort_key_type kt, uint64_t n)
+{
+    if (kt == BSORT_U64) return n <= (uint64_t)h->direct_max && n <= 8ull * kMaxCapPairs ? 0 : 1;
+    return n <= kBatchSampledMax ? 0 : 1;
+}
+
+bool arena_alloc(bsort_server *S, uint64_t bytes, uint64_t *off)
+{
+    for (auto it = S->free_list.begin(); it != S->free_list.end(); ++it) {
+        if (it->second < bytes) continue;
+        *off = it->first;
+        const uint64_t rest = it->second - bytes;
+        const uint64_t at = it->first + bytes;
+        S->free_list.erase(it);
+        if (rest) S->free_list[at] = rest;
+        S->used += bytes;
+        if (S->used > S->peak) S->peak = S->used;
+        return true;
+    }
+    return false;
+}
+
+void arena_free(bsort_server *S, uint64_t off, uint64_t bytes)
+{
+    S->used -= bytes;
+    auto it = S->free_list.emplace(off, bytes).first;
+    auto nx = std::next(it);
+    if (nx != S->free_list.end() && it->first + it->second == nx->first) {
+        it->second += nx->second;
+        S->free_list.erase(nx);
+    }
+    if (it != S->free_list.begin()) {
+        auto pv = std::prev(it);
+        if (pv->first + pv->second == it->first) {
+            pv->second += it->second;
+            S->free_list.erase(it);
+        }
+    }
+}
+
+cudaEvent_t take_event(bsort_server *S)
+{
+    if (!S->ev_pool.empty()) {
+        cudaEvent_t e = S->ev_pool.back();
+        S->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    return e;
+}
+
+int *take_err(bsort_server *S)
+{
+    if (!S->err_pool.empty()) {
+        int *p = S->err_pool.back();
+        S->err_pool.pop_back();
+        return p;
+    }
+    void *p = nullptr;
+    if (cudaHostAlloc(&p, sizeof(int), cudaHostAllocDefault) != cudaSuccess) return nullptr;
+    return static_cast<int *>(p);
+}
+
+// Retire every job whose result is back in host memory.
+bool serve_retire(bsort_server *S)
+{
+    bool any = false;
+    for (auto &L : S->lane) {
+        while (!L.running.empty()) {
+            bsort_server::Batch &b = L.running.front();
+            bool all = true;
+            for (auto &r : b.reqs) {
+                if (!r) continue;
+                if (cudaEventQuery(r->ev) != cudaSuccess) {
+                    all = false;
+                    continue;
+                }
+                const uint64_t now = clock_ns();
+                const int word = b.err_host ? *b.err_host : 0;
+                std::lock_guard<std::mutex> lock(S->mu);
+                arena_free(S, r->off, r->bytes);
+                S->ev_pool.push_back(r->ev);
+                r->ev = nullptr;
+                r->done_ns = now;
+                if (r->status == BSORT_ENOTREADY)
+                    r->status = word == 0 ? BSORT_OK
+                                          : (word == BSORT_ETIMEOUT ? BSORT_ETIMEOUT
+                                                                   : BSORT_EINTERNAL);
+                r->done = true;
+                ++S->done_count;
+                r = nullptr;  // the caller may free it once polled
+                any = true;
+            }
+            if (!all) break;
+            S->ev_pool.push_back(b.sorted);
+            if (b.err_host) S->err_pool.push_back(b.err_host);
+            L.running.pop_front();
+        }
+    }
+    return any;
+}
+
+// Sort the jobs of one batch of a lane (in place in the arena), copy the
+// lane's error word out, then copy every result out.
+void serve_run(bsort_server *S, int li, const std::vector<bsort_server::Req *> &jobs)
+{
+    bsort_server::Lane &L = S->lane[li];
+    bsort_t ctx = L.ctx;
+    bsort_server::Batch b;
+    b.reqs = jobs;
+    b.err_host = take_err(S);
+    const uint64_t start = clock_ns();
+    const bsort_key_type kinds[3] = {BSORT_U32, BSORT_F32, BSORT_U64};
+    for (bsort_key_type kt : kinds) {
+        const uint64_t kb = key_bytes(kt);
+        std::vector<SegSpan> spans;
+        std::vector<bsort_server::Req *> owners;
+        for (auto *r : jobs)
+            if (r->kt == kt && r->status == BSORT_ENOTREADY) {
+                spans.push_back({r->off / kb, r->n});
+                owners.push_back(r);
+            }
+        // sub-batches whose workspace fits the lane's: the largest prefix
+        // that fits, found by bisection (the workspace a batch needs grows
+        // with its segments); a single job always fits
+        auto fits = [&](size_t i, size_t j) {
+            BatchPlan B;
+            return make_batch_plan(ctx, kt, spans.data() + i, (uint32_t)(j - i), &B) ==
+                       BSORT_OK &&
+                   B.total <= ctx->ws_bytes;
+        };
+        size_t i = 0;
+        while (i < spans.size()) {
+            size_t j = spans.size();
+            if (!fits(i, j)) {
+                size_t lo = i + 1, hi = j - 1;  // largest end in [lo, hi] that fits
+                while (lo < hi) {
+                    const size_t mid = (lo + hi + 1) / 2;
+                    if (fits(i, mid)) lo = mid;
+                    else hi = mid - 1;
+                }
+                j = lo;
+            }
+            const bsort_status st = run_batch(ctx, kt, S->arena, S->arena, spans.data() + i,
+                                              (uint32_t)(j - i), L.s_run);
+            if (st != BSORT_OK)
+                for (size_t q = i; q < j; ++q) owners[q]->status = st;
+            i = j;
+        }
+    }
+    if (b.err_host) {
+        cudaMemcpyAsync(b.err_host, ctx->ws, sizeof(int), cudaMemcpyDeviceToHost, L.s_run);
+        cudaMemsetAsync(ctx->ws, 0, sizeof(int), L.s_run);
+    }
+    b.sorted = take_event(S);
+    cudaEventRecord(b.sorted, L.s_run);
+    cudaStreamWaitEvent(L.s_out, b.sorted, 0);
+    const uint32_t size = (uint32_t)jobs.size();
+    for (auto *r : jobs) {
+        r->start_ns = start;
+        r->batch_size = size;
+        if (r->status == BSORT_ENOTREADY)
+            cudaMemcpyAsync(r->out, S->arena + r->off, r->n * key_bytes(r->kt),
+                            cudaMemcpyDeviceToHost, L.s_out);
+        r->ev = take_event(S);
+        cudaEventRecord(r->ev, L.s_out);
+    }
+    ++S->batches;
+    if (size > S->max_batch) S->max_batch = size;
+    L.running.push_back(b);
+}
+
+// Admit queued jobs in arrival order while the arena has room: copy their
+// keys in; a large job is sorted on lane B right away (behind the ones
+// before it), a small one waits for lane A's next batch.
+bool serve_admit(bsort_server *S)
+{
+    bool any = false;
+    for (;;) {
+        bsort_server::Req *r = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(S->mu);
+            if (S->queue.empty()) break;
+            bsort_server::Req *head = S->queue.front();
+            uint64_t off = 0;
+            if (!arena_alloc(S, head->bytes, &off)) break;
+            head->off = off;
+            S->queue.pop_front();
+            r = head;
+        }
+        bsort_server::Lane &L = S->lane[r->lane];
+        cudaError_t e = cudaMemcpyAsync(S->arena + r->off, r->in, r->n * key_bytes(r->kt),
+                                        cudaMemcpyHostToDevice, L.s_in);
+        if (e != cudaSuccess) r->status = BSORT_ECUDA;
+        if (r->lane == 0) {
+            S->staged.push_back(r);
+        } else {
+            cudaEvent_t in_done = take_event(S);
+            cudaEventRecord(in_done, L.s_in);
+            cudaStreamWaitEvent(L.s_run, in_done, 0);
+            S->ev_pool.push_back(in_done);  // a later record does not affect this wait
+            serve_run(S, 1, std::vector<bsort_server::Req *>(1, r));
+        }
+        any = true;
+    }
+    return any;
+}
+
+// Launch lane A's next batch when its sorting stream is idle.
+bool serve_launch(bsort_server *S)
+{
+    bsort_server::Lane &L = S->lane[0];
+    if (S->staged.empty()) return false;
+    if (!L.running.empty() && cudaEventQuery(L.running.back().sorted) != cudaSuccess)
+        return false;
+    cudaEvent_t in_done = take_event(S);
+    cudaEventRecord(in_done, L.s_in);
+    cudaStreamWaitEvent(L.s_run, in_done, 0);
+    S->ev_pool.push_back(in_done);
+    serve_run(S, 0, S->staged);
+    S->staged.clear();
+    return true;
+}
+
+void serve_loop(bsort_server *S)
+{
+    cudaSetDevice(S->h->device);
+    for (;;) {
+        bool busy = serve_retire(S);
+        busy |= serve_admit(S);
+        busy |= serve_launch(S);
+        std::unique_lock<std::mutex> lock(S->mu);
+        const bool idle = S->queue.empty() && S->staged.empty() && S->lane[0].running.empty() &&
+                          S->lane[1].running.empty();
+        if (S->stop && idle) break;
+        if (!busy) {
+            if (idle) S->cv.wait_for(lock, std::chrono::milliseconds(5));
+            else S->cv.wait_for(lock, std::chrono::microseconds(10));
+        }
+    }
+}
+
+bsort_status serve_start(bsort_t h)
+{
+    bsort_status rs = prepare(h);
+    if (rs != BSORT_OK) return rs;
+    const uint64_t budget = h->serve_budget ? h->serve_budget : kServeDefaultBudget;
+    bsort_server *S = new (std::nothrow) bsort_server();
+    if (!S) return fail(h, BSORT_ENOMEM, "server state");
+    S->h = h;
+    uint64_t arena = budget / 2;
+    if (arena > kServeArenaMax) arena = kServeArenaMax;
+    arena = arena / kServeAlign * kServeAlign;
+    S->arena_bytes = arena;
+    // the rest of the budget: the two lanes' workspaces
+    const uint64_t ws_lane = (budget - arena) / 2 / kAlign * kAlign;
+    S->hb = new (std::nothrow) bsort_ctx();
+    if (!S->hb) {
+        delete S;
+        return fail(h, BSORT_ENOMEM, "server state");
+    }
+    S->hb->device = h->device;
+    S->hb->direct_max = h->direct_max;
+    if (!h->ws_fixed) {
+        rs = ensure_workspace(h, ws_lane);
+        if (rs == BSORT_OK) h->ws_fixed = true;
+    }
+    if (rs == BSORT_OK) rs = prepare(S->hb);
+    if (rs == BSORT_OK) rs = ensure_workspace(S->hb, ws_lane);
+    if (rs != BSORT_OK) {
+        delete S->hb;
+        delete S;
+        return fail(h, rs, "serving workspace of %llu bytes", (unsigned long long)ws_lane);
+    }
+    S->hb->ws_fixed = true;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void **>(&S->arena), arena);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        bsort_destroy(S->hb);
+        delete S;
+        return fail(h, BSORT_ENOMEM, "serving arena of %llu bytes: %s",
+                    (unsigned long long)arena, cudaGetErrorString(e));
+    }
+    S->free_list[0] = arena;
+    int lo_prio = 0, hi_prio = 0;
+    cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio);
+    S->lane[0].ctx = h;
+    S->lane[1].ctx = S->hb;
+    for (int li = 0; li < 2; ++li) {
+        bsort_server::Lane &L = S->lane[li];
+        const int prio = li == 0 ? hi_prio : lo_prio;
+        if (cudaStreamCreateWithPriority(&L.s_in, cudaStreamNonBlocking, prio) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&L.s_run, cudaStreamNonBlocking, prio) != cudaSuccess ||
+            cudaStreamCreateWithPriority(&L.s_out, cudaStreamNonBlocking, prio) != cudaSuccess) {
+            cudaFree(S->arena);
+            bsort_destroy(S->hb);
+            delete S;
+            return fail(h, BSORT_ECUDA, "stream creation failed");
+        }
+    }
+    h->server = S;
+    S->worker = std::thread(serve_loop, S);
+    return BSORT_OK;
+}
+
+void serve_stop(bsort_t h)
+{
+    bsort_server *S = h->server;
+    if (!S) return;
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    S->worker.join();
+    cudaSetDevice(h->device);
+    for (auto &L : S->lane) {
+        cudaStreamSynchronize(L.s_in);
+        cudaStreamSynchronize(L.s_run);
+        cudaStreamSynchronize(L.s_out);
+        cudaStreamDestroy(L.s_in);
+        cudaStreamDestroy(L.s_run);
+        cudaStreamDestroy(L.s_out);
+    }
+    for (auto &kv : S->tickets) delete kv.second;
+    for (cudaEvent_t e : S->ev_pool) cudaEventDestroy(e);
+    for (int *p : S->err_pool) cudaFreeHost(p);
+    cudaFree(S->arena);
+    bsort_destroy(S->hb);
+    delete S;
+    h->server = nullptr;
 }
 
 bool overlaps(const void *a, uint64_t abytes, const void *b, uint64_t bbytes)
@@ -864,6 +1414,7 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
         h->force_t = cfg->tile;
         h->force_s = cfg->samples;
         h->force_b = cfg->buckets;
+        h->serve_budget = cfg->serve_budget_bytes;
         if (cfg->batch_direct_max) {
             if (cfg->batch_direct_max > 8u * (uint32_t)kMaxCapKeys) {
                 delete h;
@@ -911,6 +1462,7 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
 bsort_status bsort_destroy(bsort_t h)
 {
     if (!h) return BSORT_EINVAL;
+    serve_stop(h);
     if (h->ws_owned && h->ws) {
         cudaSetDevice(h->device);
         cudaFree(h->ws);
@@ -939,8 +1491,10 @@ bsort_status bsort_sort_keys(bsort_t h, bsort_key_type kt, const void *d_keys_in
                              uint64_t n, void *cuda_stream)
 {
     if (!h) return BSORT_EINVAL;
+    if (h->server) return fail(h, BSORT_EBUSY, "the handle serves requests (bsort_submit)");
     if (n && (!d_keys_in || !d_keys_out)) return fail(h, BSORT_EINVAL, "null key pointer");
-    if (n && d_keys_in != d_keys_out && overlaps(d_keys_in, n * 4, d_keys_out, n * 4))
+    const uint64_t kb = kt == BSORT_U64 ? 8 : 4;
+    if (n && d_keys_in != d_keys_out && overlaps(d_keys_in, n * kb, d_keys_out, n * kb))
         return fail(h, BSORT_EINVAL, "input and output overlap partially");
     return run_sort(h, kt, d_keys_in, nullptr, d_keys_out, nullptr, 0, n,
                     static_cast<cudaStream_t>(cuda_stream));
@@ -951,6 +1505,7 @@ bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_i
                               uint32_t val_bytes, uint64_t n, void *cuda_stream)
 {
     if (!h) return BSORT_EINVAL;
+    if (h->server) return fail(h, BSORT_EBUSY, "the handle serves requests (bsort_submit)");
     if (val_bytes != 4 && val_bytes != 8) return fail(h, BSORT_EINVAL, "val_bytes must be 4 or 8");
     if (n && (!d_keys_in || !d_keys_out || !d_vals_in || !d_vals_out))
         return fail(h, BSORT_EINVAL, "null key/value pointer");
@@ -967,8 +1522,11 @@ bsort_status bsort_plan_batch(bsort_t h, bsort_key_type kt, const uint64_t *seg_
                               uint32_t num_segs, bsort_batch_info *out)
 {
     if (!h || !out) return BSORT_EINVAL;
+    std::vector<SegSpan> spans;
+    bsort_status st = spans_from_offsets(h, seg_offsets, num_segs, &spans);
+    if (st != BSORT_OK) return st;
     BatchPlan B;
-    bsort_status st = make_batch_plan(h, kt, seg_offsets, num_segs, &B);
+    st = make_batch_plan(h, kt, spans.data(), num_segs, &B);
     if (st != BSORT_OK) return st;
     *out = B.info;
     return BSORT_OK;
@@ -979,19 +1537,116 @@ bsort_status bsort_sort_batch(bsort_t h, bsort_key_type kt, const void *d_keys_i
                               void *cuda_stream)
 {
     if (!h) return BSORT_EINVAL;
+    if (h->server) return fail(h, BSORT_EBUSY, "the handle serves requests (bsort_submit)");
     if (num_segs && !seg_offsets) return fail(h, BSORT_EINVAL, "null segment offsets");
     const uint64_t end = num_segs ? seg_offsets[num_segs] : 0;
+    const uint64_t kb = kt == BSORT_U64 ? 8 : 4;
     if (end && (!d_keys_in || !d_keys_out)) return fail(h, BSORT_EINVAL, "null key pointer");
-    if (end && d_keys_in != d_keys_out && overlaps(d_keys_in, end * 4, d_keys_out, end * 4))
+    if (end && d_keys_in != d_keys_out && overlaps(d_keys_in, end * kb, d_keys_out, end * kb))
         return fail(h, BSORT_EINVAL, "input and output overlap partially");
-    return run_batch(h, kt, d_keys_in, d_keys_out, seg_offsets, num_segs,
+    std::vector<SegSpan> spans;
+    bsort_status st = spans_from_offsets(h, seg_offsets, num_segs, &spans);
+    if (st != BSORT_OK) return st;
+    return run_batch(h, kt, d_keys_in, d_keys_out, spans.data(), num_segs,
                      static_cast<cudaStream_t>(cuda_stream));
 }
+
+bsort_status bsort_submit(bsort_t h, const bsort_request *req, uint64_t *ticket)
+{
+    if (!h || !req || !ticket) return BSORT_EINVAL;
+    const bsort_key_type kt = req->key_type;
+    if (kt != BSORT_U32 && kt != BSORT_F32 && kt != BSORT_U64)
+        return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
+    if (req->n && (!req->h_keys_in || !req->h_keys_out))
+        return fail(h, BSORT_EINVAL, "null key pointer");
+    if (req->n >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "n = %llu too large",
+                                     (unsigned long long)req->n);
+    if (!h->server) {
+        bsort_status rs = serve_start(h);
+        if (rs != BSORT_OK) return rs;
+    }
+    bsort_server *S = h->server;
+    const uint64_t kb = key_bytes(kt);
+    const uint64_t bytes = (req->n * kb + kServeAlign - 1) / kServeAlign * kServeAlign;
+    if (bytes > S->arena_bytes)
+        return fail(h, BSORT_ENOMEM, "request of %llu bytes exceeds the serving arena (%llu)",
+                    (unsigned long long)bytes, (unsigned long long)S->arena_bytes);
+    const int lane = lane_of(h, kt, req->n);
+    if (req->n > 1) {  // its batch alone must fit the lane's workspace
+        SegSpan one = {0, req->n};
+        BatchPlan B;
+        bsort_status rs = make_batch_plan(h, kt, &one, 1, &B);
+        if (rs != BSORT_OK) return rs;
+        const uint64_t ws = S->lane[lane].ctx->ws_bytes;
+        if (B.total > ws)
+            return fail(h, BSORT_ENOMEM, "request needs %llu workspace bytes, serving has %llu",
+                        (unsigned long long)B.total, (unsigned long long)ws);
+    }
+    auto *r = new (std::nothrow) bsort_server::Req();
+    if (!r) return fail(h, BSORT_ENOMEM, "request state");
+    r->kt = kt;
+    r->in = req->h_keys_in;
+    r->out = req->h_keys_out;
+    r->n = req->n;
+    r->lane = lane;
+    r->bytes = bytes ? bytes : kServeAlign;
+    r->submit_ns = clock_ns();
+    {
+        std::lock_guard<std::mutex> lock(S->mu);
+        r->ticket = S->next_ticket++;
+        S->tickets[r->ticket] = r;
+        S->queue.push_back(r);
+    }
+    S->cv.notify_one();
+    *ticket = r->ticket;
+    return BSORT_OK;
+}
+
+bsort_status bsort_poll(bsort_t h, uint64_t ticket, bsort_result *out)
+{
+    if (!h || !out) return BSORT_EINVAL;
+    bsort_server *S = h->server;
+    if (!S) return fail(h, BSORT_EINVAL, "no request was submitted on this handle");
+    std::lock_guard<std::mutex> lock(S->mu);
+    auto it = S->tickets.find(ticket);
+    if (it == S->tickets.end()) return BSORT_EINVAL;
+    bsort_server::Req *r = it->second;
+    if (!r->done) return BSORT_ENOTREADY;
+    out->status = r->status;
+    out->batch_size = r->batch_size;
+    out->submit_ns = r->submit_ns;
+    out->start_ns = r->start_ns;
+    out->done_ns = r->done_ns;
+    S->tickets.erase(it);
+    delete r;
+    return BSORT_OK;
+}
+
+bsort_status bsort_serve_stats(bsort_t h, bsort_serve_info *out)
+{
+    if (!h || !out) return BSORT_EINVAL;
+    memset(out, 0, sizeof(*out));
+    bsort_server *S = h->server;
+    if (!S) return BSORT_OK;
+    std::lock_guard<std::mutex> lock(S->mu);
+    out->arena_bytes = S->arena_bytes;
+    out->workspace_bytes = h->ws_bytes + S->hb->ws_bytes;
+    out->arena_used_bytes = S->used;
+    out->arena_peak_bytes = S->peak;
+    out->queued = S->queue.size();
+    out->completed = S->done_count;
+    out->batches = S->batches;
+    out->max_batch = S->max_batch;
+    return BSORT_OK;
+}
+
+uint64_t bsort_clock_ns(void) { return clock_ns(); }
 
 bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_keys_in,
                                   void *h_keys_out, uint64_t n, void *cuda_stream)
 {
     if (!h) return BSORT_EINVAL;
+    if (h->server) return fail(h, BSORT_EBUSY, "the handle serves requests (bsort_submit)");
     if (n && (!h_keys_in || !h_keys_out)) return fail(h, BSORT_EINVAL, "null key pointer");
     if (n == 0) return BSORT_OK;
     bsort_status rs = prepare(h);
@@ -1001,15 +1656,16 @@ bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_ke
     if (rs != BSORT_OK) return rs;
     // staging: one device copy of the keys placed after the job's workspace
     const uint64_t stage = P.total;
-    rs = ensure_workspace(h, stage + align_up(n * 4));
+    const uint64_t bytes = n * (uint64_t)P.kb;
+    rs = ensure_workspace(h, stage + align_up(bytes));
     if (rs != BSORT_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     void *d_buf = static_cast<unsigned char *>(h->ws) + stage;
-    cudaError_t e = cudaMemcpyAsync(d_buf, h_keys_in, n * 4, cudaMemcpyHostToDevice, st);
+    cudaError_t e = cudaMemcpyAsync(d_buf, h_keys_in, bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
     rs = run_sort(h, kt, d_buf, nullptr, d_buf, nullptr, 0, n, st);
     if (rs != BSORT_OK) return rs;
-    e = cudaMemcpyAsync(h_keys_out, d_buf, n * 4, cudaMemcpyDeviceToHost, st);
+    e = cudaMemcpyAsync(h_keys_out, d_buf, bytes, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
     return BSORT_OK;
 }
@@ -1042,9 +1698,9 @@ bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which, void *h
     const Plan &P = h->last;
     uint64_t off = 0, size = 0;
     switch (which) {
-    case BSORT_IM_TILES: off = P.off_tiles_k; size = P.info.n_padded * 4; break;
-    case BSORT_IM_SAMPLES: off = P.off_samples; size = (uint64_t)P.n_rec * 8; break;
-    case BSORT_IM_SPLITTERS: off = P.off_spl; size = (uint64_t)P.info.b * 8; break;
+    case BSORT_IM_TILES: off = P.off_tiles_k; size = P.info.n_padded * P.kb; break;
+    case BSORT_IM_SAMPLES: off = P.off_samples; size = (uint64_t)P.n_rec * (P.wide ? 16 : 8); break;
+    case BSORT_IM_SPLITTERS: off = P.off_spl; size = (uint64_t)P.info.b * (P.wide ? 16 : 8); break;
     case BSORT_IM_COUNTS: off = P.off_counts; size = (uint64_t)P.n_runs * 4; break;
     case BSORT_IM_OFFSETS: off = P.off_offsets; size = (uint64_t)P.n_runs * 4; break;
     case BSORT_IM_RELOCATED:
@@ -1052,7 +1708,7 @@ bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which, void *h
             return fail(h, BSORT_ENOTREADY,
                         "the relocated array is not materialised under BSORT_FLAG_LOW_MEMORY");
         off = P.off_reloc_k;
-        size = P.info.n_padded * 4;
+        size = P.info.n_padded * P.kb;
         break;
     default: return fail(h, BSORT_EINVAL, "unknown intermediate %d", (int)which);
     }
@@ -1133,6 +1789,7 @@ extern "C" bsort_status bsort_sort_keys_noalloc(bsort_key_type kt, const void *d
                                                 void *cuda_stream, int wait)
 {
     if (n > BSORT_NOALLOC_MAX_KEYS) return BSORT_EINVAL;
+    if (kt == BSORT_U64) return BSORT_EUNSUPPORTED;
     if (n && (!d_keys_in || !d_keys_out)) return BSORT_EINVAL;
     if (n && d_keys_in != d_keys_out && overlaps(d_keys_in, n * 4, d_keys_out, n * 4))
         return BSORT_EINVAL;

@@ -26,14 +26,15 @@ namespace bsort {
 // ============================================================ direct segments
 // Cluster u sorts segment u = [seg[2u], seg[2u+1]) of the input (at most
 // C*T*E keys, guaranteed by the host) into the same range of the output.
-template <int T, int E, int C>
+// K: uint32_t (uint32 / float32 keys) or uint64_t (64-bit keys).
+template <typename K, int T, int E, int C>
 __global__ void __launch_bounds__(T, 1)
-k_seg_sort(const uint32_t *__restrict__ keys_in, uint32_t *__restrict__ keys_out,
+k_seg_sort(const K *__restrict__ keys_in, K *__restrict__ keys_out,
            const uint32_t *__restrict__ seg, int is_f32, int *err)
 {
     constexpr int CH = T * E;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint32_t *sm = reinterpret_cast<uint32_t *>(smem_raw);
+    K *sm = reinterpret_cast<K *>(smem_raw);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const uint32_t u = blockIdx.x / C;
@@ -48,26 +49,28 @@ k_seg_sort(const uint32_t *__restrict__ keys_in, uint32_t *__restrict__ keys_out
     const int per = C == 1 ? CH : (len + C - 1) / C;
     const int ustart = r * per;
     const int uend = min(ustart + per, len);
-    uint32_t v[E];
+    K v[E];
 #pragma unroll
     for (int k = 0; k < E; ++k) {
         const int x = ustart + wb_pos<E>(warp, lane, k);
-        uint32_t key = 0xFFFFFFFFu;
+        K key = KeyMax<K>::v;
         if (x < uend) {
             key = keys_in[L + x];
-            if (is_f32) key = f32_encode(key);
+            if constexpr (sizeof(K) == 4)
+                if (is_f32) key = f32_encode(key);
         }
         v[k] = key;
     }
-    cta_sort<uint32_t, T, E>(v, sm, uend > ustart ? uend - ustart : 0);
-    cluster_merge<uint32_t, T, E, C>(sm, len, per);
+    cta_sort<K, T, E>(v, sm, uend > ustart ? uend - ustart : 0);
+    cluster_merge<K, T, E, C>(sm, len, per);
     const int off = r * CH;
 #pragma unroll 4
     for (int k = 0; k < E; ++k) {
         const int x = k * T + tid;
         if (off + x < len) {
-            uint32_t key = sm[pidx<uint32_t>(x)];
-            if (is_f32) key = f32_decode(key);
+            K key = sm[pidx<K>(x)];
+            if constexpr (sizeof(K) == 4)
+                if (is_f32) key = f32_decode(key);
             keys_out[L + off + x] = key;
         }
     }
@@ -271,11 +274,11 @@ cudaError_t set_smem_attr(KernelT k, int bytes, bool nonportable = false)
     return e;
 }
 
-template <int T, int E, int C>
-cudaError_t launch_seg_sort_t(const uint32_t *keys_in, uint32_t *keys_out, const uint32_t *seg,
+template <typename K, int T, int E, int C>
+cudaError_t launch_seg_sort_t(const void *keys_in, void *keys_out, const uint32_t *seg,
                               uint32_t nseg, int is_f32, int *err, cudaStream_t st)
 {
-    const int sm = padded_elems<uint32_t>(T * E) * 4;
+    const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(nseg * C, 1, 1);
     cfg.blockDim = dim3(T, 1, 1);
@@ -288,13 +291,14 @@ cudaError_t launch_seg_sort_t(const uint32_t *keys_in, uint32_t *keys_out, const
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = C > 1 ? 1 : 0;
-    return cudaLaunchKernelEx(&cfg, k_seg_sort<T, E, C>, keys_in, keys_out, seg, is_f32, err);
+    return cudaLaunchKernelEx(&cfg, k_seg_sort<K, T, E, C>, static_cast<const K *>(keys_in),
+                              static_cast<K *>(keys_out), seg, is_f32, err);
 }
 
-template <int T, int E, int C>
+template <typename K, int T, int E, int C>
 cudaError_t init_seg_sort_t()
 {
-    return set_smem_attr(k_seg_sort<T, E, C>, padded_elems<uint32_t>(T * E) * 4);
+    return set_smem_attr(k_seg_sort<K, T, E, C>, padded_elems<K>(T * E) * (int)sizeof(K));
 }
 
 }  // namespace
@@ -302,14 +306,21 @@ cudaError_t init_seg_sort_t()
 cudaError_t init_batch_kernels()
 {
     cudaError_t e = cudaSuccess;
-    if (e == cudaSuccess) e = init_seg_sort_t<128, 16, 1>();
-    if (e == cudaSuccess) e = init_seg_sort_t<256, 16, 1>();
-    if (e == cudaSuccess) e = init_seg_sort_t<512, 16, 1>();
-    if (e == cudaSuccess) e = init_seg_sort_t<1024, 16, 1>();
-    if (e == cudaSuccess) e = init_seg_sort_t<1024, 32, 1>();
-    if (e == cudaSuccess) e = init_seg_sort_t<1024, 32, 2>();
-    if (e == cudaSuccess) e = init_seg_sort_t<1024, 32, 4>();
-    if (e == cudaSuccess) e = init_seg_sort_t<1024, 32, 8>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 128, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 256, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 512, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 1024, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 1024, 32, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 1024, 32, 2>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 1024, 32, 4>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 1024, 32, 8>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint64_t, 128, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint64_t, 256, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint64_t, 512, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint64_t, 1024, 16, 1>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint64_t, 1024, 16, 2>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint64_t, 1024, 16, 4>();
+    if (e == cudaSuccess) e = init_seg_sort_t<uint64_t, 1024, 16, 8>();
     if (e == cudaSuccess)
         e = set_smem_attr(k_seg_sublist_sort<1024, 32>, padded_elems<uint32_t>(kSegTile) * 4);
     if (e == cudaSuccess)
@@ -321,28 +332,47 @@ cudaError_t init_batch_kernels()
     return e;
 }
 
-cudaError_t launch_seg_sort(int chunk, int ctas, const uint32_t *keys_in, uint32_t *keys_out,
+cudaError_t launch_seg_sort(int chunk, int ctas, bool wide, const void *keys_in, void *keys_out,
                             const uint32_t *seg, uint32_t nseg, int is_f32, int *err,
                             cudaStream_t st)
 {
     if (nseg == 0) return cudaSuccess;
+#define L(K_, T_, E_, C_) \
+    return launch_seg_sort_t<K_, T_, E_, C_>(keys_in, keys_out, seg, nseg, is_f32, err, st)
+    if (wide) {
+        if (ctas == 1) {
+            switch (chunk) {
+            case 2048: L(uint64_t, 128, 16, 1);
+            case 4096: L(uint64_t, 256, 16, 1);
+            case 8192: L(uint64_t, 512, 16, 1);
+            case 16384: L(uint64_t, 1024, 16, 1);
+            }
+        } else if (chunk == 16384) {
+            switch (ctas) {
+            case 2: L(uint64_t, 1024, 16, 2);
+            case 4: L(uint64_t, 1024, 16, 4);
+            case 8: L(uint64_t, 1024, 16, 8);
+            }
+        }
+        return cudaErrorInvalidValue;
+    }
     if (ctas == 1) {
         switch (chunk) {
-        case 2048: return launch_seg_sort_t<128, 16, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
-        case 4096: return launch_seg_sort_t<256, 16, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
-        case 8192: return launch_seg_sort_t<512, 16, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
-        case 16384: return launch_seg_sort_t<1024, 16, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
-        case 32768: return launch_seg_sort_t<1024, 32, 1>(keys_in, keys_out, seg, nseg, is_f32, err, st);
-        default: return cudaErrorInvalidValue;
+        case 2048: L(uint32_t, 128, 16, 1);
+        case 4096: L(uint32_t, 256, 16, 1);
+        case 8192: L(uint32_t, 512, 16, 1);
+        case 16384: L(uint32_t, 1024, 16, 1);
+        case 32768: L(uint32_t, 1024, 32, 1);
+        }
+    } else if (chunk == 32768) {
+        switch (ctas) {
+        case 2: L(uint32_t, 1024, 32, 2);
+        case 4: L(uint32_t, 1024, 32, 4);
+        case 8: L(uint32_t, 1024, 32, 8);
         }
     }
-    if (chunk != 32768) return cudaErrorInvalidValue;
-    switch (ctas) {
-    case 2: return launch_seg_sort_t<1024, 32, 2>(keys_in, keys_out, seg, nseg, is_f32, err, st);
-    case 4: return launch_seg_sort_t<1024, 32, 4>(keys_in, keys_out, seg, nseg, is_f32, err, st);
-    case 8: return launch_seg_sort_t<1024, 32, 8>(keys_in, keys_out, seg, nseg, is_f32, err, st);
-    default: return cudaErrorInvalidValue;
-    }
+#undef L
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_seg_sublist_sort(const uint32_t *keys_in, int is_f32, const uint32_t *sub_seg,

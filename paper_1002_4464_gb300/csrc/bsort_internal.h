@@ -118,6 +118,37 @@ cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t b,
                               uint32_t n_pad, uint32_t Q, uint32_t *units, int *err,
                               cudaStream_t st);
 
+// ---------------------------------------------------------------- 64-bit keys
+// A sample record of a 64-bit-key sort: (key, p = i*t + r), compared key
+// first, then p.
+struct __align__(16) Rec128 {
+    uint64_t key, p;
+};
+
+cudaError_t init_u64_kernels();
+cudaError_t launch_sublist_sort_u64(int chunk, int ctas, const void *keys_in, uint64_t n,
+                                    uint32_t m, uint32_t s, uint64_t *tiles, Rec128 *samples,
+                                    cudaStream_t st);
+// Step 4: merge runs of L records of src (N in all) pairwise into dst.
+cudaError_t launch_rec_merge(const Rec128 *src, Rec128 *dst, uint32_t N, uint32_t L,
+                             cudaStream_t st);
+// Step 5: b splitters sorted[floor((j+1) N / b) - 1].
+cudaError_t launch_select_splitters_u64(const Rec128 *sorted, uint32_t N, uint32_t b, Rec128 *spl,
+                                        cudaStream_t st);
+// Step 6: counts a_ij (bucket-major) and run starts i*t + c_i(j-1).
+cudaError_t launch_sample_index_u64(const uint64_t *tiles, const Rec128 *samples,
+                                    const Rec128 *spl, uint32_t t, uint32_t s, uint32_t b,
+                                    uint32_t m, uint32_t *counts, uint32_t *srcb,
+                                    cudaStream_t st);
+// Step 8 for 64-bit keys (no values).
+cudaError_t launch_relocate_u64(const uint64_t *tiles_k, const uint32_t *offsets,
+                                const uint32_t *srcb, const uint32_t *blk, uint32_t runs,
+                                uint32_t n_pad, uint64_t *reloc_k, cudaStream_t st);
+// Step 9 for 64-bit keys; units == nullptr sorts the whole input [0, n).
+cudaError_t launch_bucket_sort_u64(int chunk, int ctas, const void *src, const uint32_t *units,
+                                   uint32_t max_units, uint64_t n, uint64_t n_pad, void *out,
+                                   int *err, cudaStream_t st);
+
 // ---------------------------------------------------------------- batches
 // Sublist size of sampled segments (one 1024 x 32 CTA per sublist).
 constexpr int kSegTile = 32768;
@@ -132,8 +163,8 @@ struct SegInfo {
 
 cudaError_t init_batch_kernels();
 // Direct segments: unit u = [seg[2u], seg[2u+1]) sorted by one unit of
-// `ctas` CTAs of `chunk` keys.
-cudaError_t launch_seg_sort(int chunk, int ctas, const uint32_t *keys_in, uint32_t *keys_out,
+// `ctas` CTAs of `chunk` keys (wide: 64-bit keys).
+cudaError_t launch_seg_sort(int chunk, int ctas, bool wide, const void *keys_in, void *keys_out,
                             const uint32_t *seg, uint32_t nseg, int is_f32, int *err,
                             cudaStream_t st);
 // Sampled segments, Steps 1-3 (sub_seg[g] = segment of sublist g).

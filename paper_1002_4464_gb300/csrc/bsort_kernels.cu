@@ -347,12 +347,12 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 // stores); a lane finds its first run from the run index of its block and
 // then advances its run as its position grows (skipping empty runs by a
 // search bounded by the run index, not one by one).
-template <int T>
+template <int T, typename KT>
 __global__ void __launch_bounds__(T, 4)
-k_relocate(const uint32_t *__restrict__ tiles_k, const void *__restrict__ tiles_v,
+k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
            const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ srcb,
            const uint32_t *__restrict__ blk, uint32_t runs,
-           uint32_t n_pad, int val_bytes, uint32_t *__restrict__ reloc_k,
+           uint32_t n_pad, int val_bytes, KT *__restrict__ reloc_k,
            void *__restrict__ reloc_v)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -595,8 +595,19 @@ cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const 
 {
     constexpr int T = (kRelocPart / kBlockItems) * 32;
     const uint32_t grid = (n_pad + kRelocPart - 1) / kRelocPart;
-    k_relocate<T><<<grid, T, 0, st>>>(tiles_k, tiles_v, offsets, srcb, blk, runs, n_pad,
-                                      val_bytes, reloc_k, reloc_v);
+    k_relocate<T, uint32_t><<<grid, T, 0, st>>>(tiles_k, tiles_v, offsets, srcb, blk, runs,
+                                                n_pad, val_bytes, reloc_k, reloc_v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relocate_u64(const uint64_t *tiles_k, const uint32_t *offsets,
+                                const uint32_t *srcb, const uint32_t *blk, uint32_t runs,
+                                uint32_t n_pad, uint64_t *reloc_k, cudaStream_t st)
+{
+    constexpr int T = (kRelocPart / kBlockItems) * 32;
+    const uint32_t grid = (n_pad + kRelocPart - 1) / kRelocPart;
+    k_relocate<T, uint64_t><<<grid, T, 0, st>>>(tiles_k, nullptr, offsets, srcb, blk, runs,
+                                                n_pad, 0, reloc_k, nullptr);
     return cudaGetLastError();
 }
 
@@ -622,6 +633,7 @@ cudaError_t init_kernels()
     if (e == cudaSuccess) e = init_sort_keys_kernels();
     if (e == cudaSuccess) e = init_sort_pairs_kernels();
     if (e == cudaSuccess) e = init_batch_kernels();
+    if (e == cudaSuccess) e = init_u64_kernels();
     return e;
 }
 

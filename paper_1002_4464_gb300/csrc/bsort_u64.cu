@@ -1,0 +1,352 @@
+// bsort_u64.cu -- GPU Bucket Sort (Dehne & Zaboli, Section 4, Algorithm 1)
+// for 64-bit keys, keys only.  The steps are those of the 32-bit path; what
+// changes is the width of what they move:
+//
+//   sorted sublists and buckets hold 64-bit keys (a CTA sorts 16,384 of
+//     them; clusters of 2, 4, 8 CTAs for larger units);
+//   a sample record is the pair (key, p), p = i*t + r, stored as two 64-bit
+//     words (16 bytes), compared key first, then p (the composite order);
+//   Step 4 merges the m sorted runs of s records (one per sublist) in
+//     log2(m) merge-path passes through L2 instead of sorting chunks in SMEM.
+#include "bsort_device.cuh"
+#include "bsort_internal.h"
+#include "bsort_sort.cuh"
+
+namespace bsort {
+
+__device__ __forceinline__ bool rec_lt(const Rec128 &a, const Rec128 &b)
+{
+    return a.key < b.key || (a.key == b.key && a.p < b.p);
+}
+
+// ============================================================ Steps 1-3
+// Cluster i sorts sublist i (t = C*T*E keys) and emits the samples of its
+// ranks, as k_sublist_sort does for 32-bit keys.
+template <int T, int E, int C>
+__global__ void __launch_bounds__(T, 1)
+k_sublist_sort_u64(const uint64_t *__restrict__ keys_in, uint64_t n, uint32_t s,
+                   uint64_t *__restrict__ tiles_k, Rec128 *__restrict__ samples)
+{
+    constexpr int CH = T * E;
+    constexpr uint32_t TT = (uint32_t)C * CH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sm = reinterpret_cast<uint64_t *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t tile = blockIdx.x / C;
+    const int r = (int)(blockIdx.x % C);
+    const uint64_t base = (uint64_t)tile * TT;
+    const uint64_t avail = n > base ? n - base : 0;
+    const int len = avail < (uint64_t)TT ? (int)avail : (int)TT;
+    const int off = r * CH;
+    uint64_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int x = off + wb_pos<E>(warp, lane, k);
+        v[k] = x < len ? keys_in[base + x] : 0xFFFFFFFFFFFFFFFFull;
+    }
+    const int clen = len - off;
+    cta_sort<uint64_t, T, E>(v, sm, clen < 0 ? 0 : (clen > CH ? CH : clen));
+    cluster_merge<uint64_t, T, E, C>(sm, len);
+#pragma unroll 4
+    for (int k = 0; k < E; ++k) {
+        const int x = k * T + tid;
+        tiles_k[base + off + x] = sm[pidx<uint64_t>(x)];
+    }
+    const uint32_t w = TT / s;
+    const uint32_t k0 = (uint32_t)off / w;
+    const uint32_t k1 = (uint32_t)(off + CH) / w;
+    for (uint32_t k = k0 + tid; k < k1 && k < s; k += T) {
+        const uint32_t rank = (k + 1) * w - 1;
+        Rec128 rec;
+        rec.key = sm[pidx<uint64_t>((int)(rank - off))];
+        rec.p = base + rank;
+        samples[(uint64_t)tile * s + k] = rec;
+    }
+}
+
+// ============================================================ Step 4
+// One merge-path pass: runs of length L of src (N records) merged pairwise
+// into runs of 2L in dst.  Thread x writes outputs [x*IT, (x+1)*IT).
+template <int T, int IT>
+__global__ void __launch_bounds__(T)
+k_rec_merge(const Rec128 *__restrict__ src, Rec128 *__restrict__ dst, uint32_t N, uint32_t L)
+{
+    const uint64_t o = ((uint64_t)blockIdx.x * T + threadIdx.x) * IT;
+    if (o >= N) return;
+    const uint64_t a0 = o / (2ull * L) * (2ull * L);
+    const uint32_t la = (uint32_t)min((uint64_t)L, N - a0);
+    const uint32_t lb = a0 + L < N ? (uint32_t)min((uint64_t)L, N - a0 - L) : 0u;
+    const Rec128 *A = src + a0;
+    const Rec128 *B = A + la;
+    const uint32_t d = (uint32_t)(o - a0);
+    // co-rank: i items of A among the first d outputs (A first on ties)
+    uint32_t lo = d > lb ? d - lb : 0, hi = d < la ? d : la;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (rec_lt(B[d - 1 - mid], A[mid])) hi = mid;
+        else lo = mid + 1;
+    }
+    uint32_t i = lo, j = d - lo;
+    const uint32_t end = min(d + (uint32_t)IT, la + lb);  // d < la + lb since o < N
+    for (uint32_t x = d; x < end; ++x) {
+        const bool takeA = j >= lb || (i < la && !rec_lt(B[j], A[i]));
+        dst[a0 + x] = takeA ? A[i++] : B[j++];
+    }
+}
+
+// ============================================================ Step 5
+__global__ void k_select_splitters_u64(const Rec128 *__restrict__ sorted, uint32_t N, uint32_t b,
+                                       Rec128 *__restrict__ spl)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < b) spl[j] = sorted[(uint64_t)(j + 1) * N / b - 1];
+}
+
+// ============================================================ Step 6
+// As k_sample_index: thread (sublist i, splitters j0 .. j0+jb-1) finds
+// q = #samples <= g_j among the sublist's own s samples (binary search,
+// then galloping as j grows) and c_ij in the w-item window by binary search.
+__device__ __forceinline__ uint32_t window_count_u64(const uint64_t *__restrict__ tiles,
+                                                     uint64_t base, uint32_t q, uint32_t w,
+                                                     uint32_t t, uint32_t s, const Rec128 &g)
+{
+    if (q >= s) return t;
+    uint32_t a = q * w, b = q * w + w - 1;  // the item at rank b is > g
+    while (a < b) {
+        const uint32_t mid = (a + b) >> 1;
+        Rec128 item;
+        item.key = tiles[base + mid];
+        item.p = base + mid;
+        if (!rec_lt(g, item)) a = mid + 1;
+        else b = mid;
+    }
+    return a;
+}
+
+template <int T>
+__global__ void __launch_bounds__(T)
+k_sample_index_u64(const uint64_t *__restrict__ tiles, const Rec128 *__restrict__ samples,
+                   const Rec128 *__restrict__ spl, uint32_t t, uint32_t s, uint32_t b,
+                   uint32_t m, uint32_t *__restrict__ counts, uint32_t *__restrict__ srcb,
+                   uint32_t jb)
+{
+    const uint32_t gpt = (b + T * jb - 1) / (T * jb);
+    const uint32_t i = blockIdx.x / gpt;
+    const uint32_t j0 = ((blockIdx.x % gpt) * T + threadIdx.x) * jb;
+    if (j0 >= b) return;
+    const uint32_t j1 = min(j0 + jb, b);
+    const uint64_t base = (uint64_t)i * t;
+    const uint32_t w = t / s;
+    const Rec128 *smp = samples + (uint64_t)i * s;
+    const uint32_t jf = j0 ? j0 - 1 : 0;
+    Rec128 g = spl[jf];
+    uint32_t lo = 0, hi = s;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (!rec_lt(g, smp[mid])) lo = mid + 1;
+        else hi = mid;
+    }
+    uint32_t q = lo;
+    uint32_t prev = j0 ? window_count_u64(tiles, base, q, w, t, s, g) : 0u;
+    for (uint32_t j = j0; j < j1; ++j) {
+        g = spl[j];
+        if (q < s && !rec_lt(g, smp[q])) {
+            uint32_t step = 1, lo2 = q + 1, hi2 = q + 1;
+            while (hi2 < s && !rec_lt(g, smp[hi2])) {
+                lo2 = hi2 + 1;
+                step <<= 1;
+                hi2 = min(s, q + step);
+            }
+            hi2 = min(hi2, s);
+            while (lo2 < hi2) {
+                const uint32_t mid = (lo2 + hi2) >> 1;
+                if (!rec_lt(g, smp[mid])) lo2 = mid + 1;
+                else hi2 = mid;
+            }
+            q = lo2;
+        }
+        const uint32_t c = window_count_u64(tiles, base, q, w, t, s, g);
+        counts[(uint64_t)j * m + i] = c - prev;
+        srcb[(uint64_t)j * m + i] = (uint32_t)base + prev;
+        prev = c;
+    }
+}
+
+// ============================================================ Step 9
+// Cluster u sorts unit u = [units[1+2u], units[2+2u]) of the relocated
+// array (or, with units == nullptr, the whole input [0, n)) and writes the
+// positions below n.
+template <int T, int E, int C>
+__global__ void __launch_bounds__(T, 1)
+k_bucket_sort_u64(const uint64_t *__restrict__ src, const uint32_t *__restrict__ units,
+                  uint64_t n, uint64_t n_pad, uint64_t *__restrict__ out, int *err)
+{
+    constexpr int CH = T * E;
+    constexpr uint64_t CAP = (uint64_t)C * CH;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t *sm = reinterpret_cast<uint64_t *>(smem_raw);
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t u = blockIdx.x / C;
+    const int r = (int)(blockIdx.x % C);
+    uint64_t L = 0, R = n;
+    if (units != nullptr) {
+        if (u >= units[0]) return;
+        L = units[1 + 2 * u];
+        R = units[2 + 2 * u];
+    }
+    if (R < L || R > n_pad || R - L > CAP) {
+        if (tid == 0) set_error(err, DEV_INTERNAL);
+        return;
+    }
+    if (R == L) return;
+    const int len = (int)(R - L);
+    const int per = C == 1 ? CH : (len + C - 1) / C;
+    const int ustart = r * per;
+    const int uend = min(ustart + per, len);
+    uint64_t v[E];
+#pragma unroll
+    for (int k = 0; k < E; ++k) {
+        const int x = ustart + wb_pos<E>(warp, lane, k);
+        v[k] = x < uend ? src[L + x] : 0xFFFFFFFFFFFFFFFFull;
+    }
+    cta_sort<uint64_t, T, E>(v, sm, uend > ustart ? uend - ustart : 0);
+    cluster_merge<uint64_t, T, E, C>(sm, len, per);
+    const int off = r * CH;
+    const uint64_t lim64 = min((unsigned long long)len, (unsigned long long)(n > L ? n - L : 0));
+    const int lim = (int)lim64;
+#pragma unroll 4
+    for (int k = 0; k < E; ++k) {
+        const int x = k * T + tid;
+        if (off + x < lim) out[L + off + x] = sm[pidx<uint64_t>(x)];
+    }
+}
+
+// ============================================================ launching
+namespace {
+
+template <int T, int E, int C>
+cudaError_t init_u64_t()
+{
+    const int sm = padded_elems<uint64_t>(T * E) * 8;
+    cudaError_t e = cudaFuncSetAttribute(k_sublist_sort_u64<T, E, C>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_bucket_sort_u64<T, E, C>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    return e;
+}
+
+template <int T, int E, int C>
+cudaError_t launch_sublist_u64_t(const void *keys_in, uint64_t n, uint32_t m, uint32_t s,
+                                 uint64_t *tiles, Rec128 *samples, cudaStream_t st)
+{
+    const int sm = padded_elems<uint64_t>(T * E) * 8;
+    return launch_maybe_cluster(k_sublist_sort_u64<T, E, C>, m * C, T, sm, C, st,
+                                static_cast<const uint64_t *>(keys_in), n, s, tiles, samples);
+}
+
+template <int T, int E, int C>
+cudaError_t launch_bucket_u64_t(const void *src, const uint32_t *units, uint32_t max_units,
+                                uint64_t n, uint64_t n_pad, void *out, int *err, cudaStream_t st)
+{
+    const int sm = padded_elems<uint64_t>(T * E) * 8;
+    const unsigned grid = (units ? max_units : 1u) * C;
+    return launch_maybe_cluster(k_bucket_sort_u64<T, E, C>, grid, T, sm, C, st,
+                                static_cast<const uint64_t *>(src), units, n, n_pad,
+                                static_cast<uint64_t *>(out), err);
+}
+
+}  // namespace
+
+cudaError_t init_u64_kernels()
+{
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = init_u64_t<128, 16, 1>();
+    if (e == cudaSuccess) e = init_u64_t<256, 16, 1>();
+    if (e == cudaSuccess) e = init_u64_t<512, 16, 1>();
+    if (e == cudaSuccess) e = init_u64_t<1024, 16, 1>();
+    if (e == cudaSuccess) e = init_u64_t<1024, 16, 2>();
+    if (e == cudaSuccess) e = init_u64_t<1024, 16, 4>();
+    if (e == cudaSuccess) e = init_u64_t<1024, 16, 8>();
+    return e;
+}
+
+cudaError_t launch_sublist_sort_u64(int chunk, int ctas, const void *keys_in, uint64_t n,
+                                    uint32_t m, uint32_t s, uint64_t *tiles, Rec128 *samples,
+                                    cudaStream_t st)
+{
+#define L(T_, E_, C_) return launch_sublist_u64_t<T_, E_, C_>(keys_in, n, m, s, tiles, samples, st)
+    if (ctas == 1) {
+        switch (chunk) {
+        case 2048: L(128, 16, 1);
+        case 4096: L(256, 16, 1);
+        case 8192: L(512, 16, 1);
+        case 16384: L(1024, 16, 1);
+        }
+    } else if (chunk == 16384) {
+        switch (ctas) {
+        case 2: L(1024, 16, 2);
+        case 4: L(1024, 16, 4);
+        case 8: L(1024, 16, 8);
+        }
+    }
+#undef L
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bucket_sort_u64(int chunk, int ctas, const void *src, const uint32_t *units,
+                                   uint32_t max_units, uint64_t n, uint64_t n_pad, void *out,
+                                   int *err, cudaStream_t st)
+{
+#define L(T_, E_, C_) \
+    return launch_bucket_u64_t<T_, E_, C_>(src, units, max_units, n, n_pad, out, err, st)
+    if (ctas == 1) {
+        switch (chunk) {
+        case 2048: L(128, 16, 1);
+        case 4096: L(256, 16, 1);
+        case 8192: L(512, 16, 1);
+        case 16384: L(1024, 16, 1);
+        }
+    } else if (chunk == 16384) {
+        switch (ctas) {
+        case 2: L(1024, 16, 2);
+        case 4: L(1024, 16, 4);
+        case 8: L(1024, 16, 8);
+        }
+    }
+#undef L
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_rec_merge(const Rec128 *src, Rec128 *dst, uint32_t N, uint32_t L,
+                             cudaStream_t st)
+{
+    constexpr int T = 256, IT = 8;
+    const uint32_t grid = (uint32_t)(((uint64_t)N + T * IT - 1) / (T * IT));
+    k_rec_merge<T, IT><<<grid, T, 0, st>>>(src, dst, N, L);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_select_splitters_u64(const Rec128 *sorted, uint32_t N, uint32_t b, Rec128 *spl,
+                                        cudaStream_t st)
+{
+    k_select_splitters_u64<<<(b + 255) / 256, 256, 0, st>>>(sorted, N, b, spl);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sample_index_u64(const uint64_t *tiles, const Rec128 *samples,
+                                    const Rec128 *spl, uint32_t t, uint32_t s, uint32_t b,
+                                    uint32_t m, uint32_t *counts, uint32_t *srcb,
+                                    cudaStream_t st)
+{
+    constexpr int T = 128;
+    const uint32_t jb = b >= 8 * T ? 8 : (b + T - 1) / T;
+    const uint32_t gpt = (b + T * jb - 1) / (T * jb);
+    k_sample_index_u64<T><<<m * gpt, T, 0, st>>>(tiles, samples, spl, t, s, b, m, counts, srcb,
+                                                 jb);
+    return cudaGetLastError();
+}
+
+}  // namespace bsort

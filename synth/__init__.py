@@ -155,6 +155,20 @@ def keys_u64(n: int, seed: int) -> np.ndarray:
     return draws64(seed, n)
 
 
+def keys_zipf_u64(n: int, seed: int) -> np.ndarray:
+    """64-bit Zipf(1.1) keys over 2^10 distinct values: the 32-bit Zipf key z
+    in the high word, z ^ 0x9E3779B9 in the low word."""
+    z = keys_zipf(n, seed).astype(np.uint64)
+    return (z << np.uint64(32)) | (z ^ np.uint64(0x9E3779B9))
+
+
+def poisson_arrivals(count: int, rate: float, seed: int) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process of the given rate: sums
+    of exponential gaps -ln(1 - x_k) / rate, x_k = (x_k64 >> 11) * 2^-53."""
+    x = (draws64(seed, count) >> np.uint64(11)).astype(np.float64) * 2.0 ** -53
+    return np.cumsum(-np.log1p(-x) / rate)
+
+
 # ---------------------------------------------------------------- torch side
 
 def _mix64_t(z):

@@ -177,9 +177,9 @@ def test_plan_batch_errors():
     with pytest.raises(pkg.BsortError) as e:
         pkg.bsort_plan_batch(h, pkg.BSORT_U32, np.array([0, 10, 5], np.uint64))
     assert e.value.status == pkg.BSORT_EINVAL
-    with pytest.raises(pkg.BsortError) as e:
-        pkg.bsort_plan_batch(h, pkg.BSORT_U64, np.array([0, 10], np.uint64))
-    assert e.value.status == pkg.BSORT_EUNSUPPORTED
+    p = pkg.bsort_plan_batch(h, pkg.BSORT_U64,
+                             np.cumsum([0, 10, 131072, 131073, 600000]).astype(np.uint64))
+    assert (p.direct_segs, p.sampled_segs, p.large_segs) == (2, 0, 2)
     with pytest.raises(pkg.BsortError) as e:
         pkg.bsort_plan_batch(h, pkg.BSORT_U32, np.array([0, 1 << 32], np.uint64))
     assert e.value.status == pkg.BSORT_EUNSUPPORTED
@@ -198,3 +198,26 @@ def test_batch_sizes_generator():
     # the scaling keeps the order of the sizes
     raw = synth.batch_sizes(20000, synth.seed_for(4, 0), cap=1 << 40)
     assert np.all(np.diff(s[np.argsort(raw, kind="stable")]) >= 0)
+
+
+def test_plan_u64_keys():
+    """64-bit keys sort 64-bit words: CTAs of at most 16384 keys, units of at
+    most 8 x 16384; pairs with 64-bit keys are refused."""
+    h = _handle()
+    for n in (100, 131072, 131073, 1 << 20, (1 << 24) + 5, 1 << 28):
+        p = pkg.bsort_plan(h, pkg.BSORT_U64, 0, n)
+        assert p.unit_capacity <= 8 * 16384
+        if p.single_tile:
+            assert n <= p.unit_capacity
+        else:
+            assert p.t <= 8 * 16384 and p.m * p.t == p.n_padded >= n
+            assert p.bucket_bound == oracle.bucket_bound(p.n_padded, p.m, p.s, p.b)
+            assert p.bucket_bound <= p.unit_capacity
+    with pytest.raises(pkg.BsortError) as e:
+        pkg.bsort_plan(h, pkg.BSORT_U64, 8, 1 << 20)
+    assert e.value.status == pkg.BSORT_EUNSUPPORTED
+    pkg.bsort_destroy(h)
+    h = _handle(4096, 64)
+    p = pkg.bsort_plan(h, pkg.BSORT_U64, 0, 1 << 20)
+    assert (p.t, p.s, p.b, p.m) == (4096, 64, 64, 256)
+    pkg.bsort_destroy(h)

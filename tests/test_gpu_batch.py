@@ -117,3 +117,28 @@ def test_batch_equals_one_at_a_time():
     # and again: the batch is deterministic
     assert np.array_equal(_run(sorter, keys, off), got)
     sorter.close()
+
+
+def test_batch_u64():
+    """64-bit keys: segments up to 131072 keys sorted whole (CTAs of 16384
+    keys, clusters up to 8), larger ones by a plain sort each."""
+    sizes = np.array([0, 1, 2, 1000, 2048, 2049, 16384, 16385, 65536, 131072, 131073, 400000,
+                      7], np.int64)
+    off = np.concatenate([[3], 3 + np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1]) + 5
+    keys = synth.keys_u64(n, synth.seed_for(5, 4))
+    keys[::7] &= np.uint64(0xFF)  # duplicates
+    sorter = pkg.BucketSorter()
+    p = sorter.plan_batch(off, "u64")
+    assert p.direct_segs == 9 and p.large_segs == 2 and p.sampled_segs == 0
+    d_in = torch.from_numpy(keys.view(np.int64)).cuda()
+    d_out = torch.full_like(d_in, 0x5A5A)
+    sorter.sort_batch(d_in, off, out=d_out, key_type="u64")
+    sorter.sync()
+    got = d_out.cpu().numpy().view(np.uint64)
+    want = np.full(n, 0x5A5A, np.uint64)
+    for q in range(len(sizes)):
+        a, b = int(off[q]), int(off[q + 1])
+        want[a:b] = oracle.textbook_sort(keys[a:b], "u64")
+    assert np.array_equal(got, want)
+    sorter.close()

@@ -390,3 +390,98 @@ def test_low_memory_equals_materialised(n, t, s, kind):
         wk, wv = oracle.textbook_sort(keys, "u32", vals=np.arange(n, dtype=np.uint32))
         for ok, ov in outs:
             assert np.array_equal(ok, wk) and np.array_equal(ov, wv)
+
+
+def _check_intermediates_u64(sorter, want, n_pad, m, s, b):
+    """Intermediates of a 64-bit-key sort: 8-byte sublist items, 16-byte
+    (key, p) sample and splitter records."""
+    im = pkg
+    got_t = sorter.intermediate(im.BSORT_IM_TILES, n_pad * 8, np.uint64)
+    assert np.array_equal(got_t, want["tile_keys"].astype(np.uint64)), "Step 2 sublists"
+    got_s = sorter.intermediate(im.BSORT_IM_SAMPLES, m * s * 16, np.uint64).reshape(-1, 2)
+    assert np.array_equal(got_s[:, 0], want["samp_keys"].astype(np.uint64)), "Step 3 keys"
+    assert np.array_equal(got_s[:, 1], want["samp_p"].astype(np.uint64)), "Step 3 positions"
+    got_g = sorter.intermediate(im.BSORT_IM_SPLITTERS, b * 16, np.uint64).reshape(-1, 2)
+    assert np.array_equal(got_g[:, 0], want["spl_keys"].astype(np.uint64)), "Step 5 keys"
+    assert np.array_equal(got_g[:, 1], want["spl_p"].astype(np.uint64)), "Step 5 positions"
+    got_a = sorter.intermediate(im.BSORT_IM_COUNTS, m * b * 4, np.uint32)
+    assert np.array_equal(got_a, want["counts"].astype(np.uint32)), "Step 6 counts"
+    got_l = sorter.intermediate(im.BSORT_IM_OFFSETS, m * b * 4, np.uint32)
+    assert np.array_equal(got_l, want["offsets"].astype(np.uint32)), "Step 7 offsets"
+    got_r = sorter.intermediate(im.BSORT_IM_RELOCATED, n_pad * 8, np.uint64)
+    assert np.array_equal(got_r, want["reloc_keys"].astype(np.uint64)), "Step 8 relocation"
+
+
+def _keys_u64(kind, n, seed):
+    k = synth.keys_u64(n, seed)
+    if kind == "dup":     # few distinct values, equal high words
+        k = (k & np.uint64(0xF)) | (np.uint64(0xDEADBEEF) << np.uint64(32))
+    elif kind == "zero":
+        k = np.zeros(n, np.uint64)
+    elif kind == "low":   # differ only in the low 32 bits
+        k = k & np.uint64(0xFFFFFFFF)
+    return k
+
+
+def _gpu_sort_u64(sorter, keys):
+    d_in = torch.from_numpy(keys.view(np.int64)).cuda()
+    d_out = sorter.sort_keys(d_in, key_type="u64")
+    sorter.sync()
+    return d_out.cpu().numpy().view(np.uint64)
+
+
+@pytest.mark.parametrize("n,t,s,b", [
+    (1 << 20, 4096, 64, 0),          # config 1's shape with 64-bit keys
+    (123457, 8192, 128, 0),          # ragged tail
+    (300001, 32768, 512, 700),       # 2-CTA cluster sublists, b > s
+    (500000, 131072, 2048, 1500),    # 8-CTA cluster sublists, b < s
+])
+@pytest.mark.parametrize("kind", ["uniform", "dup", "zero", "low"])
+def test_u64_intermediates(n, t, s, b, kind):
+    keys = _keys_u64(kind, n, synth.seed_for(5, 1, n % 1000))
+    want = oracle.paper_sort(keys, t, s, "u64", b=b)
+    sorter = pkg.BucketSorter(tile=t, samples=s, buckets=b)
+    p = sorter.plan(n, "u64")
+    assert (p.t, p.s, p.b) == (t, s, b or s)
+    got = _gpu_sort_u64(sorter, keys)
+    assert np.array_equal(got, want["keys"])
+    _check_intermediates_u64(sorter, want, want["n_padded"], want["m"], s, b or s)
+    sorter.close()
+
+
+@pytest.mark.parametrize("n", [0, 1, 2, 2047, 2049, 16385, 131072, 131073, 1 << 22,
+                               (1 << 24) + 3])
+def test_u64_auto_sizes(n):
+    keys = _keys_u64("uniform", n, synth.seed_for(5, 2, n % 1000))
+    sorter = pkg.BucketSorter()
+    got = _gpu_sort_u64(sorter, keys) if n else np.zeros(0, np.uint64)
+    assert np.array_equal(got, np.sort(keys))
+    sorter.close()
+
+
+def test_u64_full_size_2e27():
+    """2^27 64-bit keys (1 GiB) against the library sort."""
+    n = 1 << 27
+    keys = synth.keys_u64(n, synth.seed_for(5, 3))
+    sorter = pkg.BucketSorter()
+    d_in = torch.from_numpy(keys.view(np.int64)).cuda()
+    d_out = sorter.sort_keys(d_in, key_type="u64")
+    sorter.sync()
+    # signed view: flip the top bit so that torch's int64 order is uint64 order
+    flip = torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
+    want = torch.sort(d_in ^ flip).values ^ flip
+    assert torch.equal(d_out, want)
+    sorter.close()
+
+
+def test_u64_host_entry():
+    n = (1 << 21) + 9
+    keys = synth.keys_u64(n, synth.seed_for(5, 5))
+    sorter = pkg.BucketSorter()
+    h_in = torch.from_numpy(keys.view(np.int64)).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    sorter.sort_keys_host(h_in, h_out, key_type="u64")
+    sorter.sync()
+    torch.cuda.synchronize()
+    assert np.array_equal(h_out.numpy().view(np.uint64), np.sort(keys))
+    sorter.close()
