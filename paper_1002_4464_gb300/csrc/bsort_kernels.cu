@@ -343,10 +343,15 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 // number of items whatever the key distribution.  Position y lies in the
 // run q (offsets[q] <= y < offsets[q+1]) and comes from position srcb[q] +
 // (y - offsets[q]) of the sorted sublists.  Each warp covers kBlockItems
-// consecutive positions with its lanes on consecutive positions (coalesced
-// stores); a lane finds its first run from the run index of its block and
-// then advances its run as its position grows (skipping empty runs by a
-// search bounded by the run index, not one by one).
+// consecutive positions, its lanes on consecutive positions (coalesced
+// stores).  The runs meeting a warp's block are blk[b] .. blk[b+1] (the run
+// index); when they are few (the usual case) the warp stages their offsets
+// and starts in shared memory, every lane resolves the sources of all its
+// positions there, and then issues all its loads at once; otherwise each
+// lane walks the runs in global memory (skipping stretches of empty runs by
+// a search bounded by the run index).
+constexpr int kRelocRunsCap = 256;  // runs a warp stages in shared memory
+
 template <int T, typename KT>
 __global__ void __launch_bounds__(T, 4)
 k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
@@ -355,14 +360,67 @@ k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
            uint32_t n_pad, int val_bytes, KT *__restrict__ reloc_k,
            void *__restrict__ reloc_v)
 {
+    constexpr int W = T / 32;
+    constexpr int P = kBlockItems / 32;  // positions per lane
+    __shared__ uint32_t s_off[W][kRelocRunsCap + 1];
+    __shared__ uint32_t s_src[W][kRelocRunsCap];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wy = blockIdx.x * (uint32_t)kRelocPart + (uint32_t)warp * kBlockItems;
-    if (wy >= n_pad) return;
+    if (wy >= n_pad) return;  // whole warp
     const uint32_t b = wy / kBlockItems;
     const uint32_t nblk = (n_pad + kBlockItems - 1) / kBlockItems;
+    const uint32_t q0 = blk[b];
+    const uint32_t q1 = b + 1 < nblk ? blk[b + 1] : runs - 1;
+    const uint32_t yend = min(wy + (uint32_t)kBlockItems, n_pad);
+    if (q1 - q0 < (uint32_t)kRelocRunsCap) {
+        const uint32_t R = q1 - q0 + 1;  // runs q0 .. q1; offsets[q1 + 1] exists
+        for (uint32_t i = lane; i <= R; i += 32) s_off[warp][i] = offsets[q0 + i];
+        for (uint32_t i = lane; i < R; i += 32) s_src[warp][i] = srcb[q0 + i];
+        __syncwarp();
+        uint32_t j = 0;  // s_off[warp][j] <= y for every y of this lane
+        constexpr int G = 8;  // positions resolved, then loaded, at a time
+#pragma unroll 1
+        for (int k0 = 0; k0 < P; k0 += G) {
+            uint32_t src[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const uint32_t y = wy + (uint32_t)lane + 32u * (uint32_t)(k0 + k);
+                while (j + 1 < R && s_off[warp][j + 1] <= y) ++j;
+                src[k] = s_src[warp][j] + (y - s_off[warp][j]);
+            }
+            KT v[G];
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const uint32_t y = wy + (uint32_t)lane + 32u * (uint32_t)(k0 + k);
+                v[k] = y < yend ? tiles_k[src[k]] : (KT)0;
+            }
+#pragma unroll
+            for (int k = 0; k < G; ++k) {
+                const uint32_t y = wy + (uint32_t)lane + 32u * (uint32_t)(k0 + k);
+                if (y < yend) reloc_k[y] = v[k];
+            }
+            if (val_bytes == 4) {
+                const uint32_t *tv = static_cast<const uint32_t *>(tiles_v);
+                uint32_t *rv = static_cast<uint32_t *>(reloc_v);
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    const uint32_t y = wy + (uint32_t)lane + 32u * (uint32_t)(k0 + k);
+                    if (y < yend) rv[y] = tv[src[k]];
+                }
+            } else if (val_bytes == 8) {
+                const uint64_t *tv = static_cast<const uint64_t *>(tiles_v);
+                uint64_t *rv = static_cast<uint64_t *>(reloc_v);
+#pragma unroll
+                for (int k = 0; k < G; ++k) {
+                    const uint32_t y = wy + (uint32_t)lane + 32u * (uint32_t)(k0 + k);
+                    if (y < yend) rv[y] = tv[src[k]];
+                }
+            }
+        }
+        return;
+    }
     uint32_t y = wy + lane;
-    uint32_t lo = blk[b];
-    uint32_t hi = b + 1 < nblk ? blk[b + 1] : runs - 1;
+    uint32_t lo = q0, hi = q1;
     while (lo < hi) {  // last run q with offsets[q] <= y
         const uint32_t mid = (lo + hi + 1) >> 1;
         if (offsets[mid] <= y) lo = mid;
@@ -371,7 +429,6 @@ k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
     uint32_t q = lo;
     uint32_t rs = offsets[q], re = offsets[q + 1];
     uint32_t base = srcb[q];
-    const uint32_t yend = min(wy + (uint32_t)kBlockItems, n_pad);
     for (; y < yend; y += 32) {
         if (y >= re) {
             run_advance<kBlockItems>(offsets, blk, nblk, runs, y, q, rs, re);
