@@ -122,6 +122,10 @@ typedef struct {
     uint32_t num_kernels;    /* kernel launches per call */
     uint64_t workspace_bytes;/* device workspace this job needs */
     uint32_t b;              /* buckets (Steps 5-9); b = s is the paper's rule */
+    uint32_t unit_small;     /* when unit_ctas > 1: buckets of at most this
+                                many items are sorted by one CTA each, the
+                                others by a unit of unit_ctas CTAs (0: one
+                                tier) */
 } bsort_plan_info;
 
 /* The plan of one batch (bsort_plan_batch). */

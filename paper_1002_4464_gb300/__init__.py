@@ -61,7 +61,7 @@ class bsort_plan_info(ctypes.Structure):
                 ("tile_ctas", ctypes.c_uint32), ("unit_ctas", ctypes.c_uint32),
                 ("unit_capacity", ctypes.c_uint64), ("single_tile", ctypes.c_uint32),
                 ("num_kernels", ctypes.c_uint32), ("workspace_bytes", ctypes.c_uint64),
-                ("b", ctypes.c_uint32)]
+                ("b", ctypes.c_uint32), ("unit_small", ctypes.c_uint32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -47,6 +47,7 @@ struct Plan {
     int vb;          // value bytes (0 keys only)
     int tile_chunk;  // items per CTA in Step 2 (t = tile_ctas * tile_chunk)
     int unit_chunk;  // items per CTA in Step 9 (capacity = unit_ctas * unit_chunk)
+    int small_chunk;  // two-tier Step 9: one-CTA units of this many items (0: one tier)
     uint32_t n_rec;      // m*s sample records
     uint32_t n_runs;     // m*b runs A_ij (counts, offsets)
     uint32_t n_rec_pad;  // rounded up to kRecordChunk
@@ -54,7 +55,7 @@ struct Plan {
     // workspace offsets (bytes)
     uint64_t off_hdr, off_tiles_k, off_tiles_v, off_reloc_k, off_reloc_v, off_samples,
         off_rec_a, off_rec_b, off_spl, off_counts, off_cum, off_offsets, off_status,
-        off_units, off_srcb, off_blk, total;
+        off_units, off_units2, off_srcb, off_blk, total;
     bool relocate;  // materialise Step 8 (else fused into Step 9's load)
 };
 
@@ -137,6 +138,24 @@ uint64_t choose_buckets(uint64_t np, uint64_t m, uint64_t s, uint64_t Q, uint64_
         if (b >= bmax) return bmax;
         if (b >= lo) return b;
     }
+}
+
+// Bucket count for a two-tier Step 9 (one-CTA units of Q1 items, cluster
+// units of Q2 >= bound for the rest): at least the smallest b whose bound
+// fits Q2, else about 1.05 average buckets per Q1, so that nearly every
+// bucket fills a one-CTA unit alone.  Returns 0 when no b <= bmax fits Q2.
+uint64_t choose_buckets_two_tier(uint64_t np, uint64_t m, uint64_t s, uint64_t Q1, uint64_t Q2,
+                                 uint64_t bmax)
+{
+    if (bound_for(np, m, s, bmax) > Q2) return 0;
+    uint64_t lo = 1, hi = bmax;
+    while (lo < hi) {
+        const uint64_t mid = (lo + hi) / 2;
+        if (bound_for(np, m, s, mid) <= Q2) hi = mid;
+        else lo = mid + 1;
+    }
+    const uint64_t b = (105 * np + 100 * Q1 - 1) / (100 * Q1);
+    return b > bmax ? bmax : (b < lo ? lo : b);
 }
 
 // Sort-unit shapes (items per CTA) and cluster sizes the kernels provide.
@@ -321,12 +340,25 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->tile_chunk = btc;
         P->unit_chunk = buc;
         I.unit_capacity = (uint64_t)buc * buk;
+        // Step 9 in two tiers when the bound needs a cluster and b can make
+        // the average bucket ~1/1.05 of the largest one-CTA unit: one-CTA
+        // units for the buckets that fit it (nearly all), cluster units only
+        // for the others
+        const uint64_t bmax = m * bs < (uint64_t)kMaxBuckets ? m * bs : (uint64_t)kMaxBuckets;
+        if (buk > 1 && !forced_b && !forced_s &&
+            (105 * I.n_padded + 100 * (uint64_t)cm - 1) / (100 * (uint64_t)cm) <= bmax) {
+            P->small_chunk = cm;
+            I.unit_small = (uint32_t)cm;
+        }
         uint64_t b = bs;  // the paper's rule, kept when s is given
         if (forced_b) {
             b = forced_b;
         } else if (!forced_s) {
-            const uint64_t bmax = m * bs < (uint64_t)kMaxBuckets ? m * bs : (uint64_t)kMaxBuckets;
-            const uint64_t bc = choose_buckets(I.n_padded, m, bs, I.unit_capacity, bmax);
+            const uint64_t bc =
+                P->small_chunk
+                    ? choose_buckets_two_tier(I.n_padded, m, bs, (uint64_t)P->small_chunk,
+                                              I.unit_capacity, bmax)
+                    : choose_buckets(I.n_padded, m, bs, I.unit_capacity, bmax);
             if (bc) b = bc;
         }
         I.b = (uint32_t)b;
@@ -336,19 +368,20 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->n_rec_pad = (uint32_t)((P->n_rec + kRecordChunk - 1) / kRecordChunk * kRecordChunk);
         P->scan_chunks = (P->n_runs + kScanChunk - 1) / kScanChunk;
         const bool reloc = P->wide || !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
+        const uint32_t s9 = P->small_chunk ? 2 : 1;  // Step-9 launches
         if (P->wide) {
             // records (16 bytes) merged from runs of s: ceil(log2 m) passes
             P->n_rec_pad = P->n_rec;
             uint32_t merges = 0;
             for (uint64_t L = bs; L < P->n_rec; L <<= 1) ++merges;
             I.num_kernels = 1 /*S2-3*/ + merges + 1 /*S5*/ + 1 /*S6*/ + 1 /*S7*/ +
-                            1 /*run index*/ + 1 /*S8*/ + 1 /*units*/ + 1 /*S9*/;
+                            1 /*run index*/ + 1 /*S8*/ + 1 /*units*/ + s9;
         } else {
             uint32_t merges = 0;
             for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
             I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
                             1 /*S6*/ + 1 /*S7*/ + 1 /*run index*/ + (reloc ? 1 : 0) /*S8*/ +
-                            1 /*units*/ + 1 /*S9*/;
+                            1 /*units*/ + s9;
         }
     }
 
@@ -379,12 +412,23 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->off_offsets = take(((uint64_t)P->n_runs + 1) * 4);
         P->off_status = take((uint64_t)P->scan_chunks * 8);
         P->off_units = take((1 + 2 * (uint64_t)I.b) * 4);
+        P->off_units2 = take(P->small_chunk ? (1 + 2 * (uint64_t)I.b) * 4 : 0);
         P->off_srcb = take((uint64_t)P->n_runs * 4);
         P->off_blk = take((np + kBlockItems - 1) / kBlockItems * 4);
     }
     P->total = o;
     I.workspace_bytes = o;
     return BSORT_OK;
+}
+
+// Grid (in units) of the cluster tier of a two-tier Step 9: units above q1
+// items are at most n_pad / (q1 + 1) and at most one per bucket.
+// (The launch covers at most 256 units at a time; its clusters then loop.)
+uint32_t large_units_max(uint64_t n_pad, uint32_t q1, uint32_t b)
+{
+    uint64_t u = n_pad / ((uint64_t)q1 + 1);
+    if (u > b) u = b;
+    return (uint32_t)(u < 256 ? u : 256);
 }
 
 bsort_status ensure_workspace(bsort_t h, uint64_t bytes)
@@ -534,13 +578,21 @@ bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout,
     SEQ(launch_block_index(offsets, P.n_runs, (uint32_t)I.n_padded, blk, st), "step8_run_index");
     SEQ(launch_relocate_u64(tiles, offsets, srcb, blk, P.n_runs, (uint32_t)I.n_padded, reloc, st),
         "step8_relocate");
-    // Step 9
-    SEQ(launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, (uint32_t)I.unit_capacity,
-                          units, err, st),
+    // Step 9 (two tiers: one-CTA units, then cluster units for larger buckets)
+    uint32_t *units2 = P.small_chunk ? reinterpret_cast<uint32_t *>(ws + P.off_units2) : nullptr;
+    const uint32_t q1 = P.small_chunk ? (uint32_t)P.small_chunk : (uint32_t)I.unit_capacity;
+    SEQ(launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, q1, (uint32_t)I.unit_capacity,
+                          units, units2, err, st),
         "step9_pack_units");
-    SEQ(launch_bucket_sort_u64(P.unit_chunk, (int)I.unit_ctas, reloc, units, I.b, n, I.n_padded,
-                               kout, err, st),
+    SEQ(launch_bucket_sort_u64(P.small_chunk ? P.small_chunk : P.unit_chunk,
+                               P.small_chunk ? 1 : (int)I.unit_ctas, reloc, units, I.b, n,
+                               I.n_padded, kout, err, st),
         "step9_bucket_sort");
+    if (P.small_chunk)
+        SEQ(launch_bucket_sort_u64(P.unit_chunk, (int)I.unit_ctas, reloc, units2,
+                                   large_units_max(I.n_padded, q1, I.b), n, I.n_padded, kout, err,
+                                   st),
+            "step9_bucket_sort_large");
     return BSORT_OK;
 }
 
@@ -641,10 +693,13 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
                             (uint32_t)I.n_padded, (int)vb, reloc_k, reloc_v, st),
             "step8_relocate");
     }
-    // Step 9: buckets packed into units of at most unit_capacity items
+    // Step 9: buckets packed into units (two tiers: one-CTA units of
+    // small_chunk items, cluster units of unit_capacity for larger buckets)
     uint32_t *units = reinterpret_cast<uint32_t *>(ws + P.off_units);
-    SEQ(launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, (uint32_t)I.unit_capacity,
-                          units, err, st),
+    uint32_t *units2 = P.small_chunk ? reinterpret_cast<uint32_t *>(ws + P.off_units2) : nullptr;
+    const uint32_t q1 = P.small_chunk ? (uint32_t)P.small_chunk : (uint32_t)I.unit_capacity;
+    SEQ(launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, q1, (uint32_t)I.unit_capacity,
+                          units, units2, err, st),
         "step9_pack_units");
     if (!P.relocate) {
         g.offsets = offsets;
@@ -654,12 +709,22 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     }
     const void *s9k = P.relocate ? (const void *)reloc_k : (const void *)tiles_k;
     const void *s9v = P.relocate ? (const void *)reloc_v : (const void *)tiles_v;
-    SEQ(P.pairs ? launch_bucket_sort_pairs(P.unit_chunk, (int)I.unit_ctas, s9k, s9v, units, I.b,
-                                           n, I.n_padded, is_f32, (int)vb, kout, vout, err, g,
-                                           st)
-                : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, s9k, units, I.b, n,
-                                          I.n_padded, is_f32, kout, err, g, st),
+    const int c1 = P.small_chunk ? P.small_chunk : P.unit_chunk;
+    const int k1 = P.small_chunk ? 1 : (int)I.unit_ctas;
+    SEQ(P.pairs ? launch_bucket_sort_pairs(c1, k1, s9k, s9v, units, I.b, n, I.n_padded, is_f32,
+                                           (int)vb, kout, vout, err, g, st)
+                : launch_bucket_sort_keys(c1, k1, s9k, units, I.b, n, I.n_padded, is_f32, kout,
+                                          err, g, st),
         "step9_bucket_sort");
+    if (P.small_chunk) {
+        const uint32_t u2 = large_units_max(I.n_padded, q1, I.b);
+        SEQ(P.pairs ? launch_bucket_sort_pairs(P.unit_chunk, (int)I.unit_ctas, s9k, s9v, units2,
+                                               u2, n, I.n_padded, is_f32, (int)vb, kout, vout,
+                                               err, g, st)
+                    : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, s9k, units2, u2, n,
+                                              I.n_padded, is_f32, kout, err, g, st),
+            "step9_bucket_sort_large");
+    }
     return BSORT_OK;
 }
 

@@ -52,6 +52,10 @@ struct GatherSrc {
     uint32_t runs = 0;
 };
 
+// Step 9 launches over at most kLoopUnits units with clusters use a grid of
+// that many clusters that loop over the device-side unit count.
+constexpr uint32_t kLoopUnits = 256;
+
 cudaError_t launch_bucket_sort_keys(int chunk, int ctas, const void *src_k, const uint32_t *units,
                                     uint32_t max_units, uint64_t n, uint64_t n_pad, int is_f32,
                                     void *out_k, int *err, const GatherSrc &g, cudaStream_t st);
@@ -112,11 +116,13 @@ constexpr int kBlockItems = 1024;
 cudaError_t launch_block_index(uint32_t *offsets, uint32_t runs, uint32_t n_pad, uint32_t *blk,
                                cudaStream_t st);
 
-// Step 9 units: pack consecutive buckets into units of at most Q items;
-// units holds 1 + 2*b words (count, then begin/end pairs).
+// Step 9 units: pack consecutive buckets into units of at most Q1 items; a
+// bucket above Q1 (at most Q2) is a unit of its own, listed in units2 (when
+// units2 == nullptr, Q1 = Q2 and all units are in units).  Each list holds
+// 1 + 2*b words (count, then begin/end pairs).
 cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t b,
-                              uint32_t n_pad, uint32_t Q, uint32_t *units, int *err,
-                              cudaStream_t st);
+                              uint32_t n_pad, uint32_t Q1, uint32_t Q2, uint32_t *units,
+                              uint32_t *units2, int *err, cudaStream_t st);
 
 // ---------------------------------------------------------------- 64-bit keys
 // A sample record of a 64-bit-key sort: (key, p = i*t + r), compared key

@@ -443,15 +443,51 @@ k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
     }
 }
 
-// Step 9 units: consecutive buckets packed greedily into units of at most Q
-// items (every bucket fits one unit, since |B_j| <= bound <= Q).  One CTA:
-// nxt[j] = the bucket after the longest run of buckets from j that fits, the
-// chain 0, nxt[0], nxt[nxt[0]], ... marks the unit starts (found by pointer
-// doubling), and a scan numbers them.  units[0] = U, then (begin, end) pairs.
+// Block-wide exclusive scan of one value per thread (T threads); *total
+// receives the sum.  Uses s_warp[T / 32].
+template <int T>
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s_warp,
+                                                         uint32_t *s_total)
+{
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    uint32_t incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    __syncthreads();  // s_warp may still be read by a previous scan
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t wv = lane < T / 32 ? s_warp[lane] : 0u;
+        uint32_t wi = wv;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+            if (lane >= o) wi += y;
+        }
+        if (lane < T / 32) s_warp[lane] = wi - wv;
+        if (lane == T / 32 - 1) *s_total = wi;
+    }
+    __syncthreads();
+    return s_warp[warp] + incl - v;
+}
+
+// Step 9 units: consecutive buckets packed greedily into units of at most
+// Q1 items; a bucket larger than Q1 (at most the bound, Q2) forms a unit of
+// its own.  One CTA: nxt[j] = the bucket after the longest run of buckets
+// from j that fits Q1 (at least bucket j itself), the chain 0, nxt[0],
+// nxt[nxt[0]], ... marks the unit starts (found by pointer doubling), and
+// two scans number the units of at most Q1 items (written to units) and
+// the larger ones (written to units2; with units2 == nullptr, Q1 = Q2 and
+// every unit goes to units).  Each list: count, then (begin, end) pairs.
 template <int T>
 __global__ void __launch_bounds__(T, 1)
 k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t b, uint32_t n_pad,
-             uint32_t Q, uint32_t *__restrict__ units, int *err)
+             uint32_t Q1, uint32_t Q2, uint32_t *__restrict__ units,
+             uint32_t *__restrict__ units2, int *err)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint32_t *Lb = reinterpret_cast<uint32_t *>(smem_raw);  // b + 1
@@ -459,25 +495,29 @@ k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t b, uint3
     uint32_t *jmp = nxt + (b + 1);                            // b + 1
     uint32_t *on = jmp + (b + 1);                             // b + 1
     __shared__ uint32_t s_warp[T / 32];
-    __shared__ uint32_t s_total;
+    __shared__ uint32_t s_total[2];
     const int tid = threadIdx.x;
     for (uint32_t j = tid; j <= b; j += T) {
         Lb[j] = j < b ? offsets[(uint64_t)j * m] : n_pad;
         on[j] = j == 0 ? 1u : 0u;
     }
     __syncthreads();
+    // largest e in [j+1, b] with Lb[e] - Lb[j] <= Q1, else j + 1
+    auto successor = [&](uint32_t j) {
+        uint32_t lo = j + 1, hi = b;
+        const uint32_t lim = Lb[j] + Q1;
+        while (lo < hi) {
+            uint32_t mid = (lo + hi + 1) >> 1;
+            if (Lb[mid] <= lim) lo = mid;
+            else hi = mid - 1;
+        }
+        return lo;
+    };
     for (uint32_t j = tid; j <= b; j += T) {
         uint32_t e = j;
         if (j < b) {
-            uint32_t lo = j + 1, hi = b;  // largest e in [j+1, b] with Lb[e] - Lb[j] <= Q
-            const uint32_t lim = Lb[j] + Q;
-            while (lo < hi) {
-                uint32_t mid = (lo + hi + 1) >> 1;
-                if (Lb[mid] <= lim) lo = mid;
-                else hi = mid - 1;
-            }
-            e = lo;
-            if (Lb[e] - Lb[j] > Q) set_error(err, DEV_INTERNAL);  // a bucket exceeds Q
+            e = successor(j);
+            if (Lb[e] - Lb[j] > Q2) set_error(err, DEV_INTERNAL);  // a bucket exceeds the bound
         }
         nxt[j] = e;
         jmp[j] = e;
@@ -496,58 +536,39 @@ k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t b, uint3
         __syncthreads();
     }
     // recompute the single-step successor (nxt was used as scratch)
-    for (uint32_t j = tid; j <= b; j += T) {
-        uint32_t e = j;
-        if (j < b) {
-            uint32_t lo = j + 1, hi = b;
-            const uint32_t lim = Lb[j] + Q;
-            while (lo < hi) {
-                uint32_t mid = (lo + hi + 1) >> 1;
-                if (Lb[mid] <= lim) lo = mid;
-                else hi = mid - 1;
-            }
-            e = lo;
-        }
-        nxt[j] = e;
-    }
+    for (uint32_t j = tid; j <= b; j += T) nxt[j] = j < b ? successor(j) : j;
     __syncthreads();
-    // number the unit starts (chain members j < b) in order: block scan
+    // number the unit starts (chain members j < b) in order, per list
     const uint32_t per = (b + T - 1) / T;
     const uint32_t j0 = tid * per;
-    uint32_t cnt = 0;
-    for (uint32_t q = 0; q < per; ++q)
-        if (j0 + q < b && on[j0 + q]) ++cnt;
-    const int lane = tid & 31, warp = tid >> 5;
-    uint32_t incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-        if (lane >= o) incl += y;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t wv = lane < T / 32 ? s_warp[lane] : 0u;
-        uint32_t wi = wv;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
-            if (lane >= o) wi += y;
-        }
-        if (lane < T / 32) s_warp[lane] = wi - wv;
-        if (lane == T / 32 - 1) s_total = wi;
-    }
-    __syncthreads();
-    uint32_t u = s_warp[warp] + incl - cnt;
+    uint32_t c_small = 0, c_large = 0;
     for (uint32_t q = 0; q < per; ++q) {
         const uint32_t j = j0 + q;
         if (j < b && on[j]) {
-            units[1 + 2 * u] = Lb[j];
-            units[2 + 2 * u] = Lb[nxt[j]];
-            ++u;
+            if (units2 == nullptr || Lb[nxt[j]] - Lb[j] <= Q1) ++c_small;
+            else ++c_large;
         }
     }
-    if (tid == 0) units[0] = s_total;
+    uint32_t u1 = block_exclusive_scan<T>(c_small, s_warp, &s_total[0]);
+    uint32_t u2 = block_exclusive_scan<T>(c_large, s_warp, &s_total[1]);
+    for (uint32_t q = 0; q < per; ++q) {
+        const uint32_t j = j0 + q;
+        if (j < b && on[j]) {
+            if (units2 == nullptr || Lb[nxt[j]] - Lb[j] <= Q1) {
+                units[1 + 2 * u1] = Lb[j];
+                units[2 + 2 * u1] = Lb[nxt[j]];
+                ++u1;
+            } else {
+                units2[1 + 2 * u2] = Lb[j];
+                units2[2 + 2 * u2] = Lb[nxt[j]];
+                ++u2;
+            }
+        }
+    }
+    if (tid == 0) {
+        units[0] = s_total[0];
+        if (units2 != nullptr) units2[0] = s_total[1];
+    }
 }
 
 // Run index of every block of kBlockItems positions of the (virtual)
@@ -677,10 +698,11 @@ cudaError_t launch_block_index(uint32_t *offsets, uint32_t runs, uint32_t n_pad,
 }
 
 cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t b, uint32_t n_pad,
-                              uint32_t Q, uint32_t *units, int *err, cudaStream_t st)
+                              uint32_t Q1, uint32_t Q2, uint32_t *units, uint32_t *units2,
+                              int *err, cudaStream_t st)
 {
     const int sm = (int)(4 * (b + 1) * 4);
-    k_pack_units<1024><<<1, 1024, sm, st>>>(offsets, m, b, n_pad, Q, units, err);
+    k_pack_units<1024><<<1, 1024, sm, st>>>(offsets, m, b, n_pad, Q1, Q2, units, units2, err);
     return cudaGetLastError();
 }
 

@@ -91,7 +91,7 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
 }
 
 // ============================================================ Step 9
-// Cluster u sorts unit u = [units[1+2u], units[2+2u]) of the relocated order
+// A cluster sorts unit u = [units[1+2u], units[2+2u]) of the relocated order
 // (consecutive whole buckets, at most C*T*E items) and writes the positions
 // below n of the result.  With units == nullptr there is one unit, [0, n),
 // read from the caller's input (raw keys, transformed on load).
@@ -104,11 +104,11 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
 // keys by original index exactly as the relocated order does, and fetch
 // each value from that position.
 template <int T, int E, bool PAIRS, int C>
-__global__ void __launch_bounds__(T, 1)
-k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
-              const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
-              int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v, int *err,
-              GatherSrc g)
+__device__ __forceinline__ void
+bucket_sort_unit(uint32_t u, const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
+                 const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
+                 int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v,
+                 int *err, const GatherSrc &g)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
     constexpr int CH = T * E;
@@ -117,7 +117,6 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
     K *sm = reinterpret_cast<K *>(smem_raw);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const uint32_t u = blockIdx.x / C;
     const int r = (int)(blockIdx.x % C);
     const bool direct = units == nullptr;
     const bool gather = g.offsets != nullptr;
@@ -219,6 +218,38 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
     }
 }
 
+// Cluster u of the grid sorts unit u (clusters beyond the unit count exit).
+template <int T, int E, bool PAIRS, int C>
+__global__ void __launch_bounds__(T, 1)
+k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
+              const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
+              int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v, int *err,
+              GatherSrc g)
+{
+    bucket_sort_unit<T, E, PAIRS, C>(blockIdx.x / C, src_k, src_v, units, n, n_pad, is_f32,
+                                     val_bytes, out_k, out_v, err, g);
+}
+
+// The same for a unit list whose length only the device knows (the cluster
+// tier of a two-tier Step 9, mostly empty): a small grid whose cluster c
+// sorts units c, c + G, c + 2G, ... (G clusters; every CTA of a cluster
+// takes the same units).
+template <int T, int E, bool PAIRS, int C>
+__global__ void __launch_bounds__(T, 1)
+k_bucket_sort_loop(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
+                   const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
+                   int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v,
+                   int *err, GatherSrc g)
+{
+    const uint32_t count = units[0];
+#pragma unroll 1
+    for (uint32_t u = blockIdx.x / C; u < count; u += gridDim.x / C) {
+        bucket_sort_unit<T, E, PAIRS, C>(u, src_k, src_v, units, n, n_pad, is_f32, val_bytes,
+                                         out_k, out_v, err, g);
+        __syncthreads();  // shared memory is reused by the next unit
+    }
+}
+
 // ============================================================ launching
 template <typename KernelT, typename... Args>
 inline cudaError_t launch_maybe_cluster(KernelT kern, unsigned grid, int block, int smem,
@@ -250,6 +281,11 @@ inline cudaError_t init_sort_pair_of_kernels()
     e = cudaFuncSetAttribute(k_bucket_sort<T, E, PAIRS, C>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
+    if (C > 1) {
+        e = cudaFuncSetAttribute(k_bucket_sort_loop<T, E, PAIRS, C>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+        if (e != cudaSuccess) return e;
+    }
     if (C > 8) {
         e = cudaFuncSetAttribute(k_sublist_sort<T, E, PAIRS, C>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -283,6 +319,11 @@ inline cudaError_t launch_bucket_sort_t(const void *src_k, const void *src_v,
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
     const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
     const unsigned grid = (units ? max_units : 1u) * C;
+    if (C > 1 && units != nullptr && max_units <= kLoopUnits)
+        return launch_maybe_cluster(k_bucket_sort_loop<T, E, PAIRS, C>, grid, T, sm, C, st,
+                                    static_cast<const uint32_t *>(src_k), src_v, units, n, n_pad,
+                                    is_f32, val_bytes, static_cast<uint32_t *>(out_k), out_v,
+                                    err, g);
     return launch_maybe_cluster(k_bucket_sort<T, E, PAIRS, C>, grid, T, sm, C, st,
                                 static_cast<const uint32_t *>(src_k), src_v, units, n, n_pad,
                                 is_f32, val_bytes, static_cast<uint32_t *>(out_k), out_v, err, g);

@@ -178,9 +178,10 @@ k_sample_index_u64(const uint64_t *__restrict__ tiles, const Rec128 *__restrict_
 // array (or, with units == nullptr, the whole input [0, n)) and writes the
 // positions below n.
 template <int T, int E, int C>
-__global__ void __launch_bounds__(T, 1)
-k_bucket_sort_u64(const uint64_t *__restrict__ src, const uint32_t *__restrict__ units,
-                  uint64_t n, uint64_t n_pad, uint64_t *__restrict__ out, int *err)
+__device__ __forceinline__ void
+bucket_sort_unit_u64(uint32_t u, const uint64_t *__restrict__ src,
+                     const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad,
+                     uint64_t *__restrict__ out, int *err)
 {
     constexpr int CH = T * E;
     constexpr uint64_t CAP = (uint64_t)C * CH;
@@ -188,7 +189,6 @@ k_bucket_sort_u64(const uint64_t *__restrict__ src, const uint32_t *__restrict__
     uint64_t *sm = reinterpret_cast<uint64_t *>(smem_raw);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const uint32_t u = blockIdx.x / C;
     const int r = (int)(blockIdx.x % C);
     uint64_t L = 0, R = n;
     if (units != nullptr) {
@@ -223,6 +223,28 @@ k_bucket_sort_u64(const uint64_t *__restrict__ src, const uint32_t *__restrict__
     }
 }
 
+template <int T, int E, int C>
+__global__ void __launch_bounds__(T, 1)
+k_bucket_sort_u64(const uint64_t *__restrict__ src, const uint32_t *__restrict__ units,
+                  uint64_t n, uint64_t n_pad, uint64_t *__restrict__ out, int *err)
+{
+    bucket_sort_unit_u64<T, E, C>(blockIdx.x / C, src, units, n, n_pad, out, err);
+}
+
+// Cluster c of a small grid sorts units c, c + G, ... of a device-sized list.
+template <int T, int E, int C>
+__global__ void __launch_bounds__(T, 1)
+k_bucket_sort_u64_loop(const uint64_t *__restrict__ src, const uint32_t *__restrict__ units,
+                       uint64_t n, uint64_t n_pad, uint64_t *__restrict__ out, int *err)
+{
+    const uint32_t count = units[0];
+#pragma unroll 1
+    for (uint32_t u = blockIdx.x / C; u < count; u += gridDim.x / C) {
+        bucket_sort_unit_u64<T, E, C>(u, src, units, n, n_pad, out, err);
+        __syncthreads();  // shared memory is reused by the next unit
+    }
+}
+
 // ============================================================ launching
 namespace {
 
@@ -234,6 +256,9 @@ cudaError_t init_u64_t()
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_bucket_sort_u64<T, E, C>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess && C > 1)
+        e = cudaFuncSetAttribute(k_bucket_sort_u64_loop<T, E, C>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     return e;
 }
@@ -253,6 +278,10 @@ cudaError_t launch_bucket_u64_t(const void *src, const uint32_t *units, uint32_t
 {
     const int sm = padded_elems<uint64_t>(T * E) * 8;
     const unsigned grid = (units ? max_units : 1u) * C;
+    if (C > 1 && units != nullptr && max_units <= kLoopUnits)
+        return launch_maybe_cluster(k_bucket_sort_u64_loop<T, E, C>, grid, T, sm, C, st,
+                                    static_cast<const uint64_t *>(src), units, n, n_pad,
+                                    static_cast<uint64_t *>(out), err);
     return launch_maybe_cluster(k_bucket_sort_u64<T, E, C>, grid, T, sm, C, st,
                                 static_cast<const uint64_t *>(src), units, n, n_pad,
                                 static_cast<uint64_t *>(out), err);

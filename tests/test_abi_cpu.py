@@ -221,3 +221,24 @@ def test_plan_u64_keys():
     p = pkg.bsort_plan(h, pkg.BSORT_U64, 0, 1 << 20)
     assert (p.t, p.s, p.b, p.m) == (4096, 64, 64, 256)
     pkg.bsort_destroy(h)
+
+
+def test_plan_two_tier_step9():
+    """When the bound needs a cluster unit and b can make the average bucket
+    about 1/1.05 of a one-CTA unit, Step 9 runs in two tiers (unit_small);
+    with s or b given, or when b would exceed its limit, in one."""
+    h = _handle()
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 28)
+    assert p.unit_ctas == 2 and p.unit_small == 32768
+    assert p.b == -(-105 * p.n_padded // (100 * 32768))
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 4, 1 << 25)
+    assert p.unit_ctas > 1 and p.unit_small == 16384
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 24)
+    assert p.unit_ctas == 1 and p.unit_small == 0
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 3 << 28)  # b capped: one tier
+    assert p.unit_small == 0
+    pkg.bsort_destroy(h)
+    h = _handle(131072, 8192)
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 28)
+    assert p.unit_small == 0 and p.b == 8192
+    pkg.bsort_destroy(h)

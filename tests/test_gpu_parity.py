@@ -485,3 +485,22 @@ def test_u64_host_entry():
     torch.cuda.synchronize()
     assert np.array_equal(h_out.numpy().view(np.uint64), np.sort(keys))
     sorter.close()
+
+
+def test_two_tier_step9_pairs_intermediates():
+    """The planner's own two-tier plan (buckets up to one CTA's 16384 words
+    sorted by one CTA, larger ones by a cluster unit): 2^25 + 3 Zipf pairs,
+    every intermediate and the stable result against the oracle."""
+    n = (1 << 25) + 3
+    keys = synth.keys_zipf(n, synth.seed_for(3, 9))
+    vals = np.arange(n, dtype=np.uint32)
+    sorter = pkg.BucketSorter()
+    p = sorter.plan(n, "u32", 4)
+    assert p.unit_small == 16384 and p.unit_ctas > 1
+    want = oracle.paper_sort(keys, p.t, p.s, "u32", vals=vals, b=p.b)
+    ok, ov = sorter.sort_pairs(_to_dev_u32(keys), _to_dev_u32(vals))
+    sorter.sync()
+    assert np.array_equal(ok.cpu().numpy().view(np.uint32), want["keys"])
+    assert np.array_equal(ov.cpu().numpy().view(np.uint32), want["vals"])
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], p.s, p.b)
+    sorter.close()
