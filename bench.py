@@ -653,19 +653,15 @@ def run_served(args, pkg, synth, dev, rank):
             kt, a, b, n, _, _ = job(nxt, slot)
             inflight[pkg.bsort_submit(srv.h, kt, a, b, n)] = (nxt, slot)
             nxt += 1
-        progressed = False
-        for t in list(inflight):
-            r = pkg.bsort_poll(srv.h, t)
-            if r is None:
-                continue
+        finished = pkg.bsort_poll_any(srv.h, 256)
+        for t, r in finished:
             k, slot = inflight.pop(t)
             assert r.status == pkg.BSORT_OK, "served job failed"
             free.append(slot)
             lat[k] = (r.done_ns - (t0 + int(arr[k] * 1e9))) / 1e6
             done_at[k] = r.done_ns
             done += 1
-            progressed = True
-        if not progressed:
+        if not finished:
             time.sleep(2e-5)
     st = srv.stats()
     srv.close()
@@ -709,11 +705,12 @@ def run_served(args, pkg, synth, dev, rank):
                 kt, a, b, n, _, _ = job(k, slot)
                 infl2[pkg.bsort_submit(srv2.h, kt, a, b, n)] = slot
                 k += 1
-            for t in list(infl2):
-                if pkg.bsort_poll(srv2.h, t) is not None:
-                    free2.append(infl2.pop(t))
-                    fin += 1
-            time.sleep(1e-5)
+            finished = pkg.bsort_poll_any(srv2.h, 256)
+            for t, _ in finished:
+                free2.append(infl2.pop(t))
+                fin += 1
+            if not finished:
+                time.sleep(1e-5)
         dt = (pkg.bsort_clock_ns() - c0) / 1e9
         srv2.close()
         return dt

@@ -254,6 +254,12 @@ bsort_status bsort_submit(bsort_t h, const bsort_request *req, uint64_t *ticket)
  * BSORT_EINVAL for an unknown ticket. */
 bsort_status bsort_poll(bsort_t h, uint64_t ticket, bsort_result *out);
 
+/* Non-blocking: up to cap finished jobs, in completion order, each with its
+ * ticket and result, released as by bsort_poll; *count receives how many
+ * (0 when none has finished). */
+bsort_status bsort_poll_any(bsort_t h, uint64_t *tickets, bsort_result *results, uint32_t cap,
+                            uint32_t *count);
+
 /* Counters of the request loop (all zero before the first submit). */
 bsort_status bsort_serve_stats(bsort_t h, bsort_serve_info *out);
 

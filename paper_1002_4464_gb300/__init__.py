@@ -23,7 +23,7 @@ __all__ = [
     "bsort_last_error", "bsort_status_string", "bsort_sort_keys_noalloc", "BucketSorter",
     "bsort_batch_info", "bsort_sort_batch", "bsort_plan_batch", "EXPORTED_SYMBOLS",
     "bsort_request", "bsort_result", "bsort_serve_info", "bsort_submit", "bsort_poll",
-    "bsort_serve_stats", "bsort_clock_ns", "SortServer",
+    "bsort_serve_stats", "bsort_clock_ns", "bsort_poll_any", "SortServer",
 ]
 
 BSORT_OK, BSORT_EINVAL, BSORT_ENOMEM, BSORT_ECUDA, BSORT_ETIMEOUT = 0, 1, 2, 3, 4
@@ -41,7 +41,7 @@ EXPORTED_SYMBOLS = (
     "bsort_get_intermediate", "bsort_kernel_times", "bsort_kernel_name",
     "bsort_last_error", "bsort_status_string", "bsort_sort_keys_noalloc",
     "bsort_sort_batch", "bsort_plan_batch", "bsort_submit", "bsort_poll", "bsort_serve_stats",
-    "bsort_clock_ns",
+    "bsort_clock_ns", "bsort_poll_any",
 )
 
 
@@ -138,6 +138,8 @@ def load_library(rebuild: bool = False):
         "bsort_submit": (i32, [H, ctypes.POINTER(bsort_request), ctypes.POINTER(u64)]),
         "bsort_poll": (i32, [H, u64, ctypes.POINTER(bsort_result)]),
         "bsort_serve_stats": (i32, [H, ctypes.POINTER(bsort_serve_info)]),
+        "bsort_poll_any": (i32, [H, ctypes.POINTER(u64), ctypes.POINTER(bsort_result), u32,
+                                 ctypes.POINTER(u32)]),
         "bsort_clock_ns": (u64, []),
     }
     for name, (res, args) in sig.items():
@@ -260,6 +262,15 @@ def bsort_poll(h, ticket):
         return None
     _check(h, st)
     return res
+
+
+def bsort_poll_any(h, cap=256):
+    """[(ticket, bsort_result)] of up to cap finished jobs (released)."""
+    tk = (ctypes.c_uint64 * cap)()
+    rs = (bsort_result * cap)()
+    cnt = ctypes.c_uint32()
+    _check(h, load_library().bsort_poll_any(h, tk, rs, cap, ctypes.byref(cnt)))
+    return [(tk[i], rs[i]) for i in range(cnt.value)]
 
 
 def bsort_serve_stats(h):
@@ -423,6 +434,13 @@ class SortServer:
             if res is not None:
                 return res
             time.sleep(sleep_s)
+
+    def poll_any(self, cap=256):
+        """[(ticket, bsort_result)] of finished jobs, in completion order."""
+        done = bsort_poll_any(self.h, cap)
+        for t, _ in done:
+            self._alive.pop(t, None)
+        return done
 
     def stats(self):
         return bsort_serve_stats(self.h).as_dict()

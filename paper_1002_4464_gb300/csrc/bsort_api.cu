@@ -158,6 +158,17 @@ uint64_t choose_buckets_two_tier(uint64_t np, uint64_t m, uint64_t s, uint64_t Q
     return b > bmax ? bmax : (b < lo ? lo : b);
 }
 
+// Whether bucket sizes are regular enough for a two-tier Step 9: on random
+// keys a bucket's size varies by about w*sqrt(m/6) (each of the m sublists
+// adds a uniform error in [0, w) at both ends); the 5% headroom of a
+// one-CTA unit of Q1 items must cover 2.5 of those, so that about 1% of the
+// buckets at most spill into the cluster tier.
+bool tiers_regular(uint64_t m, uint64_t w, uint64_t Q1)
+{
+    const double sigma = (double)w * __builtin_sqrt((double)m / 6.0);
+    return 2.5 * sigma <= (double)Q1 * (1.0 - 1.0 / 1.05);
+}
+
 // Sort-unit shapes (items per CTA) and cluster sizes the kernels provide.
 const int kChunks[] = {2048, 4096, 8192, 16384, 32768};
 const int kClusters[] = {1, 2, 4, 8};
@@ -211,25 +222,26 @@ bool tile_shape(uint64_t t, bool pairs, int *chunk, int *ctas)
 double log2d(double x) { return x > 1 ? __builtin_log2(x) : 0.0; }
 
 // Modelled cost of a plan, in units of one single-CTA sort pass over the
-// items.  The factors are measured on GB300 at n = 2^28 uint32 keys: a
-// Step-2 sublist sorted by a cluster of 2 / 4 / 8 CTAs costs 1.24 / 1.68 /
-// 2.5 passes (distributed-shared-memory merge rounds; 8-CTA clusters also
-// leave SMs idle), a Step-9 unit of 2 / 4 / 8 CTAs costs 1.65 / 2.1 / 3.1
-// passes (rounds plus unit fill); the samples cost about 1.6e-2 passes per
-// sample per key-equivalent (sorting, searching and scanning m*s records),
-// and Step 8 about 0.35 passes (0.3 with runs of w >= 32 items).
-double plan_cost(uint64_t np, uint64_t s, int tchunk, int tctas, int uchunk, int uctas)
+// items (32K-key chunks).  The factors are measured on GB300 at n = 2^28
+// uint32 keys: a Step-2 sublist sorted by a cluster of 2 / 4 / 8 CTAs costs
+// 1.32 / 1.76 / 2.6 passes (distributed-shared-memory merge rounds; 8-CTA
+// clusters also leave SMs idle); Step 9 costs 1.1 passes with one-CTA
+// units (one tier of one CTA, or two tiers) and 1.65 / 2.1 / 3.1 with
+// cluster units (rounds plus unit fill); Step 4 costs 7 passes per sample
+// per key and Step 6 3.9 per run A_ij (m*b of them); Step 8 0.3-0.35.
+double plan_cost(uint64_t np, uint64_t s, uint64_t runs, int tchunk, int tctas, int uchunk,
+                 int uctas)
 {
     const double n = (double)np;
-    auto f1 = [](int c) { return c == 1 ? 1.0 : c == 2 ? 1.24 : c == 4 ? 1.68 : 2.5; };
-    auto f9 = [](int c) { return c == 1 ? 1.3 : c == 2 ? 1.65 : c == 4 ? 2.1 : 3.1; };
+    auto f1 = [](int c) { return c == 1 ? 1.0 : c == 2 ? 1.32 : c == 4 ? 1.76 : 2.6; };
+    auto f9 = [](int c) { return c == 1 ? 1.1 : c == 2 ? 1.65 : c == 4 ? 2.1 : 3.1; };
     const double chunk_levels = log2d(tchunk) / 15.0;  // smaller chunks sort faster
     const double unit_levels = log2d(uchunk) / 15.0;
     const double t = (double)tchunk * tctas;
     const double w = t / (double)s;
     const double samples = n / w;
-    return n * (f1(tctas) * chunk_levels + f9(uctas) * unit_levels +
-                (w >= 32 ? 0.3 : 0.35)) + samples * 0.45;
+    return n * (f1(tctas) * chunk_levels + f9(uctas) * unit_levels + (w >= 32 ? 0.3 : 0.35)) +
+           7.0 * samples + 3.9 * (double)runs;
 }
 
 bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P)
@@ -297,7 +309,18 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
                 const uint64_t bound = bound_for(np, m, sv, bv);
                 int uc, uk;
                 if (!unit_for(bound, pairs, &uc, &uk)) continue;
-                const double c = plan_cost(np, sv, tc, tk, uc, uk);
+                // Step 9 as planned below: two tiers (one-CTA units) when the
+                // bound needs a cluster and b can reach ~1.05 buckets per
+                // one-CTA unit; the bucket count estimated the same way
+                const uint64_t bmx = m * sv < (uint64_t)kMaxBuckets ? m * sv : (uint64_t)kMaxBuckets;
+                const uint64_t b2 = (105 * np + 100 * (uint64_t)cm - 1) / (100 * (uint64_t)cm);
+                const bool tiers = uk > 1 && !forced_b && !forced_s && b2 <= bmx &&
+                                   bound_for(np, m, sv, b2) <= (uint64_t)uc * uk &&
+                                   tiers_regular(m, t / sv, (uint64_t)cm);
+                const uint64_t b_est = forced_b ? forced_b : forced_s ? sv
+                                       : tiers ? b2 : (21 * np + 10ull * uc * uk - 1) / (10ull * uc * uk);
+                const double c = tiers ? plan_cost(np, sv, m * b_est, tc, tk, cm, 1)
+                                       : plan_cost(np, sv, m * b_est, tc, tk, uc, uk);
                 if (best < 0 || c < best) {
                     best = c;
                     bt = t; bs = sv; btc = tc; btk = tk; buc = uc; buk = uk;
@@ -340,26 +363,29 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->tile_chunk = btc;
         P->unit_chunk = buc;
         I.unit_capacity = (uint64_t)buc * buk;
-        // Step 9 in two tiers when the bound needs a cluster and b can make
-        // the average bucket ~1/1.05 of the largest one-CTA unit: one-CTA
-        // units for the buckets that fit it (nearly all), cluster units only
-        // for the others
+        // Step 9 in two tiers when the bound needs a cluster and the
+        // average bucket is at most 1/1.05 of the largest one-CTA unit:
+        // one-CTA units for the buckets that fit it (nearly all), cluster
+        // units only for the others.  A free b is chosen for that when it can
+        // be (at most bmax buckets).
         const uint64_t bmax = m * bs < (uint64_t)kMaxBuckets ? m * bs : (uint64_t)kMaxBuckets;
-        if (buk > 1 && !forced_b && !forced_s &&
-            (105 * I.n_padded + 100 * (uint64_t)cm - 1) / (100 * (uint64_t)cm) <= bmax) {
-            P->small_chunk = cm;
-            I.unit_small = (uint32_t)cm;
-        }
+        const bool tiers_wanted =
+            buk > 1 && (105 * I.n_padded + 100 * (uint64_t)cm - 1) / (100 * (uint64_t)cm) <= bmax &&
+            tiers_regular(m, bt / bs, (uint64_t)cm);
         uint64_t b = bs;  // the paper's rule, kept when s is given
         if (forced_b) {
             b = forced_b;
         } else if (!forced_s) {
             const uint64_t bc =
-                P->small_chunk
-                    ? choose_buckets_two_tier(I.n_padded, m, bs, (uint64_t)P->small_chunk,
-                                              I.unit_capacity, bmax)
-                    : choose_buckets(I.n_padded, m, bs, I.unit_capacity, bmax);
+                tiers_wanted ? choose_buckets_two_tier(I.n_padded, m, bs, (uint64_t)cm,
+                                                       I.unit_capacity, bmax)
+                             : choose_buckets(I.n_padded, m, bs, I.unit_capacity, bmax);
             if (bc) b = bc;
+        }
+        if (buk > 1 && 105 * I.n_padded <= 100 * (uint64_t)cm * b &&
+            tiers_regular(m, bt / bs, (uint64_t)cm)) {
+            P->small_chunk = cm;
+            I.unit_small = (uint32_t)cm;
         }
         I.b = (uint32_t)b;
         I.bucket_bound = bound_for(I.n_padded, m, bs, b);
@@ -1081,6 +1107,7 @@ struct bsort_server {
     bool stop = false;
     std::deque<Req *> queue;                    // submitted, not admitted
     std::unordered_map<uint64_t, Req *> tickets;
+    std::deque<uint64_t> finished;              // done, in completion order
     uint64_t next_ticket = 1;
     std::vector<Req *> staged;   // lane A: keys copied in (or on their way)
     std::vector<cudaEvent_t> ev_pool;
@@ -1196,6 +1223,7 @@ bool serve_retire(bsort_server *S)
                                           : (word == BSORT_ETIMEOUT ? BSORT_ETIMEOUT
                                                                    : BSORT_EINTERNAL);
                 r->done = true;
+                S->finished.push_back(r->ticket);
                 ++S->done_count;
                 r = nullptr;  // the caller may free it once polled
                 any = true;
@@ -1684,6 +1712,35 @@ bsort_status bsort_poll(bsort_t h, uint64_t ticket, bsort_result *out)
     out->done_ns = r->done_ns;
     S->tickets.erase(it);
     delete r;
+    return BSORT_OK;
+}
+
+bsort_status bsort_poll_any(bsort_t h, uint64_t *tickets, bsort_result *results, uint32_t cap,
+                            uint32_t *count)
+{
+    if (!h || !count || (cap && (!tickets || !results))) return BSORT_EINVAL;
+    *count = 0;
+    bsort_server *S = h->server;
+    if (!S) return BSORT_OK;
+    std::lock_guard<std::mutex> lock(S->mu);
+    uint32_t k = 0;
+    while (k < cap && !S->finished.empty()) {
+        const uint64_t t = S->finished.front();
+        S->finished.pop_front();
+        auto it = S->tickets.find(t);
+        if (it == S->tickets.end()) continue;  // already released by bsort_poll
+        bsort_server::Req *r = it->second;
+        tickets[k] = t;
+        results[k].status = r->status;
+        results[k].batch_size = r->batch_size;
+        results[k].submit_ns = r->submit_ns;
+        results[k].start_ns = r->start_ns;
+        results[k].done_ns = r->done_ns;
+        ++k;
+        S->tickets.erase(it);
+        delete r;
+    }
+    *count = k;
     return BSORT_OK;
 }
 

@@ -229,11 +229,13 @@ def test_plan_two_tier_step9():
     with s or b given, or when b would exceed its limit, in one."""
     h = _handle()
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 28)
-    assert p.unit_ctas == 2 and p.unit_small == 32768
+    assert p.unit_ctas > 1 and p.unit_small == 32768
     assert p.b == -(-105 * p.n_padded // (100 * 32768))
+    # bucket sizes regular enough: 2.5 x w sqrt(m/6) within the 5% headroom
+    assert 2.5 * p.w * (p.m / 6) ** 0.5 <= 32768 * (1 - 1 / 1.05)
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 4, 1 << 25)
     assert p.unit_ctas > 1 and p.unit_small == 16384
-    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 24)
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 22)
     assert p.unit_ctas == 1 and p.unit_small == 0
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 3 << 28)  # b capped: one tier
     assert p.unit_small == 0
@@ -241,4 +243,8 @@ def test_plan_two_tier_step9():
     h = _handle(131072, 8192)
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 28)
     assert p.unit_small == 0 and p.b == 8192
+    pkg.bsort_destroy(h)
+    h = _handle(131072, 8192, 8602)  # a given b that fits: two tiers
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 28)
+    assert p.unit_small == 32768 and p.b == 8602
     pkg.bsort_destroy(h)

@@ -131,3 +131,26 @@ def test_arrivals_while_sorting_form_later_batches():
         assert r.status == pkg.BSORT_OK
         want = oracle.textbook_sort(keys, kt)
         assert np.array_equal(b.numpy().view(np.uint8), want.view(np.uint8))
+
+
+def test_poll_any_returns_every_job_once():
+    jobs = _mix(30, synth.seed_for(5, 12))
+    srv = pkg.SortServer(budget_bytes=1 << 30)
+    bufs, want = {}, {}
+    for kt, keys in jobs:
+        a, b = _pinned(keys), _pinned(np.zeros_like(keys))
+        t = srv.submit(a, b, kt)
+        bufs[t] = (kt, keys, b)
+    seen = {}
+    deadline = time.time() + 60
+    while len(seen) < len(jobs) and time.time() < deadline:
+        for t, r in srv.poll_any(8):
+            assert t not in seen and r.status == pkg.BSORT_OK
+            seen[t] = r
+        time.sleep(1e-4)
+    assert set(seen) == set(bufs)
+    for t, (kt, keys, b) in bufs.items():
+        assert np.array_equal(b.numpy().view(np.uint8),
+                              oracle.textbook_sort(keys, kt).view(np.uint8))
+    assert srv.poll_any(8) == []
+    srv.close()
