@@ -54,7 +54,7 @@ struct Plan {
     uint32_t scan_chunks;
     // workspace offsets (bytes)
     uint64_t off_hdr, off_tiles_k, off_tiles_v, off_reloc_k, off_reloc_v, off_samples,
-        off_rec_a, off_rec_b, off_spl, off_counts, off_cum, off_offsets, off_status,
+        off_rec_a, off_rec_b, off_spl, off_counts, off_offsets, off_status,
         off_units, off_units2, off_srcb, off_blk, total;
     bool relocate;  // materialise Step 8 (else fused into Step 9's load)
 };
@@ -140,10 +140,24 @@ uint64_t choose_buckets(uint64_t np, uint64_t m, uint64_t s, uint64_t Q, uint64_
     }
 }
 
+// Spread of bucket sizes on random keys: each of the m sublists adds a
+// uniform error in [0, w) at both ends of a bucket, so its size varies by
+// about sigma = w * sqrt(m / 6).
+double bucket_sigma(uint64_t m, uint64_t w) { return (double)w * __builtin_sqrt((double)m / 6.0); }
+
+// Average bucket a two-tier Step 9 aims at: four sigmas below one CTA's Q1
+// items, so that hardly any bucket spills into the cluster tier.
+uint64_t two_tier_target(uint64_t m, uint64_t w, uint64_t Q1)
+{
+    const double a = (double)Q1 - 4.0 * bucket_sigma(m, w);
+    return a > 0 ? (uint64_t)a : 0;
+}
+
 // Bucket count for a two-tier Step 9 (one-CTA units of Q1 items, cluster
 // units of Q2 >= bound for the rest): at least the smallest b whose bound
-// fits Q2, else about 1.05 average buckets per Q1, so that nearly every
-// bucket fills a one-CTA unit alone.  Returns 0 when no b <= bmax fits Q2.
+// fits Q2, else the b whose average bucket is two_tier_target, so that
+// nearly every bucket fills a one-CTA unit alone.  Returns 0 when no
+// b <= bmax fits Q2.
 uint64_t choose_buckets_two_tier(uint64_t np, uint64_t m, uint64_t s, uint64_t Q1, uint64_t Q2,
                                  uint64_t bmax)
 {
@@ -154,19 +168,16 @@ uint64_t choose_buckets_two_tier(uint64_t np, uint64_t m, uint64_t s, uint64_t Q
         if (bound_for(np, m, s, mid) <= Q2) hi = mid;
         else lo = mid + 1;
     }
-    const uint64_t b = (105 * np + 100 * Q1 - 1) / (100 * Q1);
+    const uint64_t avg = two_tier_target(m, np / m / s, Q1);
+    const uint64_t b = avg ? (np + avg - 1) / avg : bmax;
     return b > bmax ? bmax : (b < lo ? lo : b);
 }
 
-// Whether bucket sizes are regular enough for a two-tier Step 9: on random
-// keys a bucket's size varies by about w*sqrt(m/6) (each of the m sublists
-// adds a uniform error in [0, w) at both ends); the 5% headroom of a
-// one-CTA unit of Q1 items must cover 2.5 of those, so that about 1% of the
-// buckets at most spill into the cluster tier.
+// Whether bucket sizes are regular enough for a two-tier Step 9: the
+// average bucket four sigmas below Q1 must still fill at least 90% of it.
 bool tiers_regular(uint64_t m, uint64_t w, uint64_t Q1)
 {
-    const double sigma = (double)w * __builtin_sqrt((double)m / 6.0);
-    return 2.5 * sigma <= (double)Q1 * (1.0 - 1.0 / 1.05);
+    return 4.0 * bucket_sigma(m, w) <= 0.10 * (double)Q1;
 }
 
 // Sort-unit shapes (items per CTA) and cluster sizes the kernels provide.
@@ -313,13 +324,15 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
                 // bound needs a cluster and b can reach ~1.05 buckets per
                 // one-CTA unit; the bucket count estimated the same way
                 const uint64_t bmx = m * sv < (uint64_t)kMaxBuckets ? m * sv : (uint64_t)kMaxBuckets;
-                const uint64_t b2 = (105 * np + 100 * (uint64_t)cm - 1) / (100 * (uint64_t)cm);
+                const uint64_t tgt = two_tier_target(m, t / sv, (uint64_t)cm);
+                const uint64_t b2 = tgt ? (np + tgt - 1) / tgt : bmx + 1;
                 const bool tiers = uk > 1 && !forced_b && !forced_s && b2 <= bmx &&
                                    bound_for(np, m, sv, b2) <= (uint64_t)uc * uk &&
                                    tiers_regular(m, t / sv, (uint64_t)cm);
                 const uint64_t b_est = forced_b ? forced_b : forced_s ? sv
                                        : tiers ? b2 : (21 * np + 10ull * uc * uk - 1) / (10ull * uc * uk);
-                const double c = tiers ? plan_cost(np, sv, m * b_est, tc, tk, cm, 1)
+                // (the cluster tier's launch costs ~40 us even when nearly empty)
+                const double c = tiers ? plan_cost(np, sv, m * b_est, tc, tk, cm, 1) + 5e6
                                        : plan_cost(np, sv, m * b_est, tc, tk, uc, uk);
                 if (best < 0 || c < best) {
                     best = c;
@@ -369,9 +382,9 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         // units only for the others.  A free b is chosen for that when it can
         // be (at most bmax buckets).
         const uint64_t bmax = m * bs < (uint64_t)kMaxBuckets ? m * bs : (uint64_t)kMaxBuckets;
-        const bool tiers_wanted =
-            buk > 1 && (105 * I.n_padded + 100 * (uint64_t)cm - 1) / (100 * (uint64_t)cm) <= bmax &&
-            tiers_regular(m, bt / bs, (uint64_t)cm);
+        const uint64_t tgt = two_tier_target(m, bt / bs, (uint64_t)cm);
+        const bool tiers_wanted = buk > 1 && tgt && (I.n_padded + tgt - 1) / tgt <= bmax &&
+                                  tiers_regular(m, bt / bs, (uint64_t)cm);
         uint64_t b = bs;  // the paper's rule, kept when s is given
         if (forced_b) {
             b = forced_b;
@@ -383,7 +396,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
             if (bc) b = bc;
         }
         if (buk > 1 && 105 * I.n_padded <= 100 * (uint64_t)cm * b &&
-            tiers_regular(m, bt / bs, (uint64_t)cm)) {
+            tiers_regular(m, bt / bs, (uint64_t)cm)) {  // average at most Q1/1.05
             P->small_chunk = cm;
             I.unit_small = (uint32_t)cm;
         }
@@ -434,7 +447,6 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
                                 ? (uint64_t)P->n_rec_pad * rb : 0);
         P->off_spl = take((uint64_t)I.b * rb);
         P->off_counts = take((uint64_t)P->n_runs * 4);
-        P->off_cum = take((uint64_t)P->n_runs * 4);
         P->off_offsets = take(((uint64_t)P->n_runs + 1) * 4);
         P->off_status = take((uint64_t)P->scan_chunks * 8);
         P->off_units = take((1 + 2 * (uint64_t)I.b) * 4);
@@ -672,7 +684,6 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     uint64_t *rec_b = reinterpret_cast<uint64_t *>(ws + P.off_rec_b);
     uint64_t *spl = reinterpret_cast<uint64_t *>(ws + P.off_spl);
     uint32_t *counts = reinterpret_cast<uint32_t *>(ws + P.off_counts);
-    uint32_t *cum = reinterpret_cast<uint32_t *>(ws + P.off_cum);
     uint32_t *offsets = reinterpret_cast<uint32_t *>(ws + P.off_offsets);
     unsigned long long *status = reinterpret_cast<unsigned long long *>(ws + P.off_status);
 
@@ -706,7 +717,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     uint32_t *srcb = reinterpret_cast<uint32_t *>(ws + P.off_srcb);
     uint32_t *blk = reinterpret_cast<uint32_t *>(ws + P.off_blk);
     // Step 6
-    SEQ(launch_sample_index(tiles_k, samples, spl, I.t, I.s, I.b, I.m, counts, cum, srcb, st),
+    SEQ(launch_sample_index(tiles_k, samples, spl, I.t, I.s, I.b, I.m, counts, srcb, st),
         "step6_sample_index");
     // Step 7
     SEQ(launch_scan(counts, offsets, P.n_runs, status, ticket, err, st), "step7_prefix_sum");

@@ -80,13 +80,11 @@ cudaError_t launch_merge_pass(const uint64_t *src, uint64_t *dst, uint32_t n_pad
 cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint32_t b,
                                     uint64_t *spl, cudaStream_t st);
 
-// Step 6: for the b splitters, counts a_ij (bucket-major), cumulative counts
-// c_ij (sublist-major, c[i*b + j] = items of sublist i <= g_j) and run starts
+// Step 6: for the b splitters, counts a_ij (bucket-major) and run starts
 // srcb[j*m + i] = i*t + c_i(j-1); s samples per sublist index the sublist.
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
                                 const uint64_t *spl, uint32_t t, uint32_t s, uint32_t b,
-                                uint32_t m, uint32_t *counts, uint32_t *cum,
-                                uint32_t *srcb, cudaStream_t st);
+                                uint32_t m, uint32_t *counts, uint32_t *srcb, cudaStream_t st);
 
 // Step 7: exclusive scan of n_items uint32 counts (decoupled look-back);
 // status must hold ceil(n_items / kScanChunk) words and ticket one word,

@@ -185,8 +185,8 @@ template <int T>
 __global__ void __launch_bounds__(T)
 k_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ samples,
                const uint64_t *__restrict__ spl, uint32_t t, uint32_t s, uint32_t b,
-               uint32_t m, uint32_t *__restrict__ counts, uint32_t *__restrict__ cum,
-               uint32_t *__restrict__ srcb, uint32_t jb)
+               uint32_t m, uint32_t *__restrict__ counts, uint32_t *__restrict__ srcb,
+               uint32_t jb)
 {
     const uint32_t gpt = (b + T * jb - 1) / (T * jb);  // CTAs per sublist
     const uint32_t i = blockIdx.x / gpt;
@@ -206,7 +206,39 @@ k_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict_
         else hi = mid;
     }
     uint32_t q = lo;
-    uint32_t prev = j0 ? window_count(tiles_k, base, q, w, t, s, g) : 0u;
+    // windows of up to 32 items (16-byte aligned) stay in registers while
+    // consecutive splitters fall into the same one (about b/s of them do)
+    constexpr int kWin4 = 8;
+    const bool cached = w <= 4u * kWin4 && (w & 3) == 0;
+    uint4 win[kWin4];
+    uint32_t wq = 0xFFFFFFFFu;
+    auto count_le = [&](uint32_t qq, uint64_t gg) -> uint32_t {
+        if (!cached) return window_count(tiles_k, base, qq, w, t, s, gg);
+        if (qq >= s) return t;
+        const uint32_t r0 = qq * w;
+        if (qq != wq) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(tiles_k + base + r0);
+#pragma unroll
+            for (int v = 0; v < kWin4; ++v)
+                if ((uint32_t)v < w / 4) win[v] = p[v];
+            wq = qq;
+        }
+        const uint32_t gk = (uint32_t)(gg >> 32), gp = (uint32_t)gg;
+        const uint32_t pos0 = (uint32_t)(base + r0);
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int v = 0; v < kWin4; ++v) {
+            if ((uint32_t)v >= w / 4) break;
+            const uint4 x = win[v];
+            const uint32_t pos = pos0 + 4u * (uint32_t)v;
+            cnt += (x.x < gk || (x.x == gk && pos + 0 <= gp)) ? 1u : 0u;
+            cnt += (x.y < gk || (x.y == gk && pos + 1 <= gp)) ? 1u : 0u;
+            cnt += (x.z < gk || (x.z == gk && pos + 2 <= gp)) ? 1u : 0u;
+            cnt += (x.w < gk || (x.w == gk && pos + 3 <= gp)) ? 1u : 0u;
+        }
+        return r0 + cnt;
+    };
+    uint32_t prev = j0 ? count_le(q, g) : 0u;
     for (uint32_t j = j0; j < j1; ++j) {
         g = spl[j];
         if (q < s && smp[q] <= g) {  // q grows: gallop, then binary search
@@ -224,9 +256,8 @@ k_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict_
             }
             q = lo2;
         }
-        const uint32_t c = window_count(tiles_k, base, q, w, t, s, g);
+        const uint32_t c = count_le(q, g);
         counts[(uint64_t)j * m + i] = c - prev;
-        cum[(uint64_t)i * b + j] = c;
         srcb[(uint64_t)j * m + i] = (uint32_t)base + prev;  // A_ij starts at rank c_i(j-1)
         prev = c;
     }
@@ -647,14 +678,13 @@ cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint
 
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
                                 const uint64_t *spl, uint32_t t, uint32_t s, uint32_t b,
-                                uint32_t m, uint32_t *counts, uint32_t *cum, uint32_t *srcb,
-                                cudaStream_t st)
+                                uint32_t m, uint32_t *counts, uint32_t *srcb, cudaStream_t st)
 {
     constexpr int T = 128;
     const uint32_t jb = b >= 8 * T ? 8 : (b + T - 1) / T;  // splitters per thread
     const uint32_t gpt = (b + T * jb - 1) / (T * jb);
-    k_sample_index<T><<<m * gpt, T, 0, st>>>(tiles_k, samples, spl, t, s, b, m, counts, cum,
-                                             srcb, jb);
+    k_sample_index<T><<<m * gpt, T, 0, st>>>(tiles_k, samples, spl, t, s, b, m, counts, srcb,
+                                             jb);
     return cudaGetLastError();
 }
 

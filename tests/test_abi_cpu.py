@@ -224,15 +224,18 @@ def test_plan_u64_keys():
 
 
 def test_plan_two_tier_step9():
-    """When the bound needs a cluster unit and b can make the average bucket
-    about 1/1.05 of a one-CTA unit, Step 9 runs in two tiers (unit_small);
-    with s or b given, or when b would exceed its limit, in one."""
+    """When the bound needs a cluster unit and bucket sizes are regular
+    enough, b puts the average bucket four sigmas below a one-CTA unit and
+    Step 9 runs in two tiers (unit_small); with s given (b = s), or when b
+    would exceed its limit, in one."""
     h = _handle()
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 28)
     assert p.unit_ctas > 1 and p.unit_small == 32768
-    assert p.b == -(-105 * p.n_padded // (100 * 32768))
-    # bucket sizes regular enough: 2.5 x w sqrt(m/6) within the 5% headroom
-    assert 2.5 * p.w * (p.m / 6) ** 0.5 <= 32768 * (1 - 1 / 1.05)
+    # average bucket four sigmas (sigma = w sqrt(m/6)) below the one-CTA unit,
+    # and those four sigmas within 10% of it
+    sigma = p.w * (p.m / 6) ** 0.5
+    assert 4 * sigma <= 0.10 * 32768
+    assert p.b == -(-p.n_padded // int(32768 - 4 * sigma))
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 4, 1 << 25)
     assert p.unit_ctas > 1 and p.unit_small == 16384
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 22)
