@@ -54,9 +54,16 @@ ALU_KERNELS = ("step1_3_sublist_sort", "step9_bucket_sort", "step9_single_unit")
 # integer ALU pipe: 16 lanes per SM sub-partition x 4 x 152 SMs x 2.07 GHz
 ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12
 UNIT = "Gkeys/s"
-KERNEL_SOURCES = ["paper_1002_4464_gb300/csrc/bsort_kernels.cu",
-                  "paper_1002_4464_gb300/csrc/bsort_sort.cuh",
-                  "paper_1002_4464_gb300/csrc/bsort_device.cuh"]
+# the sources each kernel is built from (a traffic record is valid while they
+# are unchanged)
+_CSRC = "paper_1002_4464_gb300/csrc/"
+KERNEL_SOURCES = {
+    "k_sublist_sort": [_CSRC + "bsort_sort.cuh", _CSRC + "bsort_device.cuh",
+                       _CSRC + "bsort_sort_keys.cu"],
+    "k_bucket_sort": [_CSRC + "bsort_sort.cuh", _CSRC + "bsort_device.cuh",
+                      _CSRC + "bsort_sort_keys.cu"],
+}
+KERNEL_SOURCES_DEFAULT = [_CSRC + "bsort_kernels.cu", _CSRC + "bsort_device.cuh"]
 
 
 def _args():
@@ -106,9 +113,9 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _kernel_hash():
+def _kernel_hash(kernel):
     h = hashlib.sha256()
-    for rel in KERNEL_SOURCES:
+    for rel in KERNEL_SOURCES.get(kernel, KERNEL_SOURCES_DEFAULT):
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -122,10 +129,10 @@ def _traffic_for(kernel, workload):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("kernel_sources_sha256_16") != _kernel_hash():
-        return None
     e = d.get("kernels", {}).get(kernel)
     if not e or e.get("workload") != workload:
+        return None
+    if e.get("sources_sha256_16") != _kernel_hash(kernel):
         return None
     return e.get("dram_bytes_per_launch")
 
