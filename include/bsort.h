@@ -205,14 +205,15 @@ bsort_status bsort_sort_batch(bsort_t h, bsort_key_type kt, const void *d_keys_i
 /* ---- Served stream (no counterpart in the paper) ------------------------
  * bsort_submit queues one independent sort job; a request loop owned by the
  * handle (one worker thread, started by the first submit) admits queued
- * jobs in arrival order while its device arena has room (the serving budget,
+ * jobs while its device arena has room (the serving budget,
  * bsort_config.serve_budget_bytes) and copies their keys in.  Small jobs
- * (up to 524288 32-bit or 131072 64-bit keys) are sorted together as a
- * batch (bsort_sort_batch's path) as soon as the previous small batch has
- * finished sorting, on a high-priority stream; jobs that arrive meanwhile
- * are copied in and form the next batch (continuous batching).  Larger jobs
- * are sorted one at a time on a low-priority stream with a workspace of
- * their own, so small jobs are not held behind them.  Every job's result is
+ * (up to 524288 32-bit or 131072 64-bit keys) are admitted in arrival order
+ * and sorted together as a batch (bsort_sort_batch's path) as soon as the
+ * previous small batch has finished sorting, on a high-priority stream;
+ * jobs that arrive meanwhile are copied in and form the next batch
+ * (continuous batching).  Larger jobs are admitted in arrival order, at most
+ * four at a time, and sorted one at a time on a low-priority stream with a
+ * workspace of their own, so small jobs are not held behind them.  Every job's result is
  * exactly the sort of its keys.  Once a handle has served a request its
  * plain sort calls return BSORT_EBUSY. */
 typedef struct {
@@ -242,6 +243,8 @@ typedef struct {
     uint64_t completed;        /* jobs finished */
     uint64_t batches;          /* batches launched */
     uint64_t max_batch;        /* most jobs in one batch */
+    uint64_t large_jobs;       /* jobs sorted one at a time (large lane) */
+    uint64_t worker_busy_ns;   /* time the request loop spent working */
 } bsort_serve_info;
 
 /* Queue one job; *ticket identifies it for bsort_poll.  Errors: EINVAL,

@@ -92,7 +92,7 @@ class bsort_result(ctypes.Structure):
 class bsort_serve_info(ctypes.Structure):
     _fields_ = [(name, ctypes.c_uint64) for name in (
         "arena_bytes", "workspace_bytes", "arena_used_bytes", "arena_peak_bytes", "queued",
-        "completed", "batches", "max_batch")]
+        "completed", "batches", "max_batch", "large_jobs", "worker_busy_ns")]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -1116,7 +1116,8 @@ struct bsort_server {
     std::mutex mu;
     std::condition_variable cv;
     bool stop = false;
-    std::deque<Req *> queue;                    // submitted, not admitted
+    std::deque<Req *> queue[2];                 // submitted, not admitted, per lane
+    uint32_t inflight_large = 0;                // lane-B jobs admitted, not retired
     std::unordered_map<uint64_t, Req *> tickets;
     std::deque<uint64_t> finished;              // done, in completion order
     uint64_t next_ticket = 1;
@@ -1125,6 +1126,7 @@ struct bsort_server {
     std::vector<int *> err_pool;
     // statistics
     uint64_t used = 0, peak = 0, batches = 0, done_count = 0, max_batch = 0;
+    uint64_t large_jobs = 0, busy_ns = 0;
 };
 
 namespace {
@@ -1234,6 +1236,7 @@ bool serve_retire(bsort_server *S)
                                           : (word == BSORT_ETIMEOUT ? BSORT_ETIMEOUT
                                                                    : BSORT_EINTERNAL);
                 r->done = true;
+                if (r->lane == 1) --S->inflight_large;
                 S->finished.push_back(r->ticket);
                 ++S->done_count;
                 r = nullptr;  // the caller may free it once polled
@@ -1318,9 +1321,13 @@ void serve_run(bsort_server *S, int li, const std::vector<bsort_server::Req *> &
     L.running.push_back(b);
 }
 
-// Admit queued jobs in arrival order while the arena has room: copy their
-// keys in; a large job is sorted on lane B right away (behind the ones
-// before it), a small one waits for lane A's next batch.
+// Admit queued jobs of each lane in arrival order while the arena has
+// room, copying their keys in: small jobs wait for lane A's next batch; a
+// large job is sorted on lane B right away (behind the ones before it), with
+// at most kLargeDepth of them in flight so that the work queued on the
+// device stays short (a deep queue makes enqueueing block in the driver).
+constexpr uint32_t kLargeDepth = 4;
+
 bool serve_admit(bsort_server *S)
 {
     bool any = false;
@@ -1328,12 +1335,25 @@ bool serve_admit(bsort_server *S)
         bsort_server::Req *r = nullptr;
         {
             std::lock_guard<std::mutex> lock(S->mu);
-            if (S->queue.empty()) break;
-            bsort_server::Req *head = S->queue.front();
+            int li = -1;
+            if (!S->queue[0].empty()) li = 0;
+            else if (!S->queue[1].empty() && S->inflight_large < kLargeDepth) li = 1;
+            if (li < 0) break;
+            bsort_server::Req *head = S->queue[li].front();
             uint64_t off = 0;
-            if (!arena_alloc(S, head->bytes, &off)) break;
+            if (!arena_alloc(S, head->bytes, &off)) {
+                // the small lane waits for room; the large lane may still go
+                if (li == 0 && !S->queue[1].empty() && S->inflight_large < kLargeDepth) {
+                    head = S->queue[1].front();
+                    if (!arena_alloc(S, head->bytes, &off)) break;
+                    li = 1;
+                } else {
+                    break;
+                }
+            }
             head->off = off;
-            S->queue.pop_front();
+            S->queue[li].pop_front();
+            if (li == 1) ++S->inflight_large;
             r = head;
         }
         bsort_server::Lane &L = S->lane[r->lane];
@@ -1343,6 +1363,7 @@ bool serve_admit(bsort_server *S)
         if (r->lane == 0) {
             S->staged.push_back(r);
         } else {
+            ++S->large_jobs;
             cudaEvent_t in_done = take_event(S);
             cudaEventRecord(in_done, L.s_in);
             cudaStreamWaitEvent(L.s_run, in_done, 0);
@@ -1374,11 +1395,14 @@ void serve_loop(bsort_server *S)
 {
     cudaSetDevice(S->h->device);
     for (;;) {
+        const uint64_t t0 = clock_ns();
         bool busy = serve_retire(S);
         busy |= serve_admit(S);
         busy |= serve_launch(S);
+        if (busy) S->busy_ns += clock_ns() - t0;
         std::unique_lock<std::mutex> lock(S->mu);
-        const bool idle = S->queue.empty() && S->staged.empty() && S->lane[0].running.empty() &&
+        const bool idle = S->queue[0].empty() && S->queue[1].empty() && S->staged.empty() &&
+                          S->lane[0].running.empty() &&
                           S->lane[1].running.empty();
         if (S->stop && idle) break;
         if (!busy) {
@@ -1699,7 +1723,7 @@ bsort_status bsort_submit(bsort_t h, const bsort_request *req, uint64_t *ticket)
         std::lock_guard<std::mutex> lock(S->mu);
         r->ticket = S->next_ticket++;
         S->tickets[r->ticket] = r;
-        S->queue.push_back(r);
+        S->queue[r->lane].push_back(r);
     }
     S->cv.notify_one();
     *ticket = r->ticket;
@@ -1766,10 +1790,12 @@ bsort_status bsort_serve_stats(bsort_t h, bsort_serve_info *out)
     out->workspace_bytes = h->ws_bytes + S->hb->ws_bytes;
     out->arena_used_bytes = S->used;
     out->arena_peak_bytes = S->peak;
-    out->queued = S->queue.size();
+    out->queued = S->queue[0].size() + S->queue[1].size();
     out->completed = S->done_count;
     out->batches = S->batches;
     out->max_batch = S->max_batch;
+    out->large_jobs = S->large_jobs;
+    out->worker_busy_ns = S->busy_ns;
     return BSORT_OK;
 }
 
