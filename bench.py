@@ -677,7 +677,7 @@ def run_served(args, pkg, synth, dev, rank):
 
     # one at a time: the same arrivals, each sorted and copied back before the next
     one = pkg.BucketSorter(device=dev.index)
-    one._ensure(maxn, "u64", 0, extra=maxn * 8)
+    one._ensure(maxn, "u64", 0, extra=maxn * 8 + 512)
     lat1 = np.zeros(njobs)
     t1 = pkg.bsort_clock_ns() + 50_000_000
     last = t1
@@ -724,7 +724,7 @@ def run_served(args, pkg, synth, dev, rank):
 
     def capacity_one():
         one2 = pkg.BucketSorter(device=dev.index)
-        one2._ensure(maxn, "u64", 0, extra=maxn * 8)
+        one2._ensure(maxn, "u64", 0, extra=maxn * 8 + 512)
         s2 = one2._stream()
         c0 = pkg.bsort_clock_ns()
         for k in range(ncap):

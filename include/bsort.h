@@ -274,9 +274,16 @@ bsort_status bsort_plan_batch(bsort_t h, bsort_key_type kt, const uint64_t *seg_
                               uint32_t num_segs, bsort_batch_info *out);
 
 /* bsort_sort_keys on HOST buffers: copies h_keys_in to the device, sorts,
- * and copies the result back into h_keys_out, all on cuda_stream (the
- * copies are part of the call).  Pinned host memory gives asynchronous
- * copies.  Uses extra workspace for the device copy of the keys. */
+ * and copies the result back into h_keys_out, all ordered on cuda_stream
+ * (the copies are part of the call; h_keys_out is complete once the work
+ * issued on cuda_stream so far has finished).  Pinned host memory gives
+ * asynchronous copies.  For 32-bit keys over several sublists the copies
+ * overlap the sort: the keys go in as 16 chunks of whole sublists, Steps 1-3
+ * starting on each chunk once it has arrived, and Step 9 runs in 16 groups
+ * of units by output position, each group's slice of h_keys_out copied out
+ * while the next group sorts (on a copy stream of the handle, ordered
+ * against cuda_stream by events).  Uses extra workspace: the device copy of
+ * the keys (n * key bytes, rounded up to 256) plus 256 bytes. */
 bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_keys_in,
                                   void *h_keys_out, uint64_t n, void *cuda_stream);
 

@@ -375,7 +375,8 @@ class BucketSorter:
     def sort_keys_host(self, h_keys, h_out, key_type="u32"):
         """Host tensors (pinned for asynchronous copies) in and out."""
         n = h_keys.numel()
-        self._ensure(n, key_type, 0, extra=((n * h_keys.element_size() + 255) // 256) * 256)
+        self._ensure(n, key_type, 0,
+                     extra=((n * h_keys.element_size() + 255) // 256) * 256 + 256)
         bsort_sort_keys_host(self.h, _KEY_TYPES[key_type], h_keys.data_ptr(),
                              h_out.data_ptr(), n, self._stream())
         return h_out

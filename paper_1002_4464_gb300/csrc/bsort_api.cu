@@ -26,6 +26,7 @@ constexpr uint64_t kAlign = 256;
 constexpr uint64_t kMaxN = (1ull << 32) - (1ull << 16);
 constexpr uint64_t kMaxSamples = 8192;  // s per sublist (Step 6 keeps 12*s bytes in SMEM)
 constexpr int kMaxTimed = 40;   // launches recorded per call
+constexpr int kPipe = 16;       // host entry: key chunks in, position slices out
 // Batches: segments up to kBatchDirectMax keys (default) are sorted whole by
 // one unit; up to kBatchSampledMax by segment-aware sampling with sublists
 // of kSegTile keys and s = kBatchSamples (m*s <= kRecordChunk); larger ones
@@ -89,6 +90,10 @@ struct bsort_ctx {
     bool events_made = false;
     uint64_t serve_budget = 0;        // bytes for served requests (0: 4 GiB)
     bsort_server *server = nullptr;   // started by the first bsort_submit
+    // bsort_sort_keys_host: copy stream and its events (made on first use)
+    cudaStream_t xfer = nullptr;
+    cudaEvent_t xev[2 * kPipe + 2] = {};
+    int num_sms = 0;
 };
 
 namespace {
@@ -555,6 +560,42 @@ struct Seq {
         if (s_ != BSORT_OK) return s_;                   \
     } while (0)
 
+// Host buffers of bsort_sort_keys_host, overlapped with the sort: the keys
+// arrive in kPipe chunks of whole sublists and Steps 1-3 start on each chunk
+// once it is on the device; Step 9 runs in kPipe groups, group g sorting the
+// units that begin in position slice [g n'/kPipe, (g+1) n'/kPipe), and that
+// slice goes back to the host while the next group sorts (every position of
+// the slice lies in a unit that begins at or before it).  Copies run on the
+// handle's copy stream, ordered against the caller's stream by events.
+struct HostPipe {
+    const void *h_in;
+    void *h_out;
+    void *d_keys;      // device staging of the keys (the sort runs in place)
+    uint32_t *ranges;  // device: 2 (kPipe + 1) unit indices
+};
+
+bsort_status ensure_pipe(bsort_t h)
+{
+    if (h->xfer) return BSORT_OK;
+    cudaError_t e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e != cudaSuccess) return cuda_fail(h, e, "multiprocessor count");
+    for (int i = 0; i < 2 * kPipe + 2; ++i) {
+        e = cudaEventCreateWithFlags(&h->xev[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate (copy pipeline)");
+    }
+    e = cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate (copy pipeline)");
+    return BSORT_OK;
+}
+
+// the stream `to` waits for the work issued so far on `from`
+cudaError_t stream_after(cudaStream_t to, cudaStream_t from, cudaEvent_t ev)
+{
+    cudaError_t e = cudaEventRecord(ev, from);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(to, ev, 0);
+    return e;
+}
+
 // Algorithm 1 on 64-bit keys (keys only): the same steps with 64-bit sorted
 // sublists and buckets and 16-byte sample records merged in L2 (Step 4).
 bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout, uint64_t n,
@@ -635,7 +676,8 @@ bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout,
 }
 
 bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void *vin, void *kout,
-                      void *vout, uint32_t vb, uint64_t n, cudaStream_t st)
+                      void *vout, uint32_t vb, uint64_t n, cudaStream_t st,
+                      const HostPipe *hp = nullptr)
 {
     bsort_status rs = prepare(h);
     if (rs != BSORT_OK) return rs;
@@ -694,11 +736,34 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan ticket)");
 
     // Steps 1-3
-    SEQ(P.pairs ? launch_sublist_sort_pairs(P.tile_chunk, (int)I.tile_ctas, kin, vin, n, I.m,
-                                            is_f32, (int)vb, I.s, tiles_k, tiles_v, samples, st)
-                : launch_sublist_sort_keys(P.tile_chunk, (int)I.tile_ctas, kin, n, I.m, is_f32,
-                                           I.s, tiles_k, samples, st),
-        "step1_3_sublist_sort");
+    if (hp) {
+        // chunk c: copy its sublists' keys in, then sort them
+        e = stream_after(h->xfer, st, h->xev[2 * kPipe]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "order copy stream");
+        const uint32_t per = (I.m + kPipe - 1) / kPipe;
+        for (uint32_t t0 = 0, c = 0; t0 < I.m; t0 += per, ++c) {
+            const uint32_t mc = std::min(per, I.m - t0);
+            const uint64_t p0 = (uint64_t)t0 * I.t;
+            const uint64_t p1 = std::min<uint64_t>((uint64_t)(t0 + mc) * I.t, n);
+            if (p1 > p0) {
+                e = cudaMemcpyAsync(static_cast<unsigned char *>(hp->d_keys) + p0 * 4,
+                                    static_cast<const unsigned char *>(hp->h_in) + p0 * 4,
+                                    (p1 - p0) * 4, cudaMemcpyHostToDevice, h->xfer);
+                if (e == cudaSuccess) e = stream_after(st, h->xfer, h->xev[c]);
+                if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
+            }
+            SEQ(launch_sublist_sort_keys(P.tile_chunk, (int)I.tile_ctas, kin, n, mc, is_f32,
+                                         I.s, tiles_k, samples, st, t0),
+                "step1_3_sublist_sort");
+        }
+    } else {
+        SEQ(P.pairs ? launch_sublist_sort_pairs(P.tile_chunk, (int)I.tile_ctas, kin, vin, n,
+                                                I.m, is_f32, (int)vb, I.s, tiles_k, tiles_v,
+                                                samples, st)
+                    : launch_sublist_sort_keys(P.tile_chunk, (int)I.tile_ctas, kin, n, I.m,
+                                               is_f32, I.s, tiles_k, samples, st),
+            "step1_3_sublist_sort");
+    }
     // Steps 4-5
     const bool one_chunk = P.n_rec_pad == (uint32_t)kRecordChunk;
     SEQ(launch_records_chunk_sort(samples, rec_a, P.n_rec, P.n_rec_pad, one_chunk ? spl : nullptr,
@@ -748,6 +813,43 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     const void *s9v = P.relocate ? (const void *)reloc_v : (const void *)tiles_v;
     const int c1 = P.small_chunk ? P.small_chunk : P.unit_chunk;
     const int k1 = P.small_chunk ? 1 : (int)I.unit_ctas;
+    if (hp) {
+        // group g: the units of both tiers that begin in slice g, then the
+        // slice's keys to the host
+        const uint32_t np = (uint32_t)I.n_padded;
+        uint32_t *r1 = hp->ranges, *r2 = hp->ranges + kPipe + 1;
+        SEQ(launch_unit_ranges(units, np, kPipe, r1, st), "step9_unit_ranges");
+        if (units2) SEQ(launch_unit_ranges(units2, np, kPipe, r2, st), "step9_unit_ranges");
+        // resident CTAs (clusters: 7/8 of the SMs can hold them) loop over
+        // the group's units, none of them in a late wave
+        const int sms = std::max(h->num_sms, 8);
+        const uint32_t g1 = std::max(
+            1u, std::min<uint32_t>(I.b, (uint32_t)(k1 == 1 ? sms : (sms * 7 / 8) / k1)));
+        const uint32_t g2 = std::max(1u, (uint32_t)((sms * 7 / 8) / (int)I.unit_ctas));
+        for (int g = 0; g < kPipe; ++g) {
+            SEQ(launch_bucket_sort_keys_range(c1, k1, s9k, units, r1 + g, g1, n, I.n_padded,
+                                              is_f32, kout, err, st),
+                "step9_bucket_sort");
+            if (units2)
+                SEQ(launch_bucket_sort_keys_range(P.unit_chunk, (int)I.unit_ctas, s9k, units2,
+                                                  r2 + g, g2, n, I.n_padded, is_f32, kout, err,
+                                                  st),
+                    "step9_bucket_sort_large");
+            const uint64_t p0 = std::min<uint64_t>((uint64_t)g * np / kPipe, n);
+            const uint64_t p1 = std::min<uint64_t>((uint64_t)(g + 1) * np / kPipe, n);
+            if (p1 > p0) {
+                e = stream_after(h->xfer, st, h->xev[kPipe + g]);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(static_cast<unsigned char *>(hp->h_out) + p0 * 4,
+                                        static_cast<const unsigned char *>(hp->d_keys) + p0 * 4,
+                                        (p1 - p0) * 4, cudaMemcpyDeviceToHost, h->xfer);
+                if (e != cudaSuccess) return cuda_fail(h, e, "device-to-host copy");
+            }
+        }
+        e = stream_after(st, h->xfer, h->xev[2 * kPipe + 1]);
+        if (e != cudaSuccess) return cuda_fail(h, e, "order copy stream");
+        return BSORT_OK;
+    }
     SEQ(P.pairs ? launch_bucket_sort_pairs(c1, k1, s9k, s9v, units, I.b, n, I.n_padded, is_f32,
                                            (int)vb, kout, vout, err, g, st)
                 : launch_bucket_sort_keys(c1, k1, s9k, units, I.b, n, I.n_padded, is_f32, kout,
@@ -1597,6 +1699,9 @@ bsort_status bsort_destroy(bsort_t h)
     }
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
     if (h->stage) cudaFreeHost(h->stage);
+    if (h->xfer) cudaStreamDestroy(h->xfer);
+    for (int i = 0; i < 2 * kPipe + 2; ++i)
+        if (h->xev[i]) cudaEventDestroy(h->xev[i]);
     if (h->events_made)
         for (int r = 0; r < kRing; ++r)
             for (int i = 0; i <= kMaxTimed; ++i) cudaEventDestroy(h->ev[r][i]);
@@ -1820,6 +1925,21 @@ bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_ke
     if (rs != BSORT_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     void *d_buf = static_cast<unsigned char *>(h->ws) + stage;
+    if (P.kb == 4 && !P.wide && !P.info.single_tile && P.relocate) {
+        // several sublists: copies overlap Steps 1-3 and Step 9
+        rs = ensure_workspace(h, stage + align_up(bytes) + kAlign);
+        if (rs != BSORT_OK) return rs;
+        rs = ensure_pipe(h);
+        if (rs != BSORT_OK) return rs;
+        d_buf = static_cast<unsigned char *>(h->ws) + stage;
+        HostPipe hp;
+        hp.h_in = h_keys_in;
+        hp.h_out = h_keys_out;
+        hp.d_keys = d_buf;
+        hp.ranges = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(h->ws) + stage +
+                                                 align_up(bytes));
+        return run_sort(h, kt, d_buf, nullptr, d_buf, nullptr, 0, n, st, &hp);
+    }
     cudaError_t e = cudaMemcpyAsync(d_buf, h_keys_in, bytes, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
     rs = run_sort(h, kt, d_buf, nullptr, d_buf, nullptr, 0, n, st);

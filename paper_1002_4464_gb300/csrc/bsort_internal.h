@@ -28,9 +28,10 @@ cudaError_t init_sort_pairs_kernels();
 // Steps 1-3: sort every sublist of t = ctas * chunk items with a cluster of
 // `ctas` CTAs of `chunk` items each; write the sorted sublists (keys, and
 // values for pairs) and s sample records per sublist.
+// Steps 1-3 for sublists tile0 .. tile0 + m - 1.
 cudaError_t launch_sublist_sort_keys(int chunk, int ctas, const void *keys_in, uint64_t n,
                                      uint32_t m, int is_f32, uint32_t s, uint32_t *tiles_k,
-                                     uint64_t *samples, cudaStream_t st);
+                                     uint64_t *samples, cudaStream_t st, uint32_t tile0 = 0);
 cudaError_t launch_sublist_sort_pairs(int chunk, int ctas, const void *keys_in,
                                       const void *vals_in, uint64_t n, uint32_t m, int is_f32,
                                       int val_bytes, uint32_t s, uint32_t *tiles_k,
@@ -59,6 +60,16 @@ constexpr uint32_t kLoopUnits = 256;
 cudaError_t launch_bucket_sort_keys(int chunk, int ctas, const void *src_k, const uint32_t *units,
                                     uint32_t max_units, uint64_t n, uint64_t n_pad, int is_f32,
                                     void *out_k, int *err, const GatherSrc &g, cudaStream_t st);
+// Step 9 (keys) over units range[0] .. range[1] - 1 of a list, range in
+// device memory, by a grid of grid_units units that loop over them.
+cudaError_t launch_bucket_sort_keys_range(int chunk, int ctas, const void *src_k,
+                                          const uint32_t *units, const uint32_t *range,
+                                          uint32_t grid_units, uint64_t n, uint64_t n_pad,
+                                          int is_f32, void *out_k, int *err, cudaStream_t st);
+// For G position slices [g*n_pad/G, (g+1)*n_pad/G): ranges[g] = first unit of
+// the list whose begin is at or above g*n_pad/G (ranges[G] = the count).
+cudaError_t launch_unit_ranges(const uint32_t *units, uint32_t n_pad, uint32_t G,
+                               uint32_t *ranges, cudaStream_t st);
 cudaError_t launch_bucket_sort_pairs(int chunk, int ctas, const void *src_k, const void *src_v,
                                      const uint32_t *units, uint32_t max_units, uint64_t n,
                                      uint64_t n_pad, int is_f32, int val_bytes, void *out_k,

@@ -736,6 +736,36 @@ cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t b, u
     return cudaGetLastError();
 }
 
+// ranges[g] = first unit (of count units, sorted by begin) whose begin is
+// >= g * n_pad / G; ranges[G] = count.
+__global__ void k_unit_ranges(const uint32_t *__restrict__ units, uint32_t n_pad, uint32_t G,
+                              uint32_t *__restrict__ ranges)
+{
+    const uint32_t g = threadIdx.x;
+    if (g > G) return;
+    const uint32_t count = units[0];
+    if (g == G) {
+        ranges[g] = count;
+        return;
+    }
+    const uint32_t pos = (uint32_t)((uint64_t)g * n_pad / G);
+    uint32_t lo = 0, hi = count;
+    while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (units[1 + 2 * mid] < pos) lo = mid + 1;
+        else hi = mid;
+    }
+    ranges[g] = lo;
+}
+
+cudaError_t launch_unit_ranges(const uint32_t *units, uint32_t n_pad, uint32_t G,
+                               uint32_t *ranges, cudaStream_t st)
+{
+    if (G + 1 > 32) return cudaErrorInvalidValue;  // one thread per slice boundary
+    k_unit_ranges<<<1, 32, 0, st>>>(units, n_pad, G, ranges);
+    return cudaGetLastError();
+}
+
 cudaError_t init_kernels()
 {
     cudaError_t e = init_misc_kernels();

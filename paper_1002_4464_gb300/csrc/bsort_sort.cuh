@@ -16,7 +16,7 @@
 namespace bsort {
 
 // ============================================================ Steps 1-3
-// Cluster i sorts sublist i (t = C*T*E items); CTA r loads positions
+// Cluster c sorts sublist i = tile0 + c (t = C*T*E items); CTA r loads positions
 // [r*T*E, (r+1)*T*E) of the sublist and, after the merge, holds its ranks
 // [r*T*E, (r+1)*T*E): it writes them to the sorted-sublist array and emits
 // the samples (ranks (k+1)w - 1) that fall in that range as key << 32 | p,
@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(T, 1)
 k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ vals_in,
                uint64_t n, int is_f32, int val_bytes, uint32_t s,
                uint32_t *__restrict__ tiles_k, void *__restrict__ tiles_v,
-               uint64_t *__restrict__ samples)
+               uint64_t *__restrict__ samples, uint32_t tile0)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
     constexpr int CH = T * E;
@@ -35,7 +35,7 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
     K *sm = reinterpret_cast<K *>(smem_raw);
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
-    const uint32_t tile = blockIdx.x / C;
+    const uint32_t tile = tile0 + blockIdx.x / C;
     const int r = (int)(blockIdx.x % C);
     const uint64_t base = (uint64_t)tile * TT;
     const uint64_t avail = n > base ? n - base : 0;  // real items of the sublist
@@ -231,19 +231,21 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
 }
 
 // The same for a unit list whose length only the device knows (the cluster
-// tier of a two-tier Step 9, mostly empty): a small grid whose cluster c
-// sorts units c, c + G, c + 2G, ... (G clusters; every CTA of a cluster
+// tier of a two-tier Step 9, mostly empty, or a range of units given in
+// device memory, range[0] .. range[1] - 1): a small grid whose cluster c
+// sorts units lo + c, lo + c + G, ... (G clusters; every CTA of a cluster
 // takes the same units).
 template <int T, int E, bool PAIRS, int C>
 __global__ void __launch_bounds__(T, 1)
 k_bucket_sort_loop(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
                    const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
                    int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v,
-                   int *err, GatherSrc g)
+                   int *err, GatherSrc g, const uint32_t *__restrict__ range)
 {
-    const uint32_t count = units[0];
+    const uint32_t lo = range != nullptr ? range[0] : 0u;
+    const uint32_t count = range != nullptr ? range[1] : units[0];
 #pragma unroll 1
-    for (uint32_t u = blockIdx.x / C; u < count; u += gridDim.x / C) {
+    for (uint32_t u = lo + blockIdx.x / C; u < count; u += gridDim.x / C) {
         bucket_sort_unit<T, E, PAIRS, C>(u, src_k, src_v, units, n, n_pad, is_f32, val_bytes,
                                          out_k, out_v, err, g);
         __syncthreads();  // shared memory is reused by the next unit
@@ -281,11 +283,9 @@ inline cudaError_t init_sort_pair_of_kernels()
     e = cudaFuncSetAttribute(k_bucket_sort<T, E, PAIRS, C>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    if (C > 1) {
-        e = cudaFuncSetAttribute(k_bucket_sort_loop<T, E, PAIRS, C>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        if (e != cudaSuccess) return e;
-    }
+    e = cudaFuncSetAttribute(k_bucket_sort_loop<T, E, PAIRS, C>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return e;
     if (C > 8) {
         e = cudaFuncSetAttribute(k_sublist_sort<T, E, PAIRS, C>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -300,13 +300,13 @@ template <int T, int E, bool PAIRS, int C>
 inline cudaError_t launch_sublist_sort_t(const void *keys_in, const void *vals_in, uint64_t n,
                                          uint32_t m, int is_f32, int val_bytes, uint32_t s,
                                          uint32_t *tiles_k, void *tiles_v, uint64_t *samples,
-                                         cudaStream_t st)
+                                         uint32_t tile0, cudaStream_t st)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
     const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
     return launch_maybe_cluster(k_sublist_sort<T, E, PAIRS, C>, m * C, T, sm, C, st,
                                 static_cast<const uint32_t *>(keys_in), vals_in, n, is_f32,
-                                val_bytes, s, tiles_k, tiles_v, samples);
+                                val_bytes, s, tiles_k, tiles_v, samples, tile0);
 }
 
 template <int T, int E, bool PAIRS, int C>
@@ -323,10 +323,39 @@ inline cudaError_t launch_bucket_sort_t(const void *src_k, const void *src_v,
         return launch_maybe_cluster(k_bucket_sort_loop<T, E, PAIRS, C>, grid, T, sm, C, st,
                                     static_cast<const uint32_t *>(src_k), src_v, units, n, n_pad,
                                     is_f32, val_bytes, static_cast<uint32_t *>(out_k), out_v,
-                                    err, g);
+                                    err, g, (const uint32_t *)nullptr);
     return launch_maybe_cluster(k_bucket_sort<T, E, PAIRS, C>, grid, T, sm, C, st,
                                 static_cast<const uint32_t *>(src_k), src_v, units, n, n_pad,
                                 is_f32, val_bytes, static_cast<uint32_t *>(out_k), out_v, err, g);
+}
+
+// Step 9 over the units range[0] .. range[1] - 1 of a list (device memory),
+// by a grid of grid_units clusters (C > 1) or of grid_units SMs' worth of
+// CTAs (C = 1) that loop over them.
+template <int T, int E, bool PAIRS, int C>
+inline cudaError_t launch_bucket_sort_range_t(const void *src_k, const uint32_t *units,
+                                              const uint32_t *range, uint32_t grid_units,
+                                              uint64_t n, uint64_t n_pad, int is_f32,
+                                              void *out_k, int *err, cudaStream_t st)
+{
+    using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
+    const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
+    const GatherSrc none;
+    if (C == 1) {
+        // grid_units counts SMs: as many CTAs as fit on them at once
+        static const int per_sm = [sm] {
+            int o = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                    &o, k_bucket_sort_loop<T, E, PAIRS, C>, T, sm) != cudaSuccess)
+                o = 1;
+            return o < 1 ? 1 : o;
+        }();
+        grid_units *= (uint32_t)per_sm;
+    }
+    return launch_maybe_cluster(k_bucket_sort_loop<T, E, PAIRS, C>, grid_units * C, T, sm, C, st,
+                                static_cast<const uint32_t *>(src_k), (const void *)nullptr, units,
+                                n, n_pad, is_f32, 0, static_cast<uint32_t *>(out_k),
+                                (void *)nullptr, err, none, range);
 }
 
 }  // namespace bsort

@@ -21,11 +21,11 @@ cudaError_t init_sort_keys_kernels()
 
 cudaError_t launch_sublist_sort_keys(int chunk, int ctas, const void *keys_in, uint64_t n,
                                      uint32_t m, int is_f32, uint32_t s, uint32_t *tiles_k,
-                                     uint64_t *samples, cudaStream_t st)
+                                     uint64_t *samples, cudaStream_t st, uint32_t tile0)
 {
 #define L(T_, E_, C_)                                                                       \
     return launch_sublist_sort_t<T_, E_, false, C_>(keys_in, nullptr, n, m, is_f32, 0, s,   \
-                                                    tiles_k, nullptr, samples, st)
+                                                    tiles_k, nullptr, samples, tile0, st)
     if (ctas == 1) {
         switch (chunk) {
         case 2048: L(128, 16, 1);
@@ -52,6 +52,33 @@ cudaError_t launch_bucket_sort_keys(int chunk, int ctas, const void *src_k, cons
 #define L(T_, E_, C_)                                                                        \
     return launch_bucket_sort_t<T_, E_, false, C_>(src_k, nullptr, units, max_units, n,      \
                                                    n_pad, is_f32, 0, out_k, nullptr, err, g, st)
+    if (ctas == 1) {
+        switch (chunk) {
+        case 2048: L(128, 16, 1);
+        case 4096: L(256, 16, 1);
+        case 8192: L(512, 16, 1);
+        case 16384: L(1024, 16, 1);
+        case 32768: L(1024, 32, 1);
+        }
+    } else if (chunk == 32768) {
+        switch (ctas) {
+        case 2: L(1024, 32, 2);
+        case 4: L(1024, 32, 4);
+        case 8: L(1024, 32, 8);
+        }
+    }
+#undef L
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bucket_sort_keys_range(int chunk, int ctas, const void *src_k,
+                                          const uint32_t *units, const uint32_t *range,
+                                          uint32_t grid_units, uint64_t n, uint64_t n_pad,
+                                          int is_f32, void *out_k, int *err, cudaStream_t st)
+{
+#define L(T_, E_, C_)                                                                         \
+    return launch_bucket_sort_range_t<T_, E_, false, C_>(src_k, units, range, grid_units, n, \
+                                                         n_pad, is_f32, out_k, err, st)
     if (ctas == 1) {
         switch (chunk) {
         case 2048: L(128, 16, 1);

@@ -27,7 +27,7 @@ cudaError_t launch_sublist_sort_pairs(int chunk, int ctas, const void *keys_in,
 #define L(T_, E_, C_)                                                                      \
     return launch_sublist_sort_t<T_, E_, true, C_>(keys_in, vals_in, n, m, is_f32,          \
                                                    val_bytes, s, tiles_k, tiles_v, samples, \
-                                                   st)
+                                                   0u, st)
     if (ctas == 1) {
         switch (chunk) {
         case 2048: L(128, 16, 1);

@@ -224,6 +224,87 @@ def test_host_entry_point():
     sorter.close()
 
 
+def _host_pair(a):
+    h_in = torch.from_numpy(np.ascontiguousarray(a).view(np.int32)).pin_memory()
+    return h_in, torch.empty_like(h_in).pin_memory()
+
+
+def test_host_entry_overlapped_intermediates():
+    """The host entry's copies overlap Steps 1-3 (chunks of sublists) and
+    Step 9 (groups of units by position): the sublists, samples, splitters,
+    counts, offsets and relocated array are still the paper's (n = 2^20,
+    t = 4096, s = 64: m = 256 sublists in 16 chunks)."""
+    n, t, s = 1 << 20, 4096, 64
+    keys = synth.keys_u32("bucket", n, synth.seed_for(1, 7, 3))
+    want = oracle.paper_sort(keys, t, s, "u32")
+    sorter = pkg.BucketSorter(tile=t, samples=s)
+    h_in, h_out = _host_pair(keys)
+    sorter.sort_keys_host(h_in, h_out)
+    sorter.sync()
+    assert np.array_equal(h_out.numpy().view(np.uint32), want["keys"])
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], s)
+    sorter.close()
+
+
+@pytest.mark.parametrize("n,dist,kt", [
+    ((1 << 24) + 77, "uniform", "u32"),
+    ((1 << 25) + 3, "zipf", "u32"),
+    ((1 << 26) - 5, "zero", "u32"),
+    (300_001, "sorted", "u32"),
+    ((1 << 22) + 5, "gaussian", "f32"),
+])
+def test_host_entry_overlapped(n, dist, kt):
+    """Overlapped host entry on ragged sizes, plans with one and two Step-9
+    tiers, fewer sublists than copy chunks, and float keys: the output equals
+    the textbook sort bit for bit."""
+    seed = synth.seed_for(2, 7, n & 0xFF)
+    if kt == "f32":
+        keys = synth.keys_f32(dist, n, seed)
+        want = oracle.textbook_sort(keys, "f32").view(np.uint32)
+    elif dist == "zipf":
+        keys = synth.keys_zipf(n, seed)
+        want = np.sort(keys)
+    else:
+        keys = synth.keys_u32(dist, n, seed)
+        want = np.sort(keys)
+    sorter = pkg.BucketSorter()
+    h_in, h_out = _host_pair(keys)
+    sorter.sort_keys_host(h_in, h_out, key_type=kt)
+    sorter.sync()
+    assert np.array_equal(h_out.numpy().view(np.uint32), want)
+    assert np.array_equal(h_in.numpy().view(np.uint32), np.asarray(keys).view(np.uint32))
+    sorter.close()
+
+
+def test_host_entry_back_to_back_and_pageable():
+    """Two overlapped host sorts issued without a wait between them (the
+    second reuses the staging buffer and the copy events), then one from
+    pageable host memory, and one with BSORT_FLAG_LOW_MEMORY (no overlap)."""
+    n = (1 << 23) + 9
+    a = synth.keys_u32("uniform", n, synth.seed_for(2, 8))
+    b = synth.keys_u32("reverse", n, synth.seed_for(2, 9))
+    sorter = pkg.BucketSorter()
+    ha, oa = _host_pair(a)
+    hb, ob = _host_pair(b)
+    sorter.sort_keys_host(ha, oa)
+    sorter.sort_keys_host(hb, ob)
+    sorter.sync()
+    assert np.array_equal(oa.numpy().view(np.uint32), np.sort(a))
+    assert np.array_equal(ob.numpy().view(np.uint32), np.sort(b))
+    pa = torch.from_numpy(a.view(np.int32).copy())
+    po = torch.empty_like(pa)
+    sorter.sort_keys_host(pa, po)
+    sorter.sync()
+    assert np.array_equal(po.numpy().view(np.uint32), np.sort(a))
+    sorter.close()
+    low = pkg.BucketSorter(low_memory=True)
+    lo = torch.empty_like(pa)
+    low.sort_keys_host(pa, lo)
+    low.sync()
+    assert np.array_equal(lo.numpy().view(np.uint32), np.sort(a))
+    low.close()
+
+
 def test_workspace_too_small_is_enomem():
     cfg = pkg.bsort_config(device=0)
     ws = torch.empty(4096, dtype=torch.uint8, device="cuda")
