@@ -409,7 +409,7 @@ k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
         for (uint32_t i = lane; i < R; i += 32) s_src[warp][i] = srcb[q0 + i];
         __syncwarp();
         uint32_t j = 0;  // s_off[warp][j] <= y for every y of this lane
-        constexpr int G = 8;  // positions resolved, then loaded, at a time
+        constexpr int G = 16;  // positions resolved, then loaded, at a time
 #pragma unroll 1
         for (int k0 = 0; k0 < P; k0 += G) {
             uint32_t src[G];
