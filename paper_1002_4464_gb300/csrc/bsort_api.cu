@@ -56,7 +56,7 @@ struct Plan {
     // workspace offsets (bytes)
     uint64_t off_hdr, off_tiles_k, off_tiles_v, off_reloc_k, off_reloc_v, off_samples,
         off_rec_a, off_rec_b, off_spl, off_counts, off_offsets, off_status,
-        off_units, off_units2, off_srcb, off_blk, total;
+        off_units, off_units2, off_srcb, off_blk, off_cum, off_jr, total;
     bool relocate;  // materialise Step 8 (else fused into Step 9's load)
 };
 
@@ -424,7 +424,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
             uint32_t merges = 0;
             for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
             I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
-                            1 /*S6*/ + 1 /*S7*/ + 1 /*run index*/ + (reloc ? 1 : 0) /*S8*/ +
+                            2 /*S6*/ + 1 /*S7*/ + 1 /*run index*/ + (reloc ? 1 : 0) /*S8*/ +
                             1 /*units*/ + s9;
         }
     }
@@ -458,6 +458,9 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->off_units2 = take(P->small_chunk ? (1 + 2 * (uint64_t)I.b) * 4 : 0);
         P->off_srcb = take((uint64_t)P->n_runs * 4);
         P->off_blk = take((np + kBlockItems - 1) / kBlockItems * 4);
+        // Step 6 of 32-bit keys: cumulative counts and segment ranges
+        P->off_cum = take(P->wide ? 0 : (uint64_t)P->n_runs * 4);
+        P->off_jr = take(P->wide ? 0 : sample_index_scratch_words(I.t, I.m) * 4);
     }
     P->total = o;
     I.workspace_bytes = o;
@@ -782,10 +785,12 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     uint32_t *srcb = reinterpret_cast<uint32_t *>(ws + P.off_srcb);
     uint32_t *blk = reinterpret_cast<uint32_t *>(ws + P.off_blk);
     // Step 6
-    SEQ(launch_sample_index(tiles_k, samples, spl, I.t, I.s, I.b, I.m, counts, srcb, st),
-        "step6_sample_index");
-    // Step 7
-    SEQ(launch_scan(counts, offsets, P.n_runs, status, ticket, err, st), "step7_prefix_sum");
+    uint32_t *cum = reinterpret_cast<uint32_t *>(ws + P.off_cum);
+    uint32_t *jr = reinterpret_cast<uint32_t *>(ws + P.off_jr);
+    SEQ(launch_sample_index(tiles_k, spl, I.t, I.b, I.m, jr, cum, st), "step6_sample_index");
+    // Step 7 (also a_ij and the run starts from the cumulative counts)
+    SEQ(launch_scan_cum(cum, I.m, I.t, counts, srcb, offsets, P.n_runs, status, ticket, err, st),
+        "step7_prefix_sum");
     // Step 8: materialised, unless BSORT_FLAG_LOW_MEMORY fuses it into the
     // load of Step 9, which then gathers every unit from the runs A_ij
     GatherSrc g;

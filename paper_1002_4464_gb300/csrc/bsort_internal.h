@@ -91,11 +91,16 @@ cudaError_t launch_merge_pass(const uint64_t *src, uint64_t *dst, uint32_t n_pad
 cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint32_t b,
                                     uint64_t *spl, cudaStream_t st);
 
-// Step 6: for the b splitters, counts a_ij (bucket-major) and run starts
-// srcb[j*m + i] = i*t + c_i(j-1); s samples per sublist index the sublist.
-cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
-                                const uint64_t *spl, uint32_t t, uint32_t s, uint32_t b,
-                                uint32_t m, uint32_t *counts, uint32_t *srcb, cudaStream_t st);
+// Step 6: cum[j*m + i] = c_ij, the items of sorted sublist i at or below
+// splitter j (bucket-major); jr: m * max(1, t / 8192) words of scratch.
+cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *spl, uint32_t t,
+                                uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
+                                cudaStream_t st);
+// Number of scratch words launch_sample_index needs for m sublists of t.
+inline uint64_t sample_index_scratch_words(uint32_t t, uint32_t m)
+{
+    return (uint64_t)m * (t > 8192u ? t / 8192u : 1u);
+}
 
 // Step 7: exclusive scan of n_items uint32 counts (decoupled look-back);
 // status must hold ceil(n_items / kScanChunk) words and ticket one word,
@@ -103,6 +108,13 @@ cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples
 cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
                         unsigned long long *status, uint32_t *ticket, int *err,
                         cudaStream_t st);
+// Step 7 from Step 6's cumulative counts (item e = j*m + i): counts[e] =
+// a_ij = cum[e] - cum[e - m] (0 for j = 0), srcb[e] = i*t + cum[e - m] (the
+// start of run A_ij), out = the exclusive prefix of a in bucket-major order.
+cudaError_t launch_scan_cum(const uint32_t *cum, uint32_t m, uint32_t t, uint32_t *counts,
+                            uint32_t *srcb, uint32_t *out, uint32_t n_items,
+                            unsigned long long *status, uint32_t *ticket, int *err,
+                            cudaStream_t st);
 
 constexpr int kRelocateSmemMax = 220 * 1024;
 constexpr int kRelocPart = 8192;  // sublist items per Step-8 CTA

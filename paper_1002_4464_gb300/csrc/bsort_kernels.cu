@@ -5,7 +5,8 @@
 //   Step 4     k_records_sort      sort the s*m samples (chunks of 16K) ...
 //              k_merge_pass        ... then merge-path passes through L2
 //   Step 5     k_select_splitters  b evenly spaced sorted samples
-//   Step 6     k_sample_index      locate the b splitters in every sublist
+//   Step 6     k_seg_ranges        splitters per sublist segment ...
+//              k_sample_index_seg  ... located in the segment (shared memory)
 //   Step 7     k_scan              bucket-major exclusive scan (look-back)
 //   Step 8     k_relocate          move each run A_ij to l_ij
 //   Step 9     k_pack_units        pack consecutive buckets into Step-9 units
@@ -171,95 +172,86 @@ __global__ void k_select_splitters(const uint64_t *__restrict__ sorted, uint32_t
 }
 
 // ============================================================ Step 6
-// CTA x handles sublist i = x / gpt for a block of the b splitters; thread
-// k of it a contiguous run of jb splitters j0 .. j0+jb-1 (and j0-1 for the
-// count of the first).  The sublist's own s samples (every w-th item, sorted) index
-// the sorted sublist: q = #samples <= g_j (found by a binary search for j0,
-// then a forward walk, since q grows with j) gives c_ij in
-// [q*w, q*w + w - 1]; for w <= 64 the w items of that window (16-byte
-// aligned when w is a multiple of 4) are read with independent 16-byte
-// loads and the ones <= g_j counted, otherwise a binary search over the
-// window finds the count.  Items compare as key << 32 | (i*t + r).
+// c_ij = the number of items of sorted sublist i that are <= splitter g_j
+// (items compare as key << 32 | position, position = i*t + rank), so that
+// the run A_ij holds ranks [c_i,j-1, c_ij) of sublist i.  Every sublist is
+// cut into segments of `seg` items; splitter j belongs to the segment
+// [S, S + seg) that holds c_ij (the last segment also takes c_ij = t).
+// k_seg_ranges finds, per segment, the first splitter that belongs to it:
+// c_ij >= S exactly when g_j >= item S - 1, so it is the number of
+// splitters below item S - 1 (binary search over the b sorted splitters).
+// k_sample_index_seg then stages its segment in shared memory with
+// coalesced loads (the sublists are read from HBM once, whole) and finds
+// each of its splitters' c_ij by binary search there; it writes the
+// cumulative c_ij, which Step 7 turns into the run sizes a_ij and starts.
+// (The paper locates g_j in sublist i through the sublist's samples and a
+// w-item window; that reads one window per splitter with accesses no warp
+// can coalesce.  The counts are the same.)
+constexpr int kSegItems = 8192;
+
+__global__ void k_seg_ranges(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ spl,
+                             uint32_t t, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
+                             uint32_t *__restrict__ jr)
+{
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * nseg) return;
+    const uint32_t i = idx / nseg, k = idx % nseg;
+    uint32_t r = 0;
+    if (k > 0) {
+        const uint32_t x = i * t + k * seg - 1;  // item S - 1 of sublist i
+        const uint64_t v = ((uint64_t)tiles_k[x] << 32) | x;
+        uint32_t lo = 0, hi = b;
+        while (lo < hi) {  // splitters below v
+            const uint32_t mid = (lo + hi) >> 1;
+            if (spl[mid] < v) lo = mid + 1;
+            else hi = mid;
+        }
+        r = lo;
+    }
+    jr[idx] = r;
+}
 
 template <int T>
 __global__ void __launch_bounds__(T)
-k_sample_index(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ samples,
-               const uint64_t *__restrict__ spl, uint32_t t, uint32_t s, uint32_t b,
-               uint32_t m, uint32_t *__restrict__ counts, uint32_t *__restrict__ srcb,
-               uint32_t jb)
+k_sample_index_seg(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ spl,
+                   uint32_t t, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
+                   const uint32_t *__restrict__ jr, uint32_t *__restrict__ cum)
 {
-    const uint32_t gpt = (b + T * jb - 1) / (T * jb);  // CTAs per sublist
-    const uint32_t i = blockIdx.x / gpt;
-    const uint32_t j0 = ((blockIdx.x % gpt) * T + threadIdx.x) * jb;
-    if (j0 >= b) return;
-    const uint32_t j1 = min(j0 + jb, b);
-    const uint64_t base = (uint64_t)i * t;
-    const uint32_t w = t / s;
-    const uint64_t *smp = samples + (uint64_t)i * s;
-    // q for the first splitter considered (j0 - 1, or j0 when j0 = 0)
-    const uint32_t jf = j0 ? j0 - 1 : 0;
-    uint64_t g = spl[jf];
-    uint32_t lo = 0, hi = s;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (smp[mid] <= g) lo = mid + 1;
-        else hi = mid;
+    static_assert(kSegItems % (4 * T) == 0, "whole uint4 loads per thread");
+    __shared__ __align__(16) uint32_t sk[kSegItems];
+    const uint32_t i = blockIdx.x / nseg, k = blockIdx.x % nseg;
+    const uint32_t S = k * seg;
+    const uint32_t p0 = i * t + S;  // position of the segment's first item
+    const uint32_t j_lo = jr[blockIdx.x];
+    const uint32_t j_hi = k + 1 < nseg ? jr[blockIdx.x + 1] : b;
+    const uint4 *src = reinterpret_cast<const uint4 *>(tiles_k + p0);
+    uint4 *dst = reinterpret_cast<uint4 *>(sk);
+    // every load of the segment is issued before the first store, so the
+    // CTA waits for HBM once
+    constexpr int Q = kSegItems / 4 / T;
+    uint4 r[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const uint32_t v = (uint32_t)(q * T) + threadIdx.x;
+        if (v < seg / 4) r[q] = src[v];
     }
-    uint32_t q = lo;
-    // windows of up to 32 items (16-byte aligned) stay in registers while
-    // consecutive splitters fall into the same one (about b/s of them do)
-    constexpr int kWin4 = 8;
-    const bool cached = w <= 4u * kWin4 && (w & 3) == 0;
-    uint4 win[kWin4];
-    uint32_t wq = 0xFFFFFFFFu;
-    auto count_le = [&](uint32_t qq, uint64_t gg) -> uint32_t {
-        if (!cached) return window_count(tiles_k, base, qq, w, t, s, gg);
-        if (qq >= s) return t;
-        const uint32_t r0 = qq * w;
-        if (qq != wq) {
-            const uint4 *p = reinterpret_cast<const uint4 *>(tiles_k + base + r0);
 #pragma unroll
-            for (int v = 0; v < kWin4; ++v)
-                if ((uint32_t)v < w / 4) win[v] = p[v];
-            wq = qq;
+    for (int q = 0; q < Q; ++q) {
+        const uint32_t v = (uint32_t)(q * T) + threadIdx.x;
+        if (v < seg / 4) dst[v] = r[q];
+    }
+    __syncthreads();
+    for (uint32_t j = j_lo + threadIdx.x; j < j_hi; j += T) {
+        const uint64_t g = spl[j];
+        const uint32_t gk = (uint32_t)(g >> 32), gp = (uint32_t)g;
+        uint32_t lo = 0, hi = seg;
+        while (lo < hi) {  // segment items <= g
+            const uint32_t mid = (lo + hi) >> 1;
+            const uint32_t key = sk[mid];
+            if (key < gk || (key == gk && p0 + mid <= gp)) lo = mid + 1;
+            else hi = mid;
         }
-        const uint32_t gk = (uint32_t)(gg >> 32), gp = (uint32_t)gg;
-        const uint32_t pos0 = (uint32_t)(base + r0);
-        uint32_t cnt = 0;
-#pragma unroll
-        for (int v = 0; v < kWin4; ++v) {
-            if ((uint32_t)v >= w / 4) break;
-            const uint4 x = win[v];
-            const uint32_t pos = pos0 + 4u * (uint32_t)v;
-            cnt += (x.x < gk || (x.x == gk && pos + 0 <= gp)) ? 1u : 0u;
-            cnt += (x.y < gk || (x.y == gk && pos + 1 <= gp)) ? 1u : 0u;
-            cnt += (x.z < gk || (x.z == gk && pos + 2 <= gp)) ? 1u : 0u;
-            cnt += (x.w < gk || (x.w == gk && pos + 3 <= gp)) ? 1u : 0u;
-        }
-        return r0 + cnt;
-    };
-    uint32_t prev = j0 ? count_le(q, g) : 0u;
-    for (uint32_t j = j0; j < j1; ++j) {
-        g = spl[j];
-        if (q < s && smp[q] <= g) {  // q grows: gallop, then binary search
-            uint32_t step = 1, lo2 = q + 1, hi2 = q + 1;
-            while (hi2 < s && smp[hi2] <= g) {
-                lo2 = hi2 + 1;
-                step <<= 1;
-                hi2 = min(s, q + step);
-            }
-            hi2 = min(hi2, s);
-            while (lo2 < hi2) {  // first index in [lo2, hi2) with smp > g
-                const uint32_t mid = (lo2 + hi2) >> 1;
-                if (smp[mid] <= g) lo2 = mid + 1;
-                else hi2 = mid;
-            }
-            q = lo2;
-        }
-        const uint32_t c = count_le(q, g);
-        counts[(uint64_t)j * m + i] = c - prev;
-        srcb[(uint64_t)j * m + i] = (uint32_t)base + prev;  // A_ij starts at rank c_i(j-1)
-        prev = c;
+        cum[(uint64_t)j * m + i] = S + lo;
     }
 }
 
@@ -277,23 +269,57 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
 template <int T, int ITEMS>
 __global__ void __launch_bounds__(T)
 k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_items,
-       unsigned long long *status, uint32_t *ticket, int *err)
+       unsigned long long *status, uint32_t *ticket, int *err, const uint32_t *__restrict__ cum,
+       uint32_t m, uint32_t t, uint32_t *__restrict__ counts, uint32_t *__restrict__ srcb)
 {
     __shared__ uint32_t s_chunk;
     __shared__ uint32_t s_warp[T / 32];
     __shared__ uint32_t s_prefix;
     __shared__ uint32_t s_last;
+    // the chunk's items, staged so that global loads and stores are
+    // coalesced while each thread scans ITEMS consecutive items (padded:
+    // one spare word per 32, so the per-thread runs hit distinct banks)
+    __shared__ uint32_t s_items[T * ITEMS + T * ITEMS / 32];
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (tid == 0) s_chunk = atomicAdd(ticket, 1u);
     __syncthreads();
     const uint32_t chunk = s_chunk;
-    const uint64_t base = (uint64_t)chunk * (T * ITEMS) + (uint64_t)tid * ITEMS;
+    const uint64_t cbase = (uint64_t)chunk * (T * ITEMS);
+    auto spad = [](int x) { return x + (x >> 5); };
+    if (cum == nullptr) {
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const uint64_t e = cbase + (uint64_t)(k * T + tid);
+            s_items[spad(k * T + tid)] = e < n_items ? in[e] : 0u;
+        }
+    } else {
+        // item e = j*m + i from the cumulative counts of Step 6:
+        // a_ij = c_ij - c_i,j-1 and A_ij starts at position i*t + c_i,j-1
+        uint32_t i = (uint32_t)((cbase + (uint64_t)tid) % m);
+        const uint32_t di = (uint32_t)T % m;
+#pragma unroll
+        for (int k = 0; k < ITEMS; ++k) {
+            const uint64_t e = cbase + (uint64_t)(k * T + tid);
+            uint32_t a = 0u;
+            if (e < n_items) {
+                const uint32_t c = cum[e];
+                const uint32_t p = e >= m ? cum[e - m] : 0u;
+                a = c - p;
+                counts[e] = a;
+                srcb[e] = i * t + p;
+            }
+            s_items[spad(k * T + tid)] = a;
+            i += di;
+            if (i >= m) i -= m;
+        }
+    }
+    __syncthreads();
     uint32_t x[ITEMS];
     uint32_t sum = 0;
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-        x[k] = (base + k < n_items) ? in[base + k] : 0u;
+        x[k] = s_items[spad(tid * ITEMS + k)];
         sum += x[k];
     }
     // block-wide exclusive scan of the per-thread sums
@@ -363,8 +389,14 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
     uint32_t run = s_prefix + s_warp[warp] + (incl - sum);
 #pragma unroll
     for (int k = 0; k < ITEMS; ++k) {
-        if (base + k < n_items) out[base + k] = run;
+        s_items[spad(tid * ITEMS + k)] = run;
         run += x[k];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+        const uint64_t e = cbase + (uint64_t)(k * T + tid);
+        if (e < n_items) out[e] = s_items[spad(k * T + tid)];
     }
 }
 
@@ -676,15 +708,17 @@ cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint
     return cudaGetLastError();
 }
 
-cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *samples,
-                                const uint64_t *spl, uint32_t t, uint32_t s, uint32_t b,
-                                uint32_t m, uint32_t *counts, uint32_t *srcb, cudaStream_t st)
+cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *spl, uint32_t t,
+                                uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
+                                cudaStream_t st)
 {
-    constexpr int T = 128;
-    const uint32_t jb = b >= 8 * T ? 8 : (b + T - 1) / T;  // splitters per thread
-    const uint32_t gpt = (b + T * jb - 1) / (T * jb);
-    k_sample_index<T><<<m * gpt, T, 0, st>>>(tiles_k, samples, spl, t, s, b, m, counts, srcb,
-                                             jb);
+    const uint32_t seg = t < (uint32_t)kSegItems ? t : (uint32_t)kSegItems;
+    const uint32_t nseg = t / seg;
+    const uint32_t ns = m * nseg;
+    k_seg_ranges<<<(ns + 255) / 256, 256, 0, st>>>(tiles_k, spl, t, b, m, nseg, seg, jr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sample_index_seg<256><<<ns, 256, 0, st>>>(tiles_k, spl, t, b, m, nseg, seg, jr, cum);
     return cudaGetLastError();
 }
 
@@ -692,7 +726,19 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
                         unsigned long long *status, uint32_t *ticket, int *err, cudaStream_t st)
 {
     const uint32_t chunks = (n_items + kScanChunk - 1) / kScanChunk;
-    k_scan<256, 16><<<chunks, 256, 0, st>>>(in, out, n_items, status, ticket, err);
+    k_scan<256, 16><<<chunks, 256, 0, st>>>(in, out, n_items, status, ticket, err, nullptr, 1u,
+                                            0u, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_cum(const uint32_t *cum, uint32_t m, uint32_t t, uint32_t *counts,
+                            uint32_t *srcb, uint32_t *out, uint32_t n_items,
+                            unsigned long long *status, uint32_t *ticket, int *err,
+                            cudaStream_t st)
+{
+    const uint32_t chunks = (n_items + kScanChunk - 1) / kScanChunk;
+    k_scan<256, 16><<<chunks, 256, 0, st>>>(nullptr, out, n_items, status, ticket, err, cum, m,
+                                            t, counts, srcb);
     return cudaGetLastError();
 }
 
