@@ -408,11 +408,16 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 // (y - offsets[q]) of the sorted sublists.  Each warp covers kBlockItems
 // consecutive positions, its lanes on consecutive positions (coalesced
 // stores).  The runs meeting a warp's block are blk[b] .. blk[b+1] (the run
-// index); when they are few (the usual case) the warp stages their offsets
-// and starts in shared memory, every lane resolves the sources of all its
-// positions there, and then issues all its loads at once; otherwise each
-// lane walks the runs in global memory (skipping stretches of empty runs by
-// a search bounded by the run index).
+// index); when they are few (the usual case) the warp stages them in shared
+// memory as a list of the non-empty runs in order, each as the difference
+// srcb - offsets (so that position y of the run comes from that + y), and
+// a bitmap of the block with a bit at every run start after the first:
+// the run of position y is then the number of bits set up to y (one
+// population count and a prefix over the bitmap's words, held one word per
+// lane), with no per-position walk; a lane resolves sixteen positions and
+// then issues their loads together.  Otherwise each lane walks the runs in
+// global memory (skipping stretches of empty runs by a search bounded by
+// the run index).
 constexpr int kRelocRunsCap = 256;  // runs a warp stages in shared memory
 
 template <int T, typename KT>
@@ -426,7 +431,8 @@ k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
     constexpr int W = T / 32;
     constexpr int P = kBlockItems / 32;  // positions per lane
     __shared__ uint32_t s_off[W][kRelocRunsCap + 1];
-    __shared__ uint32_t s_src[W][kRelocRunsCap];
+    __shared__ uint32_t s_src[W][kRelocRunsCap];  // then: srcb - offsets of the non-empty runs
+    __shared__ uint32_t s_bm[W][32];              // run starts in the warp's block
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t wy = blockIdx.x * (uint32_t)kRelocPart + (uint32_t)warp * kBlockItems;
     if (wy >= n_pad) return;  // whole warp
@@ -437,19 +443,61 @@ k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
     const uint32_t yend = min(wy + (uint32_t)kBlockItems, n_pad);
     if (q1 - q0 < (uint32_t)kRelocRunsCap) {
         const uint32_t R = q1 - q0 + 1;  // runs q0 .. q1; offsets[q1 + 1] exists
-        for (uint32_t i = lane; i <= R; i += 32) s_off[warp][i] = offsets[q0 + i];
-        for (uint32_t i = lane; i < R; i += 32) s_src[warp][i] = srcb[q0 + i];
+        uint32_t *so = s_off[warp];
+        uint32_t *sd = s_src[warp];
+        for (uint32_t i = lane; i <= R; i += 32) so[i] = offsets[q0 + i];
+        for (uint32_t i = lane; i < R; i += 32) sd[i] = srcb[q0 + i];
         __syncwarp();
-        uint32_t j = 0;  // s_off[warp][j] <= y for every y of this lane
+        // run q0 holds wy; a later run counts if it is non-empty and starts
+        // inside the block.  Compact them in order (in place: entry k of
+        // the list is written at or below the entry it comes from) and set
+        // the bitmap bit of each start.
+        uint32_t *bm = s_bm[warp];
+        bm[lane] = 0u;
+        __syncwarp();
+        const uint32_t lt = (1u << lane) - 1u;
+        uint32_t nk = 0;
+        for (uint32_t r0 = 0; r0 < R; r0 += 32) {
+            const uint32_t r = r0 + lane;
+            uint32_t st = 0, d = 0;
+            bool keep = false;
+            if (r < R) {
+                st = so[r];
+                d = sd[r] - st;
+                keep = r == 0 || (so[r + 1] > st && st < yend);
+            }
+            const unsigned kb = __ballot_sync(0xFFFFFFFFu, keep);
+            __syncwarp();  // every entry of this round is read before any is rewritten
+            if (keep) {
+                sd[nk + (uint32_t)__popc(kb & lt)] = d;
+                if (r > 0) atomicOr(&bm[(st - wy) >> 5], 1u << ((st - wy) & 31u));
+            }
+            nk += (uint32_t)__popc(kb);
+            __syncwarp();  // this round's writes land before the next round's reads
+        }
+        const uint32_t word = bm[lane];  // lane w holds bitmap word w
+        // runs before word w: exclusive prefix of the words' bit counts
+        const uint32_t cnt = (uint32_t)__popc(word);
+        uint32_t pre = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, pre, o);
+            if (lane >= o) pre += y;
+        }
+        pre -= cnt;
+        const uint32_t upto = lane == 31 ? 0xFFFFFFFFu : (2u << lane) - 1u;  // bits 0 .. lane
         constexpr int G = 16;  // positions resolved, then loaded, at a time
 #pragma unroll 1
         for (int k0 = 0; k0 < P; k0 += G) {
             uint32_t src[G];
 #pragma unroll
             for (int k = 0; k < G; ++k) {
+                // position y = wy + 32 (k0 + k) + lane is bit `lane` of word k0 + k
+                const uint32_t wk = __shfl_sync(0xFFFFFFFFu, word, k0 + k);
+                const uint32_t pk = __shfl_sync(0xFFFFFFFFu, pre, k0 + k);
+                const uint32_t idx = pk + (uint32_t)__popc(wk & upto);
                 const uint32_t y = wy + (uint32_t)lane + 32u * (uint32_t)(k0 + k);
-                while (j + 1 < R && s_off[warp][j + 1] <= y) ++j;
-                src[k] = s_src[warp][j] + (y - s_off[warp][j]);
+                src[k] = sd[idx] + y;
             }
             KT v[G];
 #pragma unroll
