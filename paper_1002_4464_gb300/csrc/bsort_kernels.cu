@@ -37,12 +37,19 @@ k_records_sort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uin
     const int lane = tid & 31, warp = tid >> 5;
     const uint64_t base = (uint64_t)blockIdx.x * CAP;
     if (s >= 32u * E && s < (uint32_t)CAP) {
-        for (int x = tid; x < CAP; x += T) {
-            const uint64_t g = base + x;
-            const uint64_t r = g < n_rec ? src[g] : 0xFFFFFFFFFFFFFFFFull;
+        // all E loads of a thread are issued before its first store
+        uint64_t r[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const uint64_t g = base + (uint64_t)(k * T + tid);
+            r[k] = g < n_rec ? src[g] : 0xFFFFFFFFFFFFFFFFull;
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int x = k * T + tid;
             const int q = x / (int)s, o = x % (int)s;
             const int pos = (q & 1) ? q * (int)s + (int)s - 1 - o : x;
-            sm[pidx<uint64_t>(pos)] = r;
+            sm[pidx<uint64_t>(pos)] = r[k];
         }
         __syncthreads();
         cta_merge_runs<uint64_t, T, E>(sm, (int)s);
@@ -117,7 +124,7 @@ __device__ __forceinline__ uint32_t merge_path_warp(const uint64_t *A, uint32_t 
 // the input ranges of its outputs by merge path in global memory, stages
 // them in SMEM, merges per thread, and writes back through SMEM.
 template <int T, int E>
-__global__ void __launch_bounds__(T)
+__global__ void __launch_bounds__(T, 4)
 k_merge_pass(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uint32_t n_pad,
              uint32_t L)
 {
@@ -141,10 +148,24 @@ k_merge_pass(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uint3
     const uint32_t i0 = s_split[0], i1 = s_split[1];
     const uint32_t j0 = d0 - i0, j1 = d1 - i1;
     const int na = (int)(i1 - i0), nb = (int)(j1 - j0);
-    for (int x = tid; x < na; x += T) sm[pidx<uint64_t>(x)] = src[a0 + i0 + x];
-    for (int x = tid; x < nb; x += T) sm[pidx<uint64_t>(na + x)] = src[b0 + j0 + x];
+    const int cnt = na + nb;  // <= TILE = T*E
+    {
+        // all E loads of a thread are issued before its first store
+        uint64_t r[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int x = k * T + tid;
+            r[k] = 0;
+            if (x < na) r[k] = src[a0 + i0 + x];
+            else if (x < cnt) r[k] = src[b0 + j0 + (x - na)];
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int x = k * T + tid;
+            if (x < cnt) sm[pidx<uint64_t>(x)] = r[k];
+        }
+    }
     __syncthreads();
-    const int cnt = na + nb;
     const int d = tid * E;
     uint64_t v[E];
     if (d < cnt) {
