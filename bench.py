@@ -76,6 +76,9 @@ def _args():
     p.add_argument("--dist", default="uniform")
     p.add_argument("--key-type", default="u32", choices=["u32", "f32", "u64"],
                    help="u64: uniform 64-bit keys (the --dist option is ignored)")
+    p.add_argument("--pairs", action="store_true",
+                   help="key-value pairs: uint32 keys with uint32 values = original index "
+                        "(bsort_sort_pairs); e2e is not taken")
     p.add_argument("--dists", action="store_true",
                    help="also time every distribution (spread across distributions)")
     p.add_argument("--e2e-steps", type=int, default=3)
@@ -232,13 +235,15 @@ def _sample_keys(args, rank, count):
 
 
 def _kb(args):
-    """Key bytes of the workload."""
-    return 8 if args.key_type == "u64" else 4
+    """Bytes per item of the workload (key, plus the value of a pair)."""
+    return 8 if args.key_type == "u64" or getattr(args, "pairs", False) else 4
 
 
 def _dist_index(name):
     import synth
-    return synth.DISTRIBUTIONS.index(name)
+    if name in synth.DISTRIBUTIONS:
+        return synth.DISTRIBUTIONS.index(name)
+    return len(synth.DISTRIBUTIONS) + ("zipf", "16distinct").index(name)
 
 
 def job_time_ms(local_ms, world, device):
@@ -291,9 +296,12 @@ def run_reference(args):
 
 
 def _config(args, world):
-    return {"workload": "%s %s keys-only sort, n=2^%d per GPU" % (
-                args.dist, args.key_type, max(args.n.bit_length() - 1, 0)) if args.n & (args.n - 1) == 0
-            else "%s %s keys-only sort, n=%d per GPU" % (args.dist, args.key_type, args.n),
+    what = ("key-value (uint32 value = original index) sort" if getattr(args, "pairs", False)
+            else "keys-only sort")
+    return {"workload": "%s %s %s, n=2^%d per GPU" % (
+                args.dist, args.key_type, what, max(args.n.bit_length() - 1, 0))
+            if args.n & (args.n - 1) == 0
+            else "%s %s %s, n=%d per GPU" % (args.dist, args.key_type, what, args.n),
             "n": args.n, "key_type": args.key_type, "distribution": args.dist,
             "global_keys": args.n * world, "parallelism": "replicas x%d" % world,
             "l2_policy": "input (%d MB) larger than the 129 MB L2; no flush" % (args.n * _kb(args) >> 20)
@@ -316,21 +324,31 @@ def run_ours(args):
 
     def make_keys(dname):
         seed = synth.seed_for(2, _dist_index(dname), rank)
+        if dname in ("zipf", "16distinct"):  # heavy-duplicate uint32 keys
+            kn = synth.keys_zipf(args.n, seed) if dname == "zipf" else synth.keys_16distinct(args.n, seed)
+            return torch.from_numpy(kn.view(np.int32)).to(dev)
         if args.key_type == "f32":
             return synth.keys_f32_torch(dname, args.n, seed, device=dev)
         if args.key_type == "u64":
             return synth.draws64_torch(seed, args.n, device=dev)
         return synth.keys_u32_torch(dname, args.n, seed, device=dev)
 
+    if args.pairs and args.key_type != "u32":
+        raise SystemExit("--pairs takes uint32 keys")
     keys = make_keys(args.dist)
     out = torch.empty_like(keys)
+    vals = torch.arange(args.n, dtype=torch.int32, device=dev) if args.pairs else None
+    out_v = torch.empty_like(vals) if args.pairs else None
     sorter = pkg.BucketSorter(device=local, timing=True, tile=args.tile, samples=args.samples,
                               buckets=args.buckets)
     plan = sorter.plan(args.n, args.key_type)
     stream = torch.cuda.current_stream(dev)
 
     def one_step(k_in):
-        sorter.sort_keys(k_in, out=out, key_type=args.key_type)
+        if args.pairs:
+            sorter.sort_pairs(k_in, vals, out_keys=out, out_vals=out_v)
+        else:
+            sorter.sort_keys(k_in, out=out, key_type=args.key_type)
 
     for _ in range(max(args.warmup, 3)):
         one_step(keys)
@@ -342,6 +360,11 @@ def run_ours(args):
         kin = keys.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
         assert int(kin.sum()) == int(o.sum()), "multiset changed"
         del kin
+        if args.pairs:  # stable: equal keys keep their original order (value = index)
+            same = o[1:] == o[:-1]
+            assert bool((out_v[1:][same] > out_v[:-1][same]).all()), "not stable"
+            assert bool((keys[out_v.long()] == out).all()), "values do not follow keys"
+            del same
     if args.key_type == "u64":  # unsigned order = signed order with the top bit flipped
         o = out ^ torch.tensor(-(1 << 63), dtype=torch.int64, device=dev)
         assert bool((o[1:] >= o[:-1]).all()), "output not sorted"
@@ -413,7 +436,7 @@ def run_ours(args):
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     e2e = None
-    if args.e2e_steps > 0:
+    if args.e2e_steps > 0 and not args.pairs:
         h_in = keys.cpu().pin_memory()
         h_out = torch.empty_like(h_in).pin_memory()
         sorter.sort_keys_host(h_in, h_out, key_type=args.key_type)  # warm-up (workspace)
@@ -437,7 +460,7 @@ def run_ours(args):
     dists = None
     if args.dists:
         dists = {}
-        for dname in synth.DISTRIBUTIONS:
+        for dname in (("uniform", "zipf", "16distinct") if args.pairs else synth.DISTRIBUTIONS):
             kd = make_keys(dname)
             for _ in range(3):
                 one_step(kd)
@@ -481,11 +504,12 @@ def run_ours(args):
             t_spent += dt
         cpu = {"value": statistics.median(rates), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "first %d keys of this workload, %d repetitions, Algorithm 1 with "
-                         "t=%d, s=%d, single-threaded C (host has %d cores)"
-                         % (sample_n, len(rates), t_o, s_o, _cpu_cores())}
+                         "t=%d, s=%d, single-threaded C (host has %d cores)%s"
+                         % (sample_n, len(rates), t_o, s_o, _cpu_cores(),
+                            ", keys only" if args.pairs else "")}
 
     sorter.close()
-    del keys, out
+    del keys, out, vals, out_v
     batched = run_batched(args, pkg, synth, dev, stream, rank, world) if args.batch_arrays else None
     served = run_served(args, pkg, synth, dev, rank) if args.serve_seconds > 0 else None
 
@@ -494,7 +518,8 @@ def run_ours(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": args.key_type, "data": "synthetic (SplitMix64 %s keys)" % args.dist,
+            "dtype": args.key_type + ("+u32" if args.pairs else ""),
+            "data": "synthetic (SplitMix64 %s keys)" % args.dist,
             "config": _config(args, world), "roofline": roofline, "cpu_baseline": cpu,
             "e2e": e2e, "gpu_launches": plan.num_kernels * args.steps,
             "clocks": clk, "per_kernel_ms": per_kernel,

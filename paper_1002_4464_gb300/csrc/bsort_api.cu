@@ -237,27 +237,35 @@ bool tile_shape(uint64_t t, bool pairs, int *chunk, int *ctas)
 
 double log2d(double x) { return x > 1 ? __builtin_log2(x) : 0.0; }
 
-// Modelled cost of a plan, in units of one single-CTA sort pass over the
-// items (32K-key chunks).  The factors are measured on GB300 at n = 2^28
-// uint32 keys: a Step-2 sublist sorted by a cluster of 2 / 4 / 8 CTAs costs
-// 1.32 / 1.76 / 2.6 passes (distributed-shared-memory merge rounds; 8-CTA
-// clusters also leave SMs idle); Step 9 costs 1.1 passes with one-CTA
-// units (one tier of one CTA, or two tiers) and 1.65 / 2.1 / 3.1 with
-// cluster units (rounds plus unit fill); Step 4 costs 7 passes per sample
-// per key and Step 6 3.9 per run A_ij (m*b of them); Step 8 0.3-0.35.
+// Modelled cost of a plan, in units of about 8.1 ps (one unit per key is
+// one single-CTA sort pass over 32K-key chunks).  The factors are measured
+// on GB300 at n = 2^28 uint32 keys: a Step-2 sublist sorted by one CTA or
+// a cluster of 2 / 4 / 8 CTAs costs 1.04 / 1.29 / 1.75 / 2.6 passes
+// (distributed-shared-memory merge rounds; 8-CTA clusters also leave SMs
+// idle); Step 9 costs 1.1 passes with one-CTA units (one tier of one CTA,
+// or two tiers) and 1.65 / 2.1 / 3.1 with cluster units (rounds plus unit
+// fill).  Step 4 costs 6.8 units per sample; Steps 6-8 0.325 per key plus
+// 1.85 per run A_ij (m*b of them), and 4 more per run when a 1024-position
+// block of the relocation meets more runs than it stages (more than ~200
+// on average).  64-bit keys keep the sample-window Step 6 (3.9 per run).
 double plan_cost(uint64_t np, uint64_t s, uint64_t runs, int tchunk, int tctas, int uchunk,
-                 int uctas)
+                 int uctas, bool wide)
 {
     const double n = (double)np;
-    auto f1 = [](int c) { return c == 1 ? 1.0 : c == 2 ? 1.32 : c == 4 ? 1.76 : 2.6; };
+    auto f1 = [](int c) { return c == 1 ? 1.04 : c == 2 ? 1.29 : c == 4 ? 1.75 : 2.6; };
     auto f9 = [](int c) { return c == 1 ? 1.1 : c == 2 ? 1.65 : c == 4 ? 2.1 : 3.1; };
     const double chunk_levels = log2d(tchunk) / 15.0;  // smaller chunks sort faster
     const double unit_levels = log2d(uchunk) / 15.0;
     const double t = (double)tchunk * tctas;
     const double w = t / (double)s;
     const double samples = n / w;
-    return n * (f1(tctas) * chunk_levels + f9(uctas) * unit_levels + (w >= 32 ? 0.3 : 0.35)) +
-           7.0 * samples + 3.9 * (double)runs;
+    const double r = (double)runs;
+    if (wide)
+        return n * (f1(tctas) * chunk_levels + f9(uctas) * unit_levels + (w >= 32 ? 0.3 : 0.35)) +
+               7.0 * samples + 3.9 * r;
+    const double per_run = 1.85 + (1024.0 * r > 200.0 * n ? 4.0 : 0.0);
+    return n * (f1(tctas) * chunk_levels + f9(uctas) * unit_levels + 0.325) + 6.8 * samples +
+           per_run * r;
 }
 
 bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P)
@@ -306,6 +314,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         // candidates: forced t or every sublist shape; forced s or every
         // power of two with w = t/s >= 16 and s <= kMaxSamples.  The unit is
         // sized for b = s (or the forced b); the bucket count is chosen after.
+        const bool wide = kt == BSORT_U64;
         double best = -1.0;
         uint64_t bt = 0, bs = 0;
         int btc = 0, btk = 0, buc = 0, buk = 0;
@@ -337,8 +346,8 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
                 const uint64_t b_est = forced_b ? forced_b : forced_s ? sv
                                        : tiers ? b2 : (21 * np + 10ull * uc * uk - 1) / (10ull * uc * uk);
                 // (the cluster tier's launch costs ~40 us even when nearly empty)
-                const double c = tiers ? plan_cost(np, sv, m * b_est, tc, tk, cm, 1) + 5e6
-                                       : plan_cost(np, sv, m * b_est, tc, tk, uc, uk);
+                const double c = tiers ? plan_cost(np, sv, m * b_est, tc, tk, cm, 1, wide) + 5e6
+                                       : plan_cost(np, sv, m * b_est, tc, tk, uc, uk, wide);
                 if (best < 0 || c < best) {
                     best = c;
                     bt = t; bs = sv; btc = tc; btk = tk; buc = uc; buk = uk;

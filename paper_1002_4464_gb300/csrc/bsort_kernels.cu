@@ -629,9 +629,22 @@ k_pack_units(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t b, uint3
     __shared__ uint32_t s_warp[T / 32];
     __shared__ uint32_t s_total[2];
     const int tid = threadIdx.x;
-    for (uint32_t j = tid; j <= b; j += T) {
-        Lb[j] = j < b ? offsets[(uint64_t)j * m] : n_pad;
-        on[j] = j == 0 ? 1u : 0u;
+    // bucket starts (one strided load each): four loads in flight per thread
+    for (uint32_t j0 = tid; j0 <= b; j0 += 4 * T) {
+        uint32_t l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = j0 + (uint32_t)u * T;
+            l[u] = j < b ? offsets[(uint64_t)j * m] : n_pad;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = j0 + (uint32_t)u * T;
+            if (j <= b) {
+                Lb[j] = l[u];
+                on[j] = j == 0 ? 1u : 0u;
+            }
+        }
     }
     __syncthreads();
     // largest e in [j+1, b] with Lb[e] - Lb[j] <= Q1, else j + 1
