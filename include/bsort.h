@@ -278,11 +278,12 @@ bsort_status bsort_plan_batch(bsort_t h, bsort_key_type kt, const uint64_t *seg_
  * (the copies are part of the call; h_keys_out is complete once the work
  * issued on cuda_stream so far has finished).  Pinned host memory gives
  * asynchronous copies.  For 32-bit keys over several sublists the copies
- * overlap the sort: the keys go in as 16 chunks of whole sublists, Steps 1-3
- * starting on each chunk once it has arrived, and Step 9 runs in 16 groups
- * of units by output position, each group's slice of h_keys_out copied out
- * while the next group sorts (on a copy stream of the handle, ordered
- * against cuda_stream by events).  Uses extra workspace: the device copy of
+ * overlap the sort from 2^23 keys on: the keys go in as chunks of whole
+ * sublists (one per 8 MiB, at most 16), Steps 1-3 starting on each chunk
+ * once it has arrived, and Step 9 runs in as many groups of units by output
+ * position, each group's slice of h_keys_out copied out while the next
+ * group sorts (on a copy stream of the handle, ordered against cuda_stream
+ * by events).  Uses extra workspace: the device copy of
  * the keys (n * key bytes, rounded up to 256) plus 256 bytes. */
 bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_keys_in,
                                   void *h_keys_out, uint64_t n, void *cuda_stream);

@@ -573,9 +573,9 @@ struct Seq {
     } while (0)
 
 // Host buffers of bsort_sort_keys_host, overlapped with the sort: the keys
-// arrive in kPipe chunks of whole sublists and Steps 1-3 start on each chunk
-// once it is on the device; Step 9 runs in kPipe groups, group g sorting the
-// units that begin in position slice [g n'/kPipe, (g+1) n'/kPipe), and that
+// arrive in G chunks of whole sublists and Steps 1-3 start on each chunk
+// once it is on the device; Step 9 runs in G groups, group g sorting the
+// units that begin in position slice [g n'/G, (g+1) n'/G), and that
 // slice goes back to the host while the next group sorts (every position of
 // the slice lies in a unit that begins at or before it).  Copies run on the
 // handle's copy stream, ordered against the caller's stream by events.
@@ -584,7 +584,18 @@ struct HostPipe {
     void *h_out;
     void *d_keys;      // device staging of the keys (the sort runs in place)
     uint32_t *ranges;  // device: 2 (kPipe + 1) unit indices
+    int groups;        // chunks in and slices out, at most kPipe
 };
+
+// Chunks of the overlapped host entry for n 32-bit keys: one per 8 MiB of
+// keys, at most kPipe; 0 below 32 MiB, where the copies are too short for
+// the extra calls (about a hundred) to pay.
+int host_pipe_groups(uint64_t n)
+{
+    const uint64_t g = n * 4 / (8ull << 20);
+    if (g < 4) return 0;
+    return g > (uint64_t)kPipe ? kPipe : (int)g;
+}
 
 bsort_status ensure_pipe(bsort_t h)
 {
@@ -752,7 +763,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
         // chunk c: copy its sublists' keys in, then sort them
         e = stream_after(h->xfer, st, h->xev[2 * kPipe]);
         if (e != cudaSuccess) return cuda_fail(h, e, "order copy stream");
-        const uint32_t per = (I.m + kPipe - 1) / kPipe;
+        const uint32_t per = (I.m + hp->groups - 1) / hp->groups;
         for (uint32_t t0 = 0, c = 0; t0 < I.m; t0 += per, ++c) {
             const uint32_t mc = std::min(per, I.m - t0);
             const uint64_t p0 = (uint64_t)t0 * I.t;
@@ -832,15 +843,16 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
         // slice's keys to the host
         const uint32_t np = (uint32_t)I.n_padded;
         uint32_t *r1 = hp->ranges, *r2 = hp->ranges + kPipe + 1;
-        SEQ(launch_unit_ranges(units, np, kPipe, r1, st), "step9_unit_ranges");
-        if (units2) SEQ(launch_unit_ranges(units2, np, kPipe, r2, st), "step9_unit_ranges");
+        const int G = hp->groups;
+        SEQ(launch_unit_ranges(units, np, (uint32_t)G, r1, st), "step9_unit_ranges");
+        if (units2) SEQ(launch_unit_ranges(units2, np, (uint32_t)G, r2, st), "step9_unit_ranges");
         // resident CTAs (clusters: 7/8 of the SMs can hold them) loop over
         // the group's units, none of them in a late wave
         const int sms = std::max(h->num_sms, 8);
         const uint32_t g1 = std::max(
             1u, std::min<uint32_t>(I.b, (uint32_t)(k1 == 1 ? sms : (sms * 7 / 8) / k1)));
         const uint32_t g2 = std::max(1u, (uint32_t)((sms * 7 / 8) / (int)I.unit_ctas));
-        for (int g = 0; g < kPipe; ++g) {
+        for (int g = 0; g < G; ++g) {
             SEQ(launch_bucket_sort_keys_range(c1, k1, s9k, units, r1 + g, g1, n, I.n_padded,
                                               is_f32, kout, err, st),
                 "step9_bucket_sort");
@@ -849,8 +861,8 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
                                                   r2 + g, g2, n, I.n_padded, is_f32, kout, err,
                                                   st),
                     "step9_bucket_sort_large");
-            const uint64_t p0 = std::min<uint64_t>((uint64_t)g * np / kPipe, n);
-            const uint64_t p1 = std::min<uint64_t>((uint64_t)(g + 1) * np / kPipe, n);
+            const uint64_t p0 = std::min<uint64_t>((uint64_t)g * np / G, n);
+            const uint64_t p1 = std::min<uint64_t>((uint64_t)(g + 1) * np / G, n);
             if (p1 > p0) {
                 e = stream_after(h->xfer, st, h->xev[kPipe + g]);
                 if (e == cudaSuccess)
@@ -1939,7 +1951,8 @@ bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_ke
     if (rs != BSORT_OK) return rs;
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     void *d_buf = static_cast<unsigned char *>(h->ws) + stage;
-    if (P.kb == 4 && !P.wide && !P.info.single_tile && P.relocate) {
+    const int groups = host_pipe_groups(n);
+    if (P.kb == 4 && !P.wide && !P.info.single_tile && P.relocate && groups > 0) {
         // several sublists: copies overlap Steps 1-3 and Step 9
         rs = ensure_workspace(h, stage + align_up(bytes) + kAlign);
         if (rs != BSORT_OK) return rs;
@@ -1952,6 +1965,7 @@ bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_ke
         hp.d_keys = d_buf;
         hp.ranges = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(h->ws) + stage +
                                                  align_up(bytes));
+        hp.groups = groups;
         return run_sort(h, kt, d_buf, nullptr, d_buf, nullptr, 0, n, st, &hp);
     }
     cudaError_t e = cudaMemcpyAsync(d_buf, h_keys_in, bytes, cudaMemcpyHostToDevice, st);

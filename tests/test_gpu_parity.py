@@ -232,9 +232,9 @@ def _host_pair(a):
 def test_host_entry_overlapped_intermediates():
     """The host entry's copies overlap Steps 1-3 (chunks of sublists) and
     Step 9 (groups of units by position): the sublists, samples, splitters,
-    counts, offsets and relocated array are still the paper's (n = 2^20,
-    t = 4096, s = 64: m = 256 sublists in 16 chunks)."""
-    n, t, s = 1 << 20, 4096, 64
+    counts, offsets and relocated array are still the paper's (n = 2^23,
+    t = 4096, s = 64: m = 2048 sublists in 4 chunks)."""
+    n, t, s = 1 << 23, 4096, 64
     keys = synth.keys_u32("bucket", n, synth.seed_for(1, 7, 3))
     want = oracle.paper_sort(keys, t, s, "u32")
     sorter = pkg.BucketSorter(tile=t, samples=s)
@@ -250,13 +250,14 @@ def test_host_entry_overlapped_intermediates():
     ((1 << 24) + 77, "uniform", "u32"),
     ((1 << 25) + 3, "zipf", "u32"),
     ((1 << 26) - 5, "zero", "u32"),
+    ((1 << 23) + 5, "gaussian", "f32"),
     (300_001, "sorted", "u32"),
     ((1 << 22) + 5, "gaussian", "f32"),
 ])
 def test_host_entry_overlapped(n, dist, kt):
-    """Overlapped host entry on ragged sizes, plans with one and two Step-9
-    tiers, fewer sublists than copy chunks, and float keys: the output equals
-    the textbook sort bit for bit."""
+    """Host entry with copies overlapped (from 2^23 keys: 4, 8 and 16 chunks;
+    ragged sizes; one and two Step-9 tiers; float keys) and not (smaller n):
+    the output equals the textbook sort bit for bit."""
     seed = synth.seed_for(2, 7, n & 0xFF)
     if kt == "f32":
         keys = synth.keys_f32(dist, n, seed)
