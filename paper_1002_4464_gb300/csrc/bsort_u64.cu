@@ -95,6 +95,111 @@ k_rec_merge(const Rec128 *__restrict__ src, Rec128 *__restrict__ dst, uint32_t N
     }
 }
 
+// The same merge by tiles, when a pair of runs spans whole tiles (2L a
+// multiple of T*E): one CTA produces T*E outputs.  A warp finds the tile's
+// co-ranks by a 32-ary search in global memory, the CTA stages its A and B
+// ranges in shared memory with coalesced loads (all issued before the first
+// store), each thread merges E outputs there, and the tile goes back
+// through shared memory with coalesced stores.
+__device__ __forceinline__ uint32_t rec_corank_warp(const Rec128 *A, uint32_t la, const Rec128 *B,
+                                                    uint32_t lb, uint32_t d, int lane)
+{
+    // i = A items among the first d outputs: the first c in [lo, hi] with
+    // B[d-1-c] < A[c] (false ... true on [lo, hi)), hi if none
+    uint32_t lo = d > lb ? d - lb : 0;
+    uint32_t hi = d < la ? d : la;
+    while (hi - lo > 32) {
+        const uint32_t span = hi - lo;
+        const uint32_t c = lo + (uint32_t)(((uint64_t)span * (lane + 1)) / 33);
+        const unsigned ball = __ballot_sync(0xFFFFFFFFu, rec_lt(B[d - 1 - c], A[c]));
+        if (ball == 0) {
+            lo = lo + (uint32_t)(((uint64_t)span * 32) / 33) + 1;
+        } else {
+            const int f = __ffs(ball) - 1;
+            const uint32_t cf = lo + (uint32_t)(((uint64_t)span * (f + 1)) / 33);
+            const uint32_t cp = f ? lo + (uint32_t)(((uint64_t)span * f) / 33) + 1 : lo;
+            lo = cp;
+            hi = cf;
+        }
+    }
+    const uint32_t c = lo + lane;
+    const bool pred = c < hi ? rec_lt(B[d - 1 - c], A[c]) : true;
+    const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
+    return ball ? lo + (uint32_t)(__ffs(ball) - 1) : hi;
+}
+
+template <int T, int E>
+__global__ void __launch_bounds__(T)
+k_rec_merge_tiled(const Rec128 *__restrict__ src, Rec128 *__restrict__ dst, uint32_t N,
+                  uint32_t L)
+{
+    constexpr int TILE = T * E;
+    __shared__ Rec128 sm[TILE];
+    __shared__ uint32_t s_split[2];
+    const int tid = threadIdx.x;
+    const uint64_t o0 = (uint64_t)blockIdx.x * TILE;
+    const uint64_t a0 = o0 / (2ull * L) * (2ull * L);
+    const uint32_t la = (uint32_t)min((uint64_t)L, (uint64_t)N - a0);
+    const uint32_t lb = a0 + L < N ? (uint32_t)min((uint64_t)L, (uint64_t)N - a0 - L) : 0u;
+    const Rec128 *A = src + a0;
+    const Rec128 *B = A + la;
+    const uint32_t d0 = (uint32_t)(o0 - a0);
+    const uint32_t d1 = min(d0 + (uint32_t)TILE, la + lb);
+    if (tid < 64) {
+        const uint32_t dd = tid < 32 ? d0 : d1;
+        const uint32_t r = rec_corank_warp(A, la, B, lb, dd, tid & 31);
+        if ((tid & 31) == 0) s_split[tid >> 5] = r;
+    }
+    __syncthreads();
+    const uint32_t i0 = s_split[0], i1 = s_split[1];
+    const int na = (int)(i1 - i0), cnt = (int)(d1 - d0);
+    const int nb = cnt - na;
+    const uint32_t j0 = d0 - i0;
+    {
+        Rec128 r[E];
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int x = k * T + tid;
+            if (x < na) r[k] = A[i0 + x];
+            else if (x < cnt) r[k] = B[j0 + (x - na)];
+        }
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const int x = k * T + tid;
+            if (x < cnt) sm[x] = r[k];
+        }
+    }
+    __syncthreads();
+    // thread t: outputs [tE, tE + E) of the tile, A = sm[0, na), B = sm[na, cnt)
+    const int d = tid * E;
+    Rec128 v[E];
+    if (d < cnt) {
+        int lo = d > nb ? d - nb : 0, hi = d < na ? d : na;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (rec_lt(sm[na + d - 1 - mid], sm[mid])) hi = mid;
+            else lo = mid + 1;
+        }
+        int i = lo, j = d - lo;
+#pragma unroll
+        for (int k = 0; k < E; ++k) {
+            const bool takeA = j >= nb || (i < na && !rec_lt(sm[na + j], sm[i]));
+            // an exhausted run is never read: indices stay in [0, cnt)
+            v[k] = takeA ? sm[min(i, cnt - 1)] : sm[na + min(j, nb - 1)];
+            i += takeA ? 1 : 0;
+            j += takeA ? 0 : 1;
+        }
+    }
+    __syncthreads();
+    if (d < cnt) {
+#pragma unroll
+        for (int k = 0; k < E; ++k)
+            if (d + k < cnt) sm[d + k] = v[k];
+    }
+    __syncthreads();
+    for (int x = tid; x < cnt; x += T) dst[o0 + x] = sm[x];
+}
+
 // ============================================================ Step 5
 __global__ void k_select_splitters_u64(const Rec128 *__restrict__ sorted, uint32_t N, uint32_t b,
                                        Rec128 *__restrict__ spl)
@@ -354,6 +459,10 @@ cudaError_t launch_rec_merge(const Rec128 *src, Rec128 *dst, uint32_t N, uint32_
 {
     constexpr int T = 256, IT = 8;
     const uint32_t grid = (uint32_t)(((uint64_t)N + T * IT - 1) / (T * IT));
+    if ((2ull * L) % (T * IT) == 0) {  // pairs of runs span whole tiles
+        k_rec_merge_tiled<T, IT><<<grid, T, 0, st>>>(src, dst, N, L);
+        return cudaGetLastError();
+    }
     k_rec_merge<T, IT><<<grid, T, 0, st>>>(src, dst, N, L);
     return cudaGetLastError();
 }
