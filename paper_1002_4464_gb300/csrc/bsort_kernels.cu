@@ -74,22 +74,9 @@ k_records_sort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, uin
 }
 
 // ============================================================ Step 4 (merges)
-__device__ __forceinline__ uint32_t merge_path_global(const uint64_t *A, uint32_t la,
-                                                      const uint64_t *B, uint32_t lb,
-                                                      uint32_t d)
-{
-    uint32_t lo = d > lb ? d - lb : 0;
-    uint32_t hi = d < la ? d : la;
-    while (lo < hi) {
-        uint32_t mid = (lo + hi) >> 1;
-        if (A[mid] <= B[d - 1 - mid]) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// The same co-rank found by one warp: each round the 32 lanes test 32
-// evenly spaced candidates and the range shrinks to one gap (about 32x).
+// Co-rank of a merge path (items of A among the first d outputs, A first on
+// ties) found by one warp: each round the 32 lanes test 32 evenly spaced
+// candidates and the range shrinks to one gap (about 32x).
 __device__ __forceinline__ uint32_t merge_path_warp(const uint64_t *A, uint32_t la,
                                                     const uint64_t *B, uint32_t lb, uint32_t d,
                                                     int lane)
