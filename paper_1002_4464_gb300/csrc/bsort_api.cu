@@ -337,7 +337,9 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
                 // Step 9 as planned below: two tiers (one-CTA units) when the
                 // bound needs a cluster and b can reach ~1.05 buckets per
                 // one-CTA unit; the bucket count estimated the same way
-                const uint64_t bmx = m * sv < (uint64_t)kMaxBuckets ? m * sv : (uint64_t)kMaxBuckets;
+                // (two tiers: a unit per bucket, up to kMaxBucketsTiers buckets)
+                const uint64_t bmx = m * sv < (uint64_t)kMaxBucketsTiers ? m * sv
+                                                                         : (uint64_t)kMaxBucketsTiers;
                 const uint64_t tgt = two_tier_target(m, t / sv, (uint64_t)cm);
                 const uint64_t b2 = tgt ? (np + tgt - 1) / tgt : bmx + 1;
                 const bool tiers = uk > 1 && !forced_b && !forced_s && b2 <= bmx &&
@@ -395,9 +397,13 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         // one-CTA units for the buckets that fit it (nearly all), cluster
         // units only for the others.  A free b is chosen for that when it can
         // be (at most bmax buckets).
+        // (one tier packs buckets greedily in one CTA: at most kMaxBuckets;
+        // two tiers make every bucket a unit: at most kMaxBucketsTiers)
         const uint64_t bmax = m * bs < (uint64_t)kMaxBuckets ? m * bs : (uint64_t)kMaxBuckets;
+        const uint64_t bmax2 = m * bs < (uint64_t)kMaxBucketsTiers ? m * bs
+                                                                   : (uint64_t)kMaxBucketsTiers;
         const uint64_t tgt = two_tier_target(m, bt / bs, (uint64_t)cm);
-        const bool tiers_wanted = buk > 1 && tgt && (I.n_padded + tgt - 1) / tgt <= bmax &&
+        const bool tiers_wanted = buk > 1 && tgt && (I.n_padded + tgt - 1) / tgt <= bmax2 &&
                                   tiers_regular(m, bt / bs, (uint64_t)cm);
         uint64_t b = bs;  // the paper's rule, kept when s is given
         if (forced_b) {
@@ -405,7 +411,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         } else if (!forced_s) {
             const uint64_t bc =
                 tiers_wanted ? choose_buckets_two_tier(I.n_padded, m, bs, (uint64_t)cm,
-                                                       I.unit_capacity, bmax)
+                                                       I.unit_capacity, bmax2)
                              : choose_buckets(I.n_padded, m, bs, I.unit_capacity, bmax);
             if (bc) b = bc;
         }
@@ -413,6 +419,10 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
             tiers_regular(m, bt / bs, (uint64_t)cm)) {  // average at most Q1/1.05
             P->small_chunk = cm;
             I.unit_small = (uint32_t)cm;
+        } else if (b > (uint64_t)kMaxBuckets) {
+            // one tier after all: the greedy packing's bucket limit holds
+            const uint64_t bc = choose_buckets(I.n_padded, m, bs, I.unit_capacity, bmax);
+            b = bc ? bc : bs;
         }
         I.b = (uint32_t)b;
         I.bucket_bound = bound_for(I.n_padded, m, bs, b);
@@ -683,8 +693,11 @@ bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout,
     // Step 9 (two tiers: one-CTA units, then cluster units for larger buckets)
     uint32_t *units2 = P.small_chunk ? reinterpret_cast<uint32_t *>(ws + P.off_units2) : nullptr;
     const uint32_t q1 = P.small_chunk ? (uint32_t)P.small_chunk : (uint32_t)I.unit_capacity;
-    SEQ(launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, q1, (uint32_t)I.unit_capacity,
-                          units, units2, err, st),
+    // two tiers: a unit per bucket; one tier: buckets packed greedily
+    SEQ(P.small_chunk ? launch_units_each(offsets, I.m, I.b, (uint32_t)I.n_padded, q1,
+                                          (uint32_t)I.unit_capacity, units, units2, err, st)
+                      : launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, q1,
+                                          (uint32_t)I.unit_capacity, units, units2, err, st),
         "step9_pack_units");
     SEQ(launch_bucket_sort_u64(P.small_chunk ? P.small_chunk : P.unit_chunk,
                                P.small_chunk ? 1 : (int)I.unit_ctas, reloc, units, I.b, n,
@@ -825,8 +838,11 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     uint32_t *units = reinterpret_cast<uint32_t *>(ws + P.off_units);
     uint32_t *units2 = P.small_chunk ? reinterpret_cast<uint32_t *>(ws + P.off_units2) : nullptr;
     const uint32_t q1 = P.small_chunk ? (uint32_t)P.small_chunk : (uint32_t)I.unit_capacity;
-    SEQ(launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, q1, (uint32_t)I.unit_capacity,
-                          units, units2, err, st),
+    // two tiers: a unit per bucket; one tier: buckets packed greedily
+    SEQ(P.small_chunk ? launch_units_each(offsets, I.m, I.b, (uint32_t)I.n_padded, q1,
+                                          (uint32_t)I.unit_capacity, units, units2, err, st)
+                      : launch_pack_units(offsets, I.m, I.b, (uint32_t)I.n_padded, q1,
+                                          (uint32_t)I.unit_capacity, units, units2, err, st),
         "step9_pack_units");
     if (!P.relocate) {
         g.offsets = offsets;

@@ -76,6 +76,7 @@ cudaError_t launch_bucket_sort_pairs(int chunk, int ctas, const void *src_k, con
                                      void *out_v, int *err, const GatherSrc &g, cudaStream_t st);
 
 constexpr int kMaxBuckets = 12288;  // b (Step-9 unit packing keeps 16 b bytes in SMEM)
+constexpr int kMaxBucketsTiers = 32768;  // b of a two-tier Step 9 (a unit per bucket: 4 b bytes)
 
 // Step 4 (chunks): sort the n_rec records of src in chunks of kRecordChunk
 // into dst (which holds n_pad = chunks * kRecordChunk records, the tail
@@ -141,6 +142,11 @@ cudaError_t launch_block_index(uint32_t *offsets, uint32_t runs, uint32_t n_pad,
 // bucket above Q1 (at most Q2) is a unit of its own, listed in units2 (when
 // units2 == nullptr, Q1 = Q2 and all units are in units).  Each list holds
 // 1 + 2*b words (count, then begin/end pairs).
+// Step 9 units of a two-tier plan: one unit per bucket, in `units` (at
+// most Q1 items) or `units2`; b <= kMaxBucketsTiers.
+cudaError_t launch_units_each(const uint32_t *offsets, uint32_t m, uint32_t b, uint32_t n_pad,
+                              uint32_t Q1, uint32_t Q2, uint32_t *units, uint32_t *units2,
+                              int *err, cudaStream_t st);
 cudaError_t launch_pack_units(const uint32_t *offsets, uint32_t m, uint32_t b,
                               uint32_t n_pad, uint32_t Q1, uint32_t Q2, uint32_t *units,
                               uint32_t *units2, int *err, cudaStream_t st);

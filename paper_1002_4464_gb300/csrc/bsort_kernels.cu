@@ -594,6 +594,69 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t *s
     return s_warp[warp] + incl - v;
 }
 
+// Step 9 units of a two-tier plan: every bucket is a unit of its own (the
+// bucket count puts the average bucket four sigmas below one CTA's unit, so
+// no two buckets would fit one), listed in bucket order in `units` when it
+// has at most Q1 items and in `units2` otherwise; a bucket above Q2 (the
+// bound allows none) sets the error word.  One CTA; the b + 1 bucket starts
+// are staged in shared memory (4 (b + 1) bytes), so b is not held to the
+// greedy packing's limit.
+template <int T>
+__global__ void __launch_bounds__(T)
+k_units_each(const uint32_t *__restrict__ offsets, uint32_t m, uint32_t b, uint32_t n_pad,
+             uint32_t Q1, uint32_t Q2, uint32_t *__restrict__ units,
+             uint32_t *__restrict__ units2, int *err)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint32_t *Lb = reinterpret_cast<uint32_t *>(smem_raw);  // b + 1
+    __shared__ uint32_t s_warp[T / 32];
+    __shared__ uint32_t s_total[2];
+    const int tid = threadIdx.x;
+    for (uint32_t j0 = tid; j0 <= b; j0 += 4 * T) {  // four strided loads in flight
+        uint32_t l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = j0 + (uint32_t)u * T;
+            l[u] = j < b ? offsets[(uint64_t)j * m] : n_pad;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const uint32_t j = j0 + (uint32_t)u * T;
+            if (j <= b) Lb[j] = l[u];
+        }
+    }
+    __syncthreads();
+    uint32_t n1 = 0, n2 = 0;
+    for (uint32_t j0 = 0; j0 < b; j0 += T) {
+        const uint32_t j = j0 + (uint32_t)tid;
+        uint32_t L = 0, R = 0;
+        bool small = false, large = false;
+        if (j < b) {
+            L = Lb[j];
+            R = Lb[j + 1];
+            if (R - L > Q2) set_error(err, DEV_INTERNAL);  // a bucket exceeds the bound
+            small = R - L <= Q1;
+            large = !small;
+        }
+        const uint32_t u1 = block_exclusive_scan<T>(small ? 1u : 0u, s_warp, &s_total[0]);
+        const uint32_t u2 = block_exclusive_scan<T>(large ? 1u : 0u, s_warp, &s_total[1]);
+        if (small) {
+            units[1 + 2 * (n1 + u1)] = L;
+            units[2 + 2 * (n1 + u1)] = R;
+        }
+        if (large) {
+            units2[1 + 2 * (n2 + u2)] = L;
+            units2[2 + 2 * (n2 + u2)] = R;
+        }
+        n1 += s_total[0];
+        n2 += s_total[1];
+    }
+    if (tid == 0) {
+        units[0] = n1;
+        units2[0] = n2;
+    }
+}
+
 // Step 9 units: consecutive buckets packed greedily into units of at most
 // Q1 items; a bucket larger than Q1 (at most the bound, Q2) forms a unit of
 // its own.  One CTA: nxt[j] = the bucket after the longest run of buckets
@@ -746,6 +809,7 @@ cudaError_t init_misc_kernels()
 {
     BSORT_TRY(set_smem(k_records_sort<1024, 16>, smem_bytes_for_cap(kRecordChunk, true)));
     BSORT_TRY(set_smem(k_pack_units<1024>, 16 * (kMaxBuckets + 1)));
+    BSORT_TRY(set_smem(k_units_each<1024>, 4 * (kMaxBucketsTiers + 1)));
     return cudaSuccess;
 }
 
@@ -839,6 +903,16 @@ cudaError_t launch_block_index(uint32_t *offsets, uint32_t runs, uint32_t n_pad,
 {
     const uint32_t nblk = (n_pad + kBlockItems - 1) / kBlockItems;
     k_block_index<<<(nblk + 255) / 256, 256, 0, st>>>(offsets, runs, n_pad, blk, nblk);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_units_each(const uint32_t *offsets, uint32_t m, uint32_t b, uint32_t n_pad,
+                              uint32_t Q1, uint32_t Q2, uint32_t *units, uint32_t *units2,
+                              int *err, cudaStream_t st)
+{
+    if (b > (uint32_t)kMaxBucketsTiers || units2 == nullptr) return cudaErrorInvalidValue;
+    const int sm = (int)(4 * (b + 1));
+    k_units_each<1024><<<1, 1024, sm, st>>>(offsets, m, b, n_pad, Q1, Q2, units, units2, err);
     return cudaGetLastError();
 }
 

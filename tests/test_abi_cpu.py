@@ -226,8 +226,9 @@ def test_plan_u64_keys():
 def test_plan_two_tier_step9():
     """When the bound needs a cluster unit and bucket sizes are regular
     enough, b puts the average bucket four sigmas below a one-CTA unit and
-    Step 9 runs in two tiers (unit_small); with s given (b = s), or when b
-    would exceed its limit, in one."""
+    Step 9 runs in two tiers (unit_small; a unit per bucket, so b may reach
+    32768); with s given (b = s), or when b would exceed that limit, in one
+    (greedy packing: b at most 12288)."""
     h = _handle()
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 28)
     assert p.unit_ctas > 1 and p.unit_small == 32768
@@ -240,8 +241,10 @@ def test_plan_two_tier_step9():
     assert p.unit_ctas > 1 and p.unit_small == 16384
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 22)
     assert p.unit_ctas == 1 and p.unit_small == 0
-    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 3 << 28)  # b capped: one tier
-    assert p.unit_small == 0
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 3 << 28)  # two tiers: up to 32768 buckets
+    assert p.unit_small == 32768 and 12288 < p.b <= 32768
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 30)  # b capped: one tier
+    assert p.unit_small == 0 and p.b <= 12288
     pkg.bsort_destroy(h)
     h = _handle(131072, 8192)
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 28)
