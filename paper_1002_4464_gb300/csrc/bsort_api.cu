@@ -437,7 +437,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
             P->n_rec_pad = P->n_rec;
             uint32_t merges = 0;
             for (uint64_t L = bs; L < P->n_rec; L <<= 1) ++merges;
-            I.num_kernels = 1 /*S2-3*/ + merges + 1 /*S5*/ + 1 /*S6*/ + 1 /*S7*/ +
+            I.num_kernels = 1 /*S2-3*/ + merges + 1 /*S5*/ + 2 /*S6*/ + 1 /*S7*/ +
                             1 /*run index*/ + 1 /*S8*/ + 1 /*units*/ + s9;
         } else {
             uint32_t merges = 0;
@@ -477,9 +477,9 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->off_units2 = take(P->small_chunk ? (1 + 2 * (uint64_t)I.b) * 4 : 0);
         P->off_srcb = take((uint64_t)P->n_runs * 4);
         P->off_blk = take((np + kBlockItems - 1) / kBlockItems * 4);
-        // Step 6 of 32-bit keys: cumulative counts and segment ranges
-        P->off_cum = take(P->wide ? 0 : (uint64_t)P->n_runs * 4);
-        P->off_jr = take(P->wide ? 0 : sample_index_scratch_words(I.t, I.m) * 4);
+        // Step 6: cumulative counts and segment ranges
+        P->off_cum = take((uint64_t)P->n_runs * 4);
+        P->off_jr = take(sample_index_scratch_words(I.t, I.m, P->wide ? 4096u : 8192u) * 4);
     }
     P->total = o;
     I.workspace_bytes = o;
@@ -682,10 +682,13 @@ bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout,
     // Step 5
     SEQ(launch_select_splitters_u64(src, P.n_rec, I.b, spl, st), "step5_splitters");
     // Step 6
-    SEQ(launch_sample_index_u64(tiles, samples, spl, I.t, I.s, I.b, I.m, counts, srcb, st),
+    uint32_t *cum = reinterpret_cast<uint32_t *>(ws + P.off_cum);
+    uint32_t *jr = reinterpret_cast<uint32_t *>(ws + P.off_jr);
+    SEQ(launch_sample_index_seg_u64(tiles, spl, I.t, I.b, I.m, jr, cum, st),
         "step6_sample_index");
-    // Step 7
-    SEQ(launch_scan(counts, offsets, P.n_runs, status, ticket, err, st), "step7_prefix_sum");
+    // Step 7 (also a_ij and the run starts from the cumulative counts)
+    SEQ(launch_scan_cum(cum, I.m, I.t, counts, srcb, offsets, P.n_runs, status, ticket, err, st),
+        "step7_prefix_sum");
     // Step 8
     SEQ(launch_block_index(offsets, P.n_runs, (uint32_t)I.n_padded, blk, st), "step8_run_index");
     SEQ(launch_relocate_u64(tiles, offsets, srcb, blk, P.n_runs, (uint32_t)I.n_padded, reloc, st),

@@ -97,10 +97,11 @@ cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *spl, uint32_t t,
                                 uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
                                 cudaStream_t st);
-// Number of scratch words launch_sample_index needs for m sublists of t.
-inline uint64_t sample_index_scratch_words(uint32_t t, uint32_t m)
+// Number of scratch words launch_sample_index (segments of 8192 keys) or
+// launch_sample_index_seg_u64 (4096) needs for m sublists of t.
+inline uint64_t sample_index_scratch_words(uint32_t t, uint32_t m, uint32_t seg_items = 8192u)
 {
-    return (uint64_t)m * (t > 8192u ? t / 8192u : 1u);
+    return (uint64_t)m * (t > seg_items ? t / seg_items : 1u);
 }
 
 // Step 7: exclusive scan of n_items uint32 counts (decoupled look-back);
@@ -169,10 +170,11 @@ cudaError_t launch_rec_merge(const Rec128 *src, Rec128 *dst, uint32_t N, uint32_
 cudaError_t launch_select_splitters_u64(const Rec128 *sorted, uint32_t N, uint32_t b, Rec128 *spl,
                                         cudaStream_t st);
 // Step 6: counts a_ij (bucket-major) and run starts i*t + c_i(j-1).
-cudaError_t launch_sample_index_u64(const uint64_t *tiles, const Rec128 *samples,
-                                    const Rec128 *spl, uint32_t t, uint32_t s, uint32_t b,
-                                    uint32_t m, uint32_t *counts, uint32_t *srcb,
-                                    cudaStream_t st);
+// Step 6 of 64-bit keys by segments of 4096 keys: cum[j*m + i] = c_ij
+// (as launch_sample_index); jr: sample_index_scratch_words(t, m, 4096).
+cudaError_t launch_sample_index_seg_u64(const uint64_t *tiles, const Rec128 *spl, uint32_t t,
+                                        uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
+                                        cudaStream_t st);
 // Step 8 for 64-bit keys (no values).
 cudaError_t launch_relocate_u64(const uint64_t *tiles_k, const uint32_t *offsets,
                                 const uint32_t *srcb, const uint32_t *blk, uint32_t runs,

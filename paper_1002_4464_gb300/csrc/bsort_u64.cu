@@ -208,73 +208,77 @@ __global__ void k_select_splitters_u64(const Rec128 *__restrict__ sorted, uint32
     if (j < b) spl[j] = sorted[(uint64_t)(j + 1) * N / b - 1];
 }
 
-// ============================================================ Step 6
-// As k_sample_index: thread (sublist i, splitters j0 .. j0+jb-1) finds
-// q = #samples <= g_j among the sublist's own s samples (binary search,
-// then galloping as j grows) and c_ij in the w-item window by binary search.
-__device__ __forceinline__ uint32_t window_count_u64(const uint64_t *__restrict__ tiles,
-                                                     uint64_t base, uint32_t q, uint32_t w,
-                                                     uint32_t t, uint32_t s, const Rec128 &g)
+// ============================================================ Step 6 (segments)
+// As the 32-bit path's Step 6: c_ij = items of sorted sublist i at or below
+// splitter j in (key, position) order, found in the segment of the sublist
+// that holds it.  Segments of 4096 keys (32 KB of shared memory); the first
+// splitter of segment [S, S + seg) is the number of splitters below item
+// S - 1.  Writes the cumulative c_ij bucket-major (Step 7 forms a_ij).
+constexpr int kSegItemsU64 = 4096;
+
+__global__ void k_seg_ranges_u64(const uint64_t *__restrict__ tiles, const Rec128 *__restrict__ spl,
+                                 uint32_t t, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
+                                 uint32_t *__restrict__ jr)
 {
-    if (q >= s) return t;
-    uint32_t a = q * w, b = q * w + w - 1;  // the item at rank b is > g
-    while (a < b) {
-        const uint32_t mid = (a + b) >> 1;
-        Rec128 item;
-        item.key = tiles[base + mid];
-        item.p = base + mid;
-        if (!rec_lt(g, item)) a = mid + 1;
-        else b = mid;
+    const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= m * nseg) return;
+    const uint32_t i = idx / nseg, k = idx % nseg;
+    uint32_t r = 0;
+    if (k > 0) {
+        Rec128 v;
+        v.p = (uint64_t)i * t + (uint64_t)k * seg - 1;  // item S - 1 of sublist i
+        v.key = tiles[v.p];
+        uint32_t lo = 0, hi = b;
+        while (lo < hi) {  // splitters below v
+            const uint32_t mid = (lo + hi) >> 1;
+            if (rec_lt(spl[mid], v)) lo = mid + 1;
+            else hi = mid;
+        }
+        r = lo;
     }
-    return a;
+    jr[idx] = r;
 }
 
 template <int T>
 __global__ void __launch_bounds__(T)
-k_sample_index_u64(const uint64_t *__restrict__ tiles, const Rec128 *__restrict__ samples,
-                   const Rec128 *__restrict__ spl, uint32_t t, uint32_t s, uint32_t b,
-                   uint32_t m, uint32_t *__restrict__ counts, uint32_t *__restrict__ srcb,
-                   uint32_t jb)
+k_sample_index_seg_u64(const uint64_t *__restrict__ tiles, const Rec128 *__restrict__ spl,
+                       uint32_t t, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
+                       const uint32_t *__restrict__ jr, uint32_t *__restrict__ cum)
 {
-    const uint32_t gpt = (b + T * jb - 1) / (T * jb);
-    const uint32_t i = blockIdx.x / gpt;
-    const uint32_t j0 = ((blockIdx.x % gpt) * T + threadIdx.x) * jb;
-    if (j0 >= b) return;
-    const uint32_t j1 = min(j0 + jb, b);
-    const uint64_t base = (uint64_t)i * t;
-    const uint32_t w = t / s;
-    const Rec128 *smp = samples + (uint64_t)i * s;
-    const uint32_t jf = j0 ? j0 - 1 : 0;
-    Rec128 g = spl[jf];
-    uint32_t lo = 0, hi = s;
-    while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (!rec_lt(g, smp[mid])) lo = mid + 1;
-        else hi = mid;
+    static_assert(kSegItemsU64 % (2 * T) == 0, "whole uint4 loads per thread");
+    __shared__ __align__(16) uint64_t sk[kSegItemsU64];
+    const uint32_t i = blockIdx.x / nseg, k = blockIdx.x % nseg;
+    const uint32_t S = k * seg;
+    const uint64_t p0 = (uint64_t)i * t + S;  // position of the segment's first item
+    const uint32_t j_lo = jr[blockIdx.x];
+    const uint32_t j_hi = k + 1 < nseg ? jr[blockIdx.x + 1] : b;
+    const uint4 *src = reinterpret_cast<const uint4 *>(tiles + p0);
+    uint4 *dst = reinterpret_cast<uint4 *>(sk);
+    constexpr int Q = kSegItemsU64 / 2 / T;  // all loads before the first store
+    uint4 r[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const uint32_t v = (uint32_t)(q * T) + threadIdx.x;
+        if (v < seg / 2) r[q] = src[v];
     }
-    uint32_t q = lo;
-    uint32_t prev = j0 ? window_count_u64(tiles, base, q, w, t, s, g) : 0u;
-    for (uint32_t j = j0; j < j1; ++j) {
-        g = spl[j];
-        if (q < s && !rec_lt(g, smp[q])) {
-            uint32_t step = 1, lo2 = q + 1, hi2 = q + 1;
-            while (hi2 < s && !rec_lt(g, smp[hi2])) {
-                lo2 = hi2 + 1;
-                step <<= 1;
-                hi2 = min(s, q + step);
-            }
-            hi2 = min(hi2, s);
-            while (lo2 < hi2) {
-                const uint32_t mid = (lo2 + hi2) >> 1;
-                if (!rec_lt(g, smp[mid])) lo2 = mid + 1;
-                else hi2 = mid;
-            }
-            q = lo2;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const uint32_t v = (uint32_t)(q * T) + threadIdx.x;
+        if (v < seg / 2) dst[v] = r[q];
+    }
+    __syncthreads();
+    for (uint32_t j = j_lo + threadIdx.x; j < j_hi; j += T) {
+        const Rec128 g = spl[j];
+        uint32_t lo = 0, hi = seg;
+        while (lo < hi) {  // segment items <= g
+            const uint32_t mid = (lo + hi) >> 1;
+            Rec128 item;
+            item.key = sk[mid];
+            item.p = p0 + mid;
+            if (!rec_lt(g, item)) lo = mid + 1;
+            else hi = mid;
         }
-        const uint32_t c = window_count_u64(tiles, base, q, w, t, s, g);
-        counts[(uint64_t)j * m + i] = c - prev;
-        srcb[(uint64_t)j * m + i] = (uint32_t)base + prev;
-        prev = c;
+        cum[(uint64_t)j * m + i] = S + lo;
     }
 }
 
@@ -474,16 +478,18 @@ cudaError_t launch_select_splitters_u64(const Rec128 *sorted, uint32_t N, uint32
     return cudaGetLastError();
 }
 
-cudaError_t launch_sample_index_u64(const uint64_t *tiles, const Rec128 *samples,
-                                    const Rec128 *spl, uint32_t t, uint32_t s, uint32_t b,
-                                    uint32_t m, uint32_t *counts, uint32_t *srcb,
-                                    cudaStream_t st)
+
+cudaError_t launch_sample_index_seg_u64(const uint64_t *tiles, const Rec128 *spl, uint32_t t,
+                                        uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
+                                        cudaStream_t st)
 {
-    constexpr int T = 128;
-    const uint32_t jb = b >= 8 * T ? 8 : (b + T - 1) / T;
-    const uint32_t gpt = (b + T * jb - 1) / (T * jb);
-    k_sample_index_u64<T><<<m * gpt, T, 0, st>>>(tiles, samples, spl, t, s, b, m, counts, srcb,
-                                                 jb);
+    const uint32_t seg = t < (uint32_t)kSegItemsU64 ? t : (uint32_t)kSegItemsU64;
+    const uint32_t nseg = t / seg;
+    const uint32_t ns = m * nseg;
+    k_seg_ranges_u64<<<(ns + 255) / 256, 256, 0, st>>>(tiles, spl, t, b, m, nseg, seg, jr);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_sample_index_seg_u64<256><<<ns, 256, 0, st>>>(tiles, spl, t, b, m, nseg, seg, jr, cum);
     return cudaGetLastError();
 }
 
