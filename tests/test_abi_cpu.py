@@ -254,3 +254,34 @@ def test_plan_two_tier_step9():
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 28)
     assert p.unit_small == 32768 and p.b == 8602
     pkg.bsort_destroy(h)
+
+
+def test_plan_invariants_sweep():
+    """Over sizes from 2^17 to 3 * 2^28 and every key type: the bucket bound
+    of the plan (the oracle's formula) fits the Step-9 unit, one-tier plans
+    keep b within the greedy packing's 12288 buckets, two-tier plans within
+    32768 with a one-CTA small unit, and b never exceeds the m*s samples."""
+    h = _handle()
+    sizes = [(1 << k) + d for k in range(17, 29) for d in (0, 12345)] + [3 << 28]
+    for kt, vb in ((pkg.BSORT_U32, 0), (pkg.BSORT_F32, 0), (pkg.BSORT_U32, 4),
+                   (pkg.BSORT_U32, 8), (pkg.BSORT_U64, 0)):
+        for n in sizes:
+            try:
+                p = pkg.bsort_plan(h, kt, vb, n)
+            except pkg.BsortError as e:  # sizes beyond what a plan can hold
+                assert e.status == pkg.BSORT_EUNSUPPORTED
+                continue
+            if p.single_tile:
+                assert n <= p.unit_capacity
+                continue
+            assert p.m * p.t == p.n_padded >= n > (p.m - 1) * p.t
+            assert p.t % p.s == 0 and p.w == p.t // p.s
+            assert 1 <= p.b <= p.m * p.s
+            assert p.bucket_bound == oracle.bucket_bound(p.n_padded, p.m, p.s, p.b)
+            assert p.bucket_bound <= p.unit_capacity
+            if p.unit_small:
+                assert p.b <= 32768 and p.unit_small < p.unit_capacity
+                assert p.unit_small == (16384 if (vb or kt == pkg.BSORT_U64) else 32768)
+            else:
+                assert p.b <= 12288
+    pkg.bsort_destroy(h)
