@@ -612,12 +612,19 @@ bsort_status ensure_pipe(bsort_t h)
     if (h->xfer) return BSORT_OK;
     cudaError_t e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) return cuda_fail(h, e, "multiprocessor count");
-    for (int i = 0; i < 2 * kPipe + 2; ++i) {
-        e = cudaEventCreateWithFlags(&h->xev[i], cudaEventDisableTiming);
-        if (e != cudaSuccess) return cuda_fail(h, e, "cudaEventCreate (copy pipeline)");
+    // all or nothing: a failed call leaves no events behind to leak on the next
+    cudaEvent_t ev[2 * kPipe + 2] = {};
+    cudaStream_t xs = nullptr;
+    for (int i = 0; i < 2 * kPipe + 2 && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&xs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        for (cudaEvent_t x : ev)
+            if (x) cudaEventDestroy(x);
+        return cuda_fail(h, e, "copy stream and events of the host entry");
     }
-    e = cudaStreamCreateWithFlags(&h->xfer, cudaStreamNonBlocking);
-    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamCreate (copy pipeline)");
+    for (int i = 0; i < 2 * kPipe + 2; ++i) h->xev[i] = ev[i];
+    h->xfer = xs;
     return BSORT_OK;
 }
 
