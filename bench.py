@@ -79,6 +79,8 @@ def _args():
     p.add_argument("--dist", default="uniform")
     p.add_argument("--key-type", default="u32", choices=["u32", "f32", "u64"],
                    help="u64: uniform 64-bit keys (the --dist option is ignored)")
+    p.add_argument("--small-reps", type=int, default=200,
+                   help="2^20-key sorts repeated with and without CUDA-graph replay (0: skip)")
     p.add_argument("--pairs", action="store_true",
                    help="key-value pairs: uint32 keys with uint32 values = original index "
                         "(bsort_sort_pairs); e2e is not taken")
@@ -314,6 +316,39 @@ def _config(args, world):
             if args.n * _kb(args) > 129 * 2 ** 20 else "input smaller than L2 (resident)"}
 
 
+def _small_sorts(args, pkg, synth, dev, local, rank, stream, sorter):
+    """2^20 uint32 keys sorted args.small_reps times on the same buffers,
+    with a launch per kernel and with one CUDA-graph launch per sort."""
+    import torch
+    ns = 1 << 20
+    ks = synth.keys_u32_torch("uniform", ns, synth.seed_for(2, 0, rank), device=dev)
+    os_ = torch.empty_like(ks)
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    out = {"n": ns, "reps": args.small_reps,
+           "kernels_per_sort": sorter.plan(ns, "u32").num_kernels}
+    with torch.cuda.stream(side):
+        for graphs in (False, True):
+            s2 = pkg.BucketSorter(device=local, graphs=graphs)
+            for _ in range(5):
+                s2.sort_keys(ks, out=os_)
+            s2.sync()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(side)
+            for _ in range(args.small_reps):
+                s2.sort_keys(ks, out=os_)
+            b.record(side)
+            side.synchronize()
+            s2.sync()
+            out["ms_per_sort_graph" if graphs else "ms_per_sort_launches"] = \
+                a.elapsed_time(b) / args.small_reps
+            s2.close()
+    stream.wait_stream(side)
+    out["speedup"] = out["ms_per_sort_launches"] / out["ms_per_sort_graph"]
+    return out
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -463,6 +498,16 @@ def run_ours(args):
                "ms_per_step": ems}
         del h_in, h_out
 
+    # a small sort repeated on the same buffers: one launch per kernel
+    # against one graph launch per sort (BSORT_FLAG_GRAPHS), on a created
+    # stream (the legacy default stream cannot be captured)
+    small = None
+    if args.small_reps > 0:
+        try:
+            small = _small_sorts(args, pkg, synth, dev, local, rank, stream, sorter)
+        except Exception as e:  # reported, not fatal: the headline stands
+            small = {"error": "%s: %s" % (type(e).__name__, str(e)[:200])}
+
     dists = None
     if args.dists:
         dists = {}
@@ -533,6 +578,8 @@ def run_ours(args):
                      if k in ("t", "s", "b", "m", "w", "bucket_bound", "unit_capacity",
                               "tile_ctas", "unit_ctas", "num_kernels")},
         }
+        if small is not None:
+            line["small_sort"] = small
         if dists is not None:
             line["distributions"] = dists
         if batched is not None:

@@ -72,6 +72,22 @@ typedef enum {
                                       shrinks by n'*(key+value) bytes, at some
                                       cost in speed; BSORT_IM_RELOCATED is then
                                       not available */
+#define BSORT_FLAG_GRAPHS 0x4u     /* bsort_sort_keys / bsort_sort_pairs
+                                      capture their launch sequence as a CUDA
+                                      graph the first time they see a call
+                                      (key type, value bytes, n, the four
+                                      buffer pointers, the stream, the
+                                      workspace) and replay it with one graph
+                                      launch when the same call repeats (new
+                                      contents in the same buffers are fine);
+                                      the handle keeps the 16 most recent
+                                      graphs and drops them all when its
+                                      workspace moves.  Not combined with
+                                      BSORT_FLAG_TIMING (no kernel times are
+                                      recorded for captured calls); calls on
+                                      the legacy default stream (NULL), or on
+                                      a stream that is already capturing,
+                                      are issued as usual */
 
 typedef struct {
     int device;                /* CUDA device ordinal the handle works on */

@@ -90,6 +90,20 @@ struct bsort_ctx {
     bool events_made = false;
     uint64_t serve_budget = 0;        // bytes for served requests (0: 4 GiB)
     bsort_server *server = nullptr;   // started by the first bsort_submit
+    // BSORT_FLAG_GRAPHS: replayable launch sequences of plain sorts
+    struct Graph {
+        int kt = 0;
+        uint32_t vb = 0;
+        uint64_t n = 0;
+        const void *kin = nullptr, *vin = nullptr;
+        void *kout = nullptr, *vout = nullptr, *ws = nullptr;
+        cudaStream_t st = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        uint64_t used = 0;
+    };
+    std::vector<Graph> graphs;
+    uint64_t graph_clock = 0;
+    bool capturing = false;  // no timing events while a sort is captured
     // bsort_sort_keys_host: copy stream and its events (made on first use)
     cudaStream_t xfer = nullptr;
     cudaEvent_t xev[2 * kPipe + 2] = {};
@@ -496,12 +510,19 @@ uint32_t large_units_max(uint64_t n_pad, uint32_t q1, uint32_t b)
     return (uint32_t)(u < 256 ? u : 256);
 }
 
+void drop_graphs(bsort_t h)
+{
+    for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
+    h->graphs.clear();
+}
+
 bsort_status ensure_workspace(bsort_t h, uint64_t bytes)
 {
     if (bytes <= h->ws_bytes) return BSORT_OK;
     if (h->ws_fixed)
         return fail(h, BSORT_ENOMEM, "job needs %llu workspace bytes, handle has %llu",
                     (unsigned long long)bytes, (unsigned long long)h->ws_bytes);
+    drop_graphs(h);  // they point into the old workspace
     if (h->ws_owned && h->ws) {
         cudaError_t e = cudaFree(h->ws);
         h->ws = nullptr;
@@ -554,7 +575,8 @@ struct Seq {
     bool timing;
     int slot = 0;
     int n = 0;
-    Seq(bsort_t h_, cudaStream_t st_) : h(h_), st(st_), timing((h_->flags & BSORT_FLAG_TIMING) != 0)
+    Seq(bsort_t h_, cudaStream_t st_)
+        : h(h_), st(st_), timing((h_->flags & BSORT_FLAG_TIMING) != 0 && !h_->capturing)
     {
         if (!timing) return;
         slot = (int)(h->call_seq % kRing);
@@ -917,6 +939,79 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
             "step9_bucket_sort_large");
     }
     return BSORT_OK;
+}
+
+// run_sort through the handle's graph cache (BSORT_FLAG_GRAPHS): the plan
+// and the workspace are settled first, outside any capture; a call seen
+// before is one graph launch, a new one is captured from the stream,
+// instantiated and launched.
+bsort_status run_sort_graph(bsort_t h, bsort_key_type kt, const void *kin, const void *vin,
+                            void *kout, void *vout, uint32_t vb, uint64_t n, cudaStream_t st)
+{
+    // (the legacy default stream cannot be captured: its calls launch as usual)
+    if (!(h->flags & BSORT_FLAG_GRAPHS) || n == 0 || st == nullptr || st == cudaStreamLegacy)
+        return run_sort(h, kt, kin, vin, kout, vout, vb, n, st);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone)  // the caller is capturing: part of its graph
+        return run_sort(h, kt, kin, vin, kout, vout, vb, n, st);
+    bsort_status rs = prepare(h);
+    if (rs != BSORT_OK) return rs;
+    Plan P;
+    rs = make_plan(h, kt, vb, n, &P);
+    if (rs != BSORT_OK) return rs;
+    rs = ensure_workspace(h, P.total);
+    if (rs != BSORT_OK) return rs;
+    for (auto &g : h->graphs) {
+        if (g.kt == (int)kt && g.vb == vb && g.n == n && g.kin == kin && g.vin == vin &&
+            g.kout == kout && g.vout == vout && g.ws == h->ws && g.st == st) {
+            g.used = ++h->graph_clock;
+            h->last = P;
+            h->have_last = true;
+            e = cudaGraphLaunch(g.exec, st);
+            return e == cudaSuccess ? BSORT_OK : cuda_fail(h, e, "cudaGraphLaunch");
+        }
+    }
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamBeginCapture");
+    h->capturing = true;
+    rs = run_sort(h, kt, kin, vin, kout, vout, vb, n, st);
+    h->capturing = false;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (rs != BSORT_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return rs != BSORT_OK ? rs : cuda_fail(h, e, "cudaStreamEndCapture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaGraphInstantiate");
+    constexpr size_t kGraphs = 16;
+    if (h->graphs.size() >= kGraphs) {  // drop the least recently used
+        size_t lru = 0;
+        for (size_t i = 1; i < h->graphs.size(); ++i)
+            if (h->graphs[i].used < h->graphs[lru].used) lru = i;
+        cudaGraphExecDestroy(h->graphs[lru].exec);
+        h->graphs.erase(h->graphs.begin() + (long)lru);
+    }
+    bsort_ctx::Graph g;
+    g.kt = (int)kt;
+    g.vb = vb;
+    g.n = n;
+    g.kin = kin;
+    g.vin = vin;
+    g.kout = kout;
+    g.vout = vout;
+    g.ws = h->ws;
+    g.st = st;
+    g.exec = exec;
+    g.used = ++h->graph_clock;
+    h->graphs.push_back(g);
+    e = cudaGraphLaunch(exec, st);
+    return e == cudaSuccess ? BSORT_OK : cuda_fail(h, e, "cudaGraphLaunch");
 }
 
 // ---------------------------------------------------------------- batches
@@ -1704,7 +1799,8 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
             }
             h->direct_max = cfg->batch_direct_max;
         }
-        if (cfg->flags & ~(uint32_t)(BSORT_FLAG_TIMING | BSORT_FLAG_LOW_MEMORY)) {
+        if (cfg->flags &
+            ~(uint32_t)(BSORT_FLAG_TIMING | BSORT_FLAG_LOW_MEMORY | BSORT_FLAG_GRAPHS)) {
             delete h;
             return BSORT_EINVAL;
         }
@@ -1751,6 +1847,7 @@ bsort_status bsort_destroy(bsort_t h)
     }
     if (h->stage_ev) cudaEventDestroy(h->stage_ev);
     if (h->stage) cudaFreeHost(h->stage);
+    drop_graphs(h);
     if (h->xfer) cudaStreamDestroy(h->xfer);
     for (int i = 0; i < 2 * kPipe + 2; ++i)
         if (h->xev[i]) cudaEventDestroy(h->xev[i]);
@@ -1781,8 +1878,8 @@ bsort_status bsort_sort_keys(bsort_t h, bsort_key_type kt, const void *d_keys_in
     const uint64_t kb = kt == BSORT_U64 ? 8 : 4;
     if (n && d_keys_in != d_keys_out && overlaps(d_keys_in, n * kb, d_keys_out, n * kb))
         return fail(h, BSORT_EINVAL, "input and output overlap partially");
-    return run_sort(h, kt, d_keys_in, nullptr, d_keys_out, nullptr, 0, n,
-                    static_cast<cudaStream_t>(cuda_stream));
+    return run_sort_graph(h, kt, d_keys_in, nullptr, d_keys_out, nullptr, 0, n,
+                          static_cast<cudaStream_t>(cuda_stream));
 }
 
 bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_in,
@@ -1799,8 +1896,8 @@ bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_i
     if (n && d_vals_in != d_vals_out &&
         overlaps(d_vals_in, n * val_bytes, d_vals_out, n * val_bytes))
         return fail(h, BSORT_EINVAL, "value input and output overlap partially");
-    return run_sort(h, kt, d_keys_in, d_vals_in, d_keys_out, d_vals_out, val_bytes, n,
-                    static_cast<cudaStream_t>(cuda_stream));
+    return run_sort_graph(h, kt, d_keys_in, d_vals_in, d_keys_out, d_vals_out, val_bytes, n,
+                          static_cast<cudaStream_t>(cuda_stream));
 }
 
 bsort_status bsort_plan_batch(bsort_t h, bsort_key_type kt, const uint64_t *seg_offsets,

@@ -285,3 +285,14 @@ def test_plan_invariants_sweep():
             else:
                 assert p.b <= 12288
     pkg.bsort_destroy(h)
+
+
+def test_create_flags():
+    """bsort_create takes the documented flags (timing, low memory, CUDA-graph
+    replay) and refuses unknown bits."""
+    ok = pkg.BSORT_FLAG_TIMING | pkg.BSORT_FLAG_LOW_MEMORY | pkg.BSORT_FLAG_GRAPHS
+    h = pkg.bsort_create(pkg.bsort_config(device=0, flags=ok))
+    pkg.bsort_destroy(h)
+    with pytest.raises(pkg.BsortError) as e:
+        pkg.bsort_create(pkg.bsort_config(device=0, flags=0x8))
+    assert e.value.status == pkg.BSORT_EINVAL

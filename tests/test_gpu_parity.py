@@ -306,6 +306,45 @@ def test_host_entry_back_to_back_and_pageable():
     low.close()
 
 
+def test_graph_replay():
+    """BSORT_FLAG_GRAPHS: the first call with given buffers is captured as a
+    CUDA graph and later calls replay it.  New contents in the same buffers
+    sort correctly on every replay, a new size captures again, and key-value
+    pairs stay stable."""
+    side = torch.cuda.Stream()  # the legacy default stream cannot be captured
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        _graph_replay_cases()
+    torch.cuda.synchronize()
+
+
+def _graph_replay_cases():
+    sorter = pkg.BucketSorter(graphs=True)
+    for n in ((1 << 20) + 3, 1 << 22):
+        d_in = torch.empty(n, dtype=torch.int32, device="cuda")
+        d_out = torch.empty_like(d_in)
+        for rep in range(3):
+            keys = synth.keys_u32("uniform", n, synth.seed_for(2, 10, rep))
+            d_in.copy_(torch.from_numpy(keys.view(np.int32)))
+            sorter.sort_keys(d_in, out=d_out)
+            sorter.sync()
+            assert np.array_equal(d_out.cpu().numpy().view(np.uint32), np.sort(keys))
+    n = (1 << 21) + 5
+    kk = torch.empty(n, dtype=torch.int32, device="cuda")
+    vv = torch.arange(n, dtype=torch.int32, device="cuda")
+    ok = torch.empty_like(kk)
+    ov = torch.empty_like(vv)
+    for rep in range(2):
+        keys = synth.keys_zipf(n, synth.seed_for(2, 11, rep))
+        kk.copy_(torch.from_numpy(keys.view(np.int32)))
+        sorter.sort_pairs(kk, vv, out_keys=ok, out_vals=ov)
+        sorter.sync()
+        order = np.argsort(keys, kind="stable")
+        assert np.array_equal(ok.cpu().numpy().view(np.uint32), keys[order])
+        assert np.array_equal(ov.cpu().numpy(), order.astype(np.int32))
+    sorter.close()
+
+
 def test_workspace_too_small_is_enomem():
     cfg = pkg.bsort_config(device=0)
     ws = torch.empty(4096, dtype=torch.uint8, device="cuda")
