@@ -46,7 +46,8 @@ typedef enum {
     BSORT_ENOMEM = 2,        /* workspace too small / device allocation failed */
     BSORT_ECUDA = 3,         /* a CUDA runtime call failed; see bsort_last_error */
     BSORT_ETIMEOUT = 4,      /* a bounded device-side wait ran out */
-    BSORT_EBUSY = 5,         /* reserved */
+    BSORT_EBUSY = 5,         /* the handle serves a request stream
+                                (bsort_submit) and refuses other sort calls */
     BSORT_ENOTREADY = 6,     /* no completed call to report on */
     BSORT_EUNSUPPORTED = 7,  /* valid request that this build does not serve */
     BSORT_EINTERNAL = 8      /* a device-side consistency check failed */
