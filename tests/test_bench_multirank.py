@@ -48,3 +48,25 @@ def test_two_ranks_max_time_and_whole_job_rate():
         t, v = out[r]
         assert t == 20.0  # the slower rank's time
         assert abs(v - (1 << 28) * 2 * 10 / 0.020 / 1e9) < 1e-6
+
+
+def test_reference_arm_line():
+    """bench.py --impl reference: the oracle timed on host cores prints one
+    JSON line with the contract's keys, on the same config as our arm."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
+                          "--steps", "2", "--warmup", "1", "--cpu-sample", "65536"],
+                         capture_output=True, text=True, timeout=600, check=True).stdout
+    lines = [ln for ln in out.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e", "gpu_launches"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2
+    assert d["config"]["workload"] == "uniform u32 keys-only sort, n=2^28 per GPU"
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
