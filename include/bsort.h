@@ -49,7 +49,7 @@ typedef enum {
     BSORT_EBUSY = 5,         /* the handle serves a request stream
                                 (bsort_submit) and refuses other sort calls */
     BSORT_ENOTREADY = 6,     /* no completed call to report on */
-    BSORT_EUNSUPPORTED = 7,  /* valid request that this build does not serve */
+    BSORT_EUNSUPPORTED = 7,  /* valid request that this library does not serve */
     BSORT_EINTERNAL = 8      /* a device-side consistency check failed */
 } bsort_status;
 

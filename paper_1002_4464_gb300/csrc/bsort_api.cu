@@ -289,7 +289,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
     if (vb != 0 && vb != 4 && vb != 8) return fail(h, BSORT_EINVAL, "val_bytes must be 0, 4 or 8");
     if (kt == BSORT_U64 && vb != 0)
-        return fail(h, BSORT_EUNSUPPORTED, "64-bit keys are sorted keys-only by this build");
+        return fail(h, BSORT_EUNSUPPORTED, "64-bit keys are sorted keys-only (no values)");
     if (n >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "n = %llu exceeds 2^32 - 2^16", (unsigned long long)n);
     // 64-bit keys and pairs sort 64-bit words: the smaller chunk shapes
     const bool pairs = vb != 0 || kt == BSORT_U64;
