@@ -6,8 +6,16 @@ uniformly (SplitMix64), keys only.  Prints ONE JSON line on rank 0.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--n N] [--dist uniform] [--key-type u32|f32|u64] [--pairs]
-                  [--dists] [--batch-arrays 20000] [--batch-cap 2^30]
+                  [--no-dists] [--batch-arrays 20000] [--batch-cap 2^30]
                   [--serve-seconds 60] [--serve-rate 2000] [--serve-budget B]
+                  [--merge-sort] [--cpu-sample 2^24] [--no-cpu-full]
+
+"roofline" is the HBM roofline of the dominant kernel: its algorithmic bytes
+(one read and one write of every item it moves) over its CUDA-event time,
+against the measured copy bandwidth; "distributions" times the seven key
+distributions and reports their spread; "cpu_baseline" is the CPU oracle on
+all host cores (on a 2^24-key sample; once on the whole workload when host
+memory allows; and on one core as "single_thread").
 
 The line also carries "served": a Poisson stream of sort jobs (2,000 per
 second for 60 s, 50/50 uint32/uint64, sizes log-uniform in [2^10, 2^24],
@@ -54,17 +62,15 @@ KERNEL_FN = {
     "step9_bucket_sort": "k_bucket_sort", "step9_single_unit": "k_bucket_sort",
 }
 ALU_KERNELS = ("step1_3_sublist_sort", "step9_bucket_sort", "step9_single_unit")
-# integer ALU pipe: 16 lanes per SM sub-partition x 4 x 152 SMs x 2.07 GHz
-ALU_PEAK_TOPS = 152 * 64 * 2.07e9 / 1e12
 UNIT = "Gkeys/s"
 # the sources each kernel is built from (a traffic record is valid while they
 # are unchanged)
 _CSRC = "paper_1002_4464_gb300/csrc/"
 KERNEL_SOURCES = {
     "k_sublist_sort": [_CSRC + "bsort_sort.cuh", _CSRC + "bsort_device.cuh",
-                       _CSRC + "bsort_sort_keys.cu"],
+                       _CSRC + "bsort_radix.cuh", _CSRC + "bsort_sort_keys_radix.cu"],
     "k_bucket_sort": [_CSRC + "bsort_sort.cuh", _CSRC + "bsort_device.cuh",
-                      _CSRC + "bsort_sort_keys.cu"],
+                      _CSRC + "bsort_radix.cuh", _CSRC + "bsort_sort_keys_radix.cu"],
 }
 KERNEL_SOURCES_DEFAULT = [_CSRC + "bsort_kernels.cu", _CSRC + "bsort_device.cuh"]
 
@@ -84,11 +90,18 @@ def _args():
     p.add_argument("--pairs", action="store_true",
                    help="key-value pairs: uint32 keys with uint32 values = original index "
                         "(bsort_sort_pairs); e2e is not taken")
-    p.add_argument("--dists", action="store_true",
-                   help="also time every distribution (spread across distributions)")
+    p.add_argument("--no-dists", dest="dists", action="store_false",
+                   help="skip timing every distribution (the spread across distributions)")
+    p.add_argument("--dists", dest="dists", action="store_true",
+                   help="time every distribution (the default)")
     p.add_argument("--e2e-steps", type=int, default=3)
-    p.add_argument("--cpu-sample", type=int, default=1 << 22,
-                   help="keys per CPU-oracle sample")
+    p.add_argument("--cpu-sample", type=int, default=1 << 24,
+                   help="keys per CPU-oracle sample (all host cores)")
+    p.add_argument("--no-cpu-full", dest="cpu_full", action="store_false",
+                   help="skip timing the CPU oracle once on the whole workload")
+    p.add_argument("--merge-sort", action="store_true",
+                   help="sort the 32768-key chunks of Steps 2 and 9 by comparisons "
+                        "(BSORT_FLAG_MERGE_SORT) instead of by digits")
     p.add_argument("--tile", type=int, default=0, help="force the sublist size t (0: planner)")
     p.add_argument("--samples", type=int, default=0, help="force s (0: planner)")
     p.add_argument("--buckets", type=int, default=0,
@@ -216,14 +229,26 @@ def _cpu_cores():
         return os.cpu_count() or 1
 
 
-def cpu_oracle_rate(keys_np, key_type, t, s):
-    """Time the CPU oracle (Algorithm 1 in plain C, single thread) on one
+def cpu_oracle_rate(keys_np, key_type, t, s, threads=1):
+    """Time the CPU oracle (Algorithm 1 in plain C; with threads > 1 its
+    per-sublist and per-bucket loops spread over that many threads) on one
     sample; returns (Gkeys/s, seconds)."""
     import oracle
     t0 = time.perf_counter()
-    oracle.paper_sort(keys_np, t, s, key_type, intermediates=False)
+    oracle.paper_sort(keys_np, t, s, key_type, intermediates=False, threads=threads)
     dt = time.perf_counter() - t0
     return keys_np.size / dt / 1e9, dt
+
+
+def _mem_available_bytes():
+    try:
+        with open("/proc/meminfo") as f:
+            for ln in f:
+                if ln.startswith("MemAvailable:"):
+                    return int(ln.split()[1]) * 1024
+    except OSError:
+        pass
+    return 0
 
 
 def _oracle_plan(n):
@@ -271,6 +296,50 @@ def job_throughput(n_per_rank, world, steps, ms_total):
     return n_per_rank * world * steps / (ms_total / 1e3) / 1e9
 
 
+def _cpu_baseline(args, keys):
+    """The CPU oracle on the machine's host cores: all cores on a bounded sample
+    of this workload (the reported value), one core on a smaller sample, and
+    all cores once on the whole workload when host memory allows."""
+    import numpy as np
+    cores = _cpu_cores()
+    ktype = {"u32": np.uint32, "f32": np.uint32, "u64": np.uint64}[args.key_type]
+
+    def rates(count, threads, budget_s, max_reps):
+        t_o, s_o = _oracle_plan(count)
+        knp = keys[:count].cpu().numpy().view(ktype)
+        rs, spent = [], 0.0
+        while spent < budget_s and len(rs) < max_reps:
+            r, dt = cpu_oracle_rate(knp, args.key_type, t_o, s_o, threads)
+            rs.append(r)
+            spent += dt
+        return statistics.median(rs), len(rs), t_o, s_o
+
+    n_mt = min(args.cpu_sample, args.n)
+    v_mt, reps_mt, t_o, s_o = rates(n_mt, cores, 10.0, 5)
+    n_st = min(1 << 22, args.n)
+    v_st, reps_st, _, _ = rates(n_st, 1, 5.0, 3)
+    cpu = {"value": v_mt, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "first %d keys of this workload, %d repetitions (median), Algorithm 1 "
+                     "with t=%d, s=%d, its per-sublist and per-bucket loops on %d threads%s"
+                     % (n_mt, reps_mt, t_o, s_o, cores, ", keys only" if args.pairs else ""),
+           "single_thread": {"value": v_st, "unit": UNIT, "cores": 1,
+                             "sample": "first %d keys, %d repetitions (median)"
+                                       % (n_st, reps_st)}}
+    # the whole workload once: about 64 bytes of oracle state per key
+    need = args.n * 64
+    if args.cpu_full and args.n > n_mt and _mem_available_bytes() > 2 * need:
+        try:
+            t_o, s_o = _oracle_plan(args.n)
+            knp = keys.cpu().numpy().view(ktype)
+            r, dt = cpu_oracle_rate(knp, args.key_type, t_o, s_o, cores)
+            cpu["full_workload"] = {"value": r, "unit": UNIT, "cores": cores,
+                                    "seconds": dt, "n": args.n}
+            del knp
+        except (MemoryError, ValueError) as e:
+            cpu["full_workload"] = {"error": "%s: %s" % (type(e).__name__, str(e)[:120])}
+    return cpu
+
+
 def run_reference(args):
     rank, world, local = _dist_env()
     if rank != 0:
@@ -278,23 +347,25 @@ def run_reference(args):
     sample_n = min(args.cpu_sample, args.n)
     keys = _sample_keys(args, 0, sample_n)
     t, s = _oracle_plan(sample_n)
+    cores = _cpu_cores()
     for _ in range(args.warmup):
-        cpu_oracle_rate(keys, args.key_type, t, s)
+        cpu_oracle_rate(keys, args.key_type, t, s, cores)
     times = []
     for _ in range(args.steps):
-        _, dt = cpu_oracle_rate(keys, args.key_type, t, s)
+        _, dt = cpu_oracle_rate(keys, args.key_type, t, s, cores)
         times.append(dt)
     total = sum(times)
     value = sample_n * len(times) / total / 1e9
     sample_desc = ("first %d keys of the %s %s workload (n=%d), Algorithm 1 with t=%d, s=%d, "
-                   "single thread, per step" % (sample_n, args.dist, args.key_type, args.n, t, s))
+                   "per-sublist and per-bucket loops on %d threads, per step"
+                   % (sample_n, args.dist, args.key_type, args.n, t, s, cores))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total / len(times) * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.key_type,
         "data": "synthetic", "config": _config(args, world),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": sample_desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
@@ -381,7 +452,7 @@ def run_ours(args):
     vals = torch.arange(args.n, dtype=torch.int32, device=dev) if args.pairs else None
     out_v = torch.empty_like(vals) if args.pairs else None
     sorter = pkg.BucketSorter(device=local, timing=True, tile=args.tile, samples=args.samples,
-                              buckets=args.buckets)
+                              buckets=args.buckets, merge_sort=args.merge_sort)
     plan = sorter.plan(args.n, args.key_type)
     stream = torch.cuda.current_stream(dev)
 
@@ -444,31 +515,34 @@ def run_ours(args):
         launches_per_kernel[name] = launches_per_kernel.get(name, 0) + 1
     dom = max(per_kernel, key=per_kernel.get) if per_kernel else None
     hbm_peak, peak_kind = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     roofline = None
     if dom is not None:
         dom_ms = per_kernel[dom] / launches_per_kernel[dom]
-        if dom in ALU_KERNELS:
-            # comparison sort: ALU-bound.  Algorithmic work of one launch =
-            # 2 integer ops (compare + select) per item per merge level,
-            # levels = log2(items per sort unit).
+        # HBM roofline of the dominant kernel: its algorithmic bytes are the
+        # one read and one write of every item it moves (Steps 2, 8 and 9
+        # each pass the whole array once), over its CUDA-event time
+        alg = 2 * plan.n_padded * _kb(args)
+        achieved = alg / (dom_ms / 1e3) / 1e9
+        roofline = {"bound": "hbm", "kernel": KERNEL_FN.get(dom, dom), "achieved": achieved,
+                    "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                    "peak_kind": peak_kind, "alg_bytes_per_launch": alg,
+                    "ms_per_launch": dom_ms, "sm_count": sm_count}
+        roofline["traffic"] = _traffic_for(KERNEL_FN.get(dom, dom), _config(args, 1)["workload"])
+        if args.merge_sort and dom in ALU_KERNELS:
+            # the comparison sort's own ceiling: 2 integer ops (compare +
+            # select) per item per merge level on the integer ALU pipe
+            # (16 lanes x 4 sub-partitions per SM) at the sampled clock
             unit = plan.unit_capacity if dom != "step1_3_sublist_sort" else plan.t
             levels = max(1, (int(unit) - 1).bit_length())
-            alg = 2.0 * args.n * levels
-            achieved = alg / (dom_ms / 1e3) / 1e12
-            roofline = {"bound": "alu", "kernel": KERNEL_FN.get(dom, dom),
-                        "achieved": achieved, "peak": ALU_PEAK_TOPS, "unit": "Tops/s",
-                        "frac": achieved / ALU_PEAK_TOPS,
-                        "peak_kind": "derived: 152 SMs x 64 int ops/clk (ALU pipe) x 2.07 GHz",
-                        "alg_ops_per_launch": alg, "merge_levels": levels,
-                        "ms_per_launch": dom_ms}
-        else:
-            alg = 2 * plan.n_padded * _kb(args)
-            achieved = alg / (dom_ms / 1e3) / 1e9
-            roofline = {"bound": "hbm", "kernel": KERNEL_FN.get(dom, dom), "achieved": achieved,
-                        "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                        "peak_kind": peak_kind, "alg_bytes_per_launch": alg,
-                        "ms_per_launch": dom_ms}
-        roofline["traffic"] = _traffic_for(KERNEL_FN.get(dom, dom), _config(args, 1)["workload"])
+            ops = 2.0 * args.n * levels
+            mhz = clk.get("sm_mhz") or 2070.0
+            alu_peak = sm_count * 64 * mhz * 1e6 / 1e12
+            roofline["alu_view"] = {"achieved": ops / (dom_ms / 1e3) / 1e12, "peak": alu_peak,
+                                    "unit": "Tops/s",
+                                    "frac": ops / (dom_ms / 1e3) / 1e12 / alu_peak,
+                                    "peak_kind": "derived: %d SMs x 64 int ops/clk x %.0f MHz"
+                                                 % (sm_count, mhz)}
         # whole-step HBM roofline: three read+write passes (Steps 2, 8, 9)
         whole = 6 * args.n * _kb(args) / (ms_step / 1e3) / 1e9
         roofline["step_hbm_achieved_gbs"] = whole
@@ -539,25 +613,8 @@ def run_ours(args):
         dists["spread"] = (max(rates) - min(rates)) / (sum(rates) / len(rates))
 
     cpu = None
-    if rank == 0:
-        sample_n = min(args.cpu_sample, args.n)
-        t_o, s_o = _oracle_plan(sample_n)
-        keys_np = keys[:sample_n].cpu().numpy()
-        if args.key_type == "u32":
-            keys_np = keys_np.view(np.uint32)
-        elif args.key_type == "u64":
-            keys_np = keys_np.view(np.uint64)
-        rates = []
-        t_spent = 0.0
-        while t_spent < 10.0 and len(rates) < 8:
-            r, dt = cpu_oracle_rate(keys_np, args.key_type, t_o, s_o)
-            rates.append(r)
-            t_spent += dt
-        cpu = {"value": statistics.median(rates), "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": "first %d keys of this workload, %d repetitions, Algorithm 1 with "
-                         "t=%d, s=%d, single-threaded C (host has %d cores)%s"
-                         % (sample_n, len(rates), t_o, s_o, _cpu_cores(),
-                            ", keys only" if args.pairs else "")}
+    if rank == 0 and args.cpu_sample > 0:
+        cpu = _cpu_baseline(args, keys)
 
     sorter.close()
     del keys, out, vals, out_v

@@ -89,6 +89,28 @@ typedef enum {
                                       the legacy default stream (NULL), or on
                                       a stream that is already capturing,
                                       are issued as usual */
+#define BSORT_FLAG_TEST_STALL_SCAN 0x10u /* test of the bounded device
+                                      waits, for 32-bit keys that need
+                                      sampling: the first chunk of Step 7's
+                                      look-back scan never publishes its
+                                      prefix, so the waits of later chunks
+                                      give up after a few thousand polls; the
+                                      call then stops after Step 7 (the
+                                      offsets are wrong, so Steps 8-9 are not
+                                      run and the output is not written) and
+                                      bsort_sync returns BSORT_ETIMEOUT.
+                                      Device-buffer calls only (EINVAL for
+                                      bsort_sort_keys_host).  Never set it
+                                      otherwise */
+#define BSORT_FLAG_MERGE_SORT 0x8u /* keys-only 32-bit sorts: a unit of
+                                      32768 keys sorted by one CTA (a Step-9
+                                      bucket unit, a Step-2 sublist of
+                                      t = 32768) is sorted by comparisons
+                                      (register networks and merges) instead
+                                      of by 7-bit digits over the bits that
+                                      vary in the unit (the default).  Same
+                                      result; kept to measure one against the
+                                      other */
 
 typedef struct {
     int device;                /* CUDA device ordinal the handle works on */
@@ -340,18 +362,21 @@ const char *bsort_kernel_name(bsort_t h, uint32_t index);
  * d_keys_out (the same buffer or disjoint), with the same result as
  * bsort_sort_keys.  Its scratch memory is one fixed array of 12 MiB inside
  * the library, which every GPU that loads the library keeps until the
- * process exits.  The first call on a device looks up that array's device
- * address (cudaGetSymbolAddress); make that first call before any stream
- * capture.  The call makes no cudaMalloc, cudaFree or other allocating call.
- * Every call uses the same array, so calls whose work overlaps on the GPU
- * (on different streams, or from different threads) race and corrupt each
- * other; order them on one stream.
+ * process exits.  The first call in a CUDA context (per device, and again
+ * after a device reset) looks up that array's device address
+ * (cudaGetSymbolAddress) and sets the kernels' attributes; make that first
+ * call before any stream capture.  The call makes no cudaMalloc, cudaFree or
+ * other allocating call.  Every call uses the same array, so calls whose
+ * work overlaps on the GPU (on different streams, or from different threads)
+ * race and corrupt each other; order them on one stream.
  *
  * Returns BSORT_EINVAL for n > BSORT_NOALLOC_MAX_KEYS, a null or partially
  * overlapping pointer, or a key type other than U32/F32 (BSORT_EUNSUPPORTED
  * for U64).  The call is asynchronous on cuda_stream; with wait != 0 it
  * waits for the stream and also returns the device error status
- * (BSORT_ETIMEOUT / BSORT_EINTERNAL) of this call. */
+ * (BSORT_ETIMEOUT / BSORT_EINTERNAL) recorded since the last call that
+ * reported one: this call's, or that of an earlier call made with wait = 0
+ * (whose status is kept, not lost, until such a call reads and clears it). */
 bsort_status bsort_sort_keys_noalloc(bsort_key_type kt, const void *d_keys_in,
                                      void *d_keys_out, uint64_t n, void *cuda_stream,
                                      int wait);

@@ -30,7 +30,8 @@ _lib = None
 def compile_to(src: str, out: str) -> str:
     """Compile a C source of the oracle into the shared library ``out``."""
     tmp = out + ".tmp.%d" % os.getpid()
-    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, src])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", "-o", tmp,
+                           src])
     os.replace(tmp, out)
     return out
 
@@ -72,6 +73,8 @@ def _configure(lib):
     lib.oracle_paper_sort.argtypes = [u64p, u64p, ctypes.c_uint64,
                                       ctypes.c_uint64, ctypes.c_uint64,
                                       ctypes.c_uint64, ctypes.c_uint64] + [u64p] * 13
+    lib.oracle_paper_sort_mt.restype = ctypes.c_int
+    lib.oracle_paper_sort_mt.argtypes = lib.oracle_paper_sort.argtypes + [ctypes.c_int]
     lib.oracle_textbook_sort.restype = ctypes.c_int
     lib.oracle_textbook_sort.argtypes = [u64p, u64p, ctypes.c_uint64,
                                          u64p, u64p]
@@ -139,11 +142,13 @@ def _from_u64_keys(k: np.ndarray, key_type: str) -> np.ndarray:
 
 def paper_sort(keys: np.ndarray, t: int, s: int, key_type: str = "u32",
                vals: Optional[np.ndarray] = None,
-               intermediates: bool = True, b: int = 0) -> Dict[str, np.ndarray]:
+               intermediates: bool = True, b: int = 0, threads: int = 1) -> Dict[str, np.ndarray]:
     """Run Algorithm 1 on the CPU.  Returns the sorted keys (and values) and,
     if ``intermediates``, every intermediate of Steps 2-8 (in the transformed
     key domain for float32).  ``b`` is the number of buckets (0: b = s, the
-    paper's choice)."""
+    paper's choice).  ``threads`` > 1 spreads the per-sublist and per-bucket
+    iterations of Steps 2, 6, 8 and 9 over that many threads (same code,
+    same result)."""
     lib = _load()
     n = int(np.asarray(keys).size)
     k64 = _to_u64_keys(np.asarray(keys).ravel(), key_type)
@@ -166,9 +171,14 @@ def paper_sort(keys: np.ndarray, t: int, s: int, key_type: str = "u32",
             bufs.append(arr)
         else:
             bufs.append(None)
-    rc = lib.oracle_paper_sort(_ptr(k64), _ptr(v64), n, t, s, b,
-                               KEY_MAX[key_type], _ptr(out_k), _ptr(out_v),
-                               *[_ptr(b) for b in bufs])
+    if threads > 1:
+        rc = lib.oracle_paper_sort_mt(_ptr(k64), _ptr(v64), n, t, s, b,
+                                      KEY_MAX[key_type], _ptr(out_k), _ptr(out_v),
+                                      *[_ptr(x) for x in bufs], int(threads))
+    else:
+        rc = lib.oracle_paper_sort(_ptr(k64), _ptr(v64), n, t, s, b,
+                                   KEY_MAX[key_type], _ptr(out_k), _ptr(out_v),
+                                   *[_ptr(x) for x in bufs])
     if rc != 0:
         raise ValueError("oracle_paper_sort failed (n=%d t=%d s=%d b=%d)" % (n, t, s, b))
     res["keys"] = _from_u64_keys(out_k, key_type)

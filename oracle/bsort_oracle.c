@@ -1,7 +1,7 @@
 /*
  * bsort_oracle.c -- TEST INFRASTRUCTURE, not part of the library.
  *
- * A plain, slow, single-threaded CPU statement of GPU Bucket Sort
+ * A plain, slow CPU statement of GPU Bucket Sort
  * (Dehne & Zaboli, "Deterministic Sample Sort for GPUs", Section 4,
  * Algorithm 1, Steps 1-9), written from the paper's step definitions so that
  * a reader can check every step against the text by eye.  Only the tests,
@@ -37,7 +37,14 @@
  *   - Parity is pinned by the tests (brute force on tiny inputs, an
  *     independent textbook merge sort, closed-form bucket sizes and the
  *     bucket-size bound), not by this file itself.
+ *
+ * oracle_paper_sort runs on one thread.  oracle_paper_sort_mt runs the same
+ * code with the independent iterations of Steps 2, 6 and 8 (one per
+ * sublist) and Step 9 (one per bucket) spread over POSIX threads in
+ * contiguous ranges; nothing else changes, so both give identical results.
+ * It exists only to time the oracle on all host cores.
  */
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -157,6 +164,145 @@ uint64_t oracle_num_sublists(uint64_t n, uint64_t t)
     return t ? (n + t - 1) / t : 0;
 }
 
+/* ---- running independent loop iterations on several threads ------------ */
+
+/* fn(ctx, lo, hi) runs iterations [lo, hi) of a loop whose iterations touch
+ * disjoint data; it returns nonzero on failure. */
+typedef int (*range_fn)(void *ctx, uint64_t lo, uint64_t hi);
+
+typedef struct {
+    range_fn fn;
+    void *ctx;
+    uint64_t lo, hi;
+    int rc;
+} range_job;
+
+static void *range_thread(void *arg)
+{
+    range_job *j = (range_job *)arg;
+    j->rc = j->fn(j->ctx, j->lo, j->hi);
+    return NULL;
+}
+
+/* Iterations [0, count) in `threads` contiguous ranges (threads <= 1: on the
+ * calling thread; a range whose thread cannot be started runs on the calling
+ * thread).  Returns nonzero if any range failed. */
+static int run_ranges(int threads, uint64_t count, range_fn fn, void *ctx)
+{
+    if (threads <= 1 || count < 2) return fn(ctx, 0, count);
+    if ((uint64_t)threads > count) threads = (int)count;
+    pthread_t *tid = (pthread_t *)malloc((size_t)threads * sizeof(pthread_t));
+    range_job *job = (range_job *)malloc((size_t)threads * sizeof(range_job));
+    char *live = (char *)calloc((size_t)threads, 1);
+    if (!tid || !job || !live) {
+        free(tid);
+        free(job);
+        free(live);
+        return fn(ctx, 0, count);
+    }
+    int rc = 0;
+    for (int k = 0; k < threads; ++k) {
+        job[k].fn = fn;
+        job[k].ctx = ctx;
+        job[k].lo = count * (uint64_t)k / (uint64_t)threads;
+        job[k].hi = count * (uint64_t)(k + 1) / (uint64_t)threads;
+        job[k].rc = 0;
+        live[k] = pthread_create(&tid[k], NULL, range_thread, &job[k]) == 0;
+        if (!live[k]) job[k].rc = fn(ctx, job[k].lo, job[k].hi);
+    }
+    for (int k = 0; k < threads; ++k) {
+        if (live[k]) pthread_join(tid[k], NULL);
+        rc |= job[k].rc;
+    }
+    free(tid);
+    free(job);
+    free(live);
+    return rc;
+}
+
+/* The arrays of one oracle_paper_sort call, shared by its loop bodies. */
+typedef struct {
+    oelem_t *A, *B;
+    orec_t *G;
+    uint64_t *c, *a, *l;
+    uint64_t m, t, b, np;
+} sort_state;
+
+/* Step 2: local sort of sublists [lo, hi) (stable: composite order). */
+static int step2_sublists(void *ctx, uint64_t lo, uint64_t hi)
+{
+    sort_state *st = (sort_state *)ctx;
+    oelem_t *A = st->A;
+    const uint64_t t = st->t;
+    for (uint64_t i = lo; i < hi; ++i)
+        if (msort_elems(A + i * t, t)) return -1;
+    return 0;
+}
+
+/* Step 6: sample indexing for sublists [lo, hi).  c[i][j+1] = number of
+ * items of sorted sublist i that are <= g_j in composite order, where the
+ * item at rank r of sublist i is (key, i*t + r); found by binary search
+ * because the sublist is sorted in that order.  c[i][0] = 0.  Bucket A_ij is
+ * ranks [c[i][j], c[i][j+1]) and a_ij is its size. */
+static int step6_sublists(void *ctx, uint64_t i0, uint64_t i1)
+{
+    sort_state *st = (sort_state *)ctx;
+    const oelem_t *A = st->A;
+    const orec_t *G = st->G;
+    uint64_t *c = st->c, *a = st->a;
+    const uint64_t t = st->t, b = st->b, m = st->m;
+    for (uint64_t i = i0; i < i1; ++i) {
+        c[i * (b + 1) + 0] = 0;
+        for (uint64_t j = 0; j < b; ++j) {
+            uint64_t lo = 0, hi = t; /* first rank whose item is > g_j */
+            while (lo < hi) {
+                uint64_t mid = lo + (hi - lo) / 2;
+                orec_t item;
+                item.key = A[i * t + mid].key;
+                item.p = i * t + mid;
+                if (rec_less(&G[j], &item)) hi = mid;
+                else lo = mid + 1;
+            }
+            c[i * (b + 1) + j + 1] = lo;
+        }
+        for (uint64_t j = 0; j < b; ++j)
+            a[j * m + i] = c[i * (b + 1) + j + 1] - c[i * (b + 1) + j];
+    }
+    return 0;
+}
+
+/* Step 8 for sublists [lo, hi): move every bucket A_ij to l_ij. */
+static int step8_sublists(void *ctx, uint64_t i0, uint64_t i1)
+{
+    sort_state *st = (sort_state *)ctx;
+    const oelem_t *A = st->A;
+    oelem_t *B = st->B;
+    const uint64_t *c = st->c, *a = st->a, *l = st->l;
+    const uint64_t t = st->t, b = st->b, m = st->m;
+    for (uint64_t i = i0; i < i1; ++i)
+        for (uint64_t j = 0; j < b; ++j) {
+            uint64_t src = i * t + c[i * (b + 1) + j];
+            uint64_t len = a[j * m + i];
+            for (uint64_t q = 0; q < len; ++q) B[l[j * m + i] + q] = A[src + q];
+        }
+    return 0;
+}
+
+/* Step 9 for buckets [j0, j1): sort every sublist B_j. */
+static int step9_buckets(void *ctx, uint64_t j0, uint64_t j1)
+{
+    sort_state *st = (sort_state *)ctx;
+    oelem_t *B = st->B;
+    const uint64_t *l = st->l;
+    const uint64_t b = st->b, m = st->m, np = st->np;
+    for (uint64_t j = j0; j < j1; ++j) {
+        uint64_t lo = l[j * m + 0];
+        uint64_t hi = (j + 1 < b) ? l[(j + 1) * m + 0] : np;
+        if (msort_elems(B + lo, hi - lo)) return -1;
+    }
+    return 0;
+}
+
 /*
  * GPU Bucket Sort, Algorithm 1 Steps 1-9, with every intermediate exposed.
  *
@@ -166,6 +312,7 @@ uint64_t oracle_num_sublists(uint64_t n, uint64_t t)
  *   b          : global samples = buckets (Step 5); 0 means b = s (paper)
  *   key_max    : the largest key of the key type (pad sentinel key)
  *   out_keys, out_vals : n sorted items (out_vals may be NULL)
+ *   threads    : (oracle_paper_sort_mt) threads for Steps 2, 6, 8 and 9
  *
  * Optional intermediates (NULL to skip), with m = ceil(n/t), n' = m*t:
  *   tile_keys, tile_pos   [n']   Step 2: sorted sublists, sublist-major
@@ -178,15 +325,15 @@ uint64_t oracle_num_sublists(uint64_t n, uint64_t t)
  *
  * Returns 0, or -1 on bad parameters / allocation failure.
  */
-int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
-                      uint64_t t, uint64_t s, uint64_t b, uint64_t key_max,
-                      uint64_t *out_keys, uint64_t *out_vals,
-                      uint64_t *tile_keys, uint64_t *tile_pos,
-                      uint64_t *samp_keys, uint64_t *samp_p,
-                      uint64_t *spl_keys, uint64_t *spl_p,
-                      uint64_t *counts, uint64_t *offsets,
-                      uint64_t *reloc_keys, uint64_t *reloc_pos,
-                      uint64_t *bucket_start)
+int oracle_paper_sort_mt(const uint64_t *keys, const uint64_t *vals, uint64_t n,
+                         uint64_t t, uint64_t s, uint64_t b, uint64_t key_max,
+                         uint64_t *out_keys, uint64_t *out_vals,
+                         uint64_t *tile_keys, uint64_t *tile_pos,
+                         uint64_t *samp_keys, uint64_t *samp_p,
+                         uint64_t *spl_keys, uint64_t *spl_p,
+                         uint64_t *counts, uint64_t *offsets,
+                         uint64_t *reloc_keys, uint64_t *reloc_pos,
+                         uint64_t *bucket_start, int threads)
 {
     if (n == 0) return 0;
     if (t == 0 || s == 0 || s > t || (t % s) != 0) return -1;
@@ -205,6 +352,9 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
     uint64_t *a = (uint64_t *)malloc(m * b * sizeof(uint64_t));
     uint64_t *l = (uint64_t *)malloc(m * b * sizeof(uint64_t));
     oelem_t *B = (oelem_t *)malloc(np * sizeof(oelem_t));
+    sort_state st;
+    st.A = A; st.B = B; st.G = G; st.c = c; st.a = a; st.l = l;
+    st.m = m; st.t = t; st.b = b; st.np = np;
     if (!A || !S || !G || !c || !a || !l || !B) goto fail;
 
     for (uint64_t x = 0; x < np; ++x) {
@@ -219,8 +369,7 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
     }
 
     /* Step 2: local sort of every sublist A_i (stable: composite order). */
-    for (uint64_t i = 0; i < m; ++i)
-        if (msort_elems(A + i * t, t)) goto fail;
+    if (run_ranges(threads, m, step2_sublists, &st)) goto fail;
     if (tile_keys)
         for (uint64_t x = 0; x < np; ++x) tile_keys[x] = A[x].key;
     if (tile_pos)
@@ -249,28 +398,8 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
     if (spl_p)
         for (uint64_t j = 0; j < b; ++j) spl_p[j] = G[j].p;
 
-    /* Step 6: sample indexing.  c[i][j+1] = number of items of sorted
-     * sublist i that are <= g_j in composite order, where the item at rank r
-     * of sublist i is (key, i*t + r); found by binary search because the
-     * sublist is sorted in that order.  c[i][0] = 0.  Bucket A_ij is ranks
-     * [c[i][j], c[i][j+1]) and a_ij is its size. */
-    for (uint64_t i = 0; i < m; ++i) {
-        c[i * (b + 1) + 0] = 0;
-        for (uint64_t j = 0; j < b; ++j) {
-            uint64_t lo = 0, hi = t; /* first rank whose item is > g_j */
-            while (lo < hi) {
-                uint64_t mid = lo + (hi - lo) / 2;
-                orec_t item;
-                item.key = A[i * t + mid].key;
-                item.p = i * t + mid;
-                if (rec_less(&G[j], &item)) hi = mid;
-                else lo = mid + 1;
-            }
-            c[i * (b + 1) + j + 1] = lo;
-        }
-        for (uint64_t j = 0; j < b; ++j)
-            a[j * m + i] = c[i * (b + 1) + j + 1] - c[i * (b + 1) + j];
-    }
+    /* Step 6: sample indexing, every sublist (step6_sublists). */
+    if (run_ranges(threads, m, step6_sublists, &st)) goto fail;
     if (counts) memcpy(counts, a, m * b * sizeof(uint64_t));
 
     /* Step 7: prefix sum over a_11..a_m1, a_12..a_m2, ..., a_1s..a_ms
@@ -285,12 +414,7 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
     if (offsets) memcpy(offsets, l, m * b * sizeof(uint64_t));
 
     /* Step 8: move every bucket A_ij to l_ij; B_j = A_1j u ... u A_mj. */
-    for (uint64_t i = 0; i < m; ++i)
-        for (uint64_t j = 0; j < b; ++j) {
-            uint64_t src = i * t + c[i * (b + 1) + j];
-            uint64_t len = a[j * m + i];
-            for (uint64_t q = 0; q < len; ++q) B[l[j * m + i] + q] = A[src + q];
-        }
+    if (run_ranges(threads, m, step8_sublists, &st)) goto fail;
     if (reloc_keys)
         for (uint64_t x = 0; x < np; ++x) reloc_keys[x] = B[x].key;
     if (reloc_pos)
@@ -301,11 +425,7 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
     }
 
     /* Step 9: sort every sublist B_j. */
-    for (uint64_t j = 0; j < b; ++j) {
-        uint64_t lo = l[j * m + 0];
-        uint64_t hi = (j + 1 < b) ? l[(j + 1) * m + 0] : np;
-        if (msort_elems(B + lo, hi - lo)) goto fail;
-    }
+    if (run_ranges(threads, b, step9_buckets, &st)) goto fail;
 
     /* Output: the first n items (pads are the largest items, so they are
      * exactly the last n' - n). */
@@ -319,6 +439,22 @@ int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
 fail:
     free(A); free(S); free(G); free(c); free(a); free(l); free(B);
     return -1;
+}
+
+/* The single-threaded form (the statement the tests pin). */
+int oracle_paper_sort(const uint64_t *keys, const uint64_t *vals, uint64_t n,
+                      uint64_t t, uint64_t s, uint64_t b, uint64_t key_max,
+                      uint64_t *out_keys, uint64_t *out_vals,
+                      uint64_t *tile_keys, uint64_t *tile_pos,
+                      uint64_t *samp_keys, uint64_t *samp_p,
+                      uint64_t *spl_keys, uint64_t *spl_p,
+                      uint64_t *counts, uint64_t *offsets,
+                      uint64_t *reloc_keys, uint64_t *reloc_pos,
+                      uint64_t *bucket_start)
+{
+    return oracle_paper_sort_mt(keys, vals, n, t, s, b, key_max, out_keys, out_vals,
+                                tile_keys, tile_pos, samp_keys, samp_p, spl_keys, spl_p,
+                                counts, offsets, reloc_keys, reloc_pos, bucket_start, 1);
 }
 
 /* ---- O2: independent textbook bottom-up merge sort ----------------------- */

@@ -16,7 +16,7 @@ __all__ = [
     "BSORT_OK", "BSORT_EINVAL", "BSORT_ENOMEM", "BSORT_ECUDA", "BSORT_ETIMEOUT",
     "BSORT_EBUSY", "BSORT_ENOTREADY", "BSORT_EUNSUPPORTED", "BSORT_EINTERNAL",
     "BSORT_U32", "BSORT_F32", "BSORT_U64", "BSORT_FLAG_TIMING", "BSORT_FLAG_LOW_MEMORY",
-    "BSORT_FLAG_GRAPHS",
+    "BSORT_FLAG_GRAPHS", "BSORT_FLAG_MERGE_SORT", "BSORT_FLAG_TEST_STALL_SCAN",
     "bsort_config", "bsort_plan_info", "BsortError", "load_library",
     "bsort_create", "bsort_destroy", "bsort_plan", "bsort_sort_keys",
     "bsort_sort_pairs", "bsort_sort_keys_host", "bsort_sync",
@@ -33,6 +33,8 @@ BSORT_U32, BSORT_F32, BSORT_U64 = 0, 1, 2
 BSORT_FLAG_TIMING = 0x1
 BSORT_FLAG_LOW_MEMORY = 0x2
 BSORT_FLAG_GRAPHS = 0x4
+BSORT_FLAG_MERGE_SORT = 0x8
+BSORT_FLAG_TEST_STALL_SCAN = 0x10
 (BSORT_IM_TILES, BSORT_IM_SAMPLES, BSORT_IM_SPLITTERS, BSORT_IM_COUNTS,
  BSORT_IM_OFFSETS, BSORT_IM_RELOCATED) = range(6)
 
@@ -301,12 +303,14 @@ class BucketSorter:
 
     def __init__(self, device: int = 0, tile: int = 0, samples: int = 0,
                  timing: bool = False, workspace_bytes: int = 0, low_memory: bool = False,
-                 buckets: int = 0, batch_direct_max: int = 0, graphs: bool = False):
+                 buckets: int = 0, batch_direct_max: int = 0, graphs: bool = False,
+                 merge_sort: bool = False, flags: int = 0):
         import torch
         self.torch = torch
         self.device = device
         self.flags = ((BSORT_FLAG_TIMING if timing else 0) | (BSORT_FLAG_LOW_MEMORY if low_memory else 0)
-                      | (BSORT_FLAG_GRAPHS if graphs else 0))
+                      | (BSORT_FLAG_GRAPHS if graphs else 0)
+                      | (BSORT_FLAG_MERGE_SORT if merge_sort else 0) | int(flags))
         self.tile, self.samples, self.buckets = tile, samples, buckets
         self.batch_direct_max = batch_direct_max
         self.ws = None

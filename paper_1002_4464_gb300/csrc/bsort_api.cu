@@ -15,6 +15,8 @@
 #include <utility>
 #include <vector>
 
+#include <cuda.h>
+
 #include "../../include/bsort.h"
 #include "bsort_internal.h"
 
@@ -58,6 +60,7 @@ struct Plan {
         off_rec_a, off_rec_b, off_spl, off_counts, off_offsets, off_status,
         off_units, off_units2, off_srcb, off_blk, off_cum, off_jr, total;
     bool relocate;  // materialise Step 8 (else fused into Step 9's load)
+    bool radix;     // 32768-key chunks of 32-bit keys sorted by digits
 };
 
 }  // namespace
@@ -470,6 +473,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         return at;
     };
     P->relocate = P->wide || !(h && (h->flags & BSORT_FLAG_LOW_MEMORY));
+    P->radix = !P->pairs && !P->wide && !(h && (h->flags & BSORT_FLAG_MERGE_SORT));
     P->off_hdr = take(kAlign);  // error word (int) + scan ticket (uint32)
     if (!I.single_tile) {
         const uint64_t np = I.n_padded;
@@ -749,6 +753,8 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
 {
     bsort_status rs = prepare(h);
     if (rs != BSORT_OK) return rs;
+    if (hp && (h->flags & BSORT_FLAG_TEST_STALL_SCAN))
+        return fail(h, BSORT_EINVAL, "BSORT_FLAG_TEST_STALL_SCAN is for device-buffer calls");
     Plan P;
     rs = make_plan(h, kt, vb, n, &P);
     if (rs != BSORT_OK) return rs;
@@ -781,7 +787,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
                                                1, n, n, is_f32, (int)vb, kout, vout, err, none,
                                                st)
                     : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, kin, nullptr, 1, n,
-                                              n, is_f32, kout, err, none, st),
+                                              n, is_f32, kout, err, none, st, P.radix),
             "step9_single_unit");
         return BSORT_OK;
     }
@@ -821,7 +827,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
                 if (e != cudaSuccess) return cuda_fail(h, e, "host-to-device copy");
             }
             SEQ(launch_sublist_sort_keys(P.tile_chunk, (int)I.tile_ctas, kin, n, mc, is_f32,
-                                         I.s, tiles_k, samples, st, t0),
+                                         I.s, tiles_k, samples, st, t0, P.radix),
                 "step1_3_sublist_sort");
         }
     } else {
@@ -829,7 +835,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
                                                 I.m, is_f32, (int)vb, I.s, tiles_k, tiles_v,
                                                 samples, st)
                     : launch_sublist_sort_keys(P.tile_chunk, (int)I.tile_ctas, kin, n, I.m,
-                                               is_f32, I.s, tiles_k, samples, st),
+                                               is_f32, I.s, tiles_k, samples, st, 0, P.radix),
             "step1_3_sublist_sort");
     }
     // Steps 4-5
@@ -854,8 +860,11 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     uint32_t *jr = reinterpret_cast<uint32_t *>(ws + P.off_jr);
     SEQ(launch_sample_index(tiles_k, spl, I.t, I.b, I.m, jr, cum, st), "step6_sample_index");
     // Step 7 (also a_ij and the run starts from the cumulative counts)
-    SEQ(launch_scan_cum(cum, I.m, I.t, counts, srcb, offsets, P.n_runs, status, ticket, err, st),
+    SEQ(launch_scan_cum(cum, I.m, I.t, counts, srcb, offsets, P.n_runs, status, ticket, err, st,
+                        (h->flags & BSORT_FLAG_TEST_STALL_SCAN) != 0),
         "step7_prefix_sum");
+    // a stalled scan leaves inconsistent offsets: Steps 8-9 must not read them
+    if (h->flags & BSORT_FLAG_TEST_STALL_SCAN) return BSORT_OK;
     // Step 8: materialised, unless BSORT_FLAG_LOW_MEMORY fuses it into the
     // load of Step 9, which then gathers every unit from the runs A_ij
     GatherSrc g;
@@ -902,12 +911,12 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
         const uint32_t g2 = std::max(1u, (uint32_t)((sms * 7 / 8) / (int)I.unit_ctas));
         for (int g = 0; g < G; ++g) {
             SEQ(launch_bucket_sort_keys_range(c1, k1, s9k, units, r1 + g, g1, n, I.n_padded,
-                                              is_f32, kout, err, st),
+                                              is_f32, kout, err, st, P.radix),
                 "step9_bucket_sort");
             if (units2)
                 SEQ(launch_bucket_sort_keys_range(P.unit_chunk, (int)I.unit_ctas, s9k, units2,
                                                   r2 + g, g2, n, I.n_padded, is_f32, kout, err,
-                                                  st),
+                                                  st, P.radix),
                     "step9_bucket_sort_large");
             const uint64_t p0 = std::min<uint64_t>((uint64_t)g * np / G, n);
             const uint64_t p1 = std::min<uint64_t>((uint64_t)(g + 1) * np / G, n);
@@ -927,7 +936,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     SEQ(P.pairs ? launch_bucket_sort_pairs(c1, k1, s9k, s9v, units, I.b, n, I.n_padded, is_f32,
                                            (int)vb, kout, vout, err, g, st)
                 : launch_bucket_sort_keys(c1, k1, s9k, units, I.b, n, I.n_padded, is_f32, kout,
-                                          err, g, st),
+                                          err, g, st, P.radix),
         "step9_bucket_sort");
     if (P.small_chunk) {
         const uint32_t u2 = large_units_max(I.n_padded, q1, I.b);
@@ -935,7 +944,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
                                                u2, n, I.n_padded, is_f32, (int)vb, kout, vout,
                                                err, g, st)
                     : launch_bucket_sort_keys(P.unit_chunk, (int)I.unit_ctas, s9k, units2, u2, n,
-                                              I.n_padded, is_f32, kout, err, g, st),
+                                              I.n_padded, is_f32, kout, err, g, st, P.radix),
             "step9_bucket_sort_large");
     }
     return BSORT_OK;
@@ -1800,7 +1809,8 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
             h->direct_max = cfg->batch_direct_max;
         }
         if (cfg->flags &
-            ~(uint32_t)(BSORT_FLAG_TIMING | BSORT_FLAG_LOW_MEMORY | BSORT_FLAG_GRAPHS)) {
+            ~(uint32_t)(BSORT_FLAG_TIMING | BSORT_FLAG_LOW_MEMORY | BSORT_FLAG_GRAPHS |
+                        BSORT_FLAG_MERGE_SORT | BSORT_FLAG_TEST_STALL_SCAN)) {
             delete h;
             return BSORT_EINVAL;
         }
@@ -2204,14 +2214,53 @@ const char *bsort_last_error(bsort_t h)
 // ---------------------------------------------------------------- no-alloc entry
 // Scratch for bsort_sort_keys_noalloc: a fixed device array in this file,
 // sized for the largest plan of at most BSORT_NOALLOC_MAX_KEYS keys (about
-// 8.5 MiB).  Host code may not use the symbol as a device address; the
-// device address is looked up once per device with cudaGetSymbolAddress.
+// 8.5 MiB).  Host code may not use the symbol as a device address; its
+// device address is looked up with cudaGetSymbolAddress once per CUDA
+// context (the set-up also configures the kernels' attributes), keyed by the
+// context's id, so that a device reset, which makes a new context and may
+// place the array elsewhere, is noticed and the set-up done again.
 namespace {
 constexpr size_t kNoallocScratchBytes = (size_t)12 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 constexpr int kNoallocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-void *g_noalloc_ptr[kNoallocMaxDevices] = {};
+struct NoallocSetup {
+    unsigned long long ctx_id = 0;  // context the entry below belongs to (0: none)
+    void *scratch = nullptr;        // device address of g_noalloc_scratch there
+};
+NoallocSetup g_noalloc[kNoallocMaxDevices];
+
+typedef CUresult (*CtxGetCurrentFn)(CUcontext *);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long *);
+
+// Id of the calling thread's current CUDA context, or 0 when there is none
+// or it cannot be read (the driver entry points are fetched through the
+// runtime, so the library needs no link against the driver library).
+unsigned long long current_context_id()
+{
+    static CtxGetCurrentFn get_current = nullptr;
+    static CtxGetIdFn get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<CtxGetIdFn>(f);
+    });
+    if (!get_current || !get_id) return 0;
+    CUcontext c = nullptr;
+    unsigned long long id = 0;
+    if (get_current(&c) != CUDA_SUCCESS || !c) return 0;
+    if (get_id(c, &id) != CUDA_SUCCESS) return 0;
+    return id;
+}
 }  // namespace
 
 extern "C" bsort_status bsort_sort_keys_noalloc(bsort_key_type kt, const void *d_keys_in,
@@ -2220,6 +2269,7 @@ extern "C" bsort_status bsort_sort_keys_noalloc(bsort_key_type kt, const void *d
 {
     if (n > BSORT_NOALLOC_MAX_KEYS) return BSORT_EINVAL;
     if (kt == BSORT_U64) return BSORT_EUNSUPPORTED;
+    if (kt != BSORT_U32 && kt != BSORT_F32) return BSORT_EINVAL;
     if (n && (!d_keys_in || !d_keys_out)) return BSORT_EINVAL;
     if (n && d_keys_in != d_keys_out && overlaps(d_keys_in, n * 4, d_keys_out, n * 4))
         return BSORT_EINVAL;
@@ -2229,13 +2279,19 @@ extern "C" bsort_status bsort_sort_keys_noalloc(bsort_key_type kt, const void *d
     void *scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-        if (!g_noalloc_ptr[dev]) {
+        NoallocSetup &S = g_noalloc[dev];
+        const unsigned long long id = current_context_id();
+        if (id == 0 || S.ctx_id != id) {
+            // set-up for this context: the array's device address (this also
+            // makes the context current if it was not) and kernel attributes
             void *p = nullptr;
             if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
                 return BSORT_ECUDA;
-            g_noalloc_ptr[dev] = p;
+            if (init_kernels() != cudaSuccess) return BSORT_ECUDA;
+            S.scratch = p;
+            S.ctx_id = current_context_id();  // 0 if unreadable: set up again next call
         }
-        scratch = g_noalloc_ptr[dev];
+        scratch = S.scratch;
     }
     // a handle on the stack whose fixed workspace is the scratch array
     bsort_ctx ctx;
@@ -2244,14 +2300,16 @@ extern "C" bsort_status bsort_sort_keys_noalloc(bsort_key_type kt, const void *d
     ctx.ws_bytes = kNoallocScratchBytes;
     ctx.ws_fixed = true;
     ctx.ws_owned = false;
+    ctx.kernels_ready = true;
     Plan P;
     bsort_status st = make_plan(&ctx, kt, 0, n, &P);
     if (st != BSORT_OK) return st;
     if (P.total > kNoallocScratchBytes) return BSORT_ENOMEM;
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
-    // the array keeps the previous call's contents: the error word must start
-    // at zero (the scan's state is cleared by the sort itself)
-    if (cudaMemsetAsync(scratch, 0, kAlign, stream) != cudaSuccess) return BSORT_ECUDA;
+    // The error word at the start of the array is not cleared here: kernels
+    // only ever set it (first error wins), so a failure of a call made with
+    // wait = 0 stays recorded until a call with wait != 0 reports and clears
+    // it.  The array starts at zero when the library's device code is loaded.
     st = run_sort(&ctx, kt, d_keys_in, nullptr, d_keys_out, nullptr, 0, n, stream);
     if (st != BSORT_OK || !wait) return st;
     if (cudaStreamSynchronize(stream) != cudaSuccess) return BSORT_ECUDA;
@@ -2259,5 +2317,8 @@ extern "C" bsort_status bsort_sort_keys_noalloc(bsort_key_type kt, const void *d
     if (cudaMemcpy(&word, scratch, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
         return BSORT_ECUDA;
     if (word == 0) return BSORT_OK;
+    if (cudaMemsetAsync(scratch, 0, sizeof(int), stream) != cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+        return BSORT_ECUDA;
     return word == BSORT_ETIMEOUT ? BSORT_ETIMEOUT : BSORT_EINTERNAL;
 }

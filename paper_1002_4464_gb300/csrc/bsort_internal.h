@@ -29,9 +29,28 @@ cudaError_t init_sort_pairs_kernels();
 // `ctas` CTAs of `chunk` items each; write the sorted sublists (keys, and
 // values for pairs) and s sample records per sublist.
 // Steps 1-3 for sublists tile0 .. tile0 + m - 1.
+// radix: a sublist of 32768 keys sorted by one CTA is sorted by digits
+// (cta_radix_sort) instead of by comparisons; both give the same sublists.
 cudaError_t launch_sublist_sort_keys(int chunk, int ctas, const void *keys_in, uint64_t n,
                                      uint32_t m, int is_f32, uint32_t s, uint32_t *tiles_k,
-                                     uint64_t *samples, cudaStream_t st, uint32_t tile0 = 0);
+                                     uint64_t *samples, cudaStream_t st, uint32_t tile0 = 0,
+                                     bool radix = false);
+// The radix-sorting forms (bsort_sort_keys_radix.cu) that the functions
+// above call for units of 32768 keys sorted by one CTA when `radix` is set.
+cudaError_t init_sort_keys_radix_kernels();
+cudaError_t launch_sublist_sort_keys_radix(int ctas, const void *keys_in, uint64_t n, uint32_t m,
+                                           int is_f32, uint32_t s, uint32_t *tiles_k,
+                                           uint64_t *samples, cudaStream_t st, uint32_t tile0);
+struct GatherSrc;
+cudaError_t launch_bucket_sort_keys_radix(int ctas, const void *src_k, const uint32_t *units,
+                                          uint32_t max_units, uint64_t n, uint64_t n_pad,
+                                          int is_f32, void *out_k, int *err, const GatherSrc &g,
+                                          cudaStream_t st);
+cudaError_t launch_bucket_sort_keys_range_radix(int ctas, const void *src_k,
+                                                const uint32_t *units, const uint32_t *range,
+                                                uint32_t grid_units, uint64_t n, uint64_t n_pad,
+                                                int is_f32, void *out_k, int *err,
+                                                cudaStream_t st);
 cudaError_t launch_sublist_sort_pairs(int chunk, int ctas, const void *keys_in,
                                       const void *vals_in, uint64_t n, uint32_t m, int is_f32,
                                       int val_bytes, uint32_t s, uint32_t *tiles_k,
@@ -59,13 +78,15 @@ constexpr uint32_t kLoopUnits = 256;
 
 cudaError_t launch_bucket_sort_keys(int chunk, int ctas, const void *src_k, const uint32_t *units,
                                     uint32_t max_units, uint64_t n, uint64_t n_pad, int is_f32,
-                                    void *out_k, int *err, const GatherSrc &g, cudaStream_t st);
+                                    void *out_k, int *err, const GatherSrc &g, cudaStream_t st,
+                                    bool radix = false);
 // Step 9 (keys) over units range[0] .. range[1] - 1 of a list, range in
 // device memory, by a grid of grid_units units that loop over them.
 cudaError_t launch_bucket_sort_keys_range(int chunk, int ctas, const void *src_k,
                                           const uint32_t *units, const uint32_t *range,
                                           uint32_t grid_units, uint64_t n, uint64_t n_pad,
-                                          int is_f32, void *out_k, int *err, cudaStream_t st);
+                                          int is_f32, void *out_k, int *err, cudaStream_t st,
+                                          bool radix = false);
 // For G position slices [g*n_pad/G, (g+1)*n_pad/G): ranges[g] = first unit of
 // the list whose begin is at or above g*n_pad/G (ranges[G] = the count).
 cudaError_t launch_unit_ranges(const uint32_t *units, uint32_t n_pad, uint32_t G,
@@ -113,10 +134,13 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
 // Step 7 from Step 6's cumulative counts (item e = j*m + i): counts[e] =
 // a_ij = cum[e] - cum[e - m] (0 for j = 0), srcb[e] = i*t + cum[e - m] (the
 // start of run A_ij), out = the exclusive prefix of a in bucket-major order.
+// stall_first (a test of the bounded look-back wait): chunk 0 never
+// publishes its prefix and the waits give up after a few thousand polls,
+// recording DEV_TIMEOUT in *err (the offsets are then wrong).
 cudaError_t launch_scan_cum(const uint32_t *cum, uint32_t m, uint32_t t, uint32_t *counts,
                             uint32_t *srcb, uint32_t *out, uint32_t n_items,
                             unsigned long long *status, uint32_t *ticket, int *err,
-                            cudaStream_t st);
+                            cudaStream_t st, bool stall_first = false);
 
 constexpr int kRelocateSmemMax = 220 * 1024;
 constexpr int kRelocPart = 8192;  // sublist items per Step-8 CTA

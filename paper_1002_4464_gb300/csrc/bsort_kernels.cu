@@ -268,6 +268,7 @@ constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr unsigned long long kValMask = (1ull << 62) - 1;
 constexpr int kSpinLimit = 1 << 22;  // ~0.5-1 s with the back-off below
+constexpr int kTestSpinLimit = 4096;  // the stalled-scan test: well under a millisecond
 
 __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long *p)
 {
@@ -278,7 +279,8 @@ template <int T, int ITEMS>
 __global__ void __launch_bounds__(T)
 k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_items,
        unsigned long long *status, uint32_t *ticket, int *err, const uint32_t *__restrict__ cum,
-       uint32_t m, uint32_t t, uint32_t *__restrict__ counts, uint32_t *__restrict__ srcb)
+       uint32_t m, uint32_t t, uint32_t *__restrict__ counts, uint32_t *__restrict__ srcb,
+       int spin_limit, int stall_first)
 {
     __shared__ uint32_t s_chunk;
     __shared__ uint32_t s_warp[T / 32];
@@ -357,7 +359,10 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
         const uint32_t agg = s_warp[T / 32 - 1] + s_last;
         uint32_t prefix = 0;
         if (chunk == 0) {
-            if (lane == 0) atomicExch(&status[0], kFlagInc | agg);
+            // (stall_first, a test of the bounded wait: chunk 0 never
+            // publishes, so the look-back of every later chunk that reaches
+            // it gives up after spin_limit polls and records DEV_TIMEOUT)
+            if (lane == 0 && !stall_first) atomicExch(&status[0], kFlagInc | agg);
         } else {
             if (lane == 0) atomicExch(&status[chunk], kFlagAgg | agg);
             int p = (int)chunk - 1;
@@ -368,7 +373,7 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
                 unsigned long long st = q >= 0 ? ld_volatile(&status[q]) : (kFlagInc | 0ull);
                 // wait until every inspected chunk has published something
                 while (__any_sync(0xFFFFFFFFu, (st >> 62) == 0)) {
-                    if (++spins > kSpinLimit) {
+                    if (++spins > spin_limit) {
                         timed_out = true;
                         break;
                     }
@@ -860,18 +865,20 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
 {
     const uint32_t chunks = (n_items + kScanChunk - 1) / kScanChunk;
     k_scan<256, 16><<<chunks, 256, 0, st>>>(in, out, n_items, status, ticket, err, nullptr, 1u,
-                                            0u, nullptr, nullptr);
+                                            0u, nullptr, nullptr, kSpinLimit, 0);
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan_cum(const uint32_t *cum, uint32_t m, uint32_t t, uint32_t *counts,
                             uint32_t *srcb, uint32_t *out, uint32_t n_items,
                             unsigned long long *status, uint32_t *ticket, int *err,
-                            cudaStream_t st)
+                            cudaStream_t st, bool stall_first)
 {
     const uint32_t chunks = (n_items + kScanChunk - 1) / kScanChunk;
     k_scan<256, 16><<<chunks, 256, 0, st>>>(nullptr, out, n_items, status, ticket, err, cum, m,
-                                            t, counts, srcb);
+                                            t, counts, srcb,
+                                            stall_first ? kTestSpinLimit : kSpinLimit,
+                                            stall_first ? 1 : 0);
     return cudaGetLastError();
 }
 

@@ -12,8 +12,33 @@
 
 #include "bsort_device.cuh"
 #include "bsort_internal.h"
+#include "bsort_radix.cuh"
 
 namespace bsort {
+
+// Digit width of the radix-sorting CTAs (128 digits per pass).
+constexpr int kRadixBits = 7;
+
+// Dynamic shared memory of one sorting CTA: the padded tile, plus the radix
+// sort's counters when the CTA sorts 32-bit keys by digits (RADIX).
+template <typename K, int T, int E, bool RADIX>
+constexpr int sort_smem_bytes()
+{
+    return RADIX ? RadixSmem<T, E, kRadixBits>::kBytes : padded_elems<K>(T * E) * (int)sizeof(K);
+}
+
+// The in-CTA sort of one chunk: the comparison sort (cta_sort) or, for
+// 32-bit keys, the radix sort (cta_radix_sort); both leave the same result.
+template <typename K, int T, int E, bool RADIX>
+__device__ __forceinline__ void chunk_sort(K (&v)[E], K *sm, int len)
+{
+    if constexpr (RADIX) {
+        static_assert(sizeof(K) == 4, "the radix sort takes 32-bit keys");
+        cta_radix_sort<T, E, kRadixBits>(v, sm, len);
+    } else {
+        cta_sort<K, T, E>(v, sm, len);
+    }
+}
 
 // ============================================================ Steps 1-3
 // Cluster c sorts sublist i = tile0 + c (t = C*T*E items); CTA r loads positions
@@ -21,7 +46,7 @@ namespace bsort {
 // [r*T*E, (r+1)*T*E): it writes them to the sorted-sublist array and emits
 // the samples (ranks (k+1)w - 1) that fall in that range as key << 32 | p,
 // p = i*t + r.
-template <int T, int E, bool PAIRS, int C>
+template <int T, int E, bool PAIRS, int C, bool RADIX = false>
 __global__ void __launch_bounds__(T, 1)
 k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ vals_in,
                uint64_t n, int is_f32, int val_bytes, uint32_t s,
@@ -55,7 +80,7 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
         else v[k] = (K)key;
     }
     const int clen = len - off;
-    cta_sort<K, T, E>(v, sm, clen < 0 ? 0 : (clen > CH ? CH : clen));
+    chunk_sort<K, T, E, RADIX>(v, sm, clen < 0 ? 0 : (clen > CH ? CH : clen));
     cluster_merge<K, T, E, C>(sm, len);
 
 #pragma unroll 4
@@ -103,7 +128,7 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
 // key << 32 | (position in the sorted-sublist array), which orders equal
 // keys by original index exactly as the relocated order does, and fetch
 // each value from that position.
-template <int T, int E, bool PAIRS, int C>
+template <int T, int E, bool PAIRS, int C, bool RADIX>
 __device__ __forceinline__ void
 bucket_sort_unit(uint32_t u, const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
                  const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
@@ -192,7 +217,7 @@ bucket_sort_unit(uint32_t u, const uint32_t *__restrict__ src_k, const void *__r
             else v[k] = (K)key;
         }
     }
-    cta_sort<K, T, E>(v, sm, uend > ustart ? uend - ustart : 0);
+    chunk_sort<K, T, E, RADIX>(v, sm, uend > ustart ? uend - ustart : 0);
     cluster_merge<K, T, E, C>(sm, len, per);
     const uint64_t lim64 = min((unsigned long long)len, (unsigned long long)(n > L ? n - L : 0));
     const int lim = (int)lim64;
@@ -219,14 +244,14 @@ bucket_sort_unit(uint32_t u, const uint32_t *__restrict__ src_k, const void *__r
 }
 
 // Cluster u of the grid sorts unit u (clusters beyond the unit count exit).
-template <int T, int E, bool PAIRS, int C>
+template <int T, int E, bool PAIRS, int C, bool RADIX = false>
 __global__ void __launch_bounds__(T, 1)
 k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
               const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
               int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v, int *err,
               GatherSrc g)
 {
-    bucket_sort_unit<T, E, PAIRS, C>(blockIdx.x / C, src_k, src_v, units, n, n_pad, is_f32,
+    bucket_sort_unit<T, E, PAIRS, C, RADIX>(blockIdx.x / C, src_k, src_v, units, n, n_pad, is_f32,
                                      val_bytes, out_k, out_v, err, g);
 }
 
@@ -235,7 +260,7 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
 // device memory, range[0] .. range[1] - 1): a small grid whose cluster c
 // sorts units lo + c, lo + c + G, ... (G clusters; every CTA of a cluster
 // takes the same units).
-template <int T, int E, bool PAIRS, int C>
+template <int T, int E, bool PAIRS, int C, bool RADIX = false>
 __global__ void __launch_bounds__(T, 1)
 k_bucket_sort_loop(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
                    const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
@@ -246,7 +271,7 @@ k_bucket_sort_loop(const uint32_t *__restrict__ src_k, const void *__restrict__ 
     const uint32_t count = range != nullptr ? range[1] : units[0];
 #pragma unroll 1
     for (uint32_t u = lo + blockIdx.x / C; u < count; u += gridDim.x / C) {
-        bucket_sort_unit<T, E, PAIRS, C>(u, src_k, src_v, units, n, n_pad, is_f32, val_bytes,
+        bucket_sort_unit<T, E, PAIRS, C, RADIX>(u, src_k, src_v, units, n, n_pad, is_f32, val_bytes,
                                          out_k, out_v, err, g);
         __syncthreads();  // shared memory is reused by the next unit
     }
@@ -272,44 +297,44 @@ inline cudaError_t launch_maybe_cluster(KernelT kern, unsigned grid, int block, 
     return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
-template <int T, int E, bool PAIRS, int C>
+template <int T, int E, bool PAIRS, int C, bool RADIX = false>
 inline cudaError_t init_sort_pair_of_kernels()
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
-    const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
-    cudaError_t e = cudaFuncSetAttribute(k_sublist_sort<T, E, PAIRS, C>,
+    const int sm = sort_smem_bytes<K, T, E, RADIX>();
+    cudaError_t e = cudaFuncSetAttribute(k_sublist_sort<T, E, PAIRS, C, RADIX>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_bucket_sort<T, E, PAIRS, C>,
+    e = cudaFuncSetAttribute(k_bucket_sort<T, E, PAIRS, C, RADIX>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_bucket_sort_loop<T, E, PAIRS, C>,
+    e = cudaFuncSetAttribute(k_bucket_sort_loop<T, E, PAIRS, C, RADIX>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return e;
     if (C > 8) {
-        e = cudaFuncSetAttribute(k_sublist_sort<T, E, PAIRS, C>,
+        e = cudaFuncSetAttribute(k_sublist_sort<T, E, PAIRS, C, RADIX>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_bucket_sort<T, E, PAIRS, C>,
+        e = cudaFuncSetAttribute(k_bucket_sort<T, E, PAIRS, C, RADIX>,
                                  cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     }
     return e;
 }
 
-template <int T, int E, bool PAIRS, int C>
+template <int T, int E, bool PAIRS, int C, bool RADIX = false>
 inline cudaError_t launch_sublist_sort_t(const void *keys_in, const void *vals_in, uint64_t n,
                                          uint32_t m, int is_f32, int val_bytes, uint32_t s,
                                          uint32_t *tiles_k, void *tiles_v, uint64_t *samples,
                                          uint32_t tile0, cudaStream_t st)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
-    const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
-    return launch_maybe_cluster(k_sublist_sort<T, E, PAIRS, C>, m * C, T, sm, C, st,
+    const int sm = sort_smem_bytes<K, T, E, RADIX>();
+    return launch_maybe_cluster(k_sublist_sort<T, E, PAIRS, C, RADIX>, m * C, T, sm, C, st,
                                 static_cast<const uint32_t *>(keys_in), vals_in, n, is_f32,
                                 val_bytes, s, tiles_k, tiles_v, samples, tile0);
 }
 
-template <int T, int E, bool PAIRS, int C>
+template <int T, int E, bool PAIRS, int C, bool RADIX = false>
 inline cudaError_t launch_bucket_sort_t(const void *src_k, const void *src_v,
                                         const uint32_t *units, uint32_t max_units, uint64_t n,
                                         uint64_t n_pad, int is_f32, int val_bytes, void *out_k,
@@ -317,14 +342,14 @@ inline cudaError_t launch_bucket_sort_t(const void *src_k, const void *src_v,
                                         cudaStream_t st)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
-    const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
+    const int sm = sort_smem_bytes<K, T, E, RADIX>();
     const unsigned grid = (units ? max_units : 1u) * C;
     if (C > 1 && units != nullptr && max_units <= kLoopUnits)
-        return launch_maybe_cluster(k_bucket_sort_loop<T, E, PAIRS, C>, grid, T, sm, C, st,
+        return launch_maybe_cluster(k_bucket_sort_loop<T, E, PAIRS, C, RADIX>, grid, T, sm, C, st,
                                     static_cast<const uint32_t *>(src_k), src_v, units, n, n_pad,
                                     is_f32, val_bytes, static_cast<uint32_t *>(out_k), out_v,
                                     err, g, (const uint32_t *)nullptr);
-    return launch_maybe_cluster(k_bucket_sort<T, E, PAIRS, C>, grid, T, sm, C, st,
+    return launch_maybe_cluster(k_bucket_sort<T, E, PAIRS, C, RADIX>, grid, T, sm, C, st,
                                 static_cast<const uint32_t *>(src_k), src_v, units, n, n_pad,
                                 is_f32, val_bytes, static_cast<uint32_t *>(out_k), out_v, err, g);
 }
@@ -332,27 +357,27 @@ inline cudaError_t launch_bucket_sort_t(const void *src_k, const void *src_v,
 // Step 9 over the units range[0] .. range[1] - 1 of a list (device memory),
 // by a grid of grid_units clusters (C > 1) or of grid_units SMs' worth of
 // CTAs (C = 1) that loop over them.
-template <int T, int E, bool PAIRS, int C>
+template <int T, int E, bool PAIRS, int C, bool RADIX = false>
 inline cudaError_t launch_bucket_sort_range_t(const void *src_k, const uint32_t *units,
                                               const uint32_t *range, uint32_t grid_units,
                                               uint64_t n, uint64_t n_pad, int is_f32,
                                               void *out_k, int *err, cudaStream_t st)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
-    const int sm = padded_elems<K>(T * E) * (int)sizeof(K);
+    const int sm = sort_smem_bytes<K, T, E, RADIX>();
     const GatherSrc none;
     if (C == 1) {
         // grid_units counts SMs: as many CTAs as fit on them at once
         static const int per_sm = [sm] {
             int o = 0;
             if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                    &o, k_bucket_sort_loop<T, E, PAIRS, C>, T, sm) != cudaSuccess)
+                    &o, k_bucket_sort_loop<T, E, PAIRS, C, RADIX>, T, sm) != cudaSuccess)
                 o = 1;
             return o < 1 ? 1 : o;
         }();
         grid_units *= (uint32_t)per_sm;
     }
-    return launch_maybe_cluster(k_bucket_sort_loop<T, E, PAIRS, C>, grid_units * C, T, sm, C, st,
+    return launch_maybe_cluster(k_bucket_sort_loop<T, E, PAIRS, C, RADIX>, grid_units * C, T, sm, C, st,
                                 static_cast<const uint32_t *>(src_k), (const void *)nullptr, units,
                                 n, n_pad, is_f32, 0, static_cast<uint32_t *>(out_k),
                                 (void *)nullptr, err, none, range);

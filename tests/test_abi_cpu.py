@@ -289,10 +289,12 @@ def test_plan_invariants_sweep():
 
 def test_create_flags():
     """bsort_create takes the documented flags (timing, low memory, CUDA-graph
-    replay) and refuses unknown bits."""
-    ok = pkg.BSORT_FLAG_TIMING | pkg.BSORT_FLAG_LOW_MEMORY | pkg.BSORT_FLAG_GRAPHS
+    replay, comparison sort, the stalled-scan test) and refuses unknown bits."""
+    ok = (pkg.BSORT_FLAG_TIMING | pkg.BSORT_FLAG_LOW_MEMORY | pkg.BSORT_FLAG_GRAPHS
+          | pkg.BSORT_FLAG_MERGE_SORT | pkg.BSORT_FLAG_TEST_STALL_SCAN)
     h = pkg.bsort_create(pkg.bsort_config(device=0, flags=ok))
     pkg.bsort_destroy(h)
-    with pytest.raises(pkg.BsortError) as e:
-        pkg.bsort_create(pkg.bsort_config(device=0, flags=0x8))
-    assert e.value.status == pkg.BSORT_EINVAL
+    for bad in (0x20, 0x40, 0x80000000):
+        with pytest.raises(pkg.BsortError) as e:
+            pkg.bsort_create(pkg.bsort_config(device=0, flags=bad))
+        assert e.value.status == pkg.BSORT_EINVAL

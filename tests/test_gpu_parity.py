@@ -625,3 +625,27 @@ def test_two_tier_step9_pairs_intermediates():
     assert np.array_equal(ov.cpu().numpy().view(np.uint32), want["vals"])
     _check_intermediates(sorter, want, want["n_padded"], want["m"], p.s, p.b)
     sorter.close()
+
+
+def test_scan_lookback_timeout_is_reported():
+    """Step 7's look-back waits are bounded: with its first chunk made never
+    to publish a prefix (BSORT_FLAG_TEST_STALL_SCAN: a flag that nothing
+    sets), the later chunks give up after a few thousand polls, the kernel
+    returns, and bsort_sync reports BSORT_ETIMEOUT; nothing hangs, and the
+    device then sorts correctly again."""
+    import time
+    n, t, s = 1 << 20, 4096, 64  # m*s = 16384 runs: four scan chunks
+    keys = synth.keys_u32("uniform", n, synth.seed_for(2, 13))
+    stalled = pkg.BucketSorter(tile=t, samples=s, flags=pkg.BSORT_FLAG_TEST_STALL_SCAN)
+    d_in = _to_dev_u32(keys)
+    t0 = time.perf_counter()
+    stalled.sort_keys(d_in)
+    with pytest.raises(pkg.BsortError) as e:
+        stalled.sync()
+    assert e.value.status == pkg.BSORT_ETIMEOUT
+    assert time.perf_counter() - t0 < 5.0
+    stalled.sync()  # the error word was read and cleared
+    stalled.close()
+    sorter = pkg.BucketSorter(tile=t, samples=s)
+    assert np.array_equal(_gpu_sort_keys(sorter, keys), oracle.textbook_sort(keys, "u32"))
+    sorter.close()

@@ -312,3 +312,19 @@ def test_bound_and_partition_decoupled_buckets(dist, b):
             item = (int(rk[x]), int(rp[x]))
             assert item <= spl_orig[j] and (j == 0 or item > spl_orig[j - 1])
     assert (r["keys"] == np.sort(keys)).all()
+
+
+@pytest.mark.parametrize("dist", ["uniform", "zero", "staggered"])
+@pytest.mark.parametrize("threads", [2, 5])
+def test_threaded_oracle_is_identical(dist, threads):
+    """The threaded form (Steps 2, 6, 8, 9 split into per-sublist and
+    per-bucket ranges over threads, used only to time the oracle on all host
+    cores) returns exactly the single-threaded result and intermediates."""
+    n = 100003
+    keys = synth.keys_u32(dist, n, synth.seed_for(9, 1, threads))
+    vals = np.arange(n, dtype=np.uint32)
+    one = oracle.paper_sort(keys, 2048, 64, "u32", vals=vals, b=97)
+    many = oracle.paper_sort(keys, 2048, 64, "u32", vals=vals, b=97, threads=threads)
+    assert one.keys() == many.keys()
+    for name, a in one.items():
+        assert np.array_equal(np.asarray(a), np.asarray(many[name])), name
