@@ -488,7 +488,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->off_rec_b = take(P->wide || P->n_rec_pad > (uint32_t)kRecordChunk
                                 ? (uint64_t)P->n_rec_pad * rb : 0);
         P->off_spl = take((uint64_t)I.b * rb);
-        P->off_counts = take((uint64_t)P->n_runs * 4);
+        P->off_counts = take(0);  // a_ij are read back as offset differences
         P->off_offsets = take(((uint64_t)P->n_runs + 1) * 4);
         P->off_status = take((uint64_t)P->scan_chunks * 8);
         P->off_units = take((1 + 2 * (uint64_t)I.b) * 4);
@@ -497,7 +497,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         P->off_blk = take((np + kBlockItems - 1) / kBlockItems * 4);
         // Step 6: cumulative counts and segment ranges
         P->off_cum = take((uint64_t)P->n_runs * 4);
-        P->off_jr = take(sample_index_scratch_words(I.t, I.m, P->wide ? 4096u : 8192u) * 4);
+        P->off_jr = take(sample_index_scratch_words(I.t, I.m, P->wide ? 4096u : 1024u) * 4);
     }
     P->total = o;
     I.workspace_bytes = o;
@@ -690,7 +690,6 @@ bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout,
     Rec128 *rec_a = reinterpret_cast<Rec128 *>(ws + P.off_rec_a);
     Rec128 *rec_b = reinterpret_cast<Rec128 *>(ws + P.off_rec_b);
     Rec128 *spl = reinterpret_cast<Rec128 *>(ws + P.off_spl);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(ws + P.off_counts);
     uint32_t *offsets = reinterpret_cast<uint32_t *>(ws + P.off_offsets);
     uint32_t *srcb = reinterpret_cast<uint32_t *>(ws + P.off_srcb);
     uint32_t *blk = reinterpret_cast<uint32_t *>(ws + P.off_blk);
@@ -720,7 +719,7 @@ bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout,
     SEQ(launch_sample_index_seg_u64(tiles, spl, I.t, I.b, I.m, jr, cum, st),
         "step6_sample_index");
     // Step 7 (also a_ij and the run starts from the cumulative counts)
-    SEQ(launch_scan_cum(cum, I.m, I.t, counts, srcb, offsets, P.n_runs, status, ticket, err, st),
+    SEQ(launch_scan_cum(cum, I.m, I.t, nullptr, srcb, offsets, P.n_runs, status, ticket, err, st),
         "step7_prefix_sum");
     // Step 8
     SEQ(launch_block_index(offsets, P.n_runs, (uint32_t)I.n_padded, blk, st), "step8_run_index");
@@ -799,7 +798,6 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     uint64_t *rec_a = reinterpret_cast<uint64_t *>(ws + P.off_rec_a);
     uint64_t *rec_b = reinterpret_cast<uint64_t *>(ws + P.off_rec_b);
     uint64_t *spl = reinterpret_cast<uint64_t *>(ws + P.off_spl);
-    uint32_t *counts = reinterpret_cast<uint32_t *>(ws + P.off_counts);
     uint32_t *offsets = reinterpret_cast<uint32_t *>(ws + P.off_offsets);
     unsigned long long *status = reinterpret_cast<unsigned long long *>(ws + P.off_status);
 
@@ -860,7 +858,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     uint32_t *jr = reinterpret_cast<uint32_t *>(ws + P.off_jr);
     SEQ(launch_sample_index(tiles_k, spl, I.t, I.b, I.m, jr, cum, st), "step6_sample_index");
     // Step 7 (also a_ij and the run starts from the cumulative counts)
-    SEQ(launch_scan_cum(cum, I.m, I.t, counts, srcb, offsets, P.n_runs, status, ticket, err, st,
+    SEQ(launch_scan_cum(cum, I.m, I.t, nullptr, srcb, offsets, P.n_runs, status, ticket, err, st,
                         (h->flags & BSORT_FLAG_TEST_STALL_SCAN) != 0),
         "step7_prefix_sum");
     // a stalled scan leaves inconsistent offsets: Steps 8-9 must not read them
@@ -2141,7 +2139,7 @@ bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which, void *h
     case BSORT_IM_TILES: off = P.off_tiles_k; size = P.info.n_padded * P.kb; break;
     case BSORT_IM_SAMPLES: off = P.off_samples; size = (uint64_t)P.n_rec * (P.wide ? 16 : 8); break;
     case BSORT_IM_SPLITTERS: off = P.off_spl; size = (uint64_t)P.info.b * (P.wide ? 16 : 8); break;
-    case BSORT_IM_COUNTS: off = P.off_counts; size = (uint64_t)P.n_runs * 4; break;
+    case BSORT_IM_COUNTS: off = P.off_offsets; size = (uint64_t)P.n_runs * 4; break;
     case BSORT_IM_OFFSETS: off = P.off_offsets; size = (uint64_t)P.n_runs * 4; break;
     case BSORT_IM_RELOCATED:
         if (!P.relocate)
@@ -2157,6 +2155,18 @@ bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which, void *h
                     (unsigned long long)size, (unsigned long long)bytes);
     cudaError_t e = cudaSetDevice(h->device);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (which == BSORT_IM_COUNTS) {
+        // a_ij = l_(next run) - l_ij: the offsets array ends with n' at
+        // index m*b (written with the run index of Step 8)
+        std::vector<uint32_t> l((size_t)P.n_runs + 1);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(l.data(), static_cast<unsigned char *>(h->ws) + off,
+                           l.size() * 4, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy intermediate");
+        uint32_t *a = static_cast<uint32_t *>(h_dst);
+        for (uint32_t x = 0; x < P.n_runs; ++x) a[x] = l[x + 1] - l[x];
+        return BSORT_OK;
+    }
     if (e == cudaSuccess)
         e = cudaMemcpy(h_dst, static_cast<unsigned char *>(h->ws) + off, size,
                        cudaMemcpyDeviceToHost);

@@ -49,6 +49,31 @@ __device__ __forceinline__ uint32_t f32_decode(uint32_t u)
     return u ^ mask;
 }
 
+// ---------------------------------------------------------------- L2 prefetch
+// Number of SMs of this GPU (the %nsmid special register).
+__device__ __forceinline__ uint32_t num_sms()
+{
+    uint32_t n;
+    asm("mov.u32 %0, %%nsmid;" : "=r"(n));
+    return n;
+}
+
+// Ask the L2 to fetch the 16-byte-aligned interior of [p, p + bytes) (a
+// hint: nothing is written, nothing outside the range is touched).  The
+// sorting kernels issue it for the unit the SM will most likely take next,
+// so that its keys stream from HBM while the current unit sorts in shared
+// memory.
+__device__ __forceinline__ void prefetch_l2(const void *p, uint64_t bytes)
+{
+    const uint64_t a = reinterpret_cast<uint64_t>(p);
+    const uint64_t lo = (a + 15) & ~15ull;
+    const uint64_t hi = (a + bytes) & ~15ull;
+    for (uint64_t x = lo; x < hi; x += (1u << 20)) {
+        const uint32_t len = (uint32_t)(hi - x < (1u << 20) ? hi - x : (1u << 20));
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(x), "r"(len) : "memory");
+    }
+}
+
 template <typename K> struct KeyMax;
 template <> struct KeyMax<uint32_t> { static constexpr uint32_t v = 0xFFFFFFFFu; };
 template <> struct KeyMax<uint64_t> { static constexpr uint64_t v = 0xFFFFFFFFFFFFFFFFull; };
@@ -307,6 +332,46 @@ __device__ __forceinline__ int corank_bitonic_gen(const K *sm, int la, int lb, i
     return lo;
 }
 
+// Outputs [d, d + E) of the merge of A = sm[0 .. la) ascending with B
+// stored descending at sm[la .. la + lb), as S independent merges of E/S
+// outputs each (each from its own co-rank), advanced in lockstep so that
+// their shared-memory loads overlap: a thread with many outputs and few
+// warps beside it is otherwise bound by one long chain of dependent loads.
+template <typename K, int E, int S>
+__device__ __forceinline__ void merge_bitonic_split(const K *sm, int la, int lb, int d,
+                                                    K (&v)[E])
+{
+    static_assert(E % S == 0, "S divides E");
+    constexpr int P = E / S;
+    const int end = la + lb;
+    int ia[S], ib[S];
+    K a[S], b[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+        const int dq = d + q * P;
+        const int i = corank_bitonic_gen<K>(sm, la, lb, dq);
+        ia[q] = i;
+        ib[q] = end - 1 - (dq - i);
+        a[q] = sm[pidx<K>(ia[q])];
+        b[q] = sm[pidx<K>(ib[q])];
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+            const bool p = a[q] <= b[q];
+            v[q * P + k] = p ? a[q] : b[q];
+            if (k + 1 < P) {
+                ia[q] += p ? 1 : 0;
+                ib[q] -= p ? 0 : 1;
+                const K nxt = sm[pidx<K>(p ? ia[q] : ib[q])];
+                a[q] = p ? nxt : a[q];
+                b[q] = p ? b[q] : nxt;
+            }
+        }
+    }
+}
+
 // Position of register k of thread (warp, lane) in the CTA's tile under the
 // "warp-blocked" layout: warp w owns the contiguous chunk [w*32E, (w+1)*32E)
 // and lane l its items l, l+32, l+64, ... of that chunk, so that global
@@ -385,60 +450,45 @@ __device__ __forceinline__ void cta_merge_runs(K *sm, int R)
 // of the cluster's items.  In the round with groups of G CTAs, the first G/2
 // CTAs of a group hold run A and the rest run B; CTA r finds the co-ranks of
 // its output range by a 32-ary search over the remote chunks, gathers the
-// A and B pieces into registers (pieces held by CTA r itself are read from
-// its own shared memory; each piece spans at most two chunks), waits for the
-// whole cluster, stores them as a bitonic sequence in its own SMEM, and
-// merges locally.
+// A and B pieces into registers (each piece spans at most two chunks, read
+// through distributed shared memory with ordinary loads so that many are in
+// flight at once), waits for the whole cluster, stores them as a bitonic
+// sequence in its own SMEM, and merges locally.
 __device__ __forceinline__ uint32_t smem_u32addr(const void *p)
 {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint32_t cl_mapa(uint32_t saddr, uint32_t rank)
-{
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-    return r;
-}
-
+// Generic pointer to CTA `rank`'s copy of the shared array sm (distributed
+// shared memory).  Loads through it are ordinary loads: the compiler keeps
+// many in flight, and the cluster barriers order them.
 template <typename K>
-__device__ __forceinline__ K cl_ld(uint32_t addr);
-template <>
-__device__ __forceinline__ uint32_t cl_ld<uint32_t>(uint32_t addr)
+__device__ __forceinline__ const K *cluster_ptr(K *sm, int rank)
 {
-    uint32_t v;
-    asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-    return v;
-}
-template <>
-__device__ __forceinline__ uint64_t cl_ld<uint64_t>(uint32_t addr)
-{
-    uint64_t v;
-    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
-    return v;
+    return cooperative_groups::this_cluster().map_shared_rank(sm, (unsigned)rank);
 }
 
 // Item x of the run held by CTAs first_cta, first_cta+1, ... (chunks of
 // 2^chunk_shift items), read through distributed shared memory.
 template <typename K>
-__device__ __forceinline__ K cl_load(uint32_t sm_base, int first_cta, int chunk_shift, int x)
+__device__ __forceinline__ K cl_load(K *sm, int first_cta, int chunk_shift, int x)
 {
     const int cta = first_cta + (x >> chunk_shift);
     const int off = x & ((1 << chunk_shift) - 1);
-    return cl_ld<K>(cl_mapa(sm_base, (uint32_t)cta) + (uint32_t)(pidx<K>(off) * (int)sizeof(K)));
+    return cluster_ptr(sm, cta)[pidx<K>(off)];
 }
 
 template <typename K>
-__device__ __forceinline__ int corank_cluster(uint32_t sm_base, int a_cta, int b_cta,
-                                              int chunk_shift, int la, int lb, int d, int lane)
+__device__ __forceinline__ int corank_cluster(K *sm, int a_cta, int b_cta, int chunk_shift,
+                                              int la, int lb, int d, int lane)
 {
     int lo = d > lb ? d - lb : 0;
     int hi = d < la ? d : la;
     while (hi - lo > 32) {
         const int span = hi - lo;
         const int c = lo + (int)(((long long)span * (lane + 1)) / 33);
-        const bool pred = cl_load<K>(sm_base, a_cta, chunk_shift, c) >
-                          cl_load<K>(sm_base, b_cta, chunk_shift, d - 1 - c);
+        const bool pred = cl_load<K>(sm, a_cta, chunk_shift, c) >
+                          cl_load<K>(sm, b_cta, chunk_shift, d - 1 - c);
         const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
         if (ball == 0) {
             lo = lo + (int)(((long long)span * 32) / 33) + 1;
@@ -453,36 +503,38 @@ __device__ __forceinline__ int corank_cluster(uint32_t sm_base, int a_cta, int b
     const int c = lo + lane;
     bool pred = true;
     if (c < hi)
-        pred = cl_load<K>(sm_base, a_cta, chunk_shift, c) >
-               cl_load<K>(sm_base, b_cta, chunk_shift, d - 1 - c);
+        pred = cl_load<K>(sm, a_cta, chunk_shift, c) >
+               cl_load<K>(sm, b_cta, chunk_shift, d - 1 - c);
     const unsigned ball = __ballot_sync(0xFFFFFFFFu, pred);
     return ball ? lo + __ffs(ball) - 1 : hi;
 }
 
-// One contiguous piece [x0, x0 + len) of a run held by CTAs first_cta, ...:
-// at most two chunks.  Describes where item z of the piece lives.
+// One contiguous piece [x0, ...) of a run held by CTAs first_cta, ...: at
+// most two chunks.  Item z of the piece is at p0[pidx(off0 + z)] for
+// z < split, else at p1[pidx(z - split)] (p0, p1: the two chunks, clamped to
+// the cluster; a chunk the piece does not reach is never read).
+template <typename K>
 struct Piece {
-    int cta0, off0, split;  // items [0, split) in cta0 from off0; the rest in cta0 + 1 from 0
+    const K *p0, *p1;
+    int off0, split;
 };
 
-__device__ __forceinline__ Piece make_piece(int first_cta, int chunk_shift, int x0)
+template <typename K, int C>
+__device__ __forceinline__ Piece<K> make_piece(K *sm, int first_cta, int chunk_shift, int x0)
 {
-    Piece p;
-    p.cta0 = first_cta + (x0 >> chunk_shift);
+    const int c0 = first_cta + (x0 >> chunk_shift);
+    Piece<K> p;
     p.off0 = x0 & ((1 << chunk_shift) - 1);
     p.split = (1 << chunk_shift) - p.off0;
+    p.p0 = cluster_ptr(sm, c0 < C ? c0 : C - 1);
+    p.p1 = cluster_ptr(sm, c0 + 1 < C ? c0 + 1 : C - 1);
     return p;
 }
 
 template <typename K>
-__device__ __forceinline__ K piece_load(const K *sm, uint32_t sm_base, int my_rank,
-                                        const Piece &pc, int z)
+__device__ __forceinline__ const K *piece_addr(const Piece<K> &pc, int z)
 {
-    const bool first = z < pc.split;
-    const int cta = first ? pc.cta0 : pc.cta0 + 1;
-    const int off = first ? pc.off0 + z : z - pc.split;
-    if (cta == my_rank) return sm[pidx<K>(off)];
-    return cl_ld<K>(cl_mapa(sm_base, (uint32_t)cta) + (uint32_t)(pidx<K>(off) * (int)sizeof(K)));
+    return z < pc.split ? pc.p0 + pidx<K>(pc.off0 + z) : pc.p1 + pidx<K>(z - pc.split);
 }
 
 // len: number of real items of the whole cluster; before the first round
@@ -499,7 +551,6 @@ __device__ __forceinline__ void cluster_merge(K *sm, int len, int per = T * E)
         const int r = (int)cl.block_rank();
         const int tid = threadIdx.x;
         const int lane = tid & 31, warp = tid >> 5;
-        const uint32_t sm_base = smem_u32addr(sm);
         __shared__ int s_split[2];
 #pragma unroll 1
         for (int G = 2; G <= C; G <<= 1) {
@@ -512,7 +563,7 @@ __device__ __forceinline__ void cluster_merge(K *sm, int len, int per = T * E)
             if (work) {
                 const int d0 = (r - g0) * CH;
                 if (warp < 2) {
-                    const int i = corank_cluster<K>(sm_base, g0, g0 + h, SH, h * CH, h * CH,
+                    const int i = corank_cluster<K>(sm, g0, g0 + h, SH, h * CH, h * CH,
                                                     d0 + warp * CH, lane);
                     if (lane == 0) s_split[warp] = i;
                 }
@@ -520,13 +571,12 @@ __device__ __forceinline__ void cluster_merge(K *sm, int len, int per = T * E)
                 const int i0 = s_split[0], i1 = s_split[1];
                 const int j0 = d0 - i0;
                 na = i1 - i0;
-                const Piece pa = make_piece(g0, SH, i0);
-                const Piece pb = make_piece(g0 + h, SH, j0);
+                const Piece<K> pa = make_piece<K, C>(sm, g0, SH, i0);
+                const Piece<K> pb = make_piece<K, C>(sm, g0 + h, SH, j0);
 #pragma unroll
                 for (int k = 0; k < E; ++k) {
                     const int z = k * T + tid;
-                    v[k] = z < na ? piece_load<K>(sm, sm_base, r, pa, z)
-                                  : piece_load<K>(sm, sm_base, r, pb, z - na);
+                    v[k] = *(z < na ? piece_addr(pa, z) : piece_addr(pb, z - na));
                 }
             }
             cl.sync();  // all reads of this round are done
@@ -539,8 +589,12 @@ __device__ __forceinline__ void cluster_merge(K *sm, int len, int per = T * E)
                 }
                 __syncthreads();
                 const int d = tid * E;
-                const int i = corank_bitonic_gen<K>(sm, na, CH - na, d);
-                merge_bitonic_pair<K, E>(sm, i, CH - 1 - (d - i), v);
+                if constexpr (E > 32) {
+                    merge_bitonic_split<K, E, E / 32>(sm, na, CH - na, d, v);
+                } else {
+                    const int i = corank_bitonic_gen<K>(sm, na, CH - na, d);
+                    merge_bitonic_pair<K, E>(sm, i, CH - 1 - (d - i), v);
+                }
                 __syncthreads();
 #pragma unroll
                 for (int k = 0; k < E; ++k) sm[pidx<K>(d + k)] = v[k];

@@ -114,13 +114,13 @@ cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint
                                     uint64_t *spl, cudaStream_t st);
 
 // Step 6: cum[j*m + i] = c_ij, the items of sorted sublist i at or below
-// splitter j (bucket-major); jr: m * max(1, t / 8192) words of scratch.
+// splitter j (bucket-major); jr: m * max(1, t / 1024) words of scratch.
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *spl, uint32_t t,
                                 uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
                                 cudaStream_t st);
-// Number of scratch words launch_sample_index (segments of 8192 keys) or
+// Number of scratch words launch_sample_index (segments of 1024 keys) or
 // launch_sample_index_seg_u64 (4096) needs for m sublists of t.
-inline uint64_t sample_index_scratch_words(uint32_t t, uint32_t m, uint32_t seg_items = 8192u)
+inline uint64_t sample_index_scratch_words(uint32_t t, uint32_t m, uint32_t seg_items = 1024u)
 {
     return (uint64_t)m * (t > seg_items ? t / seg_items : 1u);
 }
@@ -132,8 +132,9 @@ cudaError_t launch_scan(const uint32_t *in, uint32_t *out, uint32_t n_items,
                         unsigned long long *status, uint32_t *ticket, int *err,
                         cudaStream_t st);
 // Step 7 from Step 6's cumulative counts (item e = j*m + i): counts[e] =
-// a_ij = cum[e] - cum[e - m] (0 for j = 0), srcb[e] = i*t + cum[e - m] (the
-// start of run A_ij), out = the exclusive prefix of a in bucket-major order.
+// a_ij = cum[e] - cum[e - m] (0 for j = 0; not written when counts is
+// null), srcb[e] = i*t + cum[e - m] (the start of run A_ij), out = the
+// exclusive prefix of a in bucket-major order.
 // stall_first (a test of the bounded look-back wait): chunk 0 never
 // publishes its prefix and the waits give up after a few thousand polls,
 // recording DEV_TIMEOUT in *err (the offsets are then wrong).

@@ -188,14 +188,19 @@ __global__ void k_select_splitters(const uint64_t *__restrict__ sorted, uint32_t
 // k_seg_ranges finds, per segment, the first splitter that belongs to it:
 // c_ij >= S exactly when g_j >= item S - 1, so it is the number of
 // splitters below item S - 1 (binary search over the b sorted splitters).
-// k_sample_index_seg then stages its segment in shared memory with
-// coalesced loads (the sublists are read from HBM once, whole) and finds
-// each of its splitters' c_ij by binary search there; it writes the
-// cumulative c_ij, which Step 7 turns into the run sizes a_ij and starts.
-// (The paper locates g_j in sublist i through the sublist's samples and a
-// w-item window; that reads one window per splitter with accesses no warp
-// can coalesce.  The counts are the same.)
-constexpr int kSegItems = 8192;
+// k_sample_index_grp then takes segment k of kSub6 consecutive sublists:
+// it stages the segments in shared memory with coalesced loads (the
+// sublists are read from HBM once, whole), and its threads take the
+// (splitter, sublist) pairs splitter-major, so that the kSub6 counts of one
+// splitter, stored bucket-major at cum[j*m + i], leave as one 32-byte
+// sector; each count is a binary search in the staged segment.  It writes
+// the cumulative c_ij, which Step 7 turns into the run sizes a_ij and
+// starts.  (The paper locates g_j in sublist i through the sublist's
+// samples and a w-item window; that reads one window per splitter with
+// accesses no warp can coalesce.  The counts are the same.)
+constexpr int kSegItems = 1024;  // items of one sublist's segment
+constexpr int kSub6 = 8;         // sublists per CTA: 8 counts = one 32-byte sector
+constexpr int kSegRow = kSegItems + 4;  // staged row: rows start in different banks
 
 __global__ void k_seg_ranges(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ spl,
                              uint32_t t, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
@@ -221,45 +226,66 @@ __global__ void k_seg_ranges(const uint32_t *__restrict__ tiles_k, const uint64_
 
 template <int T>
 __global__ void __launch_bounds__(T)
-k_sample_index_seg(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ spl,
+k_sample_index_grp(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ spl,
                    uint32_t t, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
                    const uint32_t *__restrict__ jr, uint32_t *__restrict__ cum)
 {
-    static_assert(kSegItems % (4 * T) == 0, "whole uint4 loads per thread");
-    __shared__ __align__(16) uint32_t sk[kSegItems];
-    const uint32_t i = blockIdx.x / nseg, k = blockIdx.x % nseg;
+    __shared__ __align__(16) uint32_t sk[kSub6 * kSegRow];
+    __shared__ uint32_t s_lo[kSub6], s_hi[kSub6];
+    const uint32_t i0 = (blockIdx.x / nseg) * kSub6, k = blockIdx.x % nseg;
+    const uint32_t ns = min((uint32_t)kSub6, m - i0);  // sublists of this group
     const uint32_t S = k * seg;
-    const uint32_t p0 = i * t + S;  // position of the segment's first item
-    const uint32_t j_lo = jr[blockIdx.x];
-    const uint32_t j_hi = k + 1 < nseg ? jr[blockIdx.x + 1] : b;
-    const uint4 *src = reinterpret_cast<const uint4 *>(tiles_k + p0);
-    uint4 *dst = reinterpret_cast<uint4 *>(sk);
-    // every load of the segment is issued before the first store, so the
-    // CTA waits for HBM once
-    constexpr int Q = kSegItems / 4 / T;
+    const int tid = threadIdx.x;
+    if (tid < kSub6) {
+        const uint32_t ii = (uint32_t)tid;
+        s_lo[ii] = ii < ns ? jr[(i0 + ii) * nseg + k] : 0u;
+        s_hi[ii] = ii < ns ? (k + 1 < nseg ? jr[(i0 + ii) * nseg + k + 1] : b) : 0u;
+    }
+    // stage segment k of every sublist: seg/4 uint4 per sublist, all loads
+    // of a thread issued before its first store
+    const uint32_t q4 = seg / 4;
+    constexpr int Q = kSub6 * kSegItems / 4 / T;
     uint4 r[Q];
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const uint32_t v = (uint32_t)(q * T) + threadIdx.x;
-        if (v < seg / 4) r[q] = src[v];
+        const uint32_t v = (uint32_t)(q * T + tid);
+        const uint32_t ii = v / q4, o = v % q4;
+        if (ii < ns)
+            r[q] = reinterpret_cast<const uint4 *>(tiles_k + (uint64_t)(i0 + ii) * t + S)[o];
     }
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-        const uint32_t v = (uint32_t)(q * T) + threadIdx.x;
-        if (v < seg / 4) dst[v] = r[q];
+        const uint32_t v = (uint32_t)(q * T + tid);
+        const uint32_t ii = v / q4, o = v % q4;
+        if (ii < ns) reinterpret_cast<uint4 *>(sk + ii * kSegRow)[o] = r[q];
     }
     __syncthreads();
-    for (uint32_t j = j_lo + threadIdx.x; j < j_hi; j += T) {
+    uint32_t J0 = 0xFFFFFFFFu, J1 = 0;
+#pragma unroll
+    for (int ii = 0; ii < kSub6; ++ii) {
+        if ((uint32_t)ii < ns && s_lo[ii] < s_hi[ii]) {
+            J0 = min(J0, s_lo[ii]);
+            J1 = max(J1, s_hi[ii]);
+        }
+    }
+    if (J0 >= J1) return;
+    // pair p = (j - J0) * kSub6 + ii: lanes 8c .. 8c+7 hold one splitter
+    const uint32_t pairs = (J1 - J0) * kSub6;
+    for (uint32_t p = tid; p < pairs; p += T) {
+        const uint32_t j = J0 + p / kSub6, ii = p % kSub6;
+        if (ii >= ns || j < s_lo[ii] || j >= s_hi[ii]) continue;
         const uint64_t g = spl[j];
         const uint32_t gk = (uint32_t)(g >> 32), gp = (uint32_t)g;
+        const uint32_t p0 = (i0 + ii) * t + S;  // position of the segment's first item
+        const uint32_t *row = sk + ii * kSegRow;
         uint32_t lo = 0, hi = seg;
         while (lo < hi) {  // segment items <= g
             const uint32_t mid = (lo + hi) >> 1;
-            const uint32_t key = sk[mid];
+            const uint32_t key = row[mid];
             if (key < gk || (key == gk && p0 + mid <= gp)) lo = mid + 1;
             else hi = mid;
         }
-        cum[(uint64_t)j * m + i] = S + lo;
+        cum[(uint64_t)j * m + i0 + ii] = S + lo;
     }
 }
 
@@ -316,7 +342,7 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
                 const uint32_t c = cum[e];
                 const uint32_t p = e >= m ? cum[e - m] : 0u;
                 a = c - p;
-                counts[e] = a;
+                if (counts != nullptr) counts[e] = a;
                 srcb[e] = i * t + p;
             }
             s_items[spad(k * T + tid)] = a;
@@ -431,7 +457,7 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 // then issues their loads together.  Otherwise each lane walks the runs in
 // global memory (skipping stretches of empty runs by a search bounded by
 // the run index).
-constexpr int kRelocRunsCap = 256;  // runs a warp stages in shared memory
+constexpr int kRelocRunsCap = 512;  // runs a warp stages in shared memory
 
 template <int T, typename KT>
 __global__ void __launch_bounds__(T, 4)
@@ -856,7 +882,9 @@ cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *spl, ui
     k_seg_ranges<<<(ns + 255) / 256, 256, 0, st>>>(tiles_k, spl, t, b, m, nseg, seg, jr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_sample_index_seg<256><<<ns, 256, 0, st>>>(tiles_k, spl, t, b, m, nseg, seg, jr, cum);
+    const uint32_t groups = (m + kSub6 - 1) / kSub6;
+    k_sample_index_grp<256><<<groups * nseg, 256, 0, st>>>(tiles_k, spl, t, b, m, nseg, seg, jr,
+                                                          cum);
     return cudaGetLastError();
 }
 

@@ -66,6 +66,10 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
     const uint64_t avail = n > base ? n - base : 0;  // real items of the sublist
     const int len = avail < (uint64_t)TT ? (int)avail : (int)TT;
     const int off = r * CH;  // this CTA's chunk in the sublist
+    if (tid == 0) {  // the same chunk of the sublist this SM will most likely sort next
+        const uint64_t nb = base + (uint64_t)(num_sms() / C) * TT + off;
+        if (nb < n) prefetch_l2(keys_in + nb, 4 * min((uint64_t)CH, n - nb));
+    }
 
     K v[E];
 #pragma unroll
@@ -128,12 +132,14 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
 // key << 32 | (position in the sorted-sublist array), which orders equal
 // keys by original index exactly as the relocated order does, and fetch
 // each value from that position.
+// prefetch_stride: units between this one and the next this CTA's SM will
+// most likely sort (0: no prefetch), whose keys are then fetched into L2.
 template <int T, int E, bool PAIRS, int C, bool RADIX>
 __device__ __forceinline__ void
 bucket_sort_unit(uint32_t u, const uint32_t *__restrict__ src_k, const void *__restrict__ src_v,
                  const uint32_t *__restrict__ units, uint64_t n, uint64_t n_pad, int is_f32,
                  int val_bytes, uint32_t *__restrict__ out_k, void *__restrict__ out_v,
-                 int *err, const GatherSrc &g)
+                 int *err, const GatherSrc &g, uint32_t prefetch_stride)
 {
     using K = typename std::conditional<PAIRS, uint64_t, uint32_t>::type;
     constexpr int CH = T * E;
@@ -157,6 +163,14 @@ bucket_sort_unit(uint32_t u, const uint32_t *__restrict__ src_k, const void *__r
         return;  // uniform per cluster: no CTA of it reaches a cluster barrier
     }
     if (len64 == 0) return;
+    if (!direct && !gather && tid == 0 && r == 0 && prefetch_stride) {
+        // the unit this SM will most likely sort next
+        const uint32_t un = u + prefetch_stride;
+        if (un < units[0]) {
+            const uint32_t pl = units[1 + 2 * un], pr = units[2 + 2 * un];
+            if (pl < pr && pr <= n_pad) prefetch_l2(src_k + pl, 4ull * (pr - pl));
+        }
+    }
     const int len = (int)len64;
     const int off = r * CH;  // ranks of the sorted unit this CTA writes
     // the unit's real items are spread evenly over the cluster's CTAs, so
@@ -252,7 +266,7 @@ k_bucket_sort(const uint32_t *__restrict__ src_k, const void *__restrict__ src_v
               GatherSrc g)
 {
     bucket_sort_unit<T, E, PAIRS, C, RADIX>(blockIdx.x / C, src_k, src_v, units, n, n_pad, is_f32,
-                                     val_bytes, out_k, out_v, err, g);
+                                     val_bytes, out_k, out_v, err, g, num_sms() / C);
 }
 
 // The same for a unit list whose length only the device knows (the cluster
@@ -272,7 +286,7 @@ k_bucket_sort_loop(const uint32_t *__restrict__ src_k, const void *__restrict__ 
 #pragma unroll 1
     for (uint32_t u = lo + blockIdx.x / C; u < count; u += gridDim.x / C) {
         bucket_sort_unit<T, E, PAIRS, C, RADIX>(u, src_k, src_v, units, n, n_pad, is_f32, val_bytes,
-                                         out_k, out_v, err, g);
+                                         out_k, out_v, err, g, gridDim.x / C);
         __syncthreads();  // shared memory is reused by the next unit
     }
 }
