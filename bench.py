@@ -15,7 +15,8 @@ uniformly (SplitMix64), keys only.  Prints ONE JSON line on rank 0.
 against the measured copy bandwidth; "distributions" times the seven key
 distributions and reports their spread; "cpu_baseline" is the CPU oracle on
 all host cores (on a 2^24-key sample; once on the whole workload when host
-memory allows; and on one core as "single_thread").
+memory allows; and on one core as "single_thread"); "plans" times the
+measured plan table against the analytic cost model at 2^24, 2^26, 2^28.
 
 The line also carries "served": a Poisson stream of sort jobs (2,000 per
 second for 60 s, 50/50 uint32/uint64, sizes log-uniform in [2^10, 2^24],
@@ -99,6 +100,8 @@ def _args():
                    help="keys per CPU-oracle sample (all host cores)")
     p.add_argument("--no-cpu-full", dest="cpu_full", action="store_false",
                    help="skip timing the CPU oracle once on the whole workload")
+    p.add_argument("--no-plans", dest="plans", action="store_false",
+                   help="skip timing the tabled plans against the cost model's")
     p.add_argument("--merge-sort", action="store_true",
                    help="sort the 32768-key chunks of Steps 2 and 9 by comparisons "
                         "(BSORT_FLAG_MERGE_SORT) instead of by digits")
@@ -582,6 +585,38 @@ def run_ours(args):
         except Exception as e:  # reported, not fatal: the headline stands
             small = {"error": "%s: %s" % (type(e).__name__, str(e)[:200])}
 
+    # the measured plan table against the analytic cost model on prefixes
+    # of this workload (keys-only 32-bit sorts; the table covers them)
+    plans = None
+    if args.plans and not args.pairs and args.key_type != "u64":
+        plans = {}
+        for lg in (24, 26, 28):
+            nn = 1 << lg
+            if nn > args.n:
+                continue
+            row = {}
+            for label, flags in (("table", 0), ("cost_model", pkg.BSORT_FLAG_PLAN_MODEL)):
+                srt = pkg.BucketSorter(device=local, flags=flags)
+                pl = srt.plan(nn, args.key_type)
+                ki, ko = keys[:nn], out[:nn]
+                for _ in range(3):
+                    srt.sort_keys(ki, out=ko, key_type=args.key_type)
+                srt.sync()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                reps = max(5, (1 << 28) // nn * 2)
+                a.record(stream)
+                for _ in range(reps):
+                    srt.sort_keys(ki, out=ko, key_type=args.key_type)
+                b.record(stream)
+                torch.cuda.synchronize()
+                srt.sync()
+                pms = a.elapsed_time(b) / reps
+                row[label] = {"ms_per_sort": pms, "gkeys_s": nn / (pms / 1e3) / 1e9,
+                              "t": pl.t, "s": pl.s, "b": pl.b}
+                srt.close()
+            plans["2^%d" % lg] = row
+
     dists = None
     if args.dists:
         dists = {}
@@ -639,6 +674,8 @@ def run_ours(args):
             line["small_sort"] = small
         if dists is not None:
             line["distributions"] = dists
+        if plans is not None:
+            line["plans"] = plans
         if batched is not None:
             line["batched"] = batched
         if served is not None:

@@ -63,6 +63,9 @@ typedef enum {
                        no-allocation entry (BSORT_EUNSUPPORTED) */
 } bsort_key_type;
 
+/* bsort_config.buckets: let the planner choose b for the given t and s. */
+#define BSORT_BUCKETS_AUTO 0xFFFFFFFFu
+
 /* Flags for bsort_config.flags. */
 #define BSORT_FLAG_TIMING 0x1u   /* record CUDA events between the kernels of
                                     every call; see bsort_kernel_times() */
@@ -102,6 +105,11 @@ typedef enum {
                                       Device-buffer calls only (EINVAL for
                                       bsort_sort_keys_host).  Never set it
                                       otherwise */
+#define BSORT_FLAG_PLAN_MODEL 0x20u /* plan every sort with the analytic
+                                      cost model, also where a measured
+                                      (t, s) is tabled for n's size class
+                                      (keys-only 32-bit sorts); kept to
+                                      compare the two */
 #define BSORT_FLAG_MERGE_SORT 0x8u /* keys-only 32-bit sorts: a unit of
                                       32768 keys sorted by one CTA (a Step-9
                                       bucket unit, a Step-2 sublist of
@@ -128,7 +136,9 @@ typedef struct {
     uint32_t flags;            /* BSORT_FLAG_* */
     uint32_t buckets;          /* b, the number of buckets of Steps 5-9
                                   (0 = b = s when samples is given, else the
-                                  planner's choice); the splitters are the
+                                  planner's choice; BSORT_BUCKETS_AUTO = the
+                                  planner's choice also when samples is
+                                  given); the splitters are the
                                   sorted samples of rank floor((j+1)ms/b) - 1,
                                   which for b = s is the paper's S[(j+1)m - 1]
                                   (Section 4, Step 5).  1 <= b <= m*s and

@@ -17,6 +17,7 @@ __all__ = [
     "BSORT_EBUSY", "BSORT_ENOTREADY", "BSORT_EUNSUPPORTED", "BSORT_EINTERNAL",
     "BSORT_U32", "BSORT_F32", "BSORT_U64", "BSORT_FLAG_TIMING", "BSORT_FLAG_LOW_MEMORY",
     "BSORT_FLAG_GRAPHS", "BSORT_FLAG_MERGE_SORT", "BSORT_FLAG_TEST_STALL_SCAN",
+    "BSORT_FLAG_PLAN_MODEL", "BSORT_BUCKETS_AUTO",
     "bsort_config", "bsort_plan_info", "BsortError", "load_library",
     "bsort_create", "bsort_destroy", "bsort_plan", "bsort_sort_keys",
     "bsort_sort_pairs", "bsort_sort_keys_host", "bsort_sync",
@@ -35,6 +36,8 @@ BSORT_FLAG_LOW_MEMORY = 0x2
 BSORT_FLAG_GRAPHS = 0x4
 BSORT_FLAG_MERGE_SORT = 0x8
 BSORT_FLAG_TEST_STALL_SCAN = 0x10
+BSORT_FLAG_PLAN_MODEL = 0x20
+BSORT_BUCKETS_AUTO = 0xFFFFFFFF
 (BSORT_IM_TILES, BSORT_IM_SAMPLES, BSORT_IM_SPLITTERS, BSORT_IM_COUNTS,
  BSORT_IM_OFFSETS, BSORT_IM_RELOCATED) = range(6)
 

@@ -71,6 +71,7 @@ struct bsort_ctx {
     int device = 0;
     uint32_t flags = 0;
     uint32_t force_t = 0, force_s = 0, force_b = 0;
+    bool auto_b = false;  // BSORT_BUCKETS_AUTO: the planner's b even when s is given
     void *ws = nullptr;
     uint64_t ws_bytes = 0;
     bool ws_owned = false;
@@ -285,7 +286,45 @@ double plan_cost(uint64_t np, uint64_t s, uint64_t runs, int tchunk, int tctas, 
            per_run * r;
 }
 
+// Measured plans for keys-only sorts of 32-bit keys whose Step-9 units
+// (and sublists of t = 32768) are radix-sorting CTAs: (t, s) per size
+// class of n, the fastest of a sweep of t in {32768, 65536, 131072} and s in
+// {512, ..., 8192} on GB300 (uniform keys; b chosen by the planner for each
+// pair, as below).  Sizes outside the table use the cost model.
+struct TunedPlan {
+    int log2n_max;  // n <= 2^log2n_max
+    uint32_t t, s;
+};
+const TunedPlan kTuned[] = {
+#include "bsort_tuned.inc"
+};
+
+bool tuned_plan(uint64_t n, uint64_t *t, uint64_t *s)
+{
+    for (const TunedPlan &e : kTuned) {
+        if (n <= (1ull << e.log2n_max)) {
+            *t = e.t;
+            *s = e.s;
+            return true;
+        }
+    }
+    return false;
+}
+
+bsort_status make_plan_with(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P,
+                            bool use_table);
+
+// The plan of one job: the tabled (t, s) for n's size class when there is
+// one and it admits a plan, else the cost model's choice.
 bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P)
+{
+    bsort_status st = make_plan_with(h, kt, vb, n, P, true);
+    if (st == BSORT_EUNSUPPORTED) st = make_plan_with(h, kt, vb, n, P, false);
+    return st;
+}
+
+bsort_status make_plan_with(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P,
+                            bool use_table)
 {
     memset(P, 0, sizeof(*P));
     if (kt != BSORT_U32 && kt != BSORT_F32 && kt != BSORT_U64)
@@ -303,9 +342,10 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
     P->vb = (int)vb;
     bsort_plan_info &I = P->info;
     I.n = n;
-    const uint64_t forced_t = h ? h->force_t : 0;
-    const uint64_t forced_s = h ? h->force_s : 0;
+    uint64_t forced_t = h ? h->force_t : 0;
+    uint64_t forced_s = h ? h->force_s : 0;
     const uint64_t forced_b = h ? h->force_b : 0;
+    bool auto_b = h ? h->auto_b : false;  // b chosen below even if s is forced
     if (forced_b > (uint64_t)kMaxBuckets)
         return fail(h, BSORT_EUNSUPPORTED, "b = %llu exceeds %d buckets",
                     (unsigned long long)forced_b, kMaxBuckets);
@@ -328,6 +368,18 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         I.unit_capacity = (uint64_t)uchunk * uctas;
         I.num_kernels = n > 1 ? 1 : 0;
     } else {
+        // keys-only 32-bit sorts with radix units take (t, s) from the table
+        // measured for n's size class; the bucket count is then chosen below
+        // as for any plan
+        const bool radix_ok = vb == 0 && kt != BSORT_U64 &&
+                              !(h && (h->flags & (BSORT_FLAG_MERGE_SORT | BSORT_FLAG_PLAN_MODEL)));
+        uint64_t tt = 0, ts = 0;
+        if (use_table && radix_ok && !forced_t && !forced_s && !forced_b &&
+            tuned_plan(n, &tt, &ts)) {
+            forced_t = tt;
+            forced_s = ts;
+            auto_b = true;
+        }
         // candidates: forced t or every sublist shape; forced s or every
         // power of two with w = t/s >= 16 and s <= kMaxSamples.  The unit is
         // sized for b = s (or the forced b); the bucket count is chosen after.
@@ -359,10 +411,10 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
                                                                          : (uint64_t)kMaxBucketsTiers;
                 const uint64_t tgt = two_tier_target(m, t / sv, (uint64_t)cm);
                 const uint64_t b2 = tgt ? (np + tgt - 1) / tgt : bmx + 1;
-                const bool tiers = uk > 1 && !forced_b && !forced_s && b2 <= bmx &&
+                const bool tiers = uk > 1 && !forced_b && (!forced_s || auto_b) && b2 <= bmx &&
                                    bound_for(np, m, sv, b2) <= (uint64_t)uc * uk &&
                                    tiers_regular(m, t / sv, (uint64_t)cm);
-                const uint64_t b_est = forced_b ? forced_b : forced_s ? sv
+                const uint64_t b_est = forced_b ? forced_b : (forced_s && !auto_b) ? sv
                                        : tiers ? b2 : (21 * np + 10ull * uc * uk - 1) / (10ull * uc * uk);
                 // (the cluster tier's launch costs ~40 us even when nearly empty)
                 const double c = tiers ? plan_cost(np, sv, m * b_est, tc, tk, cm, 1, wide) + 5e6
@@ -425,7 +477,7 @@ bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Pl
         uint64_t b = bs;  // the paper's rule, kept when s is given
         if (forced_b) {
             b = forced_b;
-        } else if (!forced_s) {
+        } else if (!forced_s || auto_b) {
             const uint64_t bc =
                 tiers_wanted ? choose_buckets_two_tier(I.n_padded, m, bs, (uint64_t)cm,
                                                        I.unit_capacity, bmax2)
@@ -1797,7 +1849,8 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
         h->flags = cfg->flags;
         h->force_t = cfg->tile;
         h->force_s = cfg->samples;
-        h->force_b = cfg->buckets;
+        h->auto_b = cfg->buckets == BSORT_BUCKETS_AUTO;
+        h->force_b = h->auto_b ? 0u : cfg->buckets;
         h->serve_budget = cfg->serve_budget_bytes;
         if (cfg->batch_direct_max) {
             if (cfg->batch_direct_max > 8u * (uint32_t)kMaxCapKeys) {
@@ -1808,7 +1861,8 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
         }
         if (cfg->flags &
             ~(uint32_t)(BSORT_FLAG_TIMING | BSORT_FLAG_LOW_MEMORY | BSORT_FLAG_GRAPHS |
-                        BSORT_FLAG_MERGE_SORT | BSORT_FLAG_TEST_STALL_SCAN)) {
+                        BSORT_FLAG_MERGE_SORT | BSORT_FLAG_TEST_STALL_SCAN |
+                        BSORT_FLAG_PLAN_MODEL)) {
             delete h;
             return BSORT_EINVAL;
         }

@@ -26,7 +26,7 @@ cudaError_t launch_sublist_sort_keys(int chunk, int ctas, const void *keys_in, u
                                      uint64_t *samples, cudaStream_t st, uint32_t tile0,
                                      bool radix)
 {
-    if (radix && chunk == 32768 && (ctas == 1 || ctas == 2))
+    if (radix && chunk == 32768 && ctas == 1)
         return launch_sublist_sort_keys_radix(ctas, keys_in, n, m, is_f32, s, tiles_k, samples,
                                               st, tile0);
 #define L(T_, E_, C_)                                                                       \

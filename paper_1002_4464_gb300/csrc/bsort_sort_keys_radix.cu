@@ -1,9 +1,8 @@
 // bsort_sort_keys_radix.cu -- instantiations of the Step 1-3 and Step 9
-// sorting kernels whose 32768-key chunks are sorted by one CTA by digits
+// sorting kernels whose 32768-key units are sorted by one CTA by digits
 // (cta_radix_sort: 256 threads x 128 keys, 7-bit digits), for keys-only
-// sorts of uint32 / transformed float32 keys: Step-9 units of one CTA,
-// Step-2 sublists of one CTA or of a 2-CTA cluster (whose two chunks the
-// cluster merge then combines).
+// sorts of uint32 / transformed float32 keys: Step-9 units and Step-2
+// sublists of one CTA.
 #include "bsort_internal.h"
 #include "bsort_sort.cuh"
 
@@ -15,7 +14,7 @@ cudaError_t init_sort_keys_radix_kernels()
 #define I(C_)                                                    \
     e = init_sort_pair_of_kernels<256, 128, false, C_, true>();  \
     if (e != cudaSuccess) return e
-    I(1); I(2);
+    I(1);
 #undef I
     return cudaSuccess;
 }
@@ -29,7 +28,6 @@ cudaError_t launch_sublist_sort_keys_radix(int ctas, const void *keys_in, uint64
                                                             s, tiles_k, nullptr, samples,      \
                                                             tile0, st)
     if (ctas == 1) L(1);
-    if (ctas == 2) L(2);
 #undef L
     return cudaErrorInvalidValue;
 }

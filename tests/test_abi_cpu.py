@@ -289,12 +289,48 @@ def test_plan_invariants_sweep():
 
 def test_create_flags():
     """bsort_create takes the documented flags (timing, low memory, CUDA-graph
-    replay, comparison sort, the stalled-scan test) and refuses unknown bits."""
+    replay, comparison sort, the stalled-scan test, the cost-model planner)
+    and refuses unknown bits."""
     ok = (pkg.BSORT_FLAG_TIMING | pkg.BSORT_FLAG_LOW_MEMORY | pkg.BSORT_FLAG_GRAPHS
-          | pkg.BSORT_FLAG_MERGE_SORT | pkg.BSORT_FLAG_TEST_STALL_SCAN)
+          | pkg.BSORT_FLAG_MERGE_SORT | pkg.BSORT_FLAG_TEST_STALL_SCAN
+          | pkg.BSORT_FLAG_PLAN_MODEL)
     h = pkg.bsort_create(pkg.bsort_config(device=0, flags=ok))
     pkg.bsort_destroy(h)
-    for bad in (0x20, 0x40, 0x80000000):
+    for bad in (0x40, 0x80, 0x80000000):
         with pytest.raises(pkg.BsortError) as e:
             pkg.bsort_create(pkg.bsort_config(device=0, flags=bad))
         assert e.value.status == pkg.BSORT_EINVAL
+
+
+def test_tuned_plan_table_lookup():
+    """Keys-only 32-bit sorts above one unit take (t, s) from the measured
+    table for n's size class (b is then the planner's); BSORT_FLAG_PLAN_MODEL,
+    pairs, 64-bit keys and the comparison sort use the cost model; a forced
+    t/s with BSORT_BUCKETS_AUTO keeps them and lets the planner choose b."""
+    import re as _re
+    src = open(os.path.join(ROOT, "paper_1002_4464_gb300", "csrc", "bsort_tuned.inc")).read()
+    table = [tuple(map(int, m))
+             for m in _re.findall(r"^\{(\d+),\s*(\d+),\s*(\d+)\},", src, flags=_re.M)]
+    assert table and all(a[0] < b[0] for a, b in zip(table, table[1:]))
+    h = _handle()
+    model = pkg.bsort_create(pkg.bsort_config(device=0, flags=pkg.BSORT_FLAG_PLAN_MODEL))
+    for lg in (19, 20, 21, 24, 26, 28, 30):
+        n = (1 << lg) + 3
+        want = next(((t, s) for top, t, s in table if n <= (1 << top)), None)
+        for kt in (pkg.BSORT_U32, pkg.BSORT_F32):
+            p = pkg.bsort_plan(h, kt, 0, n)
+            if p.single_tile:
+                continue
+            if want is not None:
+                assert (p.t, p.s) == want, (lg, p.t, p.s)
+            assert p.unit_capacity >= p.bucket_bound
+            assert p.bucket_bound == oracle.bucket_bound(p.n_padded, p.m, p.s, p.b)
+        q = pkg.bsort_plan(model, pkg.BSORT_U32, 0, n)
+        assert q.unit_capacity >= q.bucket_bound
+    pkg.bsort_destroy(model)
+    pkg.bsort_destroy(h)
+    h = pkg.bsort_create(pkg.bsort_config(device=0, tile=65536, samples=4096,
+                                          buckets=pkg.BSORT_BUCKETS_AUTO))
+    p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 26)
+    assert (p.t, p.s) == (65536, 4096) and p.b != p.s
+    pkg.bsort_destroy(h)
