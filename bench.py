@@ -710,14 +710,17 @@ def run_batched(args, pkg, synth, dev, stream, rank, world):
     kin = keys.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
     assert int(kin.sum()) == int(o.sum()), "multiset changed"
     del o, kin, starts
+    ref = out.clone()
     sorter.kernel_times()
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    t_host = time.perf_counter()
     e0.record(stream)
     for _ in range(args.batch_steps):
         sorter.sort_batch(keys, off, out=out)
     e1.record(stream)
+    host_ms = (time.perf_counter() - t_host) * 1e3 / args.batch_steps
     torch.cuda.synchronize()
     sorter.sync()
     kt, kc = sorter.kernel_times()
@@ -726,6 +729,33 @@ def run_batched(args, pkg, synth, dev, stream, rank, world):
         per_kernel[name] = round(per_kernel.get(name, 0.0) + ms / max(kc, 1), 4)
     b_ms = job_time_ms(e0.elapsed_time(e1), world, dev) / args.batch_steps
     sorter.close()
+
+    # the same batch through the batch-graph cache (BSORT_FLAG_GRAPHS) on a
+    # created stream (the legacy default stream cannot be captured): after
+    # the first call, one graph launch per call and no planning on the host
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    gsort = pkg.BucketSorter(device=dev.index, graphs=True)
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            gsort.sort_batch(keys, off, out=out)
+        gsort.sync()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), "graph replay differs from the plain batch"
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        t_host = time.perf_counter()
+        g0.record(side)
+        for _ in range(args.batch_steps):
+            gsort.sort_batch(keys, off, out=out)
+        g1.record(side)
+        g_host_ms = (time.perf_counter() - t_host) * 1e3 / args.batch_steps
+        torch.cuda.synchronize()
+        gsort.sync()
+    g_ms = g0.elapsed_time(g1) / args.batch_steps
+    gsort.close()
+    stream.wait_stream(side)
+    del ref
 
     # the same arrays, one plain sort call each
     plain = pkg.BucketSorter(device=dev.index)
@@ -756,6 +786,10 @@ def run_batched(args, pkg, synth, dev, stream, rank, world):
                            "ms_per_batch": s_ms,
                            "launch": "one bsort_sort_keys call per array, same stream"},
             "speedup_vs_sequential": s_ms / b_ms, "gpu_launches": bplan.num_kernels,
+            "host_ms_per_call": host_ms,
+            "graph": {"value": nb * world / (g_ms / 1e3) / 1e9, "unit": UNIT,
+                      "ms_per_batch": g_ms, "host_ms_per_call": g_host_ms,
+                      "launch": "one CUDA-graph launch per call (BSORT_FLAG_GRAPHS)"},
             "plan": bplan.as_dict(), "per_kernel_ms": per_kernel}
 
 
@@ -943,6 +977,11 @@ def run_served(args, pkg, synth, dev, rank, capacity_only=False):
 
     # capacity: the first jobs of the trace back to back (closed loop), both
     # ways, in this process and in a fresh one
+    import gc
+    import torch
+    gc.collect()
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()  # device memory the earlier sections left cached
     capacity = _serve_capacity(args, pkg, dev, job, ring, maxn, ncap, cap_keys)
     capacity["fresh_process"] = _serve_capacity_subprocess(args) if rank == 0 else None
 

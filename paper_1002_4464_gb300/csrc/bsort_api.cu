@@ -106,6 +106,21 @@ struct bsort_ctx {
         uint64_t used = 0;
     };
     std::vector<Graph> graphs;
+    // BSORT_FLAG_GRAPHS for bsort_sort_batch: the launch sequence of one
+    // segment table, replayed when the same table comes again; the graph
+    // owns a pinned copy of the batch descriptors its first node uploads
+    struct BatchGraph {
+        int kt = 0;
+        const void *kin = nullptr;
+        void *kout = nullptr, *ws = nullptr;
+        cudaStream_t st = nullptr;
+        uint64_t hash = 0;
+        std::vector<uint64_t> table;  // begin, n of every segment
+        void *desc = nullptr;         // pinned descriptors
+        cudaGraphExec_t exec = nullptr;
+        uint64_t used = 0;
+    };
+    std::vector<BatchGraph> batch_graphs;
     uint64_t graph_clock = 0;
     bool capturing = false;  // no timing events while a sort is captured
     // bsort_sort_keys_host: copy stream and its events (made on first use)
@@ -570,6 +585,11 @@ void drop_graphs(bsort_t h)
 {
     for (auto &g : h->graphs) cudaGraphExecDestroy(g.exec);
     h->graphs.clear();
+    for (auto &g : h->batch_graphs) {
+        cudaGraphExecDestroy(g.exec);
+        if (g.desc) cudaFreeHost(g.desc);
+    }
+    h->batch_graphs.clear();
 }
 
 bsort_status ensure_workspace(bsort_t h, uint64_t bytes)
@@ -1251,8 +1271,13 @@ bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const SegSpan *spans,
     return BSORT_OK;
 }
 
+// stage: when not null, pinned host memory of at least the plan's
+// descriptor bytes that the caller keeps unchanged for as long as the
+// upload may run again (a captured graph replays it); the handle's shared
+// staging is used otherwise.
 bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout,
-                       const SegSpan *spans, uint32_t nsegs, cudaStream_t st)
+                       const SegSpan *spans, uint32_t nsegs, cudaStream_t st,
+                       void *stage = nullptr)
 {
     bsort_status rs = prepare(h);
     if (rs != BSORT_OK) return rs;
@@ -1281,7 +1306,20 @@ bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout
     const uint32_t *ki = static_cast<const uint32_t *>(kin);
     uint32_t *ko = static_cast<uint32_t *>(kout);
     Seq seq(h, st);
-    if (B.d_words) {
+    if (B.d_words && stage) {
+        // descriptors from the caller's pinned buffer (a graph's own)
+        uint32_t *hw = static_cast<uint32_t *>(stage);
+        const uint64_t bytes = B.d_words * 4;
+        memset(hw, 0, bytes);
+        for (int c = 0; c < kNumDirect; ++c)
+            if (!B.direct[c].empty())
+                memcpy(hw + B.d_direct[c], B.direct[c].data(), B.direct[c].size() * 4);
+        if (!B.sub_seg.empty()) memcpy(hw + B.d_sub, B.sub_seg.data(), B.sub_seg.size() * 4);
+        if (!B.segs.empty()) memcpy(hw + B.d_segs, B.segs.data(), B.segs.size() * sizeof(SegInfo));
+        if (!B.units.empty()) memcpy(hw + B.d_units, B.units.data(), B.units.size() * 4);
+        e = cudaMemcpyAsync(desc, hw, bytes, cudaMemcpyHostToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy of the batch descriptors");
+    } else if (B.d_words) {
         // descriptors: pinned staging -> workspace (the staging is reused
         // only after the previous copy out of it has completed)
         const uint64_t bytes = B.d_words * 4;
@@ -1370,6 +1408,109 @@ bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout
         if (rs != BSORT_OK) return rs;
     }
     return BSORT_OK;
+}
+
+// run_batch through the handle's batch-graph cache (BSORT_FLAG_GRAPHS): a
+// call whose segment table, key type, buffers, stream and workspace match a
+// cached graph replays it with one graph launch (no planning on the host);
+// otherwise the batch is planned, its launch sequence captured with the
+// descriptors staged in pinned memory the graph owns, and kept (the 8 most
+// recently used).
+bsort_status run_batch_graph(bsort_t h, bsort_key_type kt, const void *kin, void *kout,
+                             const SegSpan *spans, uint32_t nsegs, cudaStream_t st)
+{
+    if (!(h->flags & BSORT_FLAG_GRAPHS) || nsegs == 0 || st == nullptr || st == cudaStreamLegacy)
+        return run_batch(h, kt, kin, kout, spans, nsegs, st);
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamIsCapturing");
+    if (cs != cudaStreamCaptureStatusNone) return run_batch(h, kt, kin, kout, spans, nsegs, st);
+    uint64_t hash = 0x9E3779B97F4A7C15ull ^ nsegs;
+    for (uint32_t q = 0; q < nsegs; ++q) {
+        hash = (hash ^ spans[q].begin) * 0xBF58476D1CE4E5B9ull;
+        hash = (hash ^ spans[q].n) * 0x94D049BB133111EBull;
+    }
+    for (auto &g : h->batch_graphs) {
+        if (g.kt != (int)kt || g.kin != kin || g.kout != kout || g.st != st || g.ws != h->ws ||
+            g.hash != hash || g.table.size() != 2ull * nsegs)
+            continue;
+        bool same = true;
+        for (uint32_t q = 0; q < nsegs && same; ++q)
+            same = g.table[2 * q] == spans[q].begin && g.table[2 * q + 1] == spans[q].n;
+        if (!same) continue;
+        g.used = ++h->graph_clock;
+        e = cudaGraphLaunch(g.exec, st);
+        return e == cudaSuccess ? BSORT_OK : cuda_fail(h, e, "cudaGraphLaunch");
+    }
+    // settle the plan and the workspace outside the capture
+    bsort_status rs = prepare(h);
+    if (rs != BSORT_OK) return rs;
+    BatchPlan B;
+    rs = make_batch_plan(h, kt, spans, nsegs, &B);
+    if (rs != BSORT_OK) return rs;
+    rs = ensure_workspace(h, B.total);  // (covers the plain sorts of large segments)
+    if (rs != BSORT_OK) return rs;
+    void *desc = nullptr;
+    if (B.d_words) {
+        e = cudaHostAlloc(&desc, B.d_words * 4, cudaHostAllocDefault);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(h, BSORT_ENOMEM, "pinned descriptors of %llu bytes",
+                        (unsigned long long)(B.d_words * 4));
+        }
+    }
+    e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        if (desc) cudaFreeHost(desc);
+        return cuda_fail(h, e, "cudaStreamBeginCapture");
+    }
+    h->capturing = true;
+    rs = run_batch(h, kt, kin, kout, spans, nsegs, st, desc ? desc : nullptr);
+    h->capturing = false;
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(st, &graph);
+    if (rs != BSORT_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        if (desc) cudaFreeHost(desc);
+        cudaGetLastError();
+        return rs != BSORT_OK ? rs : cuda_fail(h, e, "cudaStreamEndCapture");
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        if (desc) cudaFreeHost(desc);
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    constexpr size_t kBatchGraphs = 8;
+    if (h->batch_graphs.size() >= kBatchGraphs) {  // drop the least recently used
+        size_t lru = 0;
+        for (size_t i = 1; i < h->batch_graphs.size(); ++i)
+            if (h->batch_graphs[i].used < h->batch_graphs[lru].used) lru = i;
+        // (its last replay may still be reading the descriptors)
+        cudaStreamSynchronize(h->batch_graphs[lru].st);
+        cudaGraphExecDestroy(h->batch_graphs[lru].exec);
+        if (h->batch_graphs[lru].desc) cudaFreeHost(h->batch_graphs[lru].desc);
+        h->batch_graphs.erase(h->batch_graphs.begin() + (long)lru);
+    }
+    bsort_ctx::BatchGraph g;
+    g.kt = (int)kt;
+    g.kin = kin;
+    g.kout = kout;
+    g.ws = h->ws;
+    g.st = st;
+    g.hash = hash;
+    g.table.reserve(2ull * nsegs);
+    for (uint32_t q = 0; q < nsegs; ++q) {
+        g.table.push_back(spans[q].begin);
+        g.table.push_back(spans[q].n);
+    }
+    g.desc = desc;
+    g.exec = exec;
+    g.used = ++h->graph_clock;
+    h->batch_graphs.push_back(std::move(g));
+    e = cudaGraphLaunch(exec, st);
+    return e == cudaSuccess ? BSORT_OK : cuda_fail(h, e, "cudaGraphLaunch");
 }
 
 }  // namespace
@@ -1991,8 +2132,8 @@ bsort_status bsort_sort_batch(bsort_t h, bsort_key_type kt, const void *d_keys_i
     std::vector<SegSpan> spans;
     bsort_status st = spans_from_offsets(h, seg_offsets, num_segs, &spans);
     if (st != BSORT_OK) return st;
-    return run_batch(h, kt, d_keys_in, d_keys_out, spans.data(), num_segs,
-                     static_cast<cudaStream_t>(cuda_stream));
+    return run_batch_graph(h, kt, d_keys_in, d_keys_out, spans.data(), num_segs,
+                           static_cast<cudaStream_t>(cuda_stream));
 }
 
 bsort_status bsort_submit(bsort_t h, const bsort_request *req, uint64_t *ticket)
