@@ -928,7 +928,7 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     // Step 6
     uint32_t *cum = reinterpret_cast<uint32_t *>(ws + P.off_cum);
     uint32_t *jr = reinterpret_cast<uint32_t *>(ws + P.off_jr);
-    SEQ(launch_sample_index(tiles_k, spl, I.t, I.b, I.m, jr, cum, st), "step6_sample_index");
+    SEQ(launch_sample_index(tiles_k, spl, I.t, I.s, I.b, I.m, jr, cum, st), "step6_sample_index");
     // Step 7 (also a_ij and the run starts from the cumulative counts)
     SEQ(launch_scan_cum(cum, I.m, I.t, nullptr, srcb, offsets, P.n_runs, status, ticket, err, st,
                         (h->flags & BSORT_FLAG_TEST_STALL_SCAN) != 0),
@@ -2366,6 +2366,17 @@ bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which, void *h
         e = cudaMemcpy(h_dst, static_cast<unsigned char *>(h->ws) + off, size,
                        cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(h, e, "copy intermediate");
+    if (!P.wide && (which == BSORT_IM_SAMPLES || which == BSORT_IM_SPLITTERS)) {
+        // records hold key << 32 | q (q = i*s + k); report key << 32 | p with
+        // p = i*t + (k+1)w - 1, the sample's position in the sorted sublists
+        const uint64_t s = P.info.s, t = P.info.t, w = P.info.w;
+        uint64_t *rec = static_cast<uint64_t *>(h_dst);
+        for (uint64_t x = 0; x < size / 8; ++x) {
+            const uint64_t q = rec[x] & 0xFFFFFFFFull;
+            const uint64_t pos = q / s * t + (q % s + 1) * w - 1;
+            rec[x] = (rec[x] & ~0xFFFFFFFFull) | (pos & 0xFFFFFFFFull);
+        }
+    }
     return BSORT_OK;
 }
 

@@ -115,8 +115,9 @@ cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint
 
 // Step 6: cum[j*m + i] = c_ij, the items of sorted sublist i at or below
 // splitter j (bucket-major); jr: m * max(1, t / 1024) words of scratch.
+// (sample records are key << 32 | q, q = i*s + k the sample's index)
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *spl, uint32_t t,
-                                uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
+                                uint32_t s, uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
                                 cudaStream_t st);
 // Number of scratch words launch_sample_index (segments of 1024 keys) or
 // launch_sample_index_seg_u64 (4096) needs for m sublists of t.

@@ -202,21 +202,31 @@ constexpr int kSegItems = 1024;  // items of one sublist's segment
 constexpr int kSub6 = 8;         // sublists per CTA: 8 counts = one 32-byte sector
 constexpr int kSegRow = kSegItems + 4;  // staged row: rows start in different banks
 
+// Position p = i*t + (k+1)w - 1 of the sample whose record holds q = i*s + k.
+__device__ __forceinline__ uint64_t sample_pos(uint32_t q, uint32_t s, uint32_t t, uint32_t w)
+{
+    return (uint64_t)(q / s) * t + (uint64_t)(q % s + 1) * w - 1;
+}
+
 __global__ void k_seg_ranges(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ spl,
-                             uint32_t t, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
-                             uint32_t *__restrict__ jr)
+                             uint32_t t, uint32_t s, uint32_t b, uint32_t m, uint32_t nseg,
+                             uint32_t seg, uint32_t *__restrict__ jr)
 {
     const uint32_t idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= m * nseg) return;
     const uint32_t i = idx / nseg, k = idx % nseg;
+    const uint32_t w = t / s;
     uint32_t r = 0;
     if (k > 0) {
-        const uint32_t x = i * t + k * seg - 1;  // item S - 1 of sublist i
-        const uint64_t v = ((uint64_t)tiles_k[x] << 32) | x;
+        const uint64_t x = (uint64_t)i * t + k * seg - 1;  // item S - 1 of sublist i
+        const uint32_t key = tiles_k[x];
         uint32_t lo = 0, hi = b;
-        while (lo < hi) {  // splitters below v
+        while (lo < hi) {  // splitters below item x in (key, position) order
             const uint32_t mid = (lo + hi) >> 1;
-            if (spl[mid] < v) lo = mid + 1;
+            const uint64_t g = spl[mid];
+            const uint32_t gk = (uint32_t)(g >> 32);
+            const bool below = gk < key || (gk == key && sample_pos((uint32_t)g, s, t, w) < x);
+            if (below) lo = mid + 1;
             else hi = mid;
         }
         r = lo;
@@ -227,7 +237,7 @@ __global__ void k_seg_ranges(const uint32_t *__restrict__ tiles_k, const uint64_
 template <int T>
 __global__ void __launch_bounds__(T)
 k_sample_index_grp(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ spl,
-                   uint32_t t, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
+                   uint32_t t, uint32_t s, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
                    const uint32_t *__restrict__ jr, uint32_t *__restrict__ cum)
 {
     __shared__ __align__(16) uint32_t sk[kSub6 * kSegRow];
@@ -269,23 +279,35 @@ k_sample_index_grp(const uint32_t *__restrict__ tiles_k, const uint64_t *__restr
         }
     }
     if (J0 >= J1) return;
-    // pair p = (j - J0) * kSub6 + ii: lanes 8c .. 8c+7 hold one splitter
+    // pair p = (j - J0) * kSub6 + ii: lanes 8c .. 8c+7 hold one splitter.
+    // Splitter g = (gk, q) is the sample at rank gr = (q mod s + 1)w - 1 of
+    // sublist gi = q / s; in (key, position) order sublist i holds
+    // upper_bound(gk) items <= g if i < gi (all its positions are lower),
+    // lower_bound(gk) if i > gi, and exactly gr + 1 if i == gi.
+    const uint32_t w = t / s;
     const uint32_t pairs = (J1 - J0) * kSub6;
     for (uint32_t p = tid; p < pairs; p += T) {
         const uint32_t j = J0 + p / kSub6, ii = p % kSub6;
         if (ii >= ns || j < s_lo[ii] || j >= s_hi[ii]) continue;
         const uint64_t g = spl[j];
-        const uint32_t gk = (uint32_t)(g >> 32), gp = (uint32_t)g;
-        const uint32_t p0 = (i0 + ii) * t + S;  // position of the segment's first item
-        const uint32_t *row = sk + ii * kSegRow;
-        uint32_t lo = 0, hi = seg;
-        while (lo < hi) {  // segment items <= g
-            const uint32_t mid = (lo + hi) >> 1;
-            const uint32_t key = row[mid];
-            if (key < gk || (key == gk && p0 + mid <= gp)) lo = mid + 1;
-            else hi = mid;
+        const uint32_t gk = (uint32_t)(g >> 32), q = (uint32_t)g;
+        const uint32_t i = i0 + ii, gi = q / s;
+        uint32_t c;
+        if (i == gi) {
+            c = (q % s + 1) * w;  // gr + 1
+        } else {
+            const bool le = i < gi;  // count keys <= gk, else keys < gk
+            const uint32_t *row = sk + ii * kSegRow;
+            uint32_t lo = 0, hi = seg;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                const uint32_t key = row[mid];
+                if (key < gk || (le && key == gk)) lo = mid + 1;
+                else hi = mid;
+            }
+            c = S + lo;
         }
-        cum[(uint64_t)j * m + i0 + ii] = S + lo;
+        cum[(uint64_t)j * m + i] = c;
     }
 }
 
@@ -873,18 +895,18 @@ cudaError_t launch_select_splitters(const uint64_t *sorted, uint32_t n_rec, uint
 }
 
 cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *spl, uint32_t t,
-                                uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
+                                uint32_t s, uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
                                 cudaStream_t st)
 {
     const uint32_t seg = t < (uint32_t)kSegItems ? t : (uint32_t)kSegItems;
     const uint32_t nseg = t / seg;
     const uint32_t ns = m * nseg;
-    k_seg_ranges<<<(ns + 255) / 256, 256, 0, st>>>(tiles_k, spl, t, b, m, nseg, seg, jr);
+    k_seg_ranges<<<(ns + 255) / 256, 256, 0, st>>>(tiles_k, spl, t, s, b, m, nseg, seg, jr);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint32_t groups = (m + kSub6 - 1) / kSub6;
-    k_sample_index_grp<256><<<groups * nseg, 256, 0, st>>>(tiles_k, spl, t, b, m, nseg, seg, jr,
-                                                          cum);
+    k_sample_index_grp<256><<<groups * nseg, 256, 0, st>>>(tiles_k, spl, t, s, b, m, nseg, seg,
+                                                          jr, cum);
     return cudaGetLastError();
 }
 

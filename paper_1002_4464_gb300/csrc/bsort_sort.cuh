@@ -107,7 +107,10 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
             tiles_k[base + off + x] = (uint32_t)e;
         }
     }
-    // Step 3: samples at ranks (k+1)w - 1 in [off, off + CH) as (key, p = i*t + r).
+    // Step 3: samples at ranks (k+1)w - 1 in [off, off + CH), as the record
+    // key << 32 | q with q = i*s + k, the sample's index: its position
+    // p = i*t + (k+1)w - 1 grows with q, so records order by (key, q) exactly
+    // as by (key, p), and q fits 32 bits whatever the size of the input.
     const uint32_t w = TT / s;
     const uint32_t k0 = (uint32_t)off / w;                // first sample in range
     const uint32_t k1 = (uint32_t)(off + CH) / w;         // one past the last
@@ -115,7 +118,7 @@ k_sublist_sort(const uint32_t *__restrict__ keys_in, const void *__restrict__ va
         const uint32_t rank = (k + 1) * w - 1;
         const K e = sm[pidx<K>((int)(rank - off))];
         const uint32_t key = PAIRS ? (uint32_t)((uint64_t)e >> 32) : (uint32_t)e;
-        samples[(uint64_t)tile * s + k] = ((uint64_t)key << 32) | (uint32_t)(base + rank);
+        samples[(uint64_t)tile * s + k] = ((uint64_t)key << 32) | (tile * s + k);
     }
 }
 
