@@ -20,8 +20,14 @@
  *   - Input and output may be the same buffer (in-place sort, as in the
  *     paper); otherwise they must not overlap.  The input is never modified
  *     when it differs from the output.
- *   - n = 0 and n = 1 are valid.  n must satisfy n < 2^32 - 2^16 (positions
- *     are 32-bit on the device); larger n returns BSORT_EUNSUPPORTED.
+ *   - n = 0 and n = 1 are valid.  Key-value pairs, 64-bit keys, batches and
+ *     served jobs take n < 2^32 - 2^16 (their positions are 32-bit on the
+ *     device).  Keys-only sorts of 32-bit keys (bsort_sort_keys,
+ *     bsort_sort_keys_host) take n up to 2^34, with a two-level plan above
+ *     2^30 keys (see bsort_plan_info.levels; planner-chosen t, s and b
+ *     only); such a call waits for its stream once, after Step 8, to read the
+ *     b bucket sizes and plan the bucket sorts.  Larger n returns
+ *     BSORT_EUNSUPPORTED.
  *   - A handle is not thread-safe; use one handle per host thread.  Calls on
  *     one handle must be ordered on one stream (they share its workspace).
  *   - Errors: argument and launch errors are returned directly.  A device
@@ -110,6 +116,12 @@ typedef enum {
                                       (t, s) is tabled for n's size class
                                       (keys-only 32-bit sorts); kept to
                                       compare the two */
+#define BSORT_FLAG_TEST_TWO_LEVEL 0x40u /* test of the two-level plan:
+                                      keys-only 32-bit sorts of more than
+                                      65536 keys take it at any size, with
+                                      top-level buckets of about 2^16 keys
+                                      (so that small inputs exercise it);
+                                      never set it otherwise */
 #define BSORT_FLAG_MERGE_SORT 0x8u /* keys-only 32-bit sorts: a unit of
                                       32768 keys sorted by one CTA (a Step-9
                                       bucket unit, a Step-2 sublist of
@@ -175,6 +187,11 @@ typedef struct {
                                 many items are sorted by one CTA each, the
                                 others by a unit of unit_ctas CTAs (0: one
                                 tier) */
+    uint32_t levels;         /* 1; 2 above 2^30 keys (keys-only 32-bit keys,
+                                planner's t/s/b): Step 9 sorts each of the b
+                                buckets, at most bucket_bound keys, by a
+                                plan of its own */
+    uint32_t pad_;
 } bsort_plan_info;
 
 /* The plan of one batch (bsort_plan_batch). */

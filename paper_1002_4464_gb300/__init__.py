@@ -17,7 +17,7 @@ __all__ = [
     "BSORT_EBUSY", "BSORT_ENOTREADY", "BSORT_EUNSUPPORTED", "BSORT_EINTERNAL",
     "BSORT_U32", "BSORT_F32", "BSORT_U64", "BSORT_FLAG_TIMING", "BSORT_FLAG_LOW_MEMORY",
     "BSORT_FLAG_GRAPHS", "BSORT_FLAG_MERGE_SORT", "BSORT_FLAG_TEST_STALL_SCAN",
-    "BSORT_FLAG_PLAN_MODEL", "BSORT_BUCKETS_AUTO",
+    "BSORT_FLAG_PLAN_MODEL", "BSORT_BUCKETS_AUTO", "BSORT_FLAG_TEST_TWO_LEVEL",
     "bsort_config", "bsort_plan_info", "BsortError", "load_library",
     "bsort_create", "bsort_destroy", "bsort_plan", "bsort_sort_keys",
     "bsort_sort_pairs", "bsort_sort_keys_host", "bsort_sync",
@@ -37,6 +37,7 @@ BSORT_FLAG_GRAPHS = 0x4
 BSORT_FLAG_MERGE_SORT = 0x8
 BSORT_FLAG_TEST_STALL_SCAN = 0x10
 BSORT_FLAG_PLAN_MODEL = 0x20
+BSORT_FLAG_TEST_TWO_LEVEL = 0x40
 BSORT_BUCKETS_AUTO = 0xFFFFFFFF
 (BSORT_IM_TILES, BSORT_IM_SAMPLES, BSORT_IM_SPLITTERS, BSORT_IM_COUNTS,
  BSORT_IM_OFFSETS, BSORT_IM_RELOCATED) = range(6)
@@ -68,7 +69,8 @@ class bsort_plan_info(ctypes.Structure):
                 ("tile_ctas", ctypes.c_uint32), ("unit_ctas", ctypes.c_uint32),
                 ("unit_capacity", ctypes.c_uint64), ("single_tile", ctypes.c_uint32),
                 ("num_kernels", ctypes.c_uint32), ("workspace_bytes", ctypes.c_uint64),
-                ("b", ctypes.c_uint32), ("unit_small", ctypes.c_uint32)]
+                ("b", ctypes.c_uint32), ("unit_small", ctypes.c_uint32),
+                ("levels", ctypes.c_uint32), ("pad_", ctypes.c_uint32)]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

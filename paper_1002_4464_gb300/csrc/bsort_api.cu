@@ -26,6 +26,14 @@ using namespace bsort;
 
 constexpr uint64_t kAlign = 256;
 constexpr uint64_t kMaxN = (1ull << 32) - (1ull << 16);
+// Keys-only sorts of 32-bit keys above kTwoLevelAbove keys (or wherever no
+// one-level plan exists) take two levels: a top level of Algorithm 1 with
+// buckets of about kTopBucket keys, each bucket then sorted by a plan of
+// its own (Step 9 may use any exact sort).  (At 2^30 keys the best one-level
+// plan sorts at 24 Gkeys/s, four 2^28-key buckets at about 40.)
+constexpr uint64_t kTwoLevelAbove = 1ull << 30;
+constexpr uint64_t kMaxTwoLevelN = 1ull << 34;
+constexpr uint64_t kTopBucket = 1ull << 28;
 constexpr uint64_t kMaxSamples = 8192;  // s per sublist (Step 6 keeps 12*s bytes in SMEM)
 constexpr int kMaxTimed = 40;   // launches recorded per call
 constexpr int kPipe = 16;       // host entry: key chunks in, position slices out
@@ -61,6 +69,9 @@ struct Plan {
         off_units, off_units2, off_srcb, off_blk, off_cum, off_jr, total;
     bool relocate;  // materialise Step 8 (else fused into Step 9's load)
     bool radix;     // 32768-key chunks of 32-bit keys sorted by digits
+    // two-level plans (n' >= 2^32): 64-bit bucket offsets, bucket starts,
+    // and the workspace of the bucket sorts
+    uint64_t off_off64, off_csum, off_cpre, off_starts, off_child, child_bytes;
 };
 
 }  // namespace
@@ -329,12 +340,107 @@ bool tuned_plan(uint64_t n, uint64_t *t, uint64_t *s)
 bsort_status make_plan_with(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P,
                             bool use_table);
 
+// Plan of n >= kMaxN 32-bit keys (keys only): the top level sorts sublists of
+// t = 32768 (one CTA each), takes b buckets of about kTopBucket keys, and the
+// largest sample distance w whose share of the bucket bound, (m-1)(w-1),
+// stays within a quarter of the average bucket; Step 9 sorts each bucket by
+// a plan of its own in a slice of the workspace sized for the bound.
+bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P);
+
+bsort_status make_plan_two_level(bsort_t h, bsort_key_type kt, uint64_t n, Plan *P)
+{
+    P->pairs = false;
+    P->wide = false;
+    P->kb = 4;
+    P->vb = 0;
+    P->relocate = true;
+    P->radix = !(h && (h->flags & BSORT_FLAG_MERGE_SORT));
+    bsort_plan_info &I = P->info;
+    const uint64_t t = 32768;
+    const uint64_t m = (n + t - 1) / t;
+    const uint64_t np = m * t;
+    // (BSORT_FLAG_TEST_TWO_LEVEL: buckets of about 2^16 keys, so that small
+    // inputs take many of them)
+    const uint64_t top = h && (h->flags & BSORT_FLAG_TEST_TWO_LEVEL) ? (1ull << 16) : kTopBucket;
+    uint64_t b = (np + top - 1) / top;
+    if (b < 2) b = 2;
+    uint64_t w = 1;
+    while (w * 2 <= t && (m - 1) * (w * 2 - 1) <= np / (4 * b)) w *= 2;
+    const uint64_t s = t / w;
+    if (m * s >= (1ull << 32) || m * b >= (1ull << 32))
+        return fail(h, BSORT_EUNSUPPORTED, "n = %llu: too many samples", (unsigned long long)n);
+    I.n = n;
+    I.n_padded = np;
+    I.t = (uint32_t)t;
+    I.s = (uint32_t)s;
+    I.m = (uint32_t)m;
+    I.w = (uint32_t)w;
+    I.b = (uint32_t)b;
+    I.bucket_bound = bound_for(np, m, s, b);
+    if (I.bucket_bound >= kMaxN)
+        return fail(h, BSORT_EUNSUPPORTED, "n = %llu: bucket bound %llu too large",
+                    (unsigned long long)n, (unsigned long long)I.bucket_bound);
+    I.tile_ctas = 1;
+    I.levels = 2;
+    P->tile_chunk = (int)t;
+    // the bucket sorts: a plan for the bound, with a quarter more room
+    bsort_ctx child;
+    child.device = h ? h->device : 0;
+    child.flags = h ? (h->flags & (BSORT_FLAG_MERGE_SORT | BSORT_FLAG_PLAN_MODEL)) : 0;
+    Plan C;
+    bsort_status rs = make_plan(&child, BSORT_U32, 0, I.bucket_bound, &C);
+    if (rs != BSORT_OK)
+        return fail(h, rs, "n = %llu: no plan for a bucket of %llu keys", (unsigned long long)n,
+                    (unsigned long long)I.bucket_bound);
+    P->child_bytes = align_up(C.total + C.total / 4 + (1u << 20));
+    I.unit_ctas = C.info.single_tile ? C.info.unit_ctas : 0;
+    I.unit_capacity = I.bucket_bound;
+    P->n_rec = (uint32_t)(m * s);
+    P->n_runs = (uint32_t)(m * b);
+    P->n_rec_pad = (uint32_t)((P->n_rec + kRecordChunk - 1) / kRecordChunk * kRecordChunk);
+    uint32_t merges = 0;
+    for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
+    I.num_kernels = 1 + 1 + merges + (merges ? 1 : 0) + 2 /*S6*/ + 3 /*S7*/ + 2 /*S8*/ +
+                    (uint32_t)b * C.info.num_kernels;
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) {
+        uint64_t at = o;
+        o = align_up(o + bytes);
+        return at;
+    };
+    const uint32_t chunks = (P->n_runs + kScanChunk - 1) / kScanChunk;
+    P->off_hdr = take(kAlign);
+    P->off_tiles_k = take(np * 4);
+    P->off_reloc_k = take(np * 4);
+    P->off_samples = take((uint64_t)P->n_rec * 8);
+    P->off_rec_a = take((uint64_t)P->n_rec_pad * 8);
+    P->off_rec_b = take(P->n_rec_pad > (uint32_t)kRecordChunk ? (uint64_t)P->n_rec_pad * 8 : 0);
+    P->off_spl = take(b * 8);
+    P->off_cum = take((uint64_t)P->n_runs * 4);
+    P->off_jr = take(sample_index_scratch_words(I.t, I.m) * 4);
+    P->off_off64 = take(((uint64_t)P->n_runs + 1) * 8);
+    P->off_csum = take((uint64_t)chunks * 4);
+    P->off_cpre = take((uint64_t)chunks * 8);
+    P->off_starts = take((b + 1) * 8);
+    P->off_child = take(P->child_bytes);
+    P->total = o;
+    I.workspace_bytes = o;
+    return BSORT_OK;
+}
+
 // The plan of one job: the tabled (t, s) for n's size class when there is
-// one and it admits a plan, else the cost model's choice.
+// one and it admits a plan, else the cost model's choice; keys-only sorts
+// of 32-bit keys that no one-level plan fits take two levels.
 bsort_status make_plan(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t n, Plan *P)
 {
     bsort_status st = make_plan_with(h, kt, vb, n, P, true);
     if (st == BSORT_EUNSUPPORTED) st = make_plan_with(h, kt, vb, n, P, false);
+    const bool forced = h && (h->force_t || h->force_s || h->force_b);
+    if (st == BSORT_EUNSUPPORTED && vb == 0 && kt != BSORT_U64 && n > (1ull << 28) && !forced &&
+        n <= kMaxTwoLevelN) {
+        memset(P, 0, sizeof(*P));
+        st = make_plan_two_level(h, kt, n, P);
+    }
     return st;
 }
 
@@ -342,12 +448,26 @@ bsort_status make_plan_with(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t 
                             bool use_table)
 {
     memset(P, 0, sizeof(*P));
+    P->info.levels = 1;
     if (kt != BSORT_U32 && kt != BSORT_F32 && kt != BSORT_U64)
         return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
     if (vb != 0 && vb != 4 && vb != 8) return fail(h, BSORT_EINVAL, "val_bytes must be 0, 4 or 8");
     if (kt == BSORT_U64 && vb != 0)
         return fail(h, BSORT_EUNSUPPORTED, "64-bit keys are sorted keys-only (no values)");
-    if (n >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "n = %llu exceeds 2^32 - 2^16", (unsigned long long)n);
+    const bool force_two = h && (h->flags & BSORT_FLAG_TEST_TWO_LEVEL) && vb == 0 &&
+                           kt != BSORT_U64 && n > 2 * 32768;
+    const bool big_keys = vb == 0 && kt != BSORT_U64 && n > kTwoLevelAbove &&
+                          !(h && (h->force_t || h->force_s || h->force_b));
+    if (force_two || (big_keys && n <= kMaxTwoLevelN)) return make_plan_two_level(h, kt, n, P);
+    if (n >= kMaxN) {
+        if (vb != 0 || kt == BSORT_U64)
+            return fail(h, BSORT_EUNSUPPORTED,
+                        "n = %llu: from 2^32 - 2^16 keys on, only keys-only sorts of 32-bit keys",
+                        (unsigned long long)n);
+        if (n > kMaxTwoLevelN)
+            return fail(h, BSORT_EUNSUPPORTED, "n = %llu exceeds 2^34", (unsigned long long)n);
+        return make_plan_two_level(h, kt, n, P);
+    }
     // 64-bit keys and pairs sort 64-bit words: the smaller chunk shapes
     const bool pairs = vb != 0 || kt == BSORT_U64;
     const int cm = max_chunk(pairs);
@@ -736,6 +856,103 @@ cudaError_t stream_after(cudaStream_t to, cudaStream_t from, cudaEvent_t ev)
 
 // Algorithm 1 on 64-bit keys (keys only): the same steps with 64-bit sorted
 // sublists and buckets and 16-byte sample records merged in L2 (Step 4).
+bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void *vin, void *kout,
+                      void *vout, uint32_t vb, uint64_t n, cudaStream_t st,
+                      const HostPipe *hp = nullptr);
+
+// A two-level plan (n' >= 2^32, keys-only 32-bit keys): Steps 1-6 as in
+// run_sort over sublists of 32768 keys, Steps 7-8 with 64-bit offsets
+// (relocation by source: the top-level runs are long), then the b bucket
+// sizes are read back (one wait for the stream) and Step 9 sorts every
+// bucket with a plan of its own, in a slice of the workspace, as 32-bit
+// keys (float keys are still in their order-preserving code and are decoded
+// in the output).
+bsort_status run_sort_two_level(bsort_t h, const Plan &P, bsort_key_type kt, const void *kin,
+                                void *kout, uint64_t n, cudaStream_t st, Seq &seq)
+{
+    const bsort_plan_info &I = P.info;
+    unsigned char *ws = static_cast<unsigned char *>(h->ws);
+    int *err = reinterpret_cast<int *>(ws + P.off_hdr);
+    const int is_f32 = kt == BSORT_F32;
+    uint32_t *tiles_k = reinterpret_cast<uint32_t *>(ws + P.off_tiles_k);
+    uint32_t *reloc_k = reinterpret_cast<uint32_t *>(ws + P.off_reloc_k);
+    uint64_t *samples = reinterpret_cast<uint64_t *>(ws + P.off_samples);
+    uint64_t *rec_a = reinterpret_cast<uint64_t *>(ws + P.off_rec_a);
+    uint64_t *rec_b = reinterpret_cast<uint64_t *>(ws + P.off_rec_b);
+    uint64_t *spl = reinterpret_cast<uint64_t *>(ws + P.off_spl);
+    uint32_t *cum = reinterpret_cast<uint32_t *>(ws + P.off_cum);
+    uint32_t *jr = reinterpret_cast<uint32_t *>(ws + P.off_jr);
+    uint64_t *off64 = reinterpret_cast<uint64_t *>(ws + P.off_off64);
+    uint32_t *csum = reinterpret_cast<uint32_t *>(ws + P.off_csum);
+    uint64_t *cpre = reinterpret_cast<uint64_t *>(ws + P.off_cpre);
+    uint64_t *starts = reinterpret_cast<uint64_t *>(ws + P.off_starts);
+    unsigned char *child_ws = ws + P.off_child;
+    // Steps 1-3
+    SEQ(launch_sublist_sort_keys(P.tile_chunk, 1, kin, n, I.m, is_f32, I.s, tiles_k, samples, st,
+                                 0, P.radix),
+        "step1_3_sublist_sort");
+    // Steps 4-5
+    const bool one_chunk = P.n_rec_pad == (uint32_t)kRecordChunk;
+    SEQ(launch_records_chunk_sort(samples, rec_a, P.n_rec, P.n_rec_pad, one_chunk ? spl : nullptr,
+                                  I.s, I.b, st),
+        "step4_sample_chunks");
+    if (!one_chunk) {
+        uint64_t *src = rec_a, *dst = rec_b;
+        for (uint32_t L = kRecordChunk; L < P.n_rec_pad; L <<= 1) {
+            SEQ(launch_merge_pass(src, dst, P.n_rec_pad, L, st), "step4_sample_merge");
+            std::swap(src, dst);
+        }
+        SEQ(launch_select_splitters(src, P.n_rec, I.b, spl, st), "step5_splitters");
+    }
+    // Step 6
+    SEQ(launch_sample_index(tiles_k, spl, I.t, I.s, I.b, I.m, jr, cum, st), "step6_sample_index");
+    // Step 7 (64-bit offsets) and Step 8 (by source)
+    SEQ(launch_scan_cum64(cum, I.m, P.n_runs, csum, cpre, I.n_padded, off64, st),
+        "step7_prefix_sum");
+    SEQ(launch_relocate_src64(tiles_k, cum, off64, I.m, I.b, I.t, reloc_k, st), "step8_relocate");
+    SEQ(launch_bucket_starts64(off64, I.m, I.b, I.n_padded, starts, st), "step9_bucket_starts");
+    std::vector<uint64_t> hs(I.b + 1);
+    cudaError_t e = cudaMemcpyAsync(hs.data(), starts, hs.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "read the bucket sizes");
+    // Step 9: every bucket by a plan of its own
+    bsort_ctx child;
+    child.device = h->device;
+    child.flags = h->flags & (BSORT_FLAG_MERGE_SORT | BSORT_FLAG_PLAN_MODEL);
+    child.ws = child_ws;
+    child.ws_bytes = P.child_bytes;
+    child.ws_fixed = true;
+    child.kernels_ready = true;
+    e = cudaMemsetAsync(child_ws, 0, sizeof(int), st);  // its error word
+    if (e != cudaSuccess) return cuda_fail(h, e, "memset(error word)");
+    // The padding is the relocated array's tail [n, n'): its keys are the
+    // last sublist's largest items, which end the last run of the last
+    // bucket.  So bucket j sorts positions [L, min(R, n)) straight into the
+    // output (the relocated array stays as Step 8 left it), float codes
+    // decoded there afterwards.
+    uint32_t *out = static_cast<uint32_t *>(kout);
+    for (uint32_t j = 0; j < I.b; ++j) {
+        const uint64_t L = hs[j], R = hs[j + 1];
+        if (R < L || R > I.n_padded || R - L > I.bucket_bound)
+            return fail(h, BSORT_EINTERNAL, "bucket %u spans [%llu, %llu)", j,
+                        (unsigned long long)L, (unsigned long long)R);
+        const uint64_t end = R < n ? R : n;
+        if (end <= L) continue;
+        bsort_status rs = run_sort(&child, BSORT_U32, reloc_k + L, nullptr, out + L, nullptr, 0,
+                                   end - L, st);
+        if (rs != BSORT_OK)
+            return fail(h, rs, "bucket %u (%llu keys): %s", j, (unsigned long long)(end - L),
+                        child.err);
+        if (is_f32) {
+            e = launch_f32_decode(out + L, out + L, end - L, st);
+            if (e != cudaSuccess) return cuda_fail(h, e, "decode a bucket");
+        }
+    }
+    e = launch_merge_error(reinterpret_cast<const int *>(child_ws), err, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "merge error words");
+    return BSORT_OK;
+}
+
 bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout, uint64_t n,
                           cudaStream_t st, Seq &seq)
 {
@@ -819,8 +1036,7 @@ bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout,
 }
 
 bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void *vin, void *kout,
-                      void *vout, uint32_t vb, uint64_t n, cudaStream_t st,
-                      const HostPipe *hp = nullptr)
+                      void *vout, uint32_t vb, uint64_t n, cudaStream_t st, const HostPipe *hp)
 {
     bsort_status rs = prepare(h);
     if (rs != BSORT_OK) return rs;
@@ -840,6 +1056,10 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     const bsort_plan_info &I = P.info;
     Seq seq(h, st);
     if (n == 0) return BSORT_OK;
+    if (I.levels == 2) {
+        if (hp) return fail(h, BSORT_EINTERNAL, "two-level plans take no host pipeline");
+        return run_sort_two_level(h, P, kt, kin, kout, n, st, seq);
+    }
     if (P.wide) return run_sort_u64(h, P, kin, kout, n, st, seq);
     if (I.single_tile) {
         if (n == 1) {
@@ -1040,6 +1260,8 @@ bsort_status run_sort_graph(bsort_t h, bsort_key_type kt, const void *kin, const
     Plan P;
     rs = make_plan(h, kt, vb, n, &P);
     if (rs != BSORT_OK) return rs;
+    if (P.info.levels == 2)  // waits for the stream mid-call: not capturable
+        return run_sort(h, kt, kin, vin, kout, vout, vb, n, st);
     rs = ensure_workspace(h, P.total);
     if (rs != BSORT_OK) return rs;
     for (auto &g : h->graphs) {
@@ -2003,7 +2225,7 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
         if (cfg->flags &
             ~(uint32_t)(BSORT_FLAG_TIMING | BSORT_FLAG_LOW_MEMORY | BSORT_FLAG_GRAPHS |
                         BSORT_FLAG_MERGE_SORT | BSORT_FLAG_TEST_STALL_SCAN |
-                        BSORT_FLAG_PLAN_MODEL)) {
+                        BSORT_FLAG_PLAN_MODEL | BSORT_FLAG_TEST_TWO_LEVEL)) {
             delete h;
             return BSORT_EINVAL;
         }
@@ -2278,7 +2500,8 @@ bsort_status bsort_sort_keys_host(bsort_t h, bsort_key_type kt, const void *h_ke
     cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
     void *d_buf = static_cast<unsigned char *>(h->ws) + stage;
     const int groups = host_pipe_groups(n);
-    if (P.kb == 4 && !P.wide && !P.info.single_tile && P.relocate && groups > 0) {
+    if (P.kb == 4 && !P.wide && !P.info.single_tile && P.relocate && groups > 0 &&
+        P.info.levels == 1) {
         // several sublists: copies overlap Steps 1-3 and Step 9
         rs = ensure_workspace(h, stage + align_up(bytes) + kAlign);
         if (rs != BSORT_OK) return rs;
@@ -2350,6 +2573,21 @@ bsort_status bsort_get_intermediate(bsort_t h, bsort_intermediate which, void *h
                     (unsigned long long)size, (unsigned long long)bytes);
     cudaError_t e = cudaSetDevice(h->device);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (P.info.levels == 2 && (which == BSORT_IM_COUNTS || which == BSORT_IM_OFFSETS)) {
+        // 64-bit offsets (ending with n' at index m*b), reported as uint32
+        // where they fit
+        if (P.info.n_padded >= (1ull << 32))
+            return fail(h, BSORT_EUNSUPPORTED, "offsets of n' >= 2^32 do not fit uint32");
+        std::vector<uint64_t> l((size_t)P.n_runs + 1);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(l.data(), static_cast<unsigned char *>(h->ws) + P.off_off64,
+                           l.size() * 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy intermediate");
+        uint32_t *a = static_cast<uint32_t *>(h_dst);
+        for (uint32_t x = 0; x < P.n_runs; ++x)
+            a[x] = (uint32_t)(which == BSORT_IM_COUNTS ? l[x + 1] - l[x] : l[x]);
+        return BSORT_OK;
+    }
     if (which == BSORT_IM_COUNTS) {
         // a_ij = l_(next run) - l_ij: the offsets array ends with n' at
         // index m*b (written with the run index of Step 8)

@@ -144,6 +144,24 @@ cudaError_t launch_scan_cum(const uint32_t *cum, uint32_t m, uint32_t t, uint32_
                             unsigned long long *status, uint32_t *ticket, int *err,
                             cudaStream_t st, bool stall_first = false);
 
+// Steps 7-8 of plans whose padded size reaches 2^32 (keys-only 32-bit keys,
+// two levels): off64[e] = bucket-major exclusive prefix of a_ij (from the
+// cumulative counts; off64[n_items] = n_pad; chunk_sums / chunk_pre hold one
+// word per kScanChunk items), the relocation by source run by run, and
+// the b + 1 bucket starts.
+cudaError_t launch_scan_cum64(const uint32_t *cum, uint32_t m, uint32_t n_items,
+                              uint32_t *chunk_sums, uint64_t *chunk_pre, uint64_t n_pad,
+                              uint64_t *off64, cudaStream_t st);
+cudaError_t launch_relocate_src64(const uint32_t *tiles_k, const uint32_t *cum,
+                                  const uint64_t *off64, uint32_t m, uint32_t b, uint32_t t,
+                                  uint32_t *reloc, cudaStream_t st);
+cudaError_t launch_bucket_starts64(const uint64_t *off64, uint32_t m, uint32_t b, uint64_t n_pad,
+                                   uint64_t *starts, cudaStream_t st);
+// dst[x] = the float32 bits of the order-preserving code src[x].
+cudaError_t launch_f32_decode(const uint32_t *src, uint32_t *dst, uint64_t n, cudaStream_t st);
+// *to takes *from's error code if it has none yet.
+cudaError_t launch_merge_error(const int *from, int *to, cudaStream_t st);
+
 constexpr int kRelocateSmemMax = 220 * 1024;
 constexpr int kRelocPart = 8192;  // sublist items per Step-8 CTA
 

@@ -840,6 +840,157 @@ __global__ void k_block_index(uint32_t *__restrict__ offsets, uint32_t runs, uin
     blk[b] = lo;
 }
 
+// ============================================================ Steps 7-8, n' >= 2^32
+// Plans whose padded size reaches 2^32 (two levels: a few buckets of about
+// 2^28 keys at the top, each then sorted by a plan of its own) keep counts
+// and sublist ranks in 32 bits but need 64-bit bucket offsets.  Step 7 runs
+// in three passes over the m*b cumulative counts (item e = j*m + i): the
+// sum of a_ij over each chunk of kScanChunk items (each a_ij <= t, so a
+// chunk's sum, at most kScanChunk * t, fits 32 bits), one CTA's 64-bit scan
+// of the chunk sums, and each chunk's rescan into off64.
+template <int T, int ITEMS>
+__global__ void __launch_bounds__(T)
+k_cum_chunk_sums(const uint32_t *__restrict__ cum, uint32_t m, uint32_t n_items,
+                 uint32_t *__restrict__ sums)
+{
+    __shared__ uint32_t s_warp[T / 32];
+    const uint64_t e0 = (uint64_t)blockIdx.x * (T * ITEMS);
+    uint32_t acc = 0;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+        const uint64_t e = e0 + (uint64_t)(k * T + threadIdx.x);
+        if (e < n_items) acc += cum[e] - (e >= m ? cum[e - m] : 0u);
+    }
+    acc = __reduce_add_sync(0xFFFFFFFFu, acc);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < T / 32; ++w) t += s_warp[w];
+        sums[blockIdx.x] = t;
+    }
+}
+
+// pre[c] = sum of sums[0 .. c) in 64 bits, by one CTA.
+template <int T>
+__global__ void __launch_bounds__(T)
+k_chunk_prefix64(const uint32_t *__restrict__ sums, uint32_t chunks, uint64_t *__restrict__ pre)
+{
+    __shared__ unsigned long long s_warp[T / 32];
+    __shared__ unsigned long long s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) s_base = 0;
+    __syncthreads();
+    for (uint32_t c0 = 0; c0 < chunks; c0 += T) {
+        const uint32_t c = c0 + (uint32_t)tid;
+        const unsigned long long v = c < chunks ? sums[c] : 0ull;
+        unsigned long long inc = v;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+            if (lane >= d) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        unsigned long long wpre = 0, tot = 0;
+        for (int w = 0; w < T / 32; ++w) {
+            wpre += w < warp ? s_warp[w] : 0ull;
+            tot += s_warp[w];
+        }
+        const unsigned long long base = s_base;
+        if (c < chunks) pre[c] = base + wpre + inc - v;
+        __syncthreads();
+        if (tid == 0) s_base = base + tot;
+        __syncthreads();
+    }
+}
+
+// off64[e] = exclusive prefix of a_ij in bucket-major order; off64[n_items] = n_pad.
+template <int T, int ITEMS>
+__global__ void __launch_bounds__(T)
+k_offsets64(const uint32_t *__restrict__ cum, uint32_t m, uint32_t n_items,
+            const uint64_t *__restrict__ pre, uint64_t n_pad, uint64_t *__restrict__ off64)
+{
+    __shared__ uint32_t s_items[T * ITEMS];
+    __shared__ uint32_t s_warp[T / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t e0 = (uint64_t)blockIdx.x * (T * ITEMS);
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {  // coalesced loads, staged
+        const uint64_t e = e0 + (uint64_t)(k * T + tid);
+        s_items[k * T + tid] = e < n_items ? cum[e] - (e >= m ? cum[e - m] : 0u) : 0u;
+    }
+    __syncthreads();
+    uint32_t x[ITEMS], sum = 0;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {  // thread-blocked: items tid*ITEMS .. + ITEMS
+        x[k] = s_items[tid * ITEMS + k];
+        sum += x[k];
+    }
+    uint32_t inc = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) s_warp[warp] = inc;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += s_warp[w];
+    uint64_t run = pre[blockIdx.x] + wpre + inc - sum;
+    const uint64_t eb = e0 + (uint64_t)tid * ITEMS;
+#pragma unroll
+    for (int k = 0; k < ITEMS; ++k) {
+        if (eb + k < n_items) off64[eb + k] = run;
+        run += x[k];
+    }
+    if (blockIdx.x == gridDim.x - 1 && tid == 0) off64[n_items] = n_pad;
+}
+
+// Step 8 by source: CTA i copies the runs A_i1 .. A_ib of sorted sublist i
+// (ranks [c_i,j-1, c_ij)) to their offsets (runs of a two-level plan are
+// long: t/b items on average, so the copies are coalesced).
+template <int T>
+__global__ void __launch_bounds__(T)
+k_relocate_src64(const uint32_t *__restrict__ tiles_k, const uint32_t *__restrict__ cum,
+                 const uint64_t *__restrict__ off64, uint32_t m, uint32_t b, uint32_t t,
+                 uint32_t *__restrict__ reloc)
+{
+    const uint32_t i = blockIdx.x;
+    const uint32_t *src = tiles_k + (uint64_t)i * t;
+    uint32_t lo = 0;
+    for (uint32_t j = 0; j < b; ++j) {
+        const uint64_t e = (uint64_t)j * m + i;
+        const uint32_t hi = cum[e];
+        uint32_t *dst = reloc + off64[e] - lo;
+        for (uint32_t r = lo + threadIdx.x; r < hi; r += T) dst[r] = src[r];
+        lo = hi;
+    }
+}
+
+// starts[j] = off64[j*m] (bucket j's first position), starts[b] = n_pad.
+__global__ void k_bucket_starts64(const uint64_t *__restrict__ off64, uint32_t m, uint32_t b,
+                                  uint64_t n_pad, uint64_t *__restrict__ starts)
+{
+    const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < b) starts[j] = off64[(uint64_t)j * m];
+    if (j == b) starts[b] = n_pad;
+}
+
+__global__ void k_f32_decode(const uint32_t *__restrict__ src, uint32_t *__restrict__ dst,
+                             uint64_t n)
+{
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x)
+        dst[x] = f32_decode(src[x]);
+}
+
+// First error of a nested sort (its own error word) into the caller's.
+__global__ void k_merge_error(const int *__restrict__ from, int *to)
+{
+    if (threadIdx.x == 0 && *from != 0) atomicCAS(to, 0, *from);
+}
+
 // ============================================================ launch wrappers
 int smem_bytes_for_cap(int cap, bool pairs)
 {
@@ -1009,6 +1160,50 @@ cudaError_t launch_unit_ranges(const uint32_t *units, uint32_t n_pad, uint32_t G
 {
     if (G + 1 > 32) return cudaErrorInvalidValue;  // one thread per slice boundary
     k_unit_ranges<<<1, 32, 0, st>>>(units, n_pad, G, ranges);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_cum64(const uint32_t *cum, uint32_t m, uint32_t n_items,
+                              uint32_t *chunk_sums, uint64_t *chunk_pre, uint64_t n_pad,
+                              uint64_t *off64, cudaStream_t st)
+{
+    const uint32_t chunks = (n_items + kScanChunk - 1) / kScanChunk;
+    k_cum_chunk_sums<256, 16><<<chunks, 256, 0, st>>>(cum, m, n_items, chunk_sums);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_chunk_prefix64<1024><<<1, 1024, 0, st>>>(chunk_sums, chunks, chunk_pre);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_offsets64<256, 16><<<chunks, 256, 0, st>>>(cum, m, n_items, chunk_pre, n_pad, off64);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relocate_src64(const uint32_t *tiles_k, const uint32_t *cum,
+                                  const uint64_t *off64, uint32_t m, uint32_t b, uint32_t t,
+                                  uint32_t *reloc, cudaStream_t st)
+{
+    k_relocate_src64<256><<<m, 256, 0, st>>>(tiles_k, cum, off64, m, b, t, reloc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bucket_starts64(const uint64_t *off64, uint32_t m, uint32_t b, uint64_t n_pad,
+                                   uint64_t *starts, cudaStream_t st)
+{
+    k_bucket_starts64<<<(b + 256) / 256, 256, 0, st>>>(off64, m, b, n_pad, starts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_f32_decode(const uint32_t *src, uint32_t *dst, uint64_t n, cudaStream_t st)
+{
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + 255) / 256;
+    k_f32_decode<<<(unsigned)(blocks < 65536 ? blocks : 65536), 256, 0, st>>>(src, dst, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_merge_error(const int *from, int *to, cudaStream_t st)
+{
+    k_merge_error<<<1, 32, 0, st>>>(from, to);
     return cudaGetLastError();
 }
 

@@ -122,7 +122,7 @@ def test_plan_pairs_and_errors():
         pkg.bsort_plan(h, pkg.BSORT_U32, 3, 100)
     assert e.value.status == pkg.BSORT_EINVAL
     with pytest.raises(pkg.BsortError) as e:
-        pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 33)
+        pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 35)
     assert e.value.status == pkg.BSORT_EUNSUPPORTED
     pkg.bsort_destroy(h)
     h = _handle(4096, 48)  # s must divide t
@@ -293,10 +293,10 @@ def test_create_flags():
     and refuses unknown bits."""
     ok = (pkg.BSORT_FLAG_TIMING | pkg.BSORT_FLAG_LOW_MEMORY | pkg.BSORT_FLAG_GRAPHS
           | pkg.BSORT_FLAG_MERGE_SORT | pkg.BSORT_FLAG_TEST_STALL_SCAN
-          | pkg.BSORT_FLAG_PLAN_MODEL)
+          | pkg.BSORT_FLAG_PLAN_MODEL | pkg.BSORT_FLAG_TEST_TWO_LEVEL)
     h = pkg.bsort_create(pkg.bsort_config(device=0, flags=ok))
     pkg.bsort_destroy(h)
-    for bad in (0x40, 0x80, 0x80000000):
+    for bad in (0x80, 0x100, 0x80000000):
         with pytest.raises(pkg.BsortError) as e:
             pkg.bsort_create(pkg.bsort_config(device=0, flags=bad))
         assert e.value.status == pkg.BSORT_EINVAL
@@ -334,3 +334,33 @@ def test_tuned_plan_table_lookup():
     p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 26)
     assert (p.t, p.s) == (65536, 4096) and p.b != p.s
     pkg.bsort_destroy(h)
+
+
+def test_plan_two_level():
+    """Above 2^30 keys (keys-only 32-bit keys, up to 2^34) the plan has two
+    levels: sublists of 32768, b buckets of about 2^28 keys whose bound (the
+    oracle's formula) stays below 2^32 - 2^16, m*s samples and m*b runs
+    within 32 bits; pairs and 64-bit keys stop below 2^32 - 2^16."""
+    h = _handle()
+    assert pkg.bsort_plan(h, pkg.BSORT_U32, 0, 1 << 30).levels == 1
+    for n in ((1 << 30) + 1, (1 << 32) - (1 << 16), (1 << 32) + 12345, 1 << 33, 1 << 34):
+        for kt in (pkg.BSORT_U32, pkg.BSORT_F32):
+            p = pkg.bsort_plan(h, kt, 0, n)
+            assert p.levels == 2 and p.t == 32768 and p.m * p.t == p.n_padded >= n
+            assert p.bucket_bound == oracle.bucket_bound(p.n_padded, p.m, p.s, p.b)
+            assert p.n_padded // p.b <= p.bucket_bound < (1 << 32) - (1 << 16)
+            assert p.bucket_bound <= 1.3 * p.n_padded / p.b  # slack within a quarter
+            assert p.m * p.s < 1 << 32 and p.m * p.b < 1 << 32
+    for kt, vb in ((pkg.BSORT_U32, 4), (pkg.BSORT_U64, 0)):
+        with pytest.raises(pkg.BsortError) as e:
+            pkg.bsort_plan(h, kt, vb, 1 << 32)
+        assert e.value.status == pkg.BSORT_EUNSUPPORTED
+    with pytest.raises(pkg.BsortError) as e:
+        pkg.bsort_plan(h, pkg.BSORT_U32, 0, (1 << 34) + 1)
+    assert e.value.status == pkg.BSORT_EUNSUPPORTED
+    pkg.bsort_destroy(h)
+    t = pkg.bsort_create(pkg.bsort_config(device=0, flags=pkg.BSORT_FLAG_TEST_TWO_LEVEL))
+    p = pkg.bsort_plan(t, pkg.BSORT_U32, 0, (1 << 22) + 777)
+    assert p.levels == 2 and p.b == -(-p.n_padded // (1 << 16))
+    assert pkg.bsort_plan(t, pkg.BSORT_U32, 4, 1 << 22).levels == 1
+    pkg.bsort_destroy(t)

@@ -649,3 +649,87 @@ def test_scan_lookback_timeout_is_reported():
     sorter = pkg.BucketSorter(tile=t, samples=s)
     assert np.array_equal(_gpu_sort_keys(sorter, keys), oracle.textbook_sort(keys, "u32"))
     sorter.close()
+
+
+@pytest.mark.parametrize("n,dist,kt", [
+    ((1 << 22) + 777, "uniform", "u32"),
+    ((1 << 21) + 5, "zero", "u32"),
+    ((1 << 21) + 3, "staggered", "u32"),
+    ((1 << 21) + 99, "gaussian", "f32"),
+])
+def test_two_level_forced_intermediates(n, dist, kt):
+    """The two-level plan of n >= 2^32 keys, forced at small n with
+    top-level buckets of about 2^16 keys (BSORT_FLAG_TEST_TWO_LEVEL): the
+    top level's sorted sublists, samples, splitters, counts, 64-bit offsets
+    and relocated array equal the oracle's Algorithm 1 with the same t, s, b,
+    and the result (every bucket sorted by a plan of its own) equals it."""
+    seed = synth.seed_for(8, synth.DISTRIBUTIONS.index(dist), n & 0xFF)
+    keys = synth.keys_f32(dist, n, seed) if kt == "f32" else synth.keys_u32(dist, n, seed)
+    sorter = pkg.BucketSorter(flags=pkg.BSORT_FLAG_TEST_TWO_LEVEL)
+    p = sorter.plan(n, kt)
+    assert p.levels == 2 and p.b > 8
+    want = oracle.paper_sort(keys, p.t, p.s, kt, b=p.b)
+    d_in = torch.from_numpy(np.ascontiguousarray(keys).view(np.int32)).cuda()
+    out = sorter.sort_keys(d_in, key_type=kt)
+    sorter.sync()
+    got = out.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, np.asarray(want["keys"]).view(np.uint32))
+    _check_intermediates(sorter, want, want["n_padded"], want["m"], p.s, p.b)
+    sorter.close()
+
+
+def test_two_level_above_2e32():
+    """n = 2^32 + 12345 uint32 keys (a two-level plan: 64-bit offsets, 17
+    buckets of about 2^28 keys): the output is nondecreasing, has the input's
+    multiset (histograms of the high and low 16 bits, wrapping sums of the
+    keys and of their squares), and its key at sampled ranks r is the r-th
+    smallest input key (fewer than r+1 input keys below it, more than r at
+    or below it), all counted on the device in chunks."""
+    n = (1 << 32) + 12345
+    free, total = torch.cuda.mem_get_info()
+    if free < 80 * 2 ** 30:
+        pytest.skip("needs about 80 GB of device memory")
+    sorter = pkg.BucketSorter()
+    p = sorter.plan(n)
+    assert p.levels == 2
+    keys = torch.empty(n, dtype=torch.int32, device="cuda")
+    chunk = 1 << 28
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        keys[c0:c1] = synth.keys_u32_torch("uniform", c1 - c0, synth.seed_for(8, 0, c0 // chunk),
+                                           device="cuda")
+    out = sorter.sort_keys(keys)
+    sorter.sync()
+
+    def u64(t):
+        return t.to(torch.int64) & 0xFFFFFFFF
+
+    hist_in = torch.zeros(2, 65536, dtype=torch.int64, device="cuda")
+    hist_out = torch.zeros_like(hist_in)
+    sums_in = torch.zeros(2, dtype=torch.int64, device="cuda")
+    sums_out = torch.zeros_like(sums_in)
+    prev = None
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        a, o = u64(keys[c0:c1]), u64(out[c0:c1])
+        assert bool((o[1:] >= o[:-1]).all()), "not sorted in chunk %d" % (c0 // chunk)
+        if prev is not None:
+            assert int(o[0]) >= prev
+        prev = int(o[-1])
+        for src, hist, sums in ((a, hist_in, sums_in), (o, hist_out, sums_out)):
+            hist[0] += torch.bincount(src >> 16, minlength=65536)
+            hist[1] += torch.bincount(src & 0xFFFF, minlength=65536)
+            sums[0] += src.sum()
+            sums[1] += (src * src).sum()
+        del a, o
+    assert torch.equal(hist_in, hist_out) and torch.equal(sums_in, sums_out)
+    gen = np.random.default_rng(12345)
+    for r in [0, n - 1] + gen.integers(0, n, 6).tolist():
+        v = int(u64(out[r:r + 1]))
+        less = le = 0
+        for c0 in range(0, n, chunk):
+            a = u64(keys[c0:min(n, c0 + chunk)])
+            less += int((a < v).sum())
+            le += int((a <= v).sum())
+        assert less <= r < le, (r, v, less, le)
+    sorter.close()
