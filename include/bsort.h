@@ -65,7 +65,9 @@ typedef enum {
                        -NaN < -inf < ... < -0 < +0 < ... < +inf < +NaN;
                        bit patterns are preserved */
     BSORT_U64 = 2   /* unsigned 64-bit keys: keys-only sorts (bsort_sort_keys,
-                       bsort_sort_keys_host); not pairs, batches or the
+                       bsort_sort_keys_host, batches, served jobs) and pairs
+                       (bsort_sort_pairs: two stable passes of the 32-bit
+                       pair sort, low key half first); not the
                        no-allocation entry (BSORT_EUNSUPPORTED) */
 } bsort_key_type;
 

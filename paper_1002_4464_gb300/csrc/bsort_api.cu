@@ -953,6 +953,62 @@ bsort_status run_sort_two_level(bsort_t h, const Plan &P, bsort_key_type kt, con
     return BSORT_OK;
 }
 
+// Key-value pairs with 64-bit keys: two stable passes of the 32-bit pair
+// sort, the least significant half first (an LSD sort over the halves, each
+// pass Algorithm 1 on 32-bit keys carrying positions): pass A orders the
+// low halves carrying the input index, pass B orders the high halves
+// (gathered in pass A's order) carrying pass A's position, and the output
+// takes key and value from input p1[p2[y]].  Stability of both passes makes
+// the result the stable order by the full key.  Scratch: five arrays of n
+// words after the passes' own workspace (plus n keys and values when
+// sorting in place).
+bsort_status run_pairs_u64(bsort_t h, const void *kin, const void *vin, void *kout, void *vout,
+                           uint32_t vb, uint64_t n, cudaStream_t st)
+{
+    bsort_status rs = prepare(h);
+    if (rs != BSORT_OK) return rs;
+    if (n >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "n = %llu exceeds 2^32 - 2^16", (unsigned long long)n);
+    if (n == 0) return BSORT_OK;
+    Plan PA;
+    rs = make_plan(h, BSORT_U32, 4, n, &PA);
+    if (rs != BSORT_OK) return rs;
+    const uint64_t words = align_up(n * 4);
+    const bool in_place = kin == kout || vin == vout;
+    const uint64_t keep = in_place ? align_up(n * 8) + align_up(n * (uint64_t)vb) : 0;
+    const uint64_t base = align_up(PA.total);
+    rs = ensure_workspace(h, base + 5 * words + keep);
+    if (rs != BSORT_OK) return rs;
+    unsigned char *ws = static_cast<unsigned char *>(h->ws) + base;
+    uint32_t *lo = reinterpret_cast<uint32_t *>(ws);
+    uint32_t *iota = reinterpret_cast<uint32_t *>(ws + words);
+    uint32_t *scratch = reinterpret_cast<uint32_t *>(ws + 2 * words);
+    uint32_t *p1 = reinterpret_cast<uint32_t *>(ws + 3 * words);
+    uint32_t *p2 = reinterpret_cast<uint32_t *>(ws + 4 * words);
+    const uint64_t *k64 = static_cast<const uint64_t *>(kin);
+    const void *v = vin;
+    cudaError_t e;
+    if (in_place) {  // keep the input: the last gather reads it while writing
+        unsigned char *kk = ws + 5 * words;
+        unsigned char *vv = kk + align_up(n * 8);
+        e = cudaMemcpyAsync(kk, kin, n * 8, cudaMemcpyDeviceToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(vv, vin, n * vb, cudaMemcpyDeviceToDevice, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "copy the input aside");
+        k64 = reinterpret_cast<const uint64_t *>(kk);
+        v = vv;
+    }
+    e = launch_u64_split(k64, lo, iota, n, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "split 64-bit keys");
+    rs = run_sort(h, BSORT_U32, lo, iota, scratch, p1, 4, n, st);  // pass A: low halves
+    if (rs != BSORT_OK) return rs;
+    e = launch_u64_gather_hi(k64, p1, lo, n, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "gather high halves");
+    rs = run_sort(h, BSORT_U32, lo, iota, scratch, p2, 4, n, st);  // pass B: high halves
+    if (rs != BSORT_OK) return rs;
+    e = launch_u64_final(k64, v, (int)vb, p1, p2, static_cast<uint64_t *>(kout), vout, n, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "apply the permutations");
+    return BSORT_OK;
+}
+
 bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout, uint64_t n,
                           cudaStream_t st, Seq &seq)
 {
@@ -2288,6 +2344,21 @@ bsort_status bsort_plan(bsort_t h, bsort_key_type kt, uint32_t val_bytes, uint64
 {
     if (!out) return fail(h, BSORT_EINVAL, "null plan pointer");
     Plan P;
+    if (kt == BSORT_U64 && val_bytes != 0) {
+        // pairs with 64-bit keys: two passes of the 32-bit pair sort (this
+        // plan) and the scratch of run_pairs_u64, in-place case included
+        if (val_bytes != 4 && val_bytes != 8)
+            return fail(h, BSORT_EINVAL, "val_bytes must be 0, 4 or 8");
+        if (n >= kMaxN)
+            return fail(h, BSORT_EUNSUPPORTED, "n = %llu exceeds 2^32 - 2^16", (unsigned long long)n);
+        bsort_status st = make_plan(h, BSORT_U32, 4, n, &P);
+        if (st != BSORT_OK) return st;
+        *out = P.info;
+        out->workspace_bytes = align_up(P.total) + 5 * align_up(n * 4) + align_up(n * 8) +
+                               align_up(n * (uint64_t)val_bytes);
+        out->num_kernels = 2 * P.info.num_kernels + 3;
+        return BSORT_OK;
+    }
     bsort_status st = make_plan(h, kt, val_bytes, n, &P);
     if (st != BSORT_OK) return st;
     *out = P.info;
@@ -2321,6 +2392,12 @@ bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_i
     if (n && d_vals_in != d_vals_out &&
         overlaps(d_vals_in, n * val_bytes, d_vals_out, n * val_bytes))
         return fail(h, BSORT_EINVAL, "value input and output overlap partially");
+    if (kt == BSORT_U64) {
+        if (n && d_keys_in != d_keys_out && overlaps(d_keys_in, n * 8, d_keys_out, n * 8))
+            return fail(h, BSORT_EINVAL, "key input and output overlap partially");
+        return run_pairs_u64(h, d_keys_in, d_vals_in, d_keys_out, d_vals_out, val_bytes, n,
+                             static_cast<cudaStream_t>(cuda_stream));
+    }
     return run_sort_graph(h, kt, d_keys_in, d_vals_in, d_keys_out, d_vals_out, val_bytes, n,
                           static_cast<cudaStream_t>(cuda_stream));
 }

@@ -162,6 +162,17 @@ cudaError_t launch_f32_decode(const uint32_t *src, uint32_t *dst, uint64_t n, cu
 // *to takes *from's error code if it has none yet.
 cudaError_t launch_merge_error(const int *from, int *to, cudaStream_t st);
 
+// Pairs with 64-bit keys as two stable passes of the 32-bit pair sort:
+// lo[x] = low half of k64[x] and iota[x] = x; hi[x] = high half of
+// k64[p1[x]]; out[y] = (k64, vals)[p1[p2[y]]].
+cudaError_t launch_u64_split(const uint64_t *k64, uint32_t *lo, uint32_t *iota, uint64_t n,
+                             cudaStream_t st);
+cudaError_t launch_u64_gather_hi(const uint64_t *k64, const uint32_t *p1, uint32_t *hi,
+                                 uint64_t n, cudaStream_t st);
+cudaError_t launch_u64_final(const uint64_t *k64, const void *vals, int val_bytes,
+                             const uint32_t *p1, const uint32_t *p2, uint64_t *out_k,
+                             void *out_v, uint64_t n, cudaStream_t st);
+
 constexpr int kRelocateSmemMax = 220 * 1024;
 constexpr int kRelocPart = 8192;  // sublist items per Step-8 CTA
 

@@ -991,6 +991,42 @@ __global__ void k_merge_error(const int *__restrict__ from, int *to)
     if (threadIdx.x == 0 && *from != 0) atomicCAS(to, 0, *from);
 }
 
+// ============================================================ pairs with 64-bit keys
+// Key-value pairs with 64-bit keys are sorted as two stable passes of the
+// 32-bit pair sort (least significant half first, carrying positions):
+// these kernels split the keys, make the index values, gather the high
+// halves in the first pass's order, and apply both permutations.
+__global__ void k_u64_split(const uint64_t *__restrict__ k64, uint32_t *__restrict__ lo,
+                            uint32_t *__restrict__ iota, uint64_t n)
+{
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x) {
+        lo[x] = (uint32_t)k64[x];
+        iota[x] = (uint32_t)x;
+    }
+}
+
+__global__ void k_u64_gather_hi(const uint64_t *__restrict__ k64, const uint32_t *__restrict__ p1,
+                                uint32_t *__restrict__ hi, uint64_t n)
+{
+    for (uint64_t x = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; x < n;
+         x += (uint64_t)gridDim.x * blockDim.x)
+        hi[x] = (uint32_t)(k64[p1[x]] >> 32);
+}
+
+template <typename V>
+__global__ void k_u64_final(const uint64_t *__restrict__ k64, const V *__restrict__ vals,
+                            const uint32_t *__restrict__ p1, const uint32_t *__restrict__ p2,
+                            uint64_t *__restrict__ out_k, V *__restrict__ out_v, uint64_t n)
+{
+    for (uint64_t y = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; y < n;
+         y += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t src = p1[p2[y]];
+        out_k[y] = k64[src];
+        out_v[y] = vals[src];
+    }
+}
+
 // ============================================================ launch wrappers
 int smem_bytes_for_cap(int cap, bool pairs)
 {
@@ -1204,6 +1240,41 @@ cudaError_t launch_f32_decode(const uint32_t *src, uint32_t *dst, uint64_t n, cu
 cudaError_t launch_merge_error(const int *from, int *to, cudaStream_t st)
 {
     k_merge_error<<<1, 32, 0, st>>>(from, to);
+    return cudaGetLastError();
+}
+
+static unsigned elementwise_grid(uint64_t n)
+{
+    const uint64_t blocks = (n + 255) / 256;
+    return (unsigned)(blocks < 65536 ? (blocks ? blocks : 1) : 65536);
+}
+
+cudaError_t launch_u64_split(const uint64_t *k64, uint32_t *lo, uint32_t *iota, uint64_t n,
+                             cudaStream_t st)
+{
+    k_u64_split<<<elementwise_grid(n), 256, 0, st>>>(k64, lo, iota, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_u64_gather_hi(const uint64_t *k64, const uint32_t *p1, uint32_t *hi,
+                                 uint64_t n, cudaStream_t st)
+{
+    k_u64_gather_hi<<<elementwise_grid(n), 256, 0, st>>>(k64, p1, hi, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_u64_final(const uint64_t *k64, const void *vals, int val_bytes,
+                             const uint32_t *p1, const uint32_t *p2, uint64_t *out_k,
+                             void *out_v, uint64_t n, cudaStream_t st)
+{
+    if (val_bytes == 4)
+        k_u64_final<uint32_t><<<elementwise_grid(n), 256, 0, st>>>(
+            k64, static_cast<const uint32_t *>(vals), p1, p2, out_k,
+            static_cast<uint32_t *>(out_v), n);
+    else
+        k_u64_final<uint64_t><<<elementwise_grid(n), 256, 0, st>>>(
+            k64, static_cast<const uint64_t *>(vals), p1, p2, out_k,
+            static_cast<uint64_t *>(out_v), n);
     return cudaGetLastError();
 }
 

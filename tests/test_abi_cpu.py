@@ -202,7 +202,8 @@ def test_batch_sizes_generator():
 
 def test_plan_u64_keys():
     """64-bit keys sort 64-bit words: CTAs of at most 16384 keys, units of at
-    most 8 x 16384; pairs with 64-bit keys are refused."""
+    most 8 x 16384; pairs with 64-bit keys plan two passes of the 32-bit pair
+    sort (that plan, with the scratch of both passes in its workspace)."""
     h = _handle()
     for n in (100, 131072, 131073, 1 << 20, (1 << 24) + 5, 1 << 28):
         p = pkg.bsort_plan(h, pkg.BSORT_U64, 0, n)
@@ -213,8 +214,13 @@ def test_plan_u64_keys():
             assert p.t <= 8 * 16384 and p.m * p.t == p.n_padded >= n
             assert p.bucket_bound == oracle.bucket_bound(p.n_padded, p.m, p.s, p.b)
             assert p.bucket_bound <= p.unit_capacity
+    q = pkg.bsort_plan(h, pkg.BSORT_U32, 4, 1 << 20)
+    p = pkg.bsort_plan(h, pkg.BSORT_U64, 8, 1 << 20)
+    assert (p.t, p.s, p.b) == (q.t, q.s, q.b)
+    assert p.workspace_bytes >= q.workspace_bytes + (1 << 20) * (5 * 4 + 8 + 8)
+    assert p.num_kernels == 2 * q.num_kernels + 3
     with pytest.raises(pkg.BsortError) as e:
-        pkg.bsort_plan(h, pkg.BSORT_U64, 8, 1 << 20)
+        pkg.bsort_plan(h, pkg.BSORT_U64, 8, 1 << 32)
     assert e.value.status == pkg.BSORT_EUNSUPPORTED
     pkg.bsort_destroy(h)
     h = _handle(4096, 64)

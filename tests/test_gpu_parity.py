@@ -733,3 +733,51 @@ def test_two_level_above_2e32():
             le += int((a <= v).sum())
         assert less <= r < le, (r, v, less, le)
     sorter.close()
+
+
+@pytest.mark.parametrize("kind", ["uniform", "few", "low_only", "high_only"])
+@pytest.mark.parametrize("vdtype", [np.uint32, np.uint64])
+def test_u64_pairs_stable(kind, vdtype):
+    """Key-value pairs with 64-bit keys (two stable passes of the 32-bit pair
+    sort, low key half first): keys and values equal the oracle's stable
+    textbook sort, on keys with many duplicates and on keys that differ only
+    in one half."""
+    n = 300007
+    u = synth.keys_u64(n, synth.seed_for(3, 7, ["uniform", "few", "low_only", "high_only"].index(kind)))
+    if kind == "few":
+        u = u & np.uint64(0xF00000000000000F)
+    elif kind == "low_only":
+        u = (u & np.uint64(0xFFFF)) | np.uint64(0xABCD000000000000)
+    elif kind == "high_only":
+        u = u & np.uint64(0xFFFF000000000000)
+    vals = np.arange(n, dtype=vdtype) * vdtype(3)
+    sorter = pkg.BucketSorter()
+    d_k = torch.from_numpy(u.view(np.int64)).cuda()
+    d_v = torch.from_numpy(vals.view(np.int32 if vdtype == np.uint32 else np.int64)).cuda()
+    ok, ov = sorter.sort_pairs(d_k, d_v, key_type="u64")
+    sorter.sync()
+    wk, wv = oracle.textbook_sort(u, "u64", vals=vals)
+    assert np.array_equal(ok.cpu().numpy().view(np.uint64), wk)
+    assert np.array_equal(ov.cpu().numpy().view(vdtype), wv)
+    # in place, and the keys and values untouched when not in place
+    assert np.array_equal(d_k.cpu().numpy().view(np.uint64), u)
+    sorter.sort_pairs(d_k, d_v, out_keys=d_k, out_vals=d_v, key_type="u64")
+    sorter.sync()
+    assert np.array_equal(d_k.cpu().numpy().view(np.uint64), wk)
+    assert np.array_equal(d_v.cpu().numpy().view(vdtype), wv)
+    sorter.close()
+
+
+def test_u64_pairs_large():
+    n = (1 << 24) + 3
+    u = synth.keys_u64(n, synth.seed_for(3, 8))
+    u[::5] = u[::5] & np.uint64(0xFFFFFFFF00000000)
+    vals = np.arange(n, dtype=np.uint32)
+    sorter = pkg.BucketSorter()
+    ok, ov = sorter.sort_pairs(torch.from_numpy(u.view(np.int64)).cuda(),
+                               torch.from_numpy(vals.view(np.int32)).cuda(), key_type="u64")
+    sorter.sync()
+    wk, wv = oracle.textbook_sort(u, "u64", vals=vals)
+    assert np.array_equal(ok.cpu().numpy().view(np.uint64), wk)
+    assert np.array_equal(ov.cpu().numpy().view(np.uint32), wv)
+    sorter.close()
