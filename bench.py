@@ -59,7 +59,8 @@ KERNEL_FN = {
     "step1_3_sublist_sort": "k_sublist_sort", "step4_sample_chunks": "k_records_sort",
     "step4_sample_merge": "k_merge_pass", "step5_splitters": "k_select_splitters",
     "step6_sample_index": "k_sample_index", "step7_prefix_sum": "k_scan",
-    "step8_relocate": "k_relocate", "step9_pack_units": "k_pack_units",
+    "step8_relocate": "k_relocate", "step7_8_scan_relocate": "k_bucket_relocate",
+    "step9_pack_units": "k_pack_units",
     "step9_bucket_sort": "k_bucket_sort", "step9_single_unit": "k_bucket_sort",
 }
 ALU_KERNELS = ("step1_3_sublist_sort", "step9_bucket_sort", "step9_single_unit")

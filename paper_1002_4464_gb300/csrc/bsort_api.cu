@@ -646,9 +646,11 @@ bsort_status make_plan_with(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t 
         } else {
             uint32_t merges = 0;
             for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
+            const uint32_t s78 = reloc && bucket_relocate_fits(I.m)
+                                     ? 1u                              /*S7-8 fused*/
+                                     : 1u + 1u + (reloc ? 1u : 0u);    /*S7, run index, S8*/
             I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
-                            2 /*S6*/ + 1 /*S7*/ + 1 /*run index*/ + (reloc ? 1 : 0) /*S8*/ +
-                            1 /*units*/ + s9;
+                            2 /*S6*/ + s78 + 1 /*units*/ + s9;
         }
     }
 
@@ -1039,11 +1041,6 @@ bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout,
     uint32_t *srcb = reinterpret_cast<uint32_t *>(ws + P.off_srcb);
     uint32_t *blk = reinterpret_cast<uint32_t *>(ws + P.off_blk);
     uint32_t *units = reinterpret_cast<uint32_t *>(ws + P.off_units);
-    unsigned long long *status = reinterpret_cast<unsigned long long *>(ws + P.off_status);
-    cudaError_t e = cudaMemsetAsync(status, 0, (size_t)P.scan_chunks * 8, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan status)");
-    e = cudaMemsetAsync(ticket, 0, 4, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan ticket)");
     // Steps 1-3
     SEQ(launch_sublist_sort_u64(P.tile_chunk, (int)I.tile_ctas, kin, n, I.m, I.s, tiles, samples,
                                 st),
@@ -1063,9 +1060,8 @@ bsort_status run_sort_u64(bsort_t h, const Plan &P, const void *kin, void *kout,
     uint32_t *jr = reinterpret_cast<uint32_t *>(ws + P.off_jr);
     SEQ(launch_sample_index_seg_u64(tiles, spl, I.t, I.b, I.m, jr, cum, st),
         "step6_sample_index");
-    // Step 7 (also a_ij and the run starts from the cumulative counts)
-    SEQ(launch_scan_cum(cum, I.m, I.t, nullptr, srcb, offsets, P.n_runs, status, ticket, err, st),
-        "step7_prefix_sum");
+    // Step 7 (one scan per bucket row; also the run starts)
+    SEQ(launch_row_scan(cum, I.m, I.t, I.b, nullptr, srcb, offsets, st), "step7_prefix_sum");
     // Step 8
     SEQ(launch_block_index(offsets, P.n_runs, (uint32_t)I.n_padded, blk, st), "step8_run_index");
     SEQ(launch_relocate_u64(tiles, offsets, srcb, blk, P.n_runs, (uint32_t)I.n_padded, reloc, st),
@@ -1149,11 +1145,15 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     uint32_t *offsets = reinterpret_cast<uint32_t *>(ws + P.off_offsets);
     unsigned long long *status = reinterpret_cast<unsigned long long *>(ws + P.off_status);
 
-    // look-back state must start at zero
-    cudaError_t e = cudaMemsetAsync(status, 0, (size_t)P.scan_chunks * 8, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan status)");
-    e = cudaMemsetAsync(ticket, 0, 4, st);
-    if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan ticket)");
+    // look-back state must start at zero (only the stalled-scan test flag
+    // runs the look-back scan here)
+    cudaError_t e = cudaSuccess;
+    if (h->flags & BSORT_FLAG_TEST_STALL_SCAN) {
+        e = cudaMemsetAsync(status, 0, (size_t)P.scan_chunks * 8, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan status)");
+        e = cudaMemsetAsync(ticket, 0, 4, st);
+        if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan ticket)");
+    }
 
     // Steps 1-3
     if (hp) {
@@ -1205,20 +1205,39 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
     uint32_t *cum = reinterpret_cast<uint32_t *>(ws + P.off_cum);
     uint32_t *jr = reinterpret_cast<uint32_t *>(ws + P.off_jr);
     SEQ(launch_sample_index(tiles_k, spl, I.t, I.s, I.b, I.m, jr, cum, st), "step6_sample_index");
-    // Step 7 (also a_ij and the run starts from the cumulative counts)
-    SEQ(launch_scan_cum(cum, I.m, I.t, nullptr, srcb, offsets, P.n_runs, status, ticket, err, st,
-                        (h->flags & BSORT_FLAG_TEST_STALL_SCAN) != 0),
-        "step7_prefix_sum");
-    // a stalled scan leaves inconsistent offsets: Steps 8-9 must not read them
-    if (h->flags & BSORT_FLAG_TEST_STALL_SCAN) return BSORT_OK;
+    // Step 7: one independent scan per bucket row of the cumulative counts.
+    // The run starts are materialised only for the gathering load of Step 9
+    // (the relocation derives them from the cumulative counts).  The
+    // stalled-scan test flag takes the decoupled look-back scan instead,
+    // with its first chunk held back.
+    if (h->flags & BSORT_FLAG_TEST_STALL_SCAN) {
+        SEQ(launch_scan_cum(cum, I.m, I.t, nullptr, srcb, offsets, P.n_runs, status, ticket, err,
+                            st, true),
+            "step7_prefix_sum");
+        // a stalled scan leaves inconsistent offsets: Steps 8-9 must not read them
+        return BSORT_OK;
+    }
     // Step 8: materialised, unless BSORT_FLAG_LOW_MEMORY fuses it into the
-    // load of Step 9, which then gathers every unit from the runs A_ij
+    // load of Step 9, which then gathers every unit from the runs A_ij.  A
+    // materialised relocation of rows that one CTA holds runs together with
+    // Step 7, a CTA per bucket.
     GatherSrc g;
-    SEQ(launch_block_index(offsets, P.n_runs, (uint32_t)I.n_padded, blk, st), "step8_run_index");
-    if (P.relocate) {
-        SEQ(launch_relocate(tiles_k, tiles_v, offsets, srcb, blk, P.n_runs,
-                            (uint32_t)I.n_padded, (int)vb, reloc_k, reloc_v, st),
-            "step8_relocate");
+    if (P.relocate && bucket_relocate_fits(I.m)) {
+        SEQ(launch_bucket_relocate(cum, I.m, I.t, I.b, (uint32_t)I.n_padded, tiles_k, tiles_v,
+                                   (int)vb, offsets, reloc_k, reloc_v, st),
+            "step7_8_scan_relocate");
+    } else {
+        SEQ(launch_row_scan(cum, I.m, I.t, I.b, nullptr, P.relocate ? nullptr : srcb, offsets,
+                            st),
+            "step7_prefix_sum");
+        SEQ(launch_block_index(offsets, P.n_runs, (uint32_t)I.n_padded, blk, st),
+            "step8_run_index");
+        if (P.relocate) {
+            SEQ(launch_relocate(tiles_k, tiles_v, offsets, nullptr, blk, P.n_runs,
+                                (uint32_t)I.n_padded, (int)vb, reloc_k, reloc_v, st, cum, I.m,
+                                I.t),
+                "step8_relocate");
+        }
     }
     // Step 9: buckets packed into units (two tiers: one-CTA units of
     // small_chunk items, cluster units of unit_capacity for larger buckets)

@@ -144,6 +144,22 @@ cudaError_t launch_scan_cum(const uint32_t *cum, uint32_t m, uint32_t t, uint32_
                             unsigned long long *status, uint32_t *ticket, int *err,
                             cudaStream_t st, bool stall_first = false);
 
+// Step 7 from the cumulative counts, one CTA per bucket row and no waits
+// between CTAs: out[j*m + i] = l_ij for the b rows of m sublists (n' <
+// 2^32); counts (a_ij) and srcb (i*t + c_i,j-1) are written when not null.
+cudaError_t launch_row_scan(const uint32_t *cum, uint32_t m, uint32_t t, uint32_t b,
+                            uint32_t *counts, uint32_t *srcb, uint32_t *out, cudaStream_t st);
+
+// Steps 7 and 8 in one kernel, one CTA per bucket (m <= 8192 sublists, m
+// a multiple of 4): offsets[j*m + i] = l_ij (and offsets[m*b] = n_pad) and
+// the relocated keys (values: val_bytes 0, 4 or 8), read from the sorted
+// sublists by the cumulative counts alone.
+bool bucket_relocate_fits(uint32_t m);
+cudaError_t launch_bucket_relocate(const uint32_t *cum, uint32_t m, uint32_t t, uint32_t b,
+                                  uint32_t n_pad, const uint32_t *tiles_k, const void *tiles_v,
+                                  int val_bytes, uint32_t *offsets, uint32_t *reloc_k,
+                                  void *reloc_v, cudaStream_t st);
+
 // Steps 7-8 of plans whose padded size reaches 2^32 (keys-only 32-bit keys,
 // two levels): off64[e] = bucket-major exclusive prefix of a_ij (from the
 // cumulative counts; off64[n_items] = n_pad; chunk_sums / chunk_pre hold one
@@ -179,11 +195,13 @@ constexpr int kRelocPart = 8192;  // sublist items per Step-8 CTA
 // Step 8: fill the relocated array B_1 ... B_b position by position from
 // the runs A_ij (offsets: l in run order with the sentinel offsets[runs] =
 // n_pad; srcb: sorted-sublist position of each run's first item, i*t +
-// c_i(j-1); blk: run index).
+// c_i(j-1), or null with cum, m and t given: then it is derived from the
+// cumulative counts; blk: run index).
 cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const uint32_t *offsets,
                             const uint32_t *srcb, const uint32_t *blk, uint32_t runs,
                             uint32_t n_pad, int val_bytes, uint32_t *reloc_k, void *reloc_v,
-                            cudaStream_t st);
+                            cudaStream_t st, const uint32_t *cum = nullptr, uint32_t m = 0,
+                            uint32_t t = 0);
 
 // Positions per entry of the run index used by Step 9's gathering load.
 constexpr int kBlockItems = 1024;

@@ -283,31 +283,54 @@ k_sample_index_grp(const uint32_t *__restrict__ tiles_k, const uint64_t *__restr
     // Splitter g = (gk, q) is the sample at rank gr = (q mod s + 1)w - 1 of
     // sublist gi = q / s; in (key, position) order sublist i holds
     // upper_bound(gk) items <= g if i < gi (all its positions are lower),
-    // lower_bound(gk) if i > gi, and exactly gr + 1 if i == gi.
-    const uint32_t w = t / s;
+    // lower_bound(gk) if i > gi, and exactly gr + 1 if i == gi.  Both bounds
+    // count the keys below a threshold (gk + 1, resp. gk; all keys when gk
+    // is the largest key and i < gi), found by a branch-free search over the
+    // power-of-two segment; each thread runs two pairs' searches side by side.
+    const uint32_t ls = 31u - (uint32_t)__clz(s);  // s and t are powers of two
+    const uint32_t w = t >> ls;
     const uint32_t pairs = (J1 - J0) * kSub6;
-    for (uint32_t p = tid; p < pairs; p += T) {
-        const uint32_t j = J0 + p / kSub6, ii = p % kSub6;
-        if (ii >= ns || j < s_lo[ii] || j >= s_hi[ii]) continue;
-        const uint64_t g = spl[j];
-        const uint32_t gk = (uint32_t)(g >> 32), q = (uint32_t)g;
-        const uint32_t i = i0 + ii, gi = q / s;
-        uint32_t c;
-        if (i == gi) {
-            c = (q % s + 1) * w;  // gr + 1
-        } else {
-            const bool le = i < gi;  // count keys <= gk, else keys < gk
-            const uint32_t *row = sk + ii * kSegRow;
-            uint32_t lo = 0, hi = seg;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                const uint32_t key = row[mid];
-                if (key < gk || (le && key == gk)) lo = mid + 1;
-                else hi = mid;
+    for (uint32_t p0 = (uint32_t)tid; p0 < pairs; p0 += 2u * T) {
+        uint32_t thr[2], res[2], jj[2], ii2[2];
+        bool act[2], srch[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const uint32_t p = p0 + (uint32_t)u * T;
+            const uint32_t j = J0 + p / kSub6, ii = p % kSub6;
+            jj[u] = j;
+            ii2[u] = ii;
+            act[u] = p < pairs && ii < ns && j >= s_lo[ii] && j < s_hi[ii];
+            srch[u] = false;
+            thr[u] = 0u;
+            res[u] = 0u;
+            if (act[u]) {
+                const uint64_t g = spl[j];
+                const uint32_t gk = (uint32_t)(g >> 32), q = (uint32_t)g;
+                const uint32_t i = i0 + ii, gi = q >> ls;
+                if (i == gi) {
+                    res[u] = ((q & (s - 1u)) + 1u) * w;  // gr + 1
+                } else if (i < gi && gk == 0xFFFFFFFFu) {
+                    res[u] = S + seg;  // every key is <= the largest key
+                } else {
+                    thr[u] = gk + (i < gi ? 1u : 0u);
+                    srch[u] = true;
+                }
             }
-            c = S + lo;
         }
-        cum[(uint64_t)j * m + i] = c;
+        const uint32_t *row0 = sk + ii2[0] * kSegRow;
+        const uint32_t *row1 = sk + (act[1] ? ii2[1] : ii2[0]) * kSegRow;
+        uint32_t b0 = 0, b1 = 0;
+        for (uint32_t hh = seg >> 1; hh > 0; hh >>= 1) {
+            if (row0[b0 + hh - 1] < thr[0]) b0 += hh;
+            if (row1[b1 + hh - 1] < thr[1]) b1 += hh;
+        }
+        b0 += row0[b0] < thr[0] ? 1u : 0u;
+        b1 += row1[b1] < thr[1] ? 1u : 0u;
+        if (srch[0]) res[0] = S + b0;
+        if (srch[1]) res[1] = S + b1;
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+            if (act[u]) cum[(uint64_t)jj[u] * m + i0 + ii2[u]] = res[u];
     }
 }
 
@@ -461,12 +484,178 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
     }
 }
 
+// Step 7 by rows.  With the cumulative counts c_ij of Step 6 the
+// bucket-major exclusive scan splits into independent rows: the items
+// before run A_ij are all items of buckets 0 .. j-1, which number
+// sum_i' c_i',j-1 (the start of bucket j), plus the runs A_i'j of the
+// sublists i' < i, so
+//   l_ij = sum_i' c_i',j-1 + sum_{i' < i} (c_i'j - c_i',j-1).
+// One CTA per bucket j computes row j from rows j and j-1 of the cumulative
+// counts, and no CTA waits for another.  A row of at most T*V sublists is
+// one piece: the bucket start and the prefix of the run sizes come from one
+// block-wide scan of the pair (sum of c_i,j-1, sum of a_ij) packed in 64
+// bits (each half stays below n' < 2^32, so no carry crosses).  Longer rows
+// take the bucket start from a first pass over row j-1 and are scanned in
+// pieces with a running carry.  counts (a_ij) and srcb (i*t + c_i,j-1, the
+// run's first sorted-sublist position) are written when not null.
+template <int T, int V>
+__global__ void __launch_bounds__(T)
+k_row_scan(const uint32_t *__restrict__ cum, uint32_t m, uint32_t t, uint32_t *__restrict__ out,
+           uint32_t *__restrict__ counts, uint32_t *__restrict__ srcb)
+{
+    constexpr int N = T * V;
+    constexpr int W = T / 32;
+    __shared__ uint32_t s_items[N + N / 32];
+    __shared__ unsigned long long s_warp[W];
+    __shared__ unsigned long long s_total;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t j = blockIdx.x;
+    const uint64_t r0 = (uint64_t)j * m;
+    const uint32_t *row = cum + r0;
+    const uint32_t *prev = j ? row - m : nullptr;
+    auto spad = [](int x) { return x + (x >> 5); };
+    // inclusive block scan of one 64-bit value per thread; s_total = sum
+    auto block_scan = [&](unsigned long long v) -> unsigned long long {
+        unsigned long long inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long wv = lane < W ? s_warp[lane] : 0ull;
+            unsigned long long wi = wv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            if (lane < W) s_warp[lane] = wi - wv;
+            if (lane == W - 1) s_total = wi;
+        }
+        __syncthreads();
+        return s_warp[warp] + inc;
+    };
+    const bool pieces = m > (uint32_t)N;
+    if (!pieces && (m & 3u) == 0) {
+        // one piece, rows of whole 16-byte words: thread tid takes items
+        // [tid*V, tid*V + V) straight from global memory as 16-byte words
+        // (all loads in flight before the first use), no staging
+        static_assert(V % 4 == 0, "V must be a multiple of 4");
+        const uint32_t i0 = (uint32_t)tid * V;
+        uint4 c4[V / 4], p4[V / 4];
+#pragma unroll
+        for (int k = 0; k < V / 4; ++k) {
+            const uint32_t i = i0 + 4u * k;
+            c4[k] = make_uint4(0u, 0u, 0u, 0u);
+            p4[k] = make_uint4(0u, 0u, 0u, 0u);
+            if (i < m) {
+                c4[k] = *reinterpret_cast<const uint4 *>(row + i);
+                if (prev != nullptr) p4[k] = *reinterpret_cast<const uint4 *>(prev + i);
+            }
+        }
+        uint32_t x[V];
+        uint32_t sum = 0, ps = 0;
+#pragma unroll
+        for (int k = 0; k < V / 4; ++k) {
+            x[4 * k + 0] = c4[k].x - p4[k].x;
+            x[4 * k + 1] = c4[k].y - p4[k].y;
+            x[4 * k + 2] = c4[k].z - p4[k].z;
+            x[4 * k + 3] = c4[k].w - p4[k].w;
+            ps += p4[k].x + p4[k].y + p4[k].z + p4[k].w;
+        }
+#pragma unroll
+        for (int k = 0; k < V; ++k) sum += x[k];
+        const unsigned long long v = ((unsigned long long)ps << 32) | (unsigned long long)sum;
+        const unsigned long long excl = block_scan(v) - v;
+        uint32_t run = (uint32_t)(s_total >> 32) + (uint32_t)excl;
+#pragma unroll
+        for (int k = 0; k < V / 4; ++k) {
+            const uint32_t i = i0 + 4u * k;
+            if (i >= m) break;
+            uint4 o;
+            o.x = run;
+            o.y = o.x + x[4 * k + 0];
+            o.z = o.y + x[4 * k + 1];
+            o.w = o.z + x[4 * k + 2];
+            run = o.w + x[4 * k + 3];
+            *reinterpret_cast<uint4 *>(out + r0 + i) = o;
+            if (counts != nullptr)
+                *reinterpret_cast<uint4 *>(counts + r0 + i) =
+                    make_uint4(x[4 * k], x[4 * k + 1], x[4 * k + 2], x[4 * k + 3]);
+            if (srcb != nullptr)
+                *reinterpret_cast<uint4 *>(srcb + r0 + i) =
+                    make_uint4(i * t + p4[k].x, (i + 1) * t + p4[k].y, (i + 2) * t + p4[k].z,
+                               (i + 3) * t + p4[k].w);
+        }
+        return;
+    }
+    uint32_t start = 0;
+    if (pieces && prev != nullptr) {
+        uint32_t ps = 0;
+        for (uint32_t i = (uint32_t)tid; i < m; i += T) ps += prev[i];
+        block_scan(ps);
+        start = (uint32_t)s_total;
+        __syncthreads();  // s_warp and s_total are reused below
+    }
+    uint32_t carry = 0;
+    for (uint32_t base = 0; base < m; base += N) {
+        uint32_t ps = 0;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int idx = k * T + tid;
+            const uint32_t i = base + (uint32_t)idx;
+            uint32_t a = 0;
+            if (i < m) {
+                const uint32_t p = prev != nullptr ? prev[i] : 0u;
+                a = row[i] - p;
+                ps += p;
+                if (counts != nullptr) counts[r0 + i] = a;
+                if (srcb != nullptr) srcb[r0 + i] = i * t + p;
+            }
+            s_items[spad(idx)] = a;
+        }
+        __syncthreads();
+        uint32_t x[V];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            x[k] = s_items[spad(tid * V + k)];
+            sum += x[k];
+        }
+        const unsigned long long v =
+            ((unsigned long long)(pieces ? 0u : ps) << 32) | (unsigned long long)sum;
+        const unsigned long long excl = block_scan(v) - v;
+        const unsigned long long tot = s_total;
+        if (!pieces) start = (uint32_t)(tot >> 32);
+        uint32_t run = start + carry + (uint32_t)excl;
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            s_items[spad(tid * V + k)] = run;
+            run += x[k];
+        }
+        carry += (uint32_t)tot;
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            const int idx = k * T + tid;
+            const uint32_t i = base + (uint32_t)idx;
+            if (i < m) out[r0 + i] = s_items[spad(idx)];
+        }
+        __syncthreads();  // s_items, s_warp and s_total are reused by the next piece
+    }
+}
+
 // ============================================================ Step 8
 // Relocation by destination: CTA c fills positions [c*kRelocPart,
 // (c+1)*kRelocPart) of the relocated array, so every CTA moves the same
 // number of items whatever the key distribution.  Position y lies in the
 // run q (offsets[q] <= y < offsets[q+1]) and comes from position srcb[q] +
-// (y - offsets[q]) of the sorted sublists.  Each warp covers kBlockItems
+// (y - offsets[q]) of the sorted sublists (with srcb null, the run start
+// i*t + c_i,j-1 of run q = j*m + i is taken from the cumulative counts).  Each warp covers kBlockItems
 // consecutive positions, its lanes on consecutive positions (coalesced
 // stores).  The runs meeting a warp's block are blk[b] .. blk[b+1] (the run
 // index); when they are few (the usual case) the warp stages them in shared
@@ -481,10 +670,21 @@ k_scan(const uint32_t *__restrict__ in, uint32_t *__restrict__ out, uint32_t n_i
 // the run index).
 constexpr int kRelocRunsCap = 512;  // runs a warp stages in shared memory
 
+// Sorted-sublist position of the first item of run q = j*m + i: srcb[q],
+// or i*t + c_i,j-1 from the cumulative counts when srcb is null.
+__device__ __forceinline__ uint32_t run_first(const uint32_t *__restrict__ srcb,
+                                              const uint32_t *__restrict__ cum, uint32_t m,
+                                              uint32_t t, uint32_t q)
+{
+    if (srcb != nullptr) return srcb[q];
+    return (q % m) * t + (q >= m ? cum[q - m] : 0u);
+}
+
 template <int T, typename KT>
 __global__ void __launch_bounds__(T, 4)
 k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
            const uint32_t *__restrict__ offsets, const uint32_t *__restrict__ srcb,
+           const uint32_t *__restrict__ cum, uint32_t m, uint32_t t,
            const uint32_t *__restrict__ blk, uint32_t runs,
            uint32_t n_pad, int val_bytes, KT *__restrict__ reloc_k,
            void *__restrict__ reloc_v)
@@ -507,7 +707,19 @@ k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
         uint32_t *so = s_off[warp];
         uint32_t *sd = s_src[warp];
         for (uint32_t i = lane; i <= R; i += 32) so[i] = offsets[q0 + i];
-        for (uint32_t i = lane; i < R; i += 32) sd[i] = srcb[q0 + i];
+        if (srcb != nullptr) {
+            for (uint32_t i = lane; i < R; i += 32) sd[i] = srcb[q0 + i];
+        } else {
+            // run q = j*m + i starts at i*t + c_i,j-1 of the sorted sublists
+            const uint32_t step = 32u % m;
+            uint32_t si = (q0 + lane) % m;
+            for (uint32_t i = lane; i < R; i += 32) {
+                const uint32_t q = q0 + i;
+                sd[i] = si * t + (q >= m ? cum[q - m] : 0u);
+                si += step;
+                if (si >= m) si -= m;
+            }
+        }
         __syncwarp();
         // run q0 holds wy; a later run counts if it is non-empty and starts
         // inside the block.  Compact them in order (in place: entry k of
@@ -600,11 +812,11 @@ k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
     }
     uint32_t q = lo;
     uint32_t rs = offsets[q], re = offsets[q + 1];
-    uint32_t base = srcb[q];
+    uint32_t base = run_first(srcb, cum, m, t, q);
     for (; y < yend; y += 32) {
         if (y >= re) {
             run_advance<kBlockItems>(offsets, blk, nblk, runs, y, q, rs, re);
-            base = srcb[q];
+            base = run_first(srcb, cum, m, t, q);
         }
         const uint32_t src = base + (y - rs);
         reloc_k[y] = tiles_k[src];
@@ -612,6 +824,216 @@ k_relocate(const KT *__restrict__ tiles_k, const void *__restrict__ tiles_v,
             static_cast<uint32_t *>(reloc_v)[y] = static_cast<const uint32_t *>(tiles_v)[src];
         else if (val_bytes == 8)
             static_cast<uint64_t *>(reloc_v)[y] = static_cast<const uint64_t *>(tiles_v)[src];
+    }
+}
+
+// Steps 7-8 fused, one CTA per bucket j (rows of at most T*V sublists, m a
+// multiple of 4).  The CTA scans row j of the cumulative counts as
+// k_row_scan does (bucket start B_j = sum_i c_i,j-1, run offsets l_ij,
+// written to `offsets` for Step 9 and for inspection), lists the non-empty
+// runs of the bucket in shared memory (local start, and sorted-sublist start
+// minus local start), and then moves the bucket itself: its warps take
+// blocks of kBlockItems consecutive positions y of the bucket, find the run
+// holding the block's first position by a 32-way search of the list, mark
+// the later run starts of the block in a bitmap and resolve each position's
+// run by a population count, as k_relocate does, with coalesced stores to
+// B_j + y.  Nothing is read back from global memory but the keys (and
+// values) themselves: no run offsets, run starts or run index.
+constexpr int kFuseT = 512, kFuseV = 16;
+constexpr uint32_t kFuseMaxM = (uint32_t)(kFuseT * kFuseV);
+
+template <int T, int V>
+__global__ void __launch_bounds__(T, 2)
+k_bucket_relocate(const uint32_t *__restrict__ cum, uint32_t m, uint32_t t, uint32_t b,
+                  uint32_t n_pad, const uint32_t *__restrict__ tiles_k,
+                  const void *__restrict__ tiles_v, int val_bytes, uint32_t *__restrict__ offsets,
+                  uint32_t *__restrict__ reloc_k, void *__restrict__ reloc_v)
+{
+    constexpr int W = T / 32;
+    constexpr int P = kBlockItems / 32;  // positions per lane in a block
+    static_assert(V % 4 == 0, "V must be a multiple of 4");
+    extern __shared__ uint32_t s_dyn[];
+    uint32_t *s_loc = s_dyn;              // [T*V + 1] local start of non-empty run k
+    uint32_t *s_d = s_dyn + T * V + 1;    // [T*V] its sorted-sublist start - local start
+    __shared__ unsigned long long s_warp[W];
+    __shared__ unsigned long long s_total;
+    __shared__ uint32_t s_bm[W][32];
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const uint32_t j = blockIdx.x;
+    const uint64_t r0 = (uint64_t)j * m;
+    const uint32_t *row = cum + r0;
+    const uint32_t *prev = j ? row - m : nullptr;
+    auto block_scan = [&](unsigned long long v) -> unsigned long long {
+        unsigned long long inc = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_warp[warp] = inc;
+        __syncthreads();
+        if (warp == 0) {
+            const unsigned long long wv = lane < W ? s_warp[lane] : 0ull;
+            unsigned long long wi = wv;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, wi, o);
+                if (lane >= o) wi += y;
+            }
+            if (lane < W) s_warp[lane] = wi - wv;
+            if (lane == W - 1) s_total = wi;
+        }
+        __syncthreads();
+        const unsigned long long r = s_warp[warp] + inc;
+        __syncthreads();  // s_warp is free again (s_total is read before the next scan ends)
+        return r;
+    };
+    // ---- Step 7 for row j: thread tid holds sublists [tid*V, tid*V + V)
+    const uint32_t i0 = (uint32_t)tid * V;
+    uint4 c4[V / 4], p4[V / 4];
+#pragma unroll
+    for (int k = 0; k < V / 4; ++k) {
+        const uint32_t i = i0 + 4u * k;
+        c4[k] = make_uint4(0u, 0u, 0u, 0u);
+        p4[k] = make_uint4(0u, 0u, 0u, 0u);
+        if (i < m) {
+            c4[k] = *reinterpret_cast<const uint4 *>(row + i);
+            if (prev != nullptr) p4[k] = *reinterpret_cast<const uint4 *>(prev + i);
+        }
+    }
+    uint32_t x[V], pv[V];
+    uint32_t sum = 0, ps = 0, nz = 0;
+#pragma unroll
+    for (int k = 0; k < V / 4; ++k) {
+        pv[4 * k + 0] = p4[k].x;
+        pv[4 * k + 1] = p4[k].y;
+        pv[4 * k + 2] = p4[k].z;
+        pv[4 * k + 3] = p4[k].w;
+        x[4 * k + 0] = c4[k].x - p4[k].x;
+        x[4 * k + 1] = c4[k].y - p4[k].y;
+        x[4 * k + 2] = c4[k].z - p4[k].z;
+        x[4 * k + 3] = c4[k].w - p4[k].w;
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        sum += x[k];
+        ps += pv[k];
+        nz += x[k] != 0u ? 1u : 0u;
+    }
+    const unsigned long long v = ((unsigned long long)ps << 32) | (unsigned long long)sum;
+    const unsigned long long excl = block_scan(v) - v;
+    const unsigned long long tot = s_total;
+    const uint32_t Bj = (uint32_t)(tot >> 32);  // bucket start
+    const uint32_t Sj = (uint32_t)tot;          // bucket size
+    const uint32_t kz = (uint32_t)(block_scan(nz) - nz);
+    const uint32_t K = (uint32_t)s_total;       // non-empty runs
+    uint32_t run = (uint32_t)excl, k = kz;
+#pragma unroll
+    for (int q = 0; q < V / 4; ++q) {
+        const uint32_t i = i0 + 4u * q;
+        if (i < m) {
+            uint4 o;
+            o.x = Bj + run;
+            o.y = o.x + x[4 * q + 0];
+            o.z = o.y + x[4 * q + 1];
+            o.w = o.z + x[4 * q + 2];
+            *reinterpret_cast<uint4 *>(offsets + r0 + i) = o;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            if (x[4 * q + e] != 0u) {
+                s_loc[k] = run;
+                s_d[k] = (i + e) * t + pv[4 * q + e] - run;
+                ++k;
+            }
+            run += x[4 * q + e];
+        }
+    }
+    if (tid == 0) {
+        s_loc[K] = Sj;
+        if (j == b - 1) offsets[(uint64_t)b * m] = n_pad;
+    }
+    __syncthreads();
+    // ---- Step 8 for bucket j
+    const uint32_t nblk = (Sj + kBlockItems - 1) / kBlockItems;
+    uint32_t *bm = s_bm[warp];
+    for (uint32_t bi = (uint32_t)warp; bi < nblk; bi += W) {
+        const uint32_t y0 = bi * (uint32_t)kBlockItems;
+        const uint32_t yend = min(y0 + (uint32_t)kBlockItems, Sj);
+        // last run k0 with s_loc[k0] <= y0 (s_loc[0] = 0)
+        uint32_t lo = 0, hi = K;
+        while (hi - lo > 1) {
+            const uint32_t step = (hi - lo + 31) >> 5;
+            const uint32_t idx = lo + (uint32_t)lane * step;
+            const bool le = idx < hi && s_loc[idx] <= y0;
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, le);  // lane 0 always
+            lo += (uint32_t)(31 - __clz((int)bal)) * step;
+            hi = min(hi, lo + step);
+        }
+        const uint32_t k0 = lo;
+        bm[lane] = 0u;
+        __syncwarp();
+        // runs after k0 that start inside the block (starts increase with k)
+        for (uint32_t kb = k0 + 1;; kb += 32) {
+            const uint32_t kk = kb + (uint32_t)lane;
+            const uint32_t st = kk < K ? s_loc[kk] : 0xFFFFFFFFu;
+            const bool in = st < yend;
+            if (in) atomicOr(&bm[(st - y0) >> 5], 1u << ((st - y0) & 31u));
+            if (__ballot_sync(0xFFFFFFFFu, in) != 0xFFFFFFFFu) break;
+        }
+        __syncwarp();
+        const uint32_t word = bm[lane];
+        const uint32_t cnt = (uint32_t)__popc(word);
+        uint32_t pre = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t yv = __shfl_up_sync(0xFFFFFFFFu, pre, o);
+            if (lane >= o) pre += yv;
+        }
+        pre = pre - cnt + k0;
+        const uint32_t upto = lane == 31 ? 0xFFFFFFFFu : (2u << lane) - 1u;
+        constexpr int G = 16;
+#pragma unroll 1
+        for (int k1 = 0; k1 < P; k1 += G) {
+            uint32_t src[G];
+#pragma unroll
+            for (int e = 0; e < G; ++e) {
+                const uint32_t wk = __shfl_sync(0xFFFFFFFFu, word, k1 + e);
+                const uint32_t pk = __shfl_sync(0xFFFFFFFFu, pre, k1 + e);
+                const uint32_t y = y0 + (uint32_t)lane + 32u * (uint32_t)(k1 + e);
+                src[e] = s_d[pk + (uint32_t)__popc(wk & upto)] + y;
+            }
+            uint32_t kv[G];
+#pragma unroll
+            for (int e = 0; e < G; ++e) {
+                const uint32_t y = y0 + (uint32_t)lane + 32u * (uint32_t)(k1 + e);
+                kv[e] = y < yend ? tiles_k[src[e]] : 0u;
+            }
+#pragma unroll
+            for (int e = 0; e < G; ++e) {
+                const uint32_t y = y0 + (uint32_t)lane + 32u * (uint32_t)(k1 + e);
+                if (y < yend) reloc_k[Bj + y] = kv[e];
+            }
+            if (val_bytes == 4) {
+                const uint32_t *tv = static_cast<const uint32_t *>(tiles_v);
+                uint32_t *rv = static_cast<uint32_t *>(reloc_v);
+#pragma unroll
+                for (int e = 0; e < G; ++e) {
+                    const uint32_t y = y0 + (uint32_t)lane + 32u * (uint32_t)(k1 + e);
+                    if (y < yend) rv[Bj + y] = tv[src[e]];
+                }
+            } else if (val_bytes == 8) {
+                const uint64_t *tv = static_cast<const uint64_t *>(tiles_v);
+                uint64_t *rv = static_cast<uint64_t *>(reloc_v);
+#pragma unroll
+                for (int e = 0; e < G; ++e) {
+                    const uint32_t y = y0 + (uint32_t)lane + 32u * (uint32_t)(k1 + e);
+                    if (y < yend) rv[Bj + y] = tv[src[e]];
+                }
+            }
+        }
+        __syncwarp();  // the bitmap is rewritten by the warp's next block
     }
 }
 
@@ -1050,6 +1472,7 @@ cudaError_t init_misc_kernels()
     BSORT_TRY(set_smem(k_records_sort<1024, 16>, smem_bytes_for_cap(kRecordChunk, true)));
     BSORT_TRY(set_smem(k_pack_units<1024>, 16 * (kMaxBuckets + 1)));
     BSORT_TRY(set_smem(k_units_each<1024>, 4 * (kMaxBucketsTiers + 1)));
+    BSORT_TRY(set_smem(k_bucket_relocate<kFuseT, kFuseV>, (int)(8 * kFuseMaxM + 4)));
     return cudaSuccess;
 }
 
@@ -1085,6 +1508,7 @@ cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *spl, ui
                                 uint32_t s, uint32_t b, uint32_t m, uint32_t *jr, uint32_t *cum,
                                 cudaStream_t st)
 {
+    if (s == 0 || (s & (s - 1)) != 0 || (t & (t - 1)) != 0) return cudaErrorInvalidValue;
     const uint32_t seg = t < (uint32_t)kSegItems ? t : (uint32_t)kSegItems;
     const uint32_t nseg = t / seg;
     const uint32_t ns = m * nseg;
@@ -1122,12 +1546,37 @@ cudaError_t launch_scan_cum(const uint32_t *cum, uint32_t m, uint32_t t, uint32_
 cudaError_t launch_relocate(const uint32_t *tiles_k, const void *tiles_v, const uint32_t *offsets,
                             const uint32_t *srcb, const uint32_t *blk, uint32_t runs,
                             uint32_t n_pad, int val_bytes, uint32_t *reloc_k, void *reloc_v,
-                            cudaStream_t st)
+                            cudaStream_t st, const uint32_t *cum, uint32_t m, uint32_t t)
 {
     constexpr int T = (kRelocPart / kBlockItems) * 32;
     const uint32_t grid = (n_pad + kRelocPart - 1) / kRelocPart;
-    k_relocate<T, uint32_t><<<grid, T, 0, st>>>(tiles_k, tiles_v, offsets, srcb, blk, runs,
-                                                n_pad, val_bytes, reloc_k, reloc_v);
+    if (srcb == nullptr && (cum == nullptr || m == 0)) return cudaErrorInvalidValue;
+    k_relocate<T, uint32_t><<<grid, T, 0, st>>>(tiles_k, tiles_v, offsets, srcb, cum, m, t, blk,
+                                                runs, n_pad, val_bytes, reloc_k, reloc_v);
+    return cudaGetLastError();
+}
+
+bool bucket_relocate_fits(uint32_t m) { return m > 0 && m <= kFuseMaxM && (m & 3u) == 0; }
+
+cudaError_t launch_bucket_relocate(const uint32_t *cum, uint32_t m, uint32_t t, uint32_t b,
+                                  uint32_t n_pad, const uint32_t *tiles_k, const void *tiles_v,
+                                  int val_bytes, uint32_t *offsets, uint32_t *reloc_k,
+                                  void *reloc_v, cudaStream_t st)
+{
+    if (!bucket_relocate_fits(m) || b == 0) return cudaErrorInvalidValue;
+    k_bucket_relocate<kFuseT, kFuseV><<<b, kFuseT, 8 * kFuseMaxM + 4, st>>>(
+        cum, m, t, b, n_pad, tiles_k, tiles_v, val_bytes, offsets, reloc_k, reloc_v);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_row_scan(const uint32_t *cum, uint32_t m, uint32_t t, uint32_t b,
+                            uint32_t *counts, uint32_t *srcb, uint32_t *out, cudaStream_t st)
+{
+    if (m == 0 || b == 0) return cudaSuccess;
+    if (m <= 2048u)
+        k_row_scan<128, 16><<<b, 128, 0, st>>>(cum, m, t, out, counts, srcb);
+    else
+        k_row_scan<512, 16><<<b, 512, 0, st>>>(cum, m, t, out, counts, srcb);
     return cudaGetLastError();
 }
 
@@ -1137,7 +1586,8 @@ cudaError_t launch_relocate_u64(const uint64_t *tiles_k, const uint32_t *offsets
 {
     constexpr int T = (kRelocPart / kBlockItems) * 32;
     const uint32_t grid = (n_pad + kRelocPart - 1) / kRelocPart;
-    k_relocate<T, uint64_t><<<grid, T, 0, st>>>(tiles_k, nullptr, offsets, srcb, blk, runs,
+    k_relocate<T, uint64_t><<<grid, T, 0, st>>>(tiles_k, nullptr, offsets, srcb, nullptr, 1u, 0u,
+                                                blk, runs,
                                                 n_pad, 0, reloc_k, nullptr);
     return cudaGetLastError();
 }
