@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(BUILD, "libbsort.so")
-SOURCES = ["bsort_sort_keys_radix.cu", "bsort_sort_keys.cu", "bsort_sort_pairs.cu",
+SOURCES = ["bsort_sort_keys_radix.cu", "bsort_sort_keys.cu", "bsort_sort_pairs.cu", "bsort_records.cu",
            "bsort_kernels.cu", "bsort_batch.cu",
            "bsort_u64.cu", "bsort_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

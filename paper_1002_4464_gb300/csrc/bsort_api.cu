@@ -66,7 +66,8 @@ struct Plan {
     // workspace offsets (bytes)
     uint64_t off_hdr, off_tiles_k, off_tiles_v, off_reloc_k, off_reloc_v, off_samples,
         off_rec_a, off_rec_b, off_spl, off_counts, off_offsets, off_status,
-        off_units, off_units2, off_srcb, off_blk, off_cum, off_jr, total;
+        off_units, off_units2, off_srcb, off_blk, off_cum, off_jr, off_rs, total;
+    bool rec_radix;  // Steps 4-5 by the radix sort of the records (else chunks + merges)
     bool relocate;  // materialise Step 8 (else fused into Step 9's load)
     bool radix;     // 32768-key chunks of 32-bit keys sorted by digits
     // two-level plans (n' >= 2^32): 64-bit bucket offsets, bucket starts,
@@ -646,11 +647,15 @@ bsort_status make_plan_with(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t 
         } else {
             uint32_t merges = 0;
             for (uint32_t L = kRecordChunk; L < P->n_rec_pad; L <<= 1) ++merges;
+            P->rec_radix = P->n_rec_pad > (uint32_t)kRecordChunk &&
+                           records_radix_fits(P->n_rec, I.b);
+            const uint32_t s45 = P->rec_radix
+                                     ? 5u  /*histogram, four digit passes*/
+                                     : 1u + merges + (merges ? 1u : 0u);  /*chunks, merges, S5*/
             const uint32_t s78 = reloc && bucket_relocate_fits(I.m)
                                      ? 1u                              /*S7-8 fused*/
                                      : 1u + 1u + (reloc ? 1u : 0u);    /*S7, run index, S8*/
-            I.num_kernels = 1 /*S2-3*/ + 1 /*S4 chunks*/ + merges + (merges ? 1 : 0) /*S5*/ +
-                            2 /*S6*/ + s78 + 1 /*units*/ + s9;
+            I.num_kernels = 1 /*S2-3*/ + s45 + 2 /*S6*/ + s78 + 1 /*units*/ + s9;
         }
     }
 
@@ -687,6 +692,7 @@ bsort_status make_plan_with(bsort_t h, bsort_key_type kt, uint32_t vb, uint64_t 
         // Step 6: cumulative counts and segment ranges
         P->off_cum = take((uint64_t)P->n_runs * 4);
         P->off_jr = take(sample_index_scratch_words(I.t, I.m, P->wide ? 4096u : 1024u) * 4);
+        P->off_rs = take(P->rec_radix ? records_radix_scratch_bytes(P->n_rec) : 0);
     }
     P->total = o;
     I.workspace_bytes = o;
@@ -752,6 +758,10 @@ bsort_status prepare(bsort_t h)
         e = init_kernels();
         if (e != cudaSuccess) return cuda_fail(h, e, "kernel attributes");
         h->kernels_ready = true;
+    }
+    if (h->num_sms == 0) {
+        e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+        if (e != cudaSuccess) return cuda_fail(h, e, "multiprocessor count");
     }
     if ((h->flags & BSORT_FLAG_TIMING) && !h->events_made) {
         for (int r = 0; r < kRing; ++r)
@@ -1184,12 +1194,26 @@ bsort_status run_sort(bsort_t h, bsort_key_type kt, const void *kin, const void 
                                                is_f32, I.s, tiles_k, samples, st, 0, P.radix),
             "step1_3_sublist_sort");
     }
-    // Steps 4-5
+    // Steps 4-5: the records by digits (large sample sets), or in chunks
+    // then merged
     const bool one_chunk = P.n_rec_pad == (uint32_t)kRecordChunk;
-    SEQ(launch_records_chunk_sort(samples, rec_a, P.n_rec, P.n_rec_pad, one_chunk ? spl : nullptr,
-                                  I.s, I.b, st),
-        "step4_sample_chunks");
-    if (!one_chunk) {
+    if (P.rec_radix) {
+        void *rs = ws + P.off_rs;
+        SEQ(launch_records_hist(samples, P.n_rec, rs, h->num_sms, st), "step4_sample_hist");
+        SEQ(launch_records_pass(0, samples, rec_a, P.n_rec, I.b, nullptr, rs, err, st),
+            "step4_sample_radix");
+        SEQ(launch_records_pass(1, rec_a, rec_b, P.n_rec, I.b, nullptr, rs, err, st),
+            "step4_sample_radix");
+        SEQ(launch_records_pass(2, rec_b, rec_a, P.n_rec, I.b, nullptr, rs, err, st),
+            "step4_sample_radix");
+        SEQ(launch_records_pass(3, rec_a, nullptr, P.n_rec, I.b, spl, rs, err, st),
+            "step4_5_radix_splitters");
+    } else {
+        SEQ(launch_records_chunk_sort(samples, rec_a, P.n_rec, P.n_rec_pad,
+                                      one_chunk ? spl : nullptr, I.s, I.b, st),
+            "step4_sample_chunks");
+    }
+    if (!P.rec_radix && !one_chunk) {
         uint64_t *src = rec_a, *dst = rec_b;
         for (uint32_t L = kRecordChunk; L < P.n_rec_pad; L <<= 1) {
             SEQ(launch_merge_pass(src, dst, P.n_rec_pad, L, st), "step4_sample_merge");

@@ -150,6 +150,20 @@ cudaError_t launch_scan_cum(const uint32_t *cum, uint32_t m, uint32_t t, uint32_
 cudaError_t launch_row_scan(const uint32_t *cum, uint32_t m, uint32_t t, uint32_t b,
                             uint32_t *counts, uint32_t *srcb, uint32_t *out, cudaStream_t st);
 
+// Steps 4-5 by a radix sort of the records (bsort_records.cu), for
+// records_radix_fits(m*s, b): launch_records_hist (zeroes the scratch of
+// records_radix_scratch_bytes, then the four digit histograms), then
+// launch_records_pass for p = 0 .. 3: samples -> rec_a -> rec_b -> rec_a,
+// and the last pass (out null) writes the b splitters to spl.
+bool records_radix_fits(uint32_t n_rec, uint32_t b);
+uint64_t records_radix_scratch_bytes(uint32_t n_rec);
+cudaError_t init_records_kernels();
+cudaError_t launch_records_hist(const uint64_t *samples, uint32_t n_rec, void *scratch, int sms,
+                                cudaStream_t st);
+cudaError_t launch_records_pass(int p, const uint64_t *in, uint64_t *out, uint32_t n_rec,
+                                uint32_t b, uint64_t *spl, void *scratch, int *err,
+                                cudaStream_t st);
+
 // Steps 7 and 8 in one kernel, one CTA per bucket (m <= 8192 sublists, m
 // a multiple of 4): offsets[j*m + i] = l_ij (and offsets[m*b] = n_pad) and
 // the relocated keys (values: val_bytes 0, 4 or 8), read from the sorted

@@ -234,12 +234,13 @@ __global__ void k_seg_ranges(const uint32_t *__restrict__ tiles_k, const uint64_
     jr[idx] = r;
 }
 
-template <int T>
-__global__ void __launch_bounds__(T)
+template <int T, int SEG>  // SEG: the segment length at compile time (0: seg)
+__global__ void __launch_bounds__(T, 5)
 k_sample_index_grp(const uint32_t *__restrict__ tiles_k, const uint64_t *__restrict__ spl,
-                   uint32_t t, uint32_t s, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg,
+                   uint32_t t, uint32_t s, uint32_t b, uint32_t m, uint32_t nseg, uint32_t seg_rt,
                    const uint32_t *__restrict__ jr, uint32_t *__restrict__ cum)
 {
+    const uint32_t seg = SEG ? (uint32_t)SEG : seg_rt;
     __shared__ __align__(16) uint32_t sk[kSub6 * kSegRow];
     __shared__ uint32_t s_lo[kSub6], s_hi[kSub6];
     const uint32_t i0 = (blockIdx.x / nseg) * kSub6, k = blockIdx.x % nseg;
@@ -320,6 +321,7 @@ k_sample_index_grp(const uint32_t *__restrict__ tiles_k, const uint64_t *__restr
         const uint32_t *row0 = sk + ii2[0] * kSegRow;
         const uint32_t *row1 = sk + (act[1] ? ii2[1] : ii2[0]) * kSegRow;
         uint32_t b0 = 0, b1 = 0;
+#pragma unroll
         for (uint32_t hh = seg >> 1; hh > 0; hh >>= 1) {
             if (row0[b0 + hh - 1] < thr[0]) b0 += hh;
             if (row1[b1 + hh - 1] < thr[1]) b1 += hh;
@@ -1516,8 +1518,12 @@ cudaError_t launch_sample_index(const uint32_t *tiles_k, const uint64_t *spl, ui
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const uint32_t groups = (m + kSub6 - 1) / kSub6;
-    k_sample_index_grp<256><<<groups * nseg, 256, 0, st>>>(tiles_k, spl, t, s, b, m, nseg, seg,
-                                                          jr, cum);
+    if (seg == (uint32_t)kSegItems)
+        k_sample_index_grp<256, kSegItems><<<groups * nseg, 256, 0, st>>>(tiles_k, spl, t, s, b,
+                                                                         m, nseg, seg, jr, cum);
+    else
+        k_sample_index_grp<256, 0><<<groups * nseg, 256, 0, st>>>(tiles_k, spl, t, s, b, m, nseg,
+                                                                 seg, jr, cum);
     return cudaGetLastError();
 }
 
@@ -1731,6 +1737,7 @@ cudaError_t launch_u64_final(const uint64_t *k64, const void *vals, int val_byte
 cudaError_t init_kernels()
 {
     cudaError_t e = init_misc_kernels();
+    if (e == cudaSuccess) e = init_records_kernels();
     if (e == cudaSuccess) e = init_sort_keys_kernels();
     if (e == cudaSuccess) e = init_sort_pairs_kernels();
     if (e == cudaSuccess) e = init_batch_kernels();
