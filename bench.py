@@ -987,6 +987,10 @@ def run_served(args, pkg, synth, dev, rank, capacity_only=False):
     torch.cuda.empty_cache()  # device memory the earlier sections left cached
     capacity = _serve_capacity(args, pkg, dev, job, ring, maxn, ncap, cap_keys)
     capacity["fresh_process"] = _serve_capacity_subprocess(args) if rank == 0 else None
+    # the same measurement once more in this process, after the fresh one
+    again = _serve_capacity(args, pkg, dev, job, ring, maxn, ncap, cap_keys)
+    capacity["again_in_process"] = {k: again[k] for k in ("served_gkeys_s",
+                                                           "one_at_a_time_gkeys_s", "speedup")}
 
     def pct(x, q):
         return float(np.percentile(x, q))
