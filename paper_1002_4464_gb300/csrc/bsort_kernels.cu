@@ -280,59 +280,60 @@ k_sample_index_grp(const uint32_t *__restrict__ tiles_k, const uint64_t *__restr
         }
     }
     if (J0 >= J1) return;
-    // pair p = (j - J0) * kSub6 + ii: lanes 8c .. 8c+7 hold one splitter.
+    // Thread (c, ii) = (tid / 8, tid mod 8) takes sublist i0 + ii and the
+    // c-th of T/8 consecutive chunks of the splitters [J0, J1), in order, so
+    // that at every step the 8 threads of a chunk write the 8 counts of one
+    // splitter (bucket-major cum[j*m + i]) as one 32-byte sector.
     // Splitter g = (gk, q) is the sample at rank gr = (q mod s + 1)w - 1 of
     // sublist gi = q / s; in (key, position) order sublist i holds
     // upper_bound(gk) items <= g if i < gi (all its positions are lower),
     // lower_bound(gk) if i > gi, and exactly gr + 1 if i == gi.  Both bounds
     // count the keys below a threshold (gk + 1, resp. gk; all keys when gk
-    // is the largest key and i < gi), found by a branch-free search over the
-    // power-of-two segment; each thread runs two pairs' searches side by side.
+    // is the largest key and i < gi).  For one sublist the thresholds do not
+    // decrease with j (splitters ascend in (gk, q), and gi with q), so the
+    // previous count bounds the next from below: the next search covers the
+    // 16 keys from there when the count lies among them (branch-free, five
+    // probes), else the whole power-of-two segment.
     const uint32_t ls = 31u - (uint32_t)__clz(s);  // s and t are powers of two
     const uint32_t w = t >> ls;
-    const uint32_t pairs = (J1 - J0) * kSub6;
-    for (uint32_t p0 = (uint32_t)tid; p0 < pairs; p0 += 2u * T) {
-        uint32_t thr[2], res[2], jj[2], ii2[2];
-        bool act[2], srch[2];
+    constexpr uint32_t kChunks = (uint32_t)T / kSub6;
+    const uint32_t ii = (uint32_t)tid % kSub6, c = (uint32_t)tid / kSub6;
+    if (ii >= ns) return;  // (no barrier follows)
+    const uint32_t per = (J1 - J0 + kChunks - 1) / kChunks;
+    const uint32_t ja = max(J0 + c * per, s_lo[ii]);
+    const uint32_t jb = min(min(J0 + (c + 1) * per, J1), s_hi[ii]);
+    const uint32_t i = i0 + ii;
+    const uint32_t *row = sk + ii * kSegRow;
+    uint32_t lb = 0;  // keys of the segment below the previous threshold
+    for (uint32_t j = ja; j < jb; ++j) {
+        const uint64_t g = spl[j];
+        const uint32_t gk = (uint32_t)(g >> 32), q = (uint32_t)g;
+        const uint32_t gi = q >> ls;
+        uint32_t res;
+        if (i == gi) {
+            res = ((q & (s - 1u)) + 1u) * w;  // gr + 1
+        } else if (i < gi && gk == 0xFFFFFFFFu) {
+            lb = seg;
+            res = S + seg;  // every key is <= the largest key
+        } else {
+            const uint32_t thr = gk + (i < gi ? 1u : 0u);
+            uint32_t bpos;
+            if (lb + 16u <= seg && row[lb + 15u] >= thr) {
+                bpos = lb;
 #pragma unroll
-        for (int u = 0; u < 2; ++u) {
-            const uint32_t p = p0 + (uint32_t)u * T;
-            const uint32_t j = J0 + p / kSub6, ii = p % kSub6;
-            jj[u] = j;
-            ii2[u] = ii;
-            act[u] = p < pairs && ii < ns && j >= s_lo[ii] && j < s_hi[ii];
-            srch[u] = false;
-            thr[u] = 0u;
-            res[u] = 0u;
-            if (act[u]) {
-                const uint64_t g = spl[j];
-                const uint32_t gk = (uint32_t)(g >> 32), q = (uint32_t)g;
-                const uint32_t i = i0 + ii, gi = q >> ls;
-                if (i == gi) {
-                    res[u] = ((q & (s - 1u)) + 1u) * w;  // gr + 1
-                } else if (i < gi && gk == 0xFFFFFFFFu) {
-                    res[u] = S + seg;  // every key is <= the largest key
-                } else {
-                    thr[u] = gk + (i < gi ? 1u : 0u);
-                    srch[u] = true;
-                }
+                for (uint32_t hh = 8; hh > 0; hh >>= 1)
+                    if (row[bpos + hh - 1] < thr) bpos += hh;
+            } else {
+                bpos = 0;
+#pragma unroll
+                for (uint32_t hh = seg >> 1; hh > 0; hh >>= 1)
+                    if (row[bpos + hh - 1] < thr) bpos += hh;
+                bpos += row[bpos] < thr ? 1u : 0u;
             }
+            lb = bpos;
+            res = S + bpos;
         }
-        const uint32_t *row0 = sk + ii2[0] * kSegRow;
-        const uint32_t *row1 = sk + (act[1] ? ii2[1] : ii2[0]) * kSegRow;
-        uint32_t b0 = 0, b1 = 0;
-#pragma unroll
-        for (uint32_t hh = seg >> 1; hh > 0; hh >>= 1) {
-            if (row0[b0 + hh - 1] < thr[0]) b0 += hh;
-            if (row1[b1 + hh - 1] < thr[1]) b1 += hh;
-        }
-        b0 += row0[b0] < thr[0] ? 1u : 0u;
-        b1 += row1[b1] < thr[1] ? 1u : 0u;
-        if (srch[0]) res[0] = S + b0;
-        if (srch[1]) res[1] = S + b1;
-#pragma unroll
-        for (int u = 0; u < 2; ++u)
-            if (act[u]) cum[(uint64_t)jj[u] * m + i0 + ii2[u]] = res[u];
+        cum[(uint64_t)j * m + i] = res;
     }
 }
 
