@@ -1,6 +1,8 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle,
 element by element and bit-exactly (sorting is integer work: the bar is
 bit-exact for keys, values, intermediates and indices)."""
+import os
+
 import numpy as np
 import pytest
 
@@ -556,11 +558,13 @@ def _gpu_sort_u64(sorter, keys):
     (123457, 8192, 128, 0),          # ragged tail
     (300001, 32768, 512, 700),       # 2-CTA cluster sublists, b > s
     (500000, 131072, 2048, 1500),    # 8-CTA cluster sublists, b < s
+    ((1 << 24) + 3, 65536, 4096, 1160),  # 4-CTA sublists, two-tier Step 9 (the 2^28 plan's shape)
 ])
 @pytest.mark.parametrize("kind", ["uniform", "dup", "zero", "low"])
 def test_u64_intermediates(n, t, s, b, kind):
     keys = _keys_u64(kind, n, synth.seed_for(5, 1, n % 1000))
-    want = oracle.paper_sort(keys, t, s, "u64", b=b)
+    want = oracle.paper_sort(keys, t, s, "u64", b=b,
+                             threads=min(8, os.cpu_count() or 1) if n > (1 << 22) else 1)
     sorter = pkg.BucketSorter(tile=t, samples=s, buckets=b)
     p = sorter.plan(n, "u64")
     assert (p.t, p.s, p.b) == (t, s, b or s)
@@ -589,6 +593,23 @@ def test_u64_full_size_2e27():
     d_out = sorter.sort_keys(d_in, key_type="u64")
     sorter.sync()
     # signed view: flip the top bit so that torch's int64 order is uint64 order
+    flip = torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
+    want = torch.sort(d_in ^ flip).values ^ flip
+    assert torch.equal(d_out, want)
+    sorter.close()
+
+
+def test_u64_full_size_2e28():
+    """2^28 64-bit keys (2 GiB) with the planner's plan (t = 65536, two-tier
+    Step 9) against the library sort."""
+    n = 1 << 28
+    keys = synth.keys_u64(n, synth.seed_for(5, 4))
+    sorter = pkg.BucketSorter()
+    p = sorter.plan(n, "u64")
+    assert p.unit_small == 16384
+    d_in = torch.from_numpy(keys.view(np.int64)).cuda()
+    d_out = sorter.sort_keys(d_in, key_type="u64")
+    sorter.sync()
     flip = torch.tensor(-(1 << 63), dtype=torch.int64, device="cuda")
     want = torch.sort(d_in ^ flip).values ^ flip
     assert torch.equal(d_out, want)
