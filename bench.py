@@ -993,7 +993,17 @@ def run_served(args, pkg, synth, dev, rank, capacity_only=False):
                                                            "one_at_a_time_gkeys_s", "speedup")}
 
     def pct(x, q):
-        return float(np.percentile(x, q))
+        return float(np.percentile(x, q)) if len(x) else None
+
+    # the tail by job kind: 64-bit keys or not, and size class (log2 n)
+    by_kind = {}
+    for w in (False, True):
+        for lo, hi in ((10, 17), (17, 20), (20, 22), (22, 25)):
+            sel = (wide == w) & (sizes >= (1 << lo)) & (sizes < (1 << hi))
+            if sel.any():
+                by_kind["%s_2^%d-2^%d" % ("u64" if w else "u32", lo, hi)] = {
+                    "jobs": int(sel.sum()), "served_p99_ms": pct(lat[sel], 99),
+                    "one_at_a_time_p99_ms": pct(lat1[sel], 99)}
 
     return {"workload": "Poisson arrivals %.0f/s for %.0f s, %d jobs, 50/50 uint32/uint64, "
                         "sizes log-uniform in [2^10, 2^24], 50/50 uniform/Zipf(1.1), pinned host "
@@ -1007,7 +1017,7 @@ def run_served(args, pkg, synth, dev, rank, capacity_only=False):
             "one_at_a_time": {"value": keys_total / span1 / 1e9, "unit": UNIT,
                               "p50_ms": pct(lat1, 50), "p99_ms": pct(lat1, 99),
                               "mean_ms": float(lat1.mean()), "jobs_per_s": njobs / span1},
-            "capacity": capacity,
+            "capacity": capacity, "p99_by_kind": by_kind,
             "latency": "sorted keys in host memory minus scheduled arrival"}
 
 
