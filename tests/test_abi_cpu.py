@@ -370,3 +370,19 @@ def test_plan_two_level():
     assert p.levels == 2 and p.b == -(-p.n_padded // (1 << 16))
     assert pkg.bsort_plan(t, pkg.BSORT_U32, 4, 1 << 22).levels == 1
     pkg.bsort_destroy(t)
+
+
+def test_plan_kernel_counts():
+    """Launches per sort as the plan reports them: Steps 1-3 (1), Steps 4-5
+    by the record radix sort (histogram + 4 digit passes) once the sample
+    set spans several chunks, else one chunk sort, Step 6 (2), Steps 7-8
+    fused when m is a multiple of 4 (1; else row scan, run index and
+    relocation, 3), the unit lists (1) and Step 9 (1, or 2 with two tiers)."""
+    h = _handle()
+    cases = [(1 << 28, 1 + 5 + 2 + 1 + 1 + 2),       # m = 8192, two tiers
+             ((1 << 24) + 77, 1 + 5 + 2 + 3 + 1 + 1),  # m = 513: separate Steps 7 and 8
+             (1 << 20, 1 + 1 + 2 + 1 + 1 + 1)]       # one chunk of sample records
+    for n, want in cases:
+        p = pkg.bsort_plan(h, pkg.BSORT_U32, 0, n)
+        assert p.num_kernels == want, (n, p.num_kernels, want)
+    pkg.bsort_destroy(h)
