@@ -102,9 +102,13 @@ typedef enum {
                                       are issued as usual */
 #define BSORT_FLAG_TEST_STALL_SCAN 0x10u /* test of the bounded device
                                       waits, for 32-bit keys that need
-                                      sampling: the first chunk of Step 7's
-                                      look-back scan never publishes its
-                                      prefix, so the waits of later chunks
+                                      sampling: Step 7 runs as the
+                                      decoupled look-back scan (the form
+                                      batches use; sorts otherwise scan
+                                      each bucket row on its own, with no
+                                      waits) and its first chunk never
+                                      publishes its prefix, so the waits of
+                                      later chunks
                                       give up after a few thousand polls; the
                                       call then stops after Step 7 (the
                                       offsets are wrong, so Steps 8-9 are not
