@@ -1,6 +1,7 @@
 // bsort_api.cu -- host runtime behind include/bsort.h: the planner (Step 1
 // parameters and the Step-9 unit), the workspace layout, the launch sequence
 // of Algorithm 1 (Dehne & Zaboli, Section 4) and the error word.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -1653,16 +1654,20 @@ bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout
             h->stage_pending = false;
         }
         if (bytes > h->stage_bytes) {
+            // grown geometrically: freeing pinned memory waits for the device,
+            // and pinning is slow, so a stream of growing batches (the request
+            // loop) must not pay them at every new maximum
+            const uint64_t grow = std::max<uint64_t>({bytes, 2 * h->stage_bytes, 1ull << 20});
             if (h->stage) cudaFreeHost(h->stage);
             h->stage = nullptr;
             h->stage_bytes = 0;
-            e = cudaHostAlloc(&h->stage, bytes, cudaHostAllocDefault);
+            e = cudaHostAlloc(&h->stage, grow, cudaHostAllocDefault);
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 return fail(h, BSORT_ENOMEM, "pinned staging of %llu bytes: %s",
-                            (unsigned long long)bytes, cudaGetErrorString(e));
+                            (unsigned long long)grow, cudaGetErrorString(e));
             }
-            h->stage_bytes = bytes;
+            h->stage_bytes = grow;
         }
         if (!h->stage_ev) {
             e = cudaEventCreateWithFlags(&h->stage_ev, cudaEventDisableTiming);
@@ -1897,6 +1902,7 @@ struct bsort_server {
     std::vector<Req *> staged;   // lane A: keys copied in (or on their way)
     std::vector<cudaEvent_t> ev_pool;
     std::vector<int *> err_pool;
+    std::vector<int *> err_blocks;  // pinned blocks the err_pool words come from
     // statistics
     uint64_t used = 0, peak = 0, batches = 0, done_count = 0, max_batch = 0;
     uint64_t large_jobs = 0, busy_ns = 0;
@@ -1971,16 +1977,23 @@ cudaEvent_t take_event(bsort_server *S)
     return e;
 }
 
+// A pinned word for a batch's copy of its lane's error word.  Words come
+// in blocks of kErrBlock from one pinned allocation each (pinning host
+// memory is slow, and the request loop must not stall on it per batch).
+constexpr int kErrBlock = 1024;
+
 int *take_err(bsort_server *S)
 {
-    if (!S->err_pool.empty()) {
-        int *p = S->err_pool.back();
-        S->err_pool.pop_back();
-        return p;
+    if (S->err_pool.empty()) {
+        void *p = nullptr;
+        if (cudaHostAlloc(&p, sizeof(int) * kErrBlock, cudaHostAllocDefault) != cudaSuccess)
+            return nullptr;
+        S->err_blocks.push_back(static_cast<int *>(p));
+        for (int i = kErrBlock - 1; i >= 0; --i) S->err_pool.push_back(static_cast<int *>(p) + i);
     }
-    void *p = nullptr;
-    if (cudaHostAlloc(&p, sizeof(int), cudaHostAllocDefault) != cudaSuccess) return nullptr;
-    return static_cast<int *>(p);
+    int *w = S->err_pool.back();
+    S->err_pool.pop_back();
+    return w;
 }
 
 // Retire every job whose result is back in host memory.
@@ -2269,7 +2282,7 @@ void serve_stop(bsort_t h)
     }
     for (auto &kv : S->tickets) delete kv.second;
     for (cudaEvent_t e : S->ev_pool) cudaEventDestroy(e);
-    for (int *p : S->err_pool) cudaFreeHost(p);
+    for (int *p : S->err_blocks) cudaFreeHost(p);
     cudaFree(S->arena);
     bsort_destroy(S->hb);
     delete S;
