@@ -2,20 +2,25 @@
 // Section 4, Algorithm 1) for sm_103a, and their launch wrappers.
 //
 //   Steps 1-3  k_sublist_sort      (bsort_sort.cuh) sort each sublist, emit samples
-//   Step 4     k_records_sort      sort the s*m samples (chunks of 16K) ...
+//   Step 4     k_rec_hist, k_rec_pass  (bsort_records.cu) radix sort of the
+//                                  sample records, splitters from its last pass;
+//              k_records_sort      or: sort the s*m samples in chunks of 16K ...
 //              k_merge_pass        ... then merge-path passes through L2
 //   Step 5     k_select_splitters  b evenly spaced sorted samples
 //   Step 6     k_seg_ranges        splitters per sublist segment ...
-//              k_sample_index_seg  ... located in the segment (shared memory)
-//   Step 7     k_scan              bucket-major exclusive scan (look-back)
-//   Step 8     k_relocate          move each run A_ij to l_ij
-//   Step 9     k_pack_units        pack consecutive buckets into Step-9 units
+//              k_sample_index_grp  ... located in the segment (shared memory)
+//   Step 7-8   k_bucket_relocate   per bucket: scan of its count row, then its runs moved
+//   Step 7     k_row_scan          or: one scan per bucket row of the counts,
+//              k_scan              or (batches): bucket-major scan with look-back
+//   Step 8     k_relocate          then: move each run A_ij to l_ij
+//   Step 9     k_units_each / k_pack_units  a unit per bucket, or buckets packed
 //              k_bucket_sort       (bsort_sort.cuh) sort each unit
 //
 // Items are compared in composite order (key, position): keys-only sorts
 // compare keys (equal keys are indistinguishable), pair sorts compare the
 // 64-bit word key << 32 | local index, which makes them stable, and the
-// sample records of Steps 3-6 are key << 32 | p with p = i*t + r.
+// sample records of Steps 3-6 are key << 32 | q with q = i*s + k, the
+// sample's index (its position i*t + (k+1)w - 1 grows with q).
 #include "bsort_device.cuh"
 #include "bsort_internal.h"
 
