@@ -72,10 +72,15 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, uint32_t valid)
 // has digit d at bits [8p, 8p + 8).  Warps take 32 consecutive records at a
 // time; a digit that all 32 lanes share (runs of equal digits are common:
 // the records of one sublist are sorted) is added once.
+// The CTA that finishes last (a ticket taken after its counts are in)
+// also turns the four histograms into the digits' first global ranks,
+// gbase[p*256 + d] = the records whose digit p is below d.
 template <int T>
 __global__ void __launch_bounds__(T)
-k_rec_hist(const uint64_t *__restrict__ rec, uint32_t n, uint32_t *__restrict__ hist)
+k_rec_hist(const uint64_t *__restrict__ rec, uint32_t n, uint32_t *__restrict__ hist,
+           uint32_t *__restrict__ done, uint32_t *__restrict__ gbase)
 {
+    static_assert(T == 256, "one thread per digit in the final scan");
     __shared__ uint32_t sh[4 * 256];
     for (int i = threadIdx.x; i < 4 * 256; i += T) sh[i] = 0u;
     __syncthreads();
@@ -111,16 +116,31 @@ k_rec_hist(const uint64_t *__restrict__ rec, uint32_t n, uint32_t *__restrict__ 
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * 256; i += T)
         if (sh[i] != 0u) atomicAdd(&hist[i], sh[i]);
+    __threadfence();
+    __syncthreads();
+    __shared__ uint32_t s_last;
+    __shared__ uint32_t s_wt[T / 32];
+    if (threadIdx.x == 0) s_last = atomicAdd(done, 1u) == gridDim.x - 1 ? 1u : 0u;
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+#pragma unroll 1
+    for (int p = 0; p < 4; ++p) {
+        uint32_t tot;
+        const uint32_t c = __ldcg(&hist[p * 256 + (int)threadIdx.x]);
+        gbase[p * 256 + (int)threadIdx.x] = block_exclusive_sum<T>(c, s_wt, tot);
+        __syncthreads();  // s_wt is reused by the next digit position
+    }
 }
 
-// One stable pass over the digit at key bits [shift, shift + 8).  hist: the
-// 256 global counts of this digit; status: tiles*256 words, ticket: one
+// One stable pass over the digit at key bits [shift, shift + 8).  gfirst:
+// the 256 digits' first global ranks; status: tiles*256 words, ticket: one
 // word, both zero at launch.  spl == nullptr: out receives the n records in
 // the new order; otherwise only spl[j] = the record of final rank r_j.
 template <int T, int E>
 __global__ void __launch_bounds__(T, 2)
 k_rec_pass(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, uint32_t n, int shift,
-           const uint32_t *__restrict__ hist, uint32_t *status, uint32_t *ticket, int *err,
+           const uint32_t *__restrict__ gfirst, uint32_t *status, uint32_t *ticket, int *err,
            uint64_t *__restrict__ spl, uint32_t b)
 {
     static_assert(T == 512 && T * E == kRsTile, "16 warps, one thread per digit in the first 8");
@@ -190,10 +210,8 @@ k_rec_pass(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, uint32_t
             run += c[w];
         }
     }
-    __syncthreads();  // s_wt is read by every thread before it is reused
-    // global first rank of each digit: the counts of the smaller digits
-    uint32_t gtot;
-    const uint32_t gbase = block_exclusive_sum<T>(tid < 256 ? hist[tid] : 0u, s_wt, gtot);
+    // global first rank of each digit (the histogram kernel's scan)
+    const uint32_t gbase = tid < 256 ? gfirst[tid] : 0u;
     __syncthreads();  // warp bases and s_start complete
     // 3. rank and stage
 #pragma unroll
@@ -283,10 +301,25 @@ k_rec_pass(const uint64_t *__restrict__ in, uint64_t *__restrict__ out, uint32_t
 
 }  // namespace
 
+// Scratch layout (32-bit words): the four digit histograms (4 * 256), the
+// digits' first global ranks (4 * 256), 16 tickets (one per digit pass, one
+// for the histogram's last CTA), then 4 * tiles * 256 look-back words; all
+// zeroed before the histogram.
+namespace {
+struct RsScratch {
+    uint32_t *hist, *gfirst, *tickets, *status;
+};
+RsScratch rs_layout(void *scratch)
+{
+    uint32_t *w = static_cast<uint32_t *>(scratch);
+    return {w, w + 4 * 256, w + 8 * 256, w + 8 * 256 + 16};
+}
+}  // namespace
+
 uint64_t records_radix_scratch_bytes(uint32_t n_rec)
 {
     const uint64_t tiles = (n_rec + kRsTile - 1) / kRsTile;
-    return 4ull * (4 * 256 + 16 + 4 * tiles * 256);
+    return 4ull * (8 * 256 + 16 + 4 * tiles * 256);
 }
 
 bool records_radix_fits(uint32_t n_rec, uint32_t b)
@@ -300,15 +333,14 @@ cudaError_t init_records_kernels()
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, kRsSmemBytes);
 }
 
-// scratch: hist (4 * 256 words), tickets (16 words), then 4 * tiles * 256
-// status words, all zeroed here before the histogram.
 cudaError_t launch_records_hist(const uint64_t *samples, uint32_t n_rec, void *scratch, int sms,
                                 cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(scratch, 0, records_radix_scratch_bytes(n_rec), st);
     if (e != cudaSuccess) return e;
-    k_rec_hist<256><<<4 * (sms > 0 ? sms : 1), 256, 0, st>>>(samples, n_rec,
-                                                              static_cast<uint32_t *>(scratch));
+    const RsScratch r = rs_layout(scratch);
+    k_rec_hist<256><<<4 * (sms > 0 ? sms : 1), 256, 0, st>>>(samples, n_rec, r.hist,
+                                                              r.tickets + 8, r.gfirst);
     return cudaGetLastError();
 }
 
@@ -319,12 +351,10 @@ cudaError_t launch_records_pass(int p, const uint64_t *in, uint64_t *out, uint32
     if (!records_radix_fits(n_rec, b) || p < 0 || p > 3) return cudaErrorInvalidValue;
     if ((p < 3) != (out != nullptr) || (p == 3) != (spl != nullptr)) return cudaErrorInvalidValue;
     const uint32_t tiles = (n_rec + kRsTile - 1) / kRsTile;
-    uint32_t *hist = static_cast<uint32_t *>(scratch);
-    uint32_t *tickets = hist + 4 * 256;
-    uint32_t *status = tickets + 16;
+    const RsScratch r = rs_layout(scratch);
     k_rec_pass<kRsT, kRsE><<<tiles, kRsT, kRsSmemBytes, st>>>(
-        in, out, n_rec, 8 * p, hist + 256 * p, status + (uint64_t)p * tiles * 256u, tickets + p,
-        err, spl, b);
+        in, out, n_rec, 8 * p, r.gfirst + 256 * p, r.status + (uint64_t)p * tiles * 256u,
+        r.tickets + p, err, spl, b);
     return cudaGetLastError();
 }
 
