@@ -267,8 +267,9 @@ bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_i
  * sequence of launches; larger ones by one plain sort each.  The segment
  * table is copied to the device from pinned staging owned by the handle.
  * kt: BSORT_U32, BSORT_F32 or BSORT_U64 (64-bit keys: segments up to
- * min(batch_direct_max, 131072) keys sorted whole, larger ones one plain
- * sort each).  Errors: EINVAL (null pointers, decreasing offsets, partial
+ * 262144 keys, or batch_direct_max when given, sorted whole — above 131072
+ * by a 16-CTA cluster, where the device schedules one, else the limit is
+ * 131072 — larger ones one plain sort each).  Errors: EINVAL (null pointers, decreasing offsets, partial
  * overlap), EUNSUPPORTED (too many keys), ENOMEM. */
 bsort_status bsort_sort_batch(bsort_t h, bsort_key_type kt, const void *d_keys_in,
                               void *d_keys_out, const uint64_t *seg_offsets,

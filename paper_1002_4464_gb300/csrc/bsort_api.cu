@@ -98,6 +98,7 @@ struct bsort_ctx {
     const char *ev_name[kMaxTimed] = {};
     int n_ev[kRing] = {};
     uint32_t direct_max = kBatchDirectMax;  // batches: largest segment sorted whole
+    bool direct_max_set = false;            // direct_max given by the caller
     void *stage = nullptr;           // pinned staging of batch descriptors
     uint64_t stage_bytes = 0;
     cudaEvent_t stage_ev = nullptr;  // last copy out of stage
@@ -1427,13 +1428,26 @@ const int kDirectShapes[kNumDirect][2] = {{2048, 1},  {4096, 1},  {8192, 1},  {1
 const char *const kDirectNames[kNumDirect] = {
     "batch_direct_2048", "batch_direct_4096", "batch_direct_8192", "batch_direct_16384",
     "batch_direct_32768", "batch_direct_2x32768", "batch_direct_4x32768", "batch_direct_8x32768"};
-constexpr int kNumDirectWide = 7;
-const int kDirectShapesWide[kNumDirectWide][2] = {{2048, 1},  {4096, 1},  {8192, 1}, {16384, 1},
-                                                  {16384, 2}, {16384, 4}, {16384, 8}};
+// (the last, a 16-CTA cluster, only where the device schedules one)
+constexpr int kNumDirectWide = 8;
+const int kDirectShapesWide[kNumDirectWide][2] = {{2048, 1},  {4096, 1},  {8192, 1},
+                                                  {16384, 1}, {16384, 2}, {16384, 4},
+                                                  {16384, 8}, {16384, 16}};
 const char *const kDirectNamesWide[kNumDirectWide] = {
-    "batch_direct_u64_2048", "batch_direct_u64_4096", "batch_direct_u64_8192",
-    "batch_direct_u64_16384", "batch_direct_u64_2x16384", "batch_direct_u64_4x16384",
-    "batch_direct_u64_8x16384"};
+    "batch_direct_u64_2048",    "batch_direct_u64_4096",   "batch_direct_u64_8192",
+    "batch_direct_u64_16384",   "batch_direct_u64_2x16384", "batch_direct_u64_4x16384",
+    "batch_direct_u64_8x16384", "batch_direct_u64_16x16384"};
+
+// Direct-segment shapes of 64-bit keys this device runs, and the largest
+// 64-bit segment sorted whole: batch_direct_max if set, else every shape.
+int wide_direct_shapes() { return batch_wide_cluster16() ? kNumDirectWide : kNumDirectWide - 1; }
+uint64_t wide_direct_max(const bsort_t h)
+{
+    const int ns = wide_direct_shapes();
+    const uint64_t largest =
+        (uint64_t)kDirectShapesWide[ns - 1][0] * (uint64_t)kDirectShapesWide[ns - 1][1];
+    return h->direct_max_set && h->direct_max < largest ? h->direct_max : largest;
+}
 
 // Host plan of one batch: direct lists per shape, sampled segments with
 // their sublists and buckets, plain-sorted large segments, and the
@@ -1485,7 +1499,7 @@ bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const SegSpan *spans,
         return fail(h, BSORT_EINVAL, "unknown key type %d", (int)kt);
     B->wide = kt == BSORT_U64;
     const int(*shapes)[2] = B->wide ? kDirectShapesWide : kDirectShapes;
-    const int nshapes = B->wide ? kNumDirectWide : kNumDirect;
+    const int nshapes = B->wide ? wide_direct_shapes() : kNumDirect;
     const uint64_t largest = (uint64_t)shapes[nshapes - 1][0] * shapes[nshapes - 1][1];
     if (nsegs && !spans) return fail(h, BSORT_EINVAL, "null segment list");
     bsort_batch_info &I = B->info;
@@ -1496,7 +1510,8 @@ bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const SegSpan *spans,
         if (spans[q].begin + spans[q].n >= kMaxN)
             return fail(h, BSORT_EUNSUPPORTED, "segment end %llu exceeds 2^32 - 2^16",
                         (unsigned long long)(spans[q].begin + spans[q].n));
-    const uint64_t dmax = h->direct_max < largest ? h->direct_max : largest;
+    const uint64_t dmax =
+        B->wide ? wide_direct_max(h) : (h->direct_max < largest ? h->direct_max : largest);
     uint64_t g = 0;  // sublists so far
     for (uint32_t q = 0; q < nsegs; ++q) {
         const uint64_t a = spans[q].begin, n = spans[q].n;
@@ -1927,7 +1942,7 @@ uint64_t key_bytes(bsort_key_type kt) { return kt == BSORT_U64 ? 8 : 4; }
 // Lane of a job: 0 when a batch sorts it as a direct or sampled segment.
 int lane_of(const bsort_t h, bsort_key_type kt, uint64_t n)
 {
-    if (kt == BSORT_U64) return n <= (uint64_t)h->direct_max && n <= 8ull * kMaxCapPairs ? 0 : 1;
+    if (kt == BSORT_U64) return n <= wide_direct_max(h) ? 0 : 1;
     return n <= kBatchSampledMax ? 0 : 1;
 }
 
@@ -2219,6 +2234,7 @@ bsort_status serve_start(bsort_t h)
     }
     S->hb->device = h->device;
     S->hb->direct_max = h->direct_max;
+    S->hb->direct_max_set = h->direct_max_set;
     if (!h->ws_fixed) {
         rs = ensure_workspace(h, ws_lane);
         if (rs == BSORT_OK) h->ws_fixed = true;
@@ -2336,6 +2352,7 @@ bsort_status bsort_create(const bsort_config *cfg, bsort_t *out)
                 return BSORT_EINVAL;
             }
             h->direct_max = cfg->batch_direct_max;
+            h->direct_max_set = true;
         }
         if (cfg->flags &
             ~(uint32_t)(BSORT_FLAG_TIMING | BSORT_FLAG_LOW_MEMORY | BSORT_FLAG_GRAPHS |

@@ -311,9 +311,42 @@ cudaError_t init_seg_sort_t()
 
 }  // namespace
 
+namespace {
+int g_wide16 = -1;  // the 16-CTA 64-bit shape: -1 not asked yet, 0 no, 1 yes
+}  // namespace
+
+// Asked once per process, on the current device (no device: no).
+bool batch_wide_cluster16()
+{
+    if (g_wide16 < 0) {
+        // non-portable cluster size: usable only if the device schedules it
+        const int sm = padded_elems<uint64_t>(16384) * 8;
+        int n = 0;
+        cudaError_t q = set_smem_attr(k_seg_sort<uint64_t, 1024, 16, 16>, sm, true);
+        if (q == cudaSuccess) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(16, 1, 1);
+            cfg.blockDim = dim3(1024, 1, 1);
+            cfg.dynamicSmemBytes = (size_t)sm;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 16;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            q = cudaOccupancyMaxActiveClusters(&n, k_seg_sort<uint64_t, 1024, 16, 16>, &cfg);
+        }
+        if (q != cudaSuccess) cudaGetLastError();  // (not an error: the shape is left out)
+        g_wide16 = q == cudaSuccess && n >= 1 ? 1 : 0;
+    }
+    return g_wide16 == 1;
+}
+
 cudaError_t init_batch_kernels()
 {
     cudaError_t e = cudaSuccess;
+    batch_wide_cluster16();
     if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 128, 16, 1>();
     if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 256, 16, 1>();
     if (e == cudaSuccess) e = init_seg_sort_t<uint32_t, 512, 16, 1>();
@@ -360,6 +393,9 @@ cudaError_t launch_seg_sort(int chunk, int ctas, bool wide, const void *keys_in,
             case 2: L(uint64_t, 1024, 16, 2);
             case 4: L(uint64_t, 1024, 16, 4);
             case 8: L(uint64_t, 1024, 16, 8);
+            case 16:
+                if (!batch_wide_cluster16()) return cudaErrorInvalidValue;
+                L(uint64_t, 1024, 16, 16);
             }
         }
         return cudaErrorInvalidValue;

@@ -284,6 +284,9 @@ struct SegInfo {
 };
 
 cudaError_t init_batch_kernels();
+// Whether the device schedules the 16-CTA cluster shape of 64-bit direct
+// segments (known after init_batch_kernels).
+bool batch_wide_cluster16();
 // Direct segments: unit u = [seg[2u], seg[2u+1]) sorted by one unit of
 // `ctas` CTAs of `chunk` keys (wide: 64-bit keys).
 cudaError_t launch_seg_sort(int chunk, int ctas, bool wide, const void *keys_in, void *keys_out,

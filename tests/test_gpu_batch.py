@@ -120,17 +120,22 @@ def test_batch_equals_one_at_a_time():
 
 
 def test_batch_u64():
-    """64-bit keys: segments up to 131072 keys sorted whole (CTAs of 16384
-    keys, clusters up to 8), larger ones by a plain sort each."""
-    sizes = np.array([0, 1, 2, 1000, 2048, 2049, 16384, 16385, 65536, 131072, 131073, 400000,
-                      7], np.int64)
+    """64-bit keys: segments up to 262144 keys sorted whole (CTAs of 16384
+    keys, clusters up to 16 where the device schedules a 16-CTA cluster,
+    else up to 8 and 131072 keys), larger ones by a plain sort each."""
+    sizes = np.array([0, 1, 2, 1000, 2048, 2049, 16384, 16385, 65536, 131072, 131073, 200001,
+                      262144, 262145, 400000, 7], np.int64)
     off = np.concatenate([[3], 3 + np.cumsum(sizes)]).astype(np.uint64)
     n = int(off[-1]) + 5
     keys = synth.keys_u64(n, synth.seed_for(5, 4))
     keys[::7] &= np.uint64(0xFF)  # duplicates
     sorter = pkg.BucketSorter()
+    wide16 = sorter.plan_batch(np.array([0, 262144], np.uint64), "u64").direct_segs == 1
     p = sorter.plan_batch(off, "u64")
-    assert p.direct_segs == 9 and p.large_segs == 2 and p.sampled_segs == 0
+    if wide16:
+        assert p.direct_segs == 12 and p.large_segs == 2 and p.sampled_segs == 0
+    else:
+        assert p.direct_segs == 9 and p.large_segs == 5 and p.sampled_segs == 0
     d_in = torch.from_numpy(keys.view(np.int64)).cuda()
     d_out = torch.full_like(d_in, 0x5A5A)
     sorter.sort_batch(d_in, off, out=d_out, key_type="u64")
