@@ -991,6 +991,19 @@ def run_served(args, pkg, synth, dev, rank, capacity_only=False):
     again = _serve_capacity(args, pkg, dev, job, ring, maxn, ncap, cap_keys)
     capacity["again_in_process"] = {k: again[k] for k in ("served_gkeys_s",
                                                            "one_at_a_time_gkeys_s", "speedup")}
+    # and with freshly pinned host buffers (same contents): the drop in this
+    # process follows the pinned buffers the open-loop runs used
+    try:
+        kept = (pools, slots)
+        pools = {key: val.clone().pin_memory() for key, val in kept[0].items()}
+        slots = [torch.empty(maxn, dtype=torch.int64).pin_memory() for _ in range(ring)]
+        nb = _serve_capacity(args, pkg, dev, job, ring, maxn, ncap, cap_keys)
+        capacity["new_pinned_buffers_in_process"] = {
+            k: nb[k] for k in ("served_gkeys_s", "one_at_a_time_gkeys_s", "speedup")}
+        pools, slots = kept
+    except Exception as e:  # reported, not fatal
+        capacity["new_pinned_buffers_in_process"] = {"error": "%s: %s" % (type(e).__name__,
+                                                                          str(e)[:200])}
 
     def pct(x, q):
         return float(np.percentile(x, q)) if len(x) else None
