@@ -25,7 +25,8 @@ budget) through bsort_submit/bsort_poll, against the same arrivals sorted
 one at a time (bsort_sort_keys_host, then a wait); latency = the time the
 sorted keys are in host memory minus the scheduled arrival.  Its "capacity"
 runs the first 4,000 jobs back to back both ways, in this process and (as
-"fresh_process") in a new one started with --serve-capacity.
+"fresh_process") in a new one started with --serve-capacity, then in this
+process again, with the same buffers and with freshly pinned ones.
 
 And "batched": the batched workload (20,000 independent
 uint32 arrays, sizes log-uniform in [2^7, 2^20], scaled to at most 2^30 keys
@@ -855,7 +856,8 @@ def _serve_capacity(args, pkg, dev, job, ring, maxn, ncap, cap_keys):
 def _serve_capacity_subprocess(args):
     """_serve_capacity in a fresh process (this script with --serve-capacity):
     in a process that has already run the other sections, the request loop's
-    closed-loop capacity measures lower (the cause is not identified)."""
+    closed-loop capacity measures lower with the pinned buffers the open-loop
+    runs used (freshly pinned buffers restore it; reported beside it)."""
     cmd = [sys.executable, os.path.abspath(__file__), "--serve-capacity",
            "--serve-seconds", repr(args.serve_seconds), "--serve-rate", repr(args.serve_rate),
            "--serve-budget", str(args.serve_budget)]
