@@ -61,7 +61,7 @@ KERNEL_FN = {
     "step4_sample_merge": "k_merge_pass", "step5_splitters": "k_select_splitters",
     "step4_sample_hist": "k_rec_hist", "step4_sample_radix": "k_rec_pass",
     "step4_5_radix_splitters": "k_rec_pass",
-    "step6_sample_index": "k_sample_index", "step7_prefix_sum": "k_scan",
+    "step6_sample_index": "k_sample_index", "step7_prefix_sum": "k_row_scan",
     "step8_relocate": "k_relocate", "step7_8_scan_relocate": "k_bucket_relocate",
     "step9_pack_units": "k_pack_units",
     "step9_bucket_sort": "k_bucket_sort", "step9_single_unit": "k_bucket_sort",
