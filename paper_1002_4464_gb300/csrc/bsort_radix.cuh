@@ -114,7 +114,7 @@ __device__ __forceinline__ void cta_radix_sort(uint32_t (&v)[E], uint32_t *sm, i
     static_assert(DB >= 1 && DB <= 7, "at most 64 counter rows");
     using S = RadixSmem<T, E, DB>;
     constexpr int W = 32 * E;  // positions of one warp
-    constexpr int G = 16;      // keys ranked per batch of atomics
+    constexpr int G = 8;      // keys ranked per batch of atomics
     __shared__ uint32_t s_wt[T / 32];
     __shared__ uint32_t s_mm[2][T / 32];
     const int tid = threadIdx.x;
