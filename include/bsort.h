@@ -206,7 +206,8 @@ typedef struct {
     uint32_t num_segs;
     uint32_t direct_segs;     /* sorted whole by one CTA or cluster */
     uint32_t sampled_segs;    /* sorted by segment-aware Algorithm 1 */
-    uint32_t large_segs;      /* above 524288 keys: one plain sort each */
+    uint32_t large_segs;      /* above 524288 32-bit or 1048576 64-bit keys:
+                                 one plain sort each */
     uint32_t sublists;        /* sublists of the sampled segments */
     uint32_t buckets;         /* buckets of the sampled segments */
     uint32_t num_kernels;     /* kernel launches per call */
@@ -269,8 +270,11 @@ bsort_status bsort_sort_pairs(bsort_t h, bsort_key_type kt, const void *d_keys_i
  * kt: BSORT_U32, BSORT_F32 or BSORT_U64 (64-bit keys: segments up to
  * 262144 keys, or batch_direct_max when given, sorted whole — above 131072
  * by a 16-CTA cluster, where the device schedules one, else the limit is
- * 131072 — larger ones one plain sort each).  Errors: EINVAL (null pointers, decreasing offsets, partial
- * overlap), EUNSUPPORTED (too many keys), ENOMEM. */
+ * 131072 —, larger ones up to 1048576 keys by the segment-aware Algorithm 1
+ * with sublists of 16384 keys and s = 256 samples per sublist (128 above
+ * 32 sublists), larger ones one plain sort each).  Errors: EINVAL (null
+ * pointers, decreasing offsets, partial overlap), EUNSUPPORTED (too many
+ * keys), ENOMEM. */
 bsort_status bsort_sort_batch(bsort_t h, bsort_key_type kt, const void *d_keys_in,
                               void *d_keys_out, const uint64_t *seg_offsets,
                               uint32_t num_segs, void *cuda_stream);
@@ -280,7 +284,8 @@ bsort_status bsort_sort_batch(bsort_t h, bsort_key_type kt, const void *d_keys_i
  * handle (one worker thread, started by the first submit) admits queued
  * jobs while its device arena has room (the serving budget,
  * bsort_config.serve_budget_bytes) and copies their keys in.  Small jobs
- * (up to 524288 32-bit or 131072 64-bit keys) are admitted in arrival order
+ * (up to 524288 32-bit or 1048576 64-bit keys: those bsort_sort_batch sorts
+ * whole or by its segment-aware sample sort) are admitted in arrival order
  * and sorted together as a batch (bsort_sort_batch's path) as soon as the
  * previous small batch has finished sorting, on a high-priority stream;
  * jobs that arrive meanwhile are copied in and form the next batch

@@ -46,6 +46,11 @@ constexpr uint32_t kBatchDirectMax = 131072;
 constexpr uint32_t kBatchSampledMax = (uint32_t)kRecordChunk / 1024 * (uint32_t)kSegTile;
 constexpr uint32_t kBatchSamples = 1024;
 constexpr uint32_t kBatchUnit = 32768;  // Step-9 unit of sampled segments
+// 64-bit keys: sublists of kSegTileU64 keys, s = 256 samples per sublist up
+// to 32 sublists and 128 above (m*s <= kSegRecordsU64), Step-9 units of
+// kSegTileU64 keys, so up to 64 sublists.
+constexpr uint32_t kBatchSampledMaxU64 = kSegRecordsU64 / 128 * (uint32_t)kSegTileU64;
+constexpr uint32_t kBatchUnitU64 = (uint32_t)kSegTileU64;
 constexpr int kRing = 64;       // calls kept for bsort_kernel_times
 
 uint64_t align_up(uint64_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
@@ -1454,7 +1459,7 @@ uint64_t wide_direct_max(const bsort_t h)
 // workspace layout (descriptors first, copied from pinned staging).
 struct BatchPlan {
     bsort_batch_info info;
-    bool wide = false;  // 64-bit keys: direct units and plain sorts only
+    bool wide = false;  // 64-bit keys
     std::vector<uint32_t> direct[kNumDirect];  // (begin, end) pairs per shape
     std::vector<SegInfo> segs;
     std::vector<uint32_t> sub_seg;
@@ -1512,6 +1517,8 @@ bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const SegSpan *spans,
                         (unsigned long long)(spans[q].begin + spans[q].n));
     const uint64_t dmax =
         B->wide ? wide_direct_max(h) : (h->direct_max < largest ? h->direct_max : largest);
+    const uint64_t tile = B->wide ? (uint64_t)kSegTileU64 : (uint64_t)kSegTile;
+    const uint64_t unit = B->wide ? (uint64_t)kBatchUnitU64 : (uint64_t)kBatchUnit;
     uint64_t g = 0;  // sublists so far
     for (uint32_t q = 0; q < nsegs; ++q) {
         const uint64_t a = spans[q].begin, n = spans[q].n;
@@ -1523,16 +1530,16 @@ bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const SegSpan *spans,
             B->direct[c].push_back((uint32_t)a);
             B->direct[c].push_back((uint32_t)(a + n));
             ++I.direct_segs;
-        } else if (n <= kBatchSampledMax && !B->wide) {
+        } else if (n <= (B->wide ? kBatchSampledMaxU64 : kBatchSampledMax)) {
             SegInfo sg = {};
             sg.g0 = (uint32_t)g;
-            sg.m = (uint32_t)((n + kSegTile - 1) / kSegTile);
-            sg.s = kBatchSamples;
-            const uint64_t np = (uint64_t)sg.m * kSegTile;
+            sg.m = (uint32_t)((n + tile - 1) / tile);
+            sg.s = B->wide ? (sg.m <= 32 ? 256u : 128u) : kBatchSamples;
+            const uint64_t np = (uint64_t)sg.m * tile;
             uint64_t lo = 1, hi = (uint64_t)sg.m * sg.s;  // smallest b whose bound fits a unit
             while (lo < hi) {
                 const uint64_t mid = (lo + hi) / 2;
-                if (bound_for(np, sg.m, sg.s, mid) <= kBatchUnit) hi = mid;
+                if (bound_for(np, sg.m, sg.s, mid) <= unit) hi = mid;
                 else lo = mid + 1;
             }
             sg.b = (uint32_t)lo;
@@ -1555,8 +1562,8 @@ bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const SegSpan *spans,
             B->large.push_back({a, n});
         }
     }
-    if (g * kSegTile >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "padded sampled segments exceed 2^32");
-    B->n_pad = g * kSegTile;
+    if (g * tile >= kMaxN) return fail(h, BSORT_EUNSUPPORTED, "padded sampled segments exceed 2^32");
+    B->n_pad = g * tile;
     I.sampled_segs = (uint32_t)B->segs.size();
     I.large_segs = (uint32_t)B->large.size();
     I.sublists = (uint32_t)g;
@@ -1596,10 +1603,12 @@ bsort_status make_batch_plan(bsort_t h, bsort_key_type kt, const SegSpan *spans,
     take(kAlign);  // error word + scan ticket
     B->off_desc = take(wds * 4);
     if (!B->segs.empty()) {
-        B->off_tiles = take(B->n_pad * 4);
-        B->off_reloc = take(B->n_pad * 4);
-        B->off_samples = take((uint64_t)B->nrec * 8);
-        B->off_spl = take((uint64_t)B->nspl * 8);
+        const uint64_t kb = B->wide ? 8 : 4;   // key bytes
+        const uint64_t rb = B->wide ? 16 : 8;  // sample record bytes
+        B->off_tiles = take(B->n_pad * kb);
+        B->off_reloc = take(B->n_pad * kb);
+        B->off_samples = take((uint64_t)B->nrec * rb);
+        B->off_spl = take((uint64_t)B->nspl * rb);
         B->off_counts = take((uint64_t)B->runs * 4);
         B->off_offsets = take(((uint64_t)B->runs + 1) * 4);
         B->off_srcb = take((uint64_t)B->runs * 4);
@@ -1717,10 +1726,6 @@ bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout
         const uint32_t *sub_seg = desc + B.d_sub;
         const SegInfo *segs = reinterpret_cast<const SegInfo *>(desc + B.d_segs);
         const uint32_t *units = desc + B.d_units;
-        uint32_t *tiles = reinterpret_cast<uint32_t *>(ws + B.off_tiles);
-        uint32_t *reloc = reinterpret_cast<uint32_t *>(ws + B.off_reloc);
-        uint64_t *samples = reinterpret_cast<uint64_t *>(ws + B.off_samples);
-        uint64_t *spl = reinterpret_cast<uint64_t *>(ws + B.off_spl);
         uint32_t *counts = reinterpret_cast<uint32_t *>(ws + B.off_counts);
         uint32_t *offsets = reinterpret_cast<uint32_t *>(ws + B.off_offsets);
         uint32_t *srcb = reinterpret_cast<uint32_t *>(ws + B.off_srcb);
@@ -1730,20 +1735,52 @@ bsort_status run_batch(bsort_t h, bsort_key_type kt, const void *kin, void *kout
         if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan status)");
         e = cudaMemsetAsync(ticket, 0, 4, st);
         if (e != cudaSuccess) return cuda_fail(h, e, "memset(scan ticket)");
-        SEQ(launch_seg_sublist_sort(ki, is_f32, sub_seg, nsub, segs, tiles, samples, st),
-            "batch_step1_3_sublist_sort");
-        SEQ(launch_seg_records(samples, segs, B.info.sampled_segs, spl, st),
-            "batch_step4_5_samples");
-        SEQ(launch_seg_sample_index(tiles, samples, spl, sub_seg, nsub, segs, counts, srcb, st),
-            "batch_step6_sample_index");
-        SEQ(launch_scan(counts, offsets, B.runs, status, ticket, err, st), "batch_step7_prefix_sum");
-        SEQ(launch_block_index(offsets, B.runs, (uint32_t)B.n_pad, blk, st), "batch_step8_run_index");
-        SEQ(launch_relocate(tiles, nullptr, offsets, srcb, blk, B.runs, (uint32_t)B.n_pad, 0,
-                            reloc, nullptr, st),
-            "batch_step8_relocate");
-        SEQ(launch_seg_bucket_sort((int)kBatchUnit, reloc, units, B.info.buckets, segs, offsets,
-                                   is_f32, ko, err, st),
-            "batch_step9_bucket_sort");
+        if (B.wide) {
+            uint64_t *tiles = reinterpret_cast<uint64_t *>(ws + B.off_tiles);
+            uint64_t *reloc = reinterpret_cast<uint64_t *>(ws + B.off_reloc);
+            Rec128 *samples = reinterpret_cast<Rec128 *>(ws + B.off_samples);
+            Rec128 *spl = reinterpret_cast<Rec128 *>(ws + B.off_spl);
+            SEQ(launch_seg_sublist_sort_u64(static_cast<const uint64_t *>(kin), sub_seg, nsub,
+                                            segs, tiles, samples, st),
+                "batch_u64_step1_3_sublist_sort");
+            SEQ(launch_seg_records_u64(samples, segs, B.info.sampled_segs, spl, st),
+                "batch_u64_step4_5_samples");
+            SEQ(launch_seg_sample_index_u64(tiles, samples, spl, sub_seg, nsub, segs, counts,
+                                            srcb, st),
+                "batch_u64_step6_sample_index");
+            SEQ(launch_scan(counts, offsets, B.runs, status, ticket, err, st),
+                "batch_u64_step7_prefix_sum");
+            SEQ(launch_block_index(offsets, B.runs, (uint32_t)B.n_pad, blk, st),
+                "batch_u64_step8_run_index");
+            SEQ(launch_relocate_u64(tiles, offsets, srcb, blk, B.runs, (uint32_t)B.n_pad, reloc,
+                                    st),
+                "batch_u64_step8_relocate");
+            SEQ(launch_seg_bucket_sort_u64(reloc, units, B.info.buckets, segs, offsets,
+                                           static_cast<uint64_t *>(kout), err, st),
+                "batch_u64_step9_bucket_sort");
+        } else {
+            uint32_t *tiles = reinterpret_cast<uint32_t *>(ws + B.off_tiles);
+            uint32_t *reloc = reinterpret_cast<uint32_t *>(ws + B.off_reloc);
+            uint64_t *samples = reinterpret_cast<uint64_t *>(ws + B.off_samples);
+            uint64_t *spl = reinterpret_cast<uint64_t *>(ws + B.off_spl);
+            SEQ(launch_seg_sublist_sort(ki, is_f32, sub_seg, nsub, segs, tiles, samples, st),
+                "batch_step1_3_sublist_sort");
+            SEQ(launch_seg_records(samples, segs, B.info.sampled_segs, spl, st),
+                "batch_step4_5_samples");
+            SEQ(launch_seg_sample_index(tiles, samples, spl, sub_seg, nsub, segs, counts, srcb,
+                                        st),
+                "batch_step6_sample_index");
+            SEQ(launch_scan(counts, offsets, B.runs, status, ticket, err, st),
+                "batch_step7_prefix_sum");
+            SEQ(launch_block_index(offsets, B.runs, (uint32_t)B.n_pad, blk, st),
+                "batch_step8_run_index");
+            SEQ(launch_relocate(tiles, nullptr, offsets, srcb, blk, B.runs, (uint32_t)B.n_pad, 0,
+                                reloc, nullptr, st),
+                "batch_step8_relocate");
+            SEQ(launch_seg_bucket_sort((int)kBatchUnit, reloc, units, B.info.buckets, segs,
+                                       offsets, is_f32, ko, err, st),
+                "batch_step9_bucket_sort");
+        }
     }
     // large segments: one plain sort each, after the batch (same stream)
     for (const auto &lg : B.large) {
@@ -1940,10 +1977,9 @@ constexpr uint64_t kServeDefaultBudget = 4ull << 30;
 uint64_t key_bytes(bsort_key_type kt) { return kt == BSORT_U64 ? 8 : 4; }
 
 // Lane of a job: 0 when a batch sorts it as a direct or sampled segment.
-int lane_of(const bsort_t h, bsort_key_type kt, uint64_t n)
+int lane_of(const bsort_t, bsort_key_type kt, uint64_t n)
 {
-    if (kt == BSORT_U64) return n <= wide_direct_max(h) ? 0 : 1;
-    return n <= kBatchSampledMax ? 0 : 1;
+    return n <= (kt == BSORT_U64 ? kBatchSampledMaxU64 : kBatchSampledMax) ? 0 : 1;
 }
 
 bool arena_alloc(bsort_server *S, uint64_t bytes, uint64_t *off)

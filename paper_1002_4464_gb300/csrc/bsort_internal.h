@@ -274,6 +274,8 @@ cudaError_t launch_bucket_sort_u64(int chunk, int ctas, const void *src, const u
 // ---------------------------------------------------------------- batches
 // Sublist size of sampled segments (one 1024 x 32 CTA per sublist).
 constexpr int kSegTile = 32768;
+// Sublist size of sampled segments of 64-bit keys (one 1024 x 16 CTA).
+constexpr int kSegTileU64 = 16384;
 
 // One sampled segment of a batch: sublists g0 .. g0+m-1 (padded positions
 // [g0*t, (g0+m)*t)), s samples per sublist at records [rec, rec + m*s),
@@ -308,5 +310,24 @@ cudaError_t launch_seg_sample_index(const uint32_t *tiles_k, const uint64_t *sam
 cudaError_t launch_seg_bucket_sort(int chunk, const uint32_t *reloc_k, const uint32_t *units,
                                    uint32_t nunits, const SegInfo *segs, const uint32_t *offsets,
                                    int is_f32, uint32_t *keys_out, int *err, cudaStream_t st);
+// Sampled segments of 64-bit keys: the same steps with sublists of
+// kSegTileU64 keys, sample records (key, p) of 16 bytes (Steps 4-5 need
+// m*s <= 8192) and Step-9 units of at most kSegTileU64 keys; Steps 7-8 are
+// the 32-bit path's scan and block index with launch_relocate_u64.
+cudaError_t launch_seg_sublist_sort_u64(const uint64_t *keys_in, const uint32_t *sub_seg,
+                                        uint32_t nsub, const SegInfo *segs, uint64_t *tiles_k,
+                                        Rec128 *samples, cudaStream_t st);
+cudaError_t launch_seg_records_u64(const Rec128 *samples, const SegInfo *segs, uint32_t nsegs,
+                                   Rec128 *spl, cudaStream_t st);
+cudaError_t launch_seg_sample_index_u64(const uint64_t *tiles_k, const Rec128 *samples,
+                                        const Rec128 *spl, const uint32_t *sub_seg,
+                                        uint32_t nsub, const SegInfo *segs, uint32_t *counts,
+                                        uint32_t *srcb, cudaStream_t st);
+cudaError_t launch_seg_bucket_sort_u64(const uint64_t *reloc_k, const uint32_t *units,
+                                       uint32_t nunits, const SegInfo *segs,
+                                       const uint32_t *offsets, uint64_t *keys_out, int *err,
+                                       cudaStream_t st);
+// Largest m*s of a sampled 64-bit segment (its records in shared memory).
+constexpr uint32_t kSegRecordsU64 = 8192;
 
 }  // namespace bsort

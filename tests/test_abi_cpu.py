@@ -172,14 +172,43 @@ def test_plan_batch_classes():
         pkg.bsort_create(pkg.bsort_config(device=0, batch_direct_max=262145))
 
 
+def test_plan_batch_classes_u64():
+    """64-bit keys: segments above the direct limit (131072 keys without a
+    device, where the 16-CTA cluster is not known to run) up to 2^20 keys
+    go through the segment-aware sample sort with sublists of 16384 keys,
+    s = 256 samples per sublist up to 32 sublists and 128 above, and b
+    buckets whose bound fits a 16384-key unit; larger ones a plain sort."""
+    sizes = [5, 131072, 131073, 262145, 524288, 524289, 1 << 20, (1 << 20) + 1, 2]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    h = _handle()
+    p = pkg.bsort_plan_batch(h, pkg.BSORT_U64, off)
+    assert p.num_segs == len(sizes) and p.n == sum(sizes)
+    assert (p.direct_segs, p.sampled_segs, p.large_segs) == (3, 5, 1)
+    sampled = (131073, 262145, 524288, 524289, 1 << 20)
+    ms = [-(-n // 16384) for n in sampled]
+    assert ms == [9, 17, 32, 33, 64]
+    assert p.sublists == sum(ms)
+    b_expect = 0
+    for m in ms:
+        s = 256 if m <= 32 else 128
+        assert m * s <= 8192  # the records of Steps 4-5 fit one CTA
+        b = next(b for b in range(1, m * s + 1)
+                 if oracle.bucket_bound(m * 16384, m, s, b) <= 16384)
+        b_expect += b
+    assert p.buckets == b_expect
+    # the plain sort of the 2^20 + 1 keys is counted with the batch's kernels
+    assert p.num_kernels > 7
+    pkg.bsort_destroy(h)
+
+
 def test_plan_batch_errors():
     h = _handle()
     with pytest.raises(pkg.BsortError) as e:
         pkg.bsort_plan_batch(h, pkg.BSORT_U32, np.array([0, 10, 5], np.uint64))
     assert e.value.status == pkg.BSORT_EINVAL
     p = pkg.bsort_plan_batch(h, pkg.BSORT_U64,
-                             np.cumsum([0, 10, 131072, 131073, 600000]).astype(np.uint64))
-    assert (p.direct_segs, p.sampled_segs, p.large_segs) == (2, 0, 2)
+                             np.cumsum([0, 10, 131072, 131073, 600000, 1 << 21]).astype(np.uint64))
+    assert (p.direct_segs, p.sampled_segs, p.large_segs) == (2, 2, 1)
     with pytest.raises(pkg.BsortError) as e:
         pkg.bsort_plan_batch(h, pkg.BSORT_U32, np.array([0, 1 << 32], np.uint64))
     assert e.value.status == pkg.BSORT_EUNSUPPORTED

@@ -122,9 +122,12 @@ def test_batch_equals_one_at_a_time():
 def test_batch_u64():
     """64-bit keys: segments up to 262144 keys sorted whole (CTAs of 16384
     keys, clusters up to 16 where the device schedules a 16-CTA cluster,
-    else up to 8 and 131072 keys), larger ones by a plain sort each."""
+    else up to 8 and 131072 keys), larger ones up to 2^20 by the
+    segment-aware sample sort (sublists of 16384 keys, s = 256 up to 32
+    sublists and 128 above), larger ones by a plain sort each."""
     sizes = np.array([0, 1, 2, 1000, 2048, 2049, 16384, 16385, 65536, 131072, 131073, 200001,
-                      262144, 262145, 400000, 7], np.int64)
+                      262144, 262145, 400000, 524288, 524289, 1 << 20, (1 << 20) + 1, 7],
+                     np.int64)
     off = np.concatenate([[3], 3 + np.cumsum(sizes)]).astype(np.uint64)
     n = int(off[-1]) + 5
     keys = synth.keys_u64(n, synth.seed_for(5, 4))
@@ -133,9 +136,9 @@ def test_batch_u64():
     wide16 = sorter.plan_batch(np.array([0, 262144], np.uint64), "u64").direct_segs == 1
     p = sorter.plan_batch(off, "u64")
     if wide16:
-        assert p.direct_segs == 12 and p.large_segs == 2 and p.sampled_segs == 0
+        assert (p.direct_segs, p.sampled_segs, p.large_segs) == (12, 5, 1)
     else:
-        assert p.direct_segs == 9 and p.large_segs == 5 and p.sampled_segs == 0
+        assert (p.direct_segs, p.sampled_segs, p.large_segs) == (9, 8, 1)
     d_in = torch.from_numpy(keys.view(np.int64)).cuda()
     d_out = torch.full_like(d_in, 0x5A5A)
     sorter.sort_batch(d_in, off, out=d_out, key_type="u64")
@@ -146,6 +149,36 @@ def test_batch_u64():
         a, b = int(off[q]), int(off[q + 1])
         want[a:b] = oracle.textbook_sort(keys[a:b], "u64")
     assert np.array_equal(got, want)
+    sorter.close()
+
+
+def test_batch_u64_sampled_ties():
+    """Sampled 64-bit segments whose keys tie: all equal to the largest key
+    (the value that pads the last sublist of a segment), 16 distinct values,
+    and all zero, beside uniform keys; the ties are ordered by position in
+    the samples and splitters, so every bucket stays within its unit."""
+    sizes = [300000, 524289, 1 << 20, 700001, 262145]
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    keys = synth.keys_u64(n, synth.seed_for(5, 6))
+    a = [int(x) for x in off]
+    keys[a[0]:a[1]] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    keys[a[1]:a[2]] &= np.uint64(0xF000000000000000)
+    keys[a[2]:a[3]] = 0
+    keys[a[4]:a[5]] |= np.uint64(0xFFFFFFFFFFFFFF00)  # near the largest key
+    sorter = pkg.BucketSorter()
+    p = sorter.plan_batch(off, "u64")
+    assert p.sampled_segs == 5 and p.large_segs == 0
+    d_in = torch.from_numpy(keys.view(np.int64)).cuda()
+    d_out = torch.empty_like(d_in)
+    sorter.sort_batch(d_in, off, out=d_out, key_type="u64")
+    sorter.sync()
+    got = d_out.cpu().numpy().view(np.uint64)
+    assert np.array_equal(got, _expect(keys, off, "u64"))
+    # in place
+    sorter.sort_batch(d_in, off, out=d_in, key_type="u64")
+    sorter.sync()
+    assert np.array_equal(d_in.cpu().numpy().view(np.uint64), got)
     sorter.close()
 
 
