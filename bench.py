@@ -7,6 +7,7 @@ uniformly (SplitMix64), keys only.  Prints ONE JSON line on rank 0.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--n N] [--dist uniform] [--key-type u32|f32|u64] [--pairs]
                   [--no-dists] [--batch-arrays 20000] [--batch-cap 2^30]
+                  [--batch-u64-arrays 400]
                   [--serve-seconds 60] [--serve-rate 2000] [--serve-budget B]
                   [--merge-sort] [--cpu-sample 2^24] [--no-cpu-full]
 
@@ -31,7 +32,8 @@ process again, with the same buffers and with freshly pinned ones.
 And "batched": the batched workload (20,000 independent
 uint32 arrays, sizes log-uniform in [2^7, 2^20], scaled to at most 2^30 keys
 in all, uniform keys) sorted by one bsort_sort_batch call, against the same
-arrays sorted by one plain bsort_sort_keys call each, on the same stream.
+arrays sorted by one plain bsort_sort_keys call each, on the same stream;
+"batched_u64" likewise for 400 uint64 arrays of 2^18 to 2^20 keys.
 
 --impl reference times the CPU oracle (a plain C statement of Algorithm 1)
 on the host cores, on a bounded sample of the same workload per step.
@@ -118,6 +120,9 @@ def _args():
     p.add_argument("--batch-cap", type=int, default=1 << 30,
                    help="batched workload: total keys at most")
     p.add_argument("--batch-steps", type=int, default=3)
+    p.add_argument("--batch-u64-arrays", type=int, default=400,
+                   help="64-bit batched workload: number of arrays, sizes log-uniform in "
+                        "[2^18, 2^20] (0: skip the batched_u64 line)")
     p.add_argument("--serve-seconds", type=float, default=60.0,
                    help="served stream: seconds of Poisson arrivals (0: skip the served line)")
     p.add_argument("--serve-rate", type=float, default=2000.0, help="arrivals per second")
@@ -658,6 +663,14 @@ def run_ours(args):
     sorter.close()
     del keys, out, vals, out_v
     batched = run_batched(args, pkg, synth, dev, stream, rank, world) if args.batch_arrays else None
+    batched_u64 = None
+    if args.batch_u64_arrays:
+        try:
+            batched_u64 = run_batched(args, pkg, synth, dev, stream, rank, world, wide=True)
+        except Exception as exc:  # reported in the line; the headline stands
+            import traceback
+            traceback.print_exc()
+            batched_u64 = {"error": "%s: %s" % (type(exc).__name__, exc)}
     served = run_served(args, pkg, synth, dev, rank) if args.serve_seconds > 0 else None
 
     if rank == 0:
@@ -682,6 +695,8 @@ def run_ours(args):
             line["plans"] = plans
         if batched is not None:
             line["batched"] = batched
+        if batched_u64 is not None:
+            line["batched_u64"] = batched_u64
         if served is not None:
             line["served"] = served
         print(json.dumps(line), flush=True)
@@ -690,30 +705,87 @@ def run_ours(args):
     return 0
 
 
-def run_batched(args, pkg, synth, dev, stream, rank, world):
+def _batched_graph(pkg, dev, stream, keys, off, out, ref, ktype, steps, world):
+    """The batch through the batch-graph cache (BSORT_FLAG_GRAPHS) on a
+    created stream (the legacy default stream cannot be captured): after the
+    first call, one graph launch per call and no planning on the host."""
+    import torch
+
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(stream)
+    gsort = pkg.BucketSorter(device=dev.index, graphs=True)
+    with torch.cuda.stream(side):
+        for _ in range(2):
+            gsort.sort_batch(keys, off, out=out, key_type=ktype)
+        gsort.sync()
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), "graph replay differs from the plain batch"
+        g0 = torch.cuda.Event(enable_timing=True)
+        g1 = torch.cuda.Event(enable_timing=True)
+        t_host = time.perf_counter()
+        g0.record(side)
+        for _ in range(steps):
+            gsort.sort_batch(keys, off, out=out, key_type=ktype)
+        g1.record(side)
+        g_host_ms = (time.perf_counter() - t_host) * 1e3 / steps
+        torch.cuda.synchronize()
+        gsort.sync()
+    g_ms = g0.elapsed_time(g1) / steps
+    gsort.close()
+    stream.wait_stream(side)
+    return {"value": keys.numel() * world / (g_ms / 1e3) / 1e9, "unit": UNIT,
+            "ms_per_batch": g_ms, "host_ms_per_call": g_host_ms,
+            "launch": "one CUDA-graph launch per call (BSORT_FLAG_GRAPHS)"}
+
+
+def run_batched(args, pkg, synth, dev, stream, rank, world, wide=False):
     """The batched workload: one bsort_sort_batch call per step against one
-    plain bsort_sort_keys call per array (same arrays, same stream)."""
+    plain bsort_sort_keys call per array (same arrays, same stream).  wide:
+    the 64-bit workload (args.batch_u64_arrays uint64 arrays, sizes
+    log-uniform in [2^18, 2^20]: the segments sorted by the 64-bit
+    segment-aware sample sort)."""
     import numpy as np
     import torch
 
-    sizes = synth.batch_sizes(args.batch_arrays, synth.seed_for(4, 0, rank), cap=args.batch_cap)
+    ktype = "u64" if wide else "u32"
+    kb = 8 if wide else 4
+    if wide:
+        sizes = synth.batch_sizes(args.batch_u64_arrays, synth.seed_for(4, 9, rank),
+                                  lo_log2=18, hi_log2=20, cap=1 << 40)
+    else:
+        sizes = synth.batch_sizes(args.batch_arrays, synth.seed_for(4, 0, rank),
+                                  cap=args.batch_cap)
     off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
     nb = int(off[-1])
-    keys = synth.keys_u32_torch("uniform", nb, synth.seed_for(4, 0, 1000 + rank), device=dev)
+    if wide:
+        keys = synth.draws64_torch(synth.seed_for(4, 9, 1000 + rank), nb, device=dev)
+    else:
+        keys = synth.keys_u32_torch("uniform", nb, synth.seed_for(4, 0, 1000 + rank), device=dev)
     out = torch.empty_like(keys)
     sorter = pkg.BucketSorter(device=dev.index, timing=True)
-    bplan = sorter.plan_batch(off)
+    bplan = sorter.plan_batch(off, ktype)
     for _ in range(3):
-        sorter.sort_batch(keys, off, out=out)
+        sorter.sort_batch(keys, off, out=out, key_type=ktype)
     sorter.sync()
-    # correctness gate: nondecreasing inside every array, same multiset
-    o = out.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    # correctness gate: nondecreasing inside every array (unsigned order),
+    # same multiset (sums of the 32-bit halves)
+    if wide:
+        o = out ^ (-(1 << 63))  # unsigned order as signed order
+        halves = [(out & 0xFFFFFFFF, (out >> 32) & 0xFFFFFFFF),
+                  (keys & 0xFFFFFFFF, (keys >> 32) & 0xFFFFFFFF)]
+        sums_out = [int(h.sum()) for h in halves[0]]
+        sums_in = [int(h.sum()) for h in halves[1]]
+        del halves
+    else:
+        o = out.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        kin = keys.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+        sums_out, sums_in = [int(o.sum())], [int(kin.sum())]
+        del kin
     starts = torch.zeros(nb, dtype=torch.bool, device=dev)
     starts[torch.from_numpy(off[:-1].astype(np.int64)).to(dev)] = True
     assert bool(((o[1:] >= o[:-1]) | starts[1:]).all()), "a batched array is not sorted"
-    kin = keys.view(torch.int32).to(torch.int64) & 0xFFFFFFFF
-    assert int(kin.sum()) == int(o.sum()), "multiset changed"
-    del o, kin, starts
+    assert sums_in == sums_out, "multiset changed"
+    del o, starts
     ref = out.clone()
     sorter.kernel_times()
     torch.cuda.synchronize()
@@ -722,7 +794,7 @@ def run_batched(args, pkg, synth, dev, stream, rank, world):
     t_host = time.perf_counter()
     e0.record(stream)
     for _ in range(args.batch_steps):
-        sorter.sort_batch(keys, off, out=out)
+        sorter.sort_batch(keys, off, out=out, key_type=ktype)
     e1.record(stream)
     host_ms = (time.perf_counter() - t_host) * 1e3 / args.batch_steps
     torch.cuda.synchronize()
@@ -734,43 +806,23 @@ def run_batched(args, pkg, synth, dev, stream, rank, world):
     b_ms = job_time_ms(e0.elapsed_time(e1), world, dev) / args.batch_steps
     sorter.close()
 
-    # the same batch through the batch-graph cache (BSORT_FLAG_GRAPHS) on a
-    # created stream (the legacy default stream cannot be captured): after
-    # the first call, one graph launch per call and no planning on the host
-    side = torch.cuda.Stream(device=dev)
-    side.wait_stream(stream)
-    gsort = pkg.BucketSorter(device=dev.index, graphs=True)
-    with torch.cuda.stream(side):
-        for _ in range(2):
-            gsort.sort_batch(keys, off, out=out)
-        gsort.sync()
-        torch.cuda.synchronize()
-        assert torch.equal(out, ref), "graph replay differs from the plain batch"
-        g0 = torch.cuda.Event(enable_timing=True)
-        g1 = torch.cuda.Event(enable_timing=True)
-        t_host = time.perf_counter()
-        g0.record(side)
-        for _ in range(args.batch_steps):
-            gsort.sort_batch(keys, off, out=out)
-        g1.record(side)
-        g_host_ms = (time.perf_counter() - t_host) * 1e3 / args.batch_steps
-        torch.cuda.synchronize()
-        gsort.sync()
-    g_ms = g0.elapsed_time(g1) / args.batch_steps
-    gsort.close()
-    stream.wait_stream(side)
+    graph = None
+    if not wide:
+        graph = _batched_graph(pkg, dev, stream, keys, off, out, ref, ktype, args.batch_steps,
+                               world)
     del ref
 
     # the same arrays, one plain sort call each
     plain = pkg.BucketSorter(device=dev.index)
-    plain._ensure(int(sizes.max()), "u32", 0)
+    plain._ensure(int(sizes.max()), ktype, 0)
     h, st = plain.h, plain._stream()
     kp, op = keys.data_ptr(), out.data_ptr()
-    bounds = [(int(off[q]) * 4, int(off[q + 1] - off[q])) for q in range(len(sizes))]
+    bounds = [(int(off[q]) * kb, int(off[q + 1] - off[q])) for q in range(len(sizes))]
+    kcode = pkg.BSORT_U64 if wide else pkg.BSORT_U32
 
     def sequential():
         for a, n in bounds:
-            pkg.bsort_sort_keys(h, pkg.BSORT_U32, kp + a, op + a, n, st)
+            pkg.bsort_sort_keys(h, kcode, kp + a, op + a, n, st)
 
     sequential()
     plain.sync()
@@ -782,8 +834,13 @@ def run_batched(args, pkg, synth, dev, stream, rank, world):
     plain.sync()
     s_ms = job_time_ms(e0.elapsed_time(e1), world, dev)
     plain.close()
-    return {"workload": "%d uint32 arrays, sizes log-uniform in [2^7, 2^20] scaled to <= %d "
-                        "keys in all, uniform keys, per GPU" % (len(sizes), args.batch_cap),
+    if wide:
+        workload = ("%d uint64 arrays, sizes log-uniform in [2^18, 2^20], uniform keys, per GPU"
+                    % len(sizes))
+    else:
+        workload = ("%d uint32 arrays, sizes log-uniform in [2^7, 2^20] scaled to <= %d keys "
+                    "in all, uniform keys, per GPU" % (len(sizes), args.batch_cap))
+    return {"workload": workload,
             "keys": nb, "value": nb * world / (b_ms / 1e3) / 1e9, "unit": UNIT,
             "ms_per_batch": b_ms, "steps": args.batch_steps,
             "sequential": {"value": nb * world / (s_ms / 1e3) / 1e9, "unit": UNIT,
@@ -791,9 +848,7 @@ def run_batched(args, pkg, synth, dev, stream, rank, world):
                            "launch": "one bsort_sort_keys call per array, same stream"},
             "speedup_vs_sequential": s_ms / b_ms, "gpu_launches": bplan.num_kernels,
             "host_ms_per_call": host_ms,
-            "graph": {"value": nb * world / (g_ms / 1e3) / 1e9, "unit": UNIT,
-                      "ms_per_batch": g_ms, "host_ms_per_call": g_host_ms,
-                      "launch": "one CUDA-graph launch per call (BSORT_FLAG_GRAPHS)"},
+            **({"graph": graph} if graph is not None else {}),
             "plan": bplan.as_dict(), "per_kernel_ms": per_kernel}
 
 
