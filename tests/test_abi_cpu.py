@@ -199,6 +199,11 @@ def test_plan_batch_classes_u64():
     # the plain sort of the 2^20 + 1 keys is counted with the batch's kernels
     assert p.num_kernels > 7
     pkg.bsort_destroy(h)
+    # a low direct limit: one-sublist sampled segments, one bucket each
+    h = pkg.bsort_create(pkg.bsort_config(device=0, batch_direct_max=2048))
+    p = pkg.bsort_plan_batch(h, pkg.BSORT_U64, np.array([0, 2049, 2049 + 16384], np.uint64))
+    assert (p.direct_segs, p.sampled_segs, p.sublists, p.buckets) == (0, 2, 2, 2)
+    pkg.bsort_destroy(h)
 
 
 def test_plan_batch_errors():

@@ -152,6 +152,32 @@ def test_batch_u64():
     sorter.close()
 
 
+@pytest.mark.parametrize("direct_max", [2048, 16384])
+def test_batch_u64_log_uniform(direct_max):
+    """64-bit keys with a low direct limit, so that sampled segments of 1 to
+    64 sublists occur: 200 arrays, log-uniform sizes in [2^7, 2^20] (at most
+    2^25 keys in all), uniform keys with every seventh key cut to 8 bits."""
+    sizes = synth.batch_sizes(200, synth.seed_for(4, 7, direct_max), cap=1 << 25)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.uint64)
+    n = int(off[-1])
+    keys = synth.keys_u64(n, synth.seed_for(4, 7, 1))
+    keys[::7] &= np.uint64(0xFF)
+    sorter = pkg.BucketSorter(batch_direct_max=direct_max)
+    p = sorter.plan_batch(off, "u64")
+    sampled = [x for x in sizes if direct_max < x <= 1 << 20]
+    assert p.sampled_segs == len(sampled) and p.large_segs == 0
+    assert p.sublists == sum(-(-int(x) // 16384) for x in sampled)
+    d_in = torch.from_numpy(keys.view(np.int64)).cuda()
+    d_out = torch.empty_like(d_in)
+    sorter.sort_batch(d_in, off, out=d_out, key_type="u64")
+    sorter.sync()
+    got = d_out.cpu().numpy().view(np.uint64)
+    seg = np.repeat(np.arange(len(sizes)), sizes)
+    want = keys[np.lexsort((keys, seg))]  # library sort, segment-major
+    assert np.array_equal(got, want)
+    sorter.close()
+
+
 def test_batch_u64_sampled_ties():
     """Sampled 64-bit segments whose keys tie: all equal to the largest key
     (the value that pads the last sublist of a segment), 16 distinct values,
