@@ -668,6 +668,8 @@ def run_ours(args):
         try:
             batched_u64 = run_batched(args, pkg, synth, dev, stream, rank, world, wide=True)
         except Exception as exc:  # reported in the line; the headline stands
+            if world > 1:
+                raise  # the other ranks wait in its collectives
             import traceback
             traceback.print_exc()
             batched_u64 = {"error": "%s: %s" % (type(exc).__name__, exc)}
