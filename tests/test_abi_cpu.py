@@ -206,6 +206,33 @@ def test_plan_batch_classes_u64():
     pkg.bsort_destroy(h)
 
 
+@pytest.mark.parametrize("n,kind", [(300000, "max"), (300000, "16"), (1 << 20, "zero"),
+                                    (1 << 20, "uniform")])
+def test_u64_sampled_plan_on_the_oracle(n, kind):
+    """The plan the batch makes for one sampled 64-bit segment (t = 16384,
+    its s and b), run through the oracle's Algorithm 1 on keys that tie:
+    every bucket fits the 16384-key Step-9 unit and the result is the
+    textbook sort."""
+    h = pkg.bsort_create(pkg.bsort_config(device=0, batch_direct_max=2048))
+    p = pkg.bsort_plan_batch(h, pkg.BSORT_U64, np.array([0, n], np.uint64))
+    pkg.bsort_destroy(h)
+    m = -(-n // 16384)
+    s = 256 if m <= 32 else 128
+    assert p.sampled_segs == 1 and p.sublists == m
+    keys = synth.keys_u64(n, synth.seed_for(5, 8, n))
+    if kind == "max":
+        keys[:] = np.uint64(0xFFFFFFFFFFFFFFFF)
+    elif kind == "16":
+        keys &= np.uint64(0xF000000000000000)
+    elif kind == "zero":
+        keys[:] = 0
+    r = oracle.paper_sort(keys, 16384, s, "u64", b=p.buckets, threads=4)
+    sizes = np.diff(r["bucket_start"].astype(np.int64))
+    assert sizes.max() <= 16384
+    assert sizes.max() <= oracle.bucket_bound(m * 16384, m, s, p.buckets)
+    assert np.array_equal(r["keys"], oracle.textbook_sort(keys, "u64"))
+
+
 def test_plan_batch_errors():
     h = _handle()
     with pytest.raises(pkg.BsortError) as e:
